@@ -1,0 +1,154 @@
+/*
+ * isdf_smw.h - C ABI of the GB300 (sm_103a) ISDF-SMW inverse dielectric library.
+ *
+ * The method (arXiv 2403.12340, "A fast low-rank inversion algorithm of
+ * dielectric matrix in GW approximation"):
+ *   - the orbital-pair functions M_(r; i,j) = psi_i(r) psi_j(r) (i occupied,
+ *     j unoccupied; Eq. Omega text) are compressed by interpolative separable
+ *     density fitting at N_mu grid points, M ~ P C with C = M[mu, :]
+ *     (Eq. ISDF, Eq. MatrixExpressionISDF);
+ *   - chi0 = 2 M Omega^-1 M^T and eps = I - V chi0 (Eq. matrices) are never
+ *     formed; instead eps^-1 = I + V P K P^T with the N_mu x N_mu capacitance
+ *     K = (1/2 (C Omega^-1 C^T)^-1 - P^T V P)^-1
+ *     (Eq. epsilon_with_SMW; K of Section "Cubic scaling algorithm";
+ *     Algorithm 3 steps 1-3).
+ *
+ * Conventions shared by every entry point
+ *   - Real (Gamma-point, Eq. 8) float64 data, column-major, grid index fastest:
+ *     grid point (x, y, z) is row r = x + n1 * (y + n2 * z).
+ *   - Discretisation (the paper drops quadrature weights; this library's
+ *     reading): orbitals are discretely orthonormal (sum_r phi_i phi_j =
+ *     delta_ij) and V = F^-1 diag(v_G / dV) F with v_G = 4 pi / |G|^2,
+ *     v_0 = 0, dV = L1 L2 L3 / N_r, G = 2 pi (m1/L1, m2/L2, m3/L3).
+ *   - Frequencies are on the imaginary axis (Hartree); Omega(i w)^-1 =
+ *     diag(D / (D^2 + w^2)), D = e_i - e_j < 0; w = 0 is the static case.
+ *   - Device pointers are CUDA global-memory addresses on the context's
+ *     device; host pointers are ordinary process memory.  All buffers are
+ *     owned by the caller.  The context owns only its workspace.
+ *   - Calls are ordered on the context's CUDA stream.  isdf_fit synchronises
+ *     that stream once (it returns the numerical rank to the host); the
+ *     other calls are asynchronous unless stated otherwise.  The caller must
+ *     keep phi and theta alive and unmodified until the next isdf_fit or
+ *     isdf_destroy, because later calls read them.
+ *   - Every entry point returns ISDF_OK (0) or a negative ISDF_ERR_* code and
+ *     never aborts the process; isdf_last_error() describes the last error.
+ *     A failed call leaves the context usable (its fit state may be reset).
+ *
+ * The whitened basis.  isdf_fit factors C C^T = L L^T by Cholesky with
+ * diagonal pivoting (rank r <= N_mu) and returns theta = P_r L_r, the
+ * auxiliary functions of the r pivot points multiplied by their Cholesky
+ * factor, i.e. theta = M C~^T with C~ = L_r^-1 C_r having orthonormal rows.
+ * theta spans the same space as P, theta C~ = P C, and the operators G, D
+ * and K reported below are expressed in this basis:
+ *   eps^-1 = I + V theta K theta^T,  K = -D (I + G D)^-1,
+ *   G = theta^T V theta,  D = -2 C~ Omega^-1 C~^T = L_r^-1 (-2 B_rr) L_r^-T.
+ * Columns r..N_mu-1 of theta and rows/columns r.. of G, D, K are zero.
+ */
+#ifndef ISDF_SMW_H
+#define ISDF_SMW_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISDF_API __attribute__((visibility("default")))
+#else
+#define ISDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isdf_ctx isdf_ctx;
+
+enum {
+  ISDF_OK = 0,
+  ISDF_ERR_ARG = -1,        /* null pointer, bad enum or flag */
+  ISDF_ERR_SHAPE = -2,      /* non-positive or inconsistent sizes, N_mu > N_r, too large */
+  ISDF_ERR_INDEX = -3,      /* interpolation index out of range or repeated */
+  ISDF_ERR_NONFINITE = -4,  /* NaN or Inf in an input */
+  ISDF_ERR_ORDER = -5,      /* no gap: max occupied energy >= min unoccupied energy */
+  ISDF_ERR_NOT_SPD = -6,    /* a capacitance factor lost positive definiteness */
+  ISDF_ERR_TIMEOUT = -7,    /* a device-side wait ran out (no hang: kernel returned) */
+  ISDF_ERR_CUDA = -8,       /* a CUDA runtime call failed */
+  ISDF_ERR_STATE = -9,      /* call out of order (e.g. apply before smw_inverse) */
+  ISDF_ERR_NOMEM = -10      /* workspace allocation failed */
+};
+
+enum { ISDF_PREC_FP64 = 0 };
+
+/* Create a context for one periodic grid n1 x n2 x n3 with cell lengths
+ * L1, L2, L3 (Bohr).  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) on the current device, which becomes the context's device.
+ * n_i in [2, 512], each a product of primes <= 13.  Allocates nothing large
+ * until isdf_fit.  On error *ctx is NULL. */
+ISDF_API int isdf_create(isdf_ctx** ctx, int n1, int n2, int n3, double L1, double L2, double L3,
+                void* cuda_stream);
+
+/* Free the context and its workspace (after synchronising its stream). */
+ISDF_API int isdf_destroy(isdf_ctx* ctx);
+
+/* ISDF fit (Eq. ISDF, Eq. MatrixExpressionISDF; least-squares reading of
+ * M = P C): theta = M C~^T with C~ the orthonormalised C of the pivot points.
+ *   phi      device, N_r x (n_v + n_c) float64, column-major (ld = N_r):
+ *            orbitals, the first n_v occupied.  Read now and by
+ *            build_polarizability.
+ *   n_v,n_c  numbers of occupied / unoccupied orbitals (>= 1 each).
+ *   mu_idx   host, n_mu int64 grid indices in [0, N_r), distinct.
+ *   n_mu     number of interpolation points, 1 <= n_mu <= N_r.
+ *   prec     ISDF_PREC_FP64.
+ *   theta    device, N_r x n_mu float64 out (ld = N_r); must not alias phi.
+ *            Later calls read it: keep it until the next fit.
+ *   rank_out host int out (may be NULL): numerical rank r of C C^T.  The
+ *            Cholesky stops when the largest remaining pivot falls below
+ *            n_mu * 2^-52 * max diag(C C^T); r < n_mu is not an error.
+ * Synchronises the context stream once. */
+ISDF_API int isdf_fit(isdf_ctx* ctx, const double* phi, int n_v, int n_c, const int64_t* mu_idx, int n_mu,
+             int prec, double* theta, int* rank_out);
+
+/* Polarizability and Coulomb operators in the ISDF basis (Algorithm 3 steps
+ * 1-2 with the direct sum over pairs, Eq. COmegaCstar):
+ *   D(w) = -2 C~ Omega(i w)^-1 C~^T and G = theta^T V theta (FFT of theta).
+ *   energies host, n_v + n_c float64 (Hartree); occupied ones all below the
+ *            unoccupied ones (else ISDF_ERR_ORDER).
+ *   omega    host, n_omega imaginary frequencies (Hartree, >= 0).
+ *   n_omega  1 .. 4096; the context keeps all D(w).
+ *   D_out    device, n_omega x n_mu x n_mu float64 out, or NULL.
+ *   G_out    device, n_mu x n_mu float64 out, or NULL.
+ * Requires a successful isdf_fit. */
+ISDF_API int build_polarizability(isdf_ctx* ctx, const double* energies, const double* omega, int n_omega,
+                         double* D_out, double* G_out);
+
+/* SMW capacitance for frequency omega[omega_index] (K of Section "Cubic
+ * scaling algorithm", Algorithm 3 step 3), in the singular-B-safe form
+ * K = -D (I + G D)^-1 = -Q Q^T, Q = R U^-T, D = R R^T, I + R^T G R = U U^T.
+ *   K_out    device, n_mu x n_mu float64 out, or NULL (K is kept in the
+ *            context for apply_eps_inv either way).
+ * ISDF_ERR_NOT_SPD if D is not positive definite in floating point. */
+ISDF_API int smw_inverse(isdf_ctx* ctx, int omega_index, double* K_out);
+
+/* Y = eps^-1(i w) X = X + V theta K theta^T X (Eq. epsilon_with_SMW).
+ *   X, Y     device, N_r x n_rhs float64 (ld = N_r); Y may equal X.
+ *   n_rhs    >= 1.
+ * Requires smw_inverse for the same omega_index. */
+ISDF_API int apply_eps_inv(isdf_ctx* ctx, int omega_index, const double* X, int n_rhs, double* Y);
+
+/* Pivot order and Cholesky factor of the last fit.
+ *   piv_out  host, n_mu int32 out (or NULL): pivot j is point mu_idx[piv[j]];
+ *            the first r are the pivot points that define theta.
+ *   L_out    device, n_mu x n_mu float64 out (or NULL): L_r in its leading
+ *            r x r block (lower triangular), zero elsewhere. */
+ISDF_API int isdf_fit_factor(isdf_ctx* ctx, int* piv_out, double* L_out);
+
+/* Message for the last error on this context ("" if none).  With ctx NULL,
+ * the last error of isdf_create on this thread. */
+ISDF_API const char* isdf_last_error(isdf_ctx* ctx);
+
+/* Library version string. */
+ISDF_API const char* isdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISDF_SMW_H */

@@ -1,0 +1,253 @@
+"""Python binding of the ISDF-SMW C ABI (include/isdf_smw.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library `lib/libisdf_smw.so` (built by `build.py`).  There is no CPU or
+PyTorch fallback: if the library is missing or fails to load, every call
+raises.  PyTorch is used for device memory and streams.
+
+Matrices are column-major (grid index fastest), as in the C ABI: a
+N_r x k matrix is a float64 CUDA tensor of shape (N_r, k) with strides
+(1, N_r); `fortran_empty` / `to_fortran` make such tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libisdf_smw.so")
+
+ISDF_OK = 0
+ERRORS = {
+    -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_SHAPE", -3: "ISDF_ERR_INDEX", -4: "ISDF_ERR_NONFINITE",
+    -5: "ISDF_ERR_ORDER", -6: "ISDF_ERR_NOT_SPD", -7: "ISDF_ERR_TIMEOUT", -8: "ISDF_ERR_CUDA",
+    -9: "ISDF_ERR_STATE", -10: "ISDF_ERR_NOMEM",
+}
+ISDF_PREC_FP64 = 0
+
+EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
+            "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version"]
+
+
+class IsdfError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+        super().__init__(f"{self.name}: {message}")
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (once).  Raises if it is missing: no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"ISDF-SMW CUDA library not built: {path} is missing "
+                          "(run __graft_entry__.build() or paper_2403_12340_gb300/build.py)")
+    lib = ctypes.CDLL(path)
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.isdf_create.argtypes = [ctypes.POINTER(P), I, I, I, D, D, D, P]
+    lib.isdf_destroy.argtypes = [P]
+    lib.isdf_fit.argtypes = [P, P, I, I, P, I, I, P, ctypes.POINTER(I)]
+    lib.build_polarizability.argtypes = [P, P, P, I, P, P]
+    lib.smw_inverse.argtypes = [P, I, P]
+    lib.apply_eps_inv.argtypes = [P, I, P, I, P]
+    lib.isdf_fit_factor.argtypes = [P, P, P]
+    lib.isdf_last_error.argtypes = [P]
+    lib.isdf_last_error.restype = ctypes.c_char_p
+    lib.isdf_version.argtypes = []
+    lib.isdf_version.restype = ctypes.c_char_p
+    for name in ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
+                 "apply_eps_inv", "isdf_fit_factor"]:
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, ctx) -> None:
+    if rc != ISDF_OK:
+        msg = load_library().isdf_last_error(ctx)
+        raise IsdfError(rc, msg.decode() if msg else "")
+
+
+def _dev_ptr(t, rows: Optional[int] = None, cols: Optional[int] = None, name: str = "tensor") -> int:
+    """Device pointer of a float64 CUDA tensor laid out column-major."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if t.dim() == 1:
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    elif t.dim() == 2:
+        r, c = t.shape
+        if c > 1 and t.stride() != (1, r):
+            raise ValueError(f"{name} must be column-major (strides (1, rows)); use to_fortran()")
+        if c == 1 and t.stride(0) != 1:
+            raise ValueError(f"{name} must have unit row stride")
+        if rows is not None and r != rows:
+            raise ValueError(f"{name} has {r} rows, expected {rows}")
+        if cols is not None and c != cols:
+            raise ValueError(f"{name} has {c} columns, expected {cols}")
+    else:
+        raise ValueError(f"{name} must be 1-D or 2-D")
+    return t.data_ptr()
+
+
+def fortran_empty(rows: int, cols: int, device="cuda"):
+    import torch
+
+    return torch.empty((cols, rows), dtype=torch.float64, device=device).t()
+
+
+def to_fortran(a, device="cuda"):
+    """Column-major float64 CUDA copy of a 2-D numpy array or tensor."""
+    import torch
+
+    t = torch.as_tensor(np.asarray(a) if not isinstance(a, torch.Tensor) else a, dtype=torch.float64)
+    out = fortran_empty(t.shape[0], t.shape[1], device)
+    out.copy_(t.to(device))
+    return out
+
+
+def version() -> str:
+    return load_library().isdf_version().decode()
+
+
+def isdf_last_error(ctx) -> str:
+    msg = load_library().isdf_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def isdf_create(n: Sequence[int], cell: Sequence[float], stream=None):
+    """Create a context on the current CUDA device; returns an opaque handle."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    s = ctypes.c_void_p(0 if stream is None else int(stream))
+    _check(lib.isdf_create(ctypes.byref(h), int(n[0]), int(n[1]), int(n[2]), float(cell[0]),
+                           float(cell[1]), float(cell[2]), s), None)
+    return h
+
+
+def isdf_destroy(ctx) -> None:
+    _check(load_library().isdf_destroy(ctx), None)
+
+
+def isdf_fit(ctx, phi, n_v: int, n_c: int, mu_idx, theta, n_r: int, prec: int = ISDF_PREC_FP64) -> int:
+    """ISDF fit; writes theta (N_r x N_mu) and returns the numerical rank."""
+    mu = np.ascontiguousarray(np.asarray(mu_idx, dtype=np.int64))
+    pp = _dev_ptr(phi, n_r, n_v + n_c, "phi")
+    pt = _dev_ptr(theta, n_r, mu.shape[0], "theta")
+    rank = ctypes.c_int(0)
+    _check(load_library().isdf_fit(ctx, pp, int(n_v), int(n_c), mu.ctypes.data, int(mu.shape[0]),
+                                   int(prec), pt, ctypes.byref(rank)), ctx)
+    return rank.value
+
+
+def build_polarizability(ctx, energies, omega, D_out=None, G_out=None) -> None:
+    e = np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
+    w = np.ascontiguousarray(np.atleast_1d(np.asarray(omega, dtype=np.float64)))
+    pd = 0 if D_out is None else _dev_ptr(D_out.reshape(-1), name="D_out")
+    pg = 0 if G_out is None else _dev_ptr(G_out.reshape(-1), name="G_out")
+    _check(load_library().build_polarizability(ctx, e.ctypes.data, w.ctypes.data, int(w.shape[0]), pd, pg),
+           ctx)
+
+
+def smw_inverse(ctx, omega_index: int = 0, K_out=None) -> None:
+    pk = 0 if K_out is None else _dev_ptr(K_out.reshape(-1), name="K_out")
+    _check(load_library().smw_inverse(ctx, int(omega_index), pk), ctx)
+
+
+def apply_eps_inv(ctx, omega_index: int, X, Y, n_r: int) -> None:
+    n_rhs = X.shape[1] if X.dim() == 2 else 1
+    px = _dev_ptr(X, n_r, None, "X")
+    py = _dev_ptr(Y, n_r, n_rhs, "Y")
+    _check(load_library().apply_eps_inv(ctx, int(omega_index), px, int(n_rhs), py), ctx)
+
+
+def isdf_fit_factor(ctx, n_mu: int, L_out=None):
+    """Pivot order (host int32 array) of the last fit; fills L_out if given."""
+    piv = np.zeros(n_mu, dtype=np.int32)
+    pl = 0 if L_out is None else _dev_ptr(L_out.reshape(-1), name="L_out")
+    _check(load_library().isdf_fit_factor(ctx, piv.ctypes.data, pl), ctx)
+    return piv
+
+
+class IsdfSmw:
+    """One context bound to one grid; thin convenience over the C ABI."""
+
+    def __init__(self, n, cell, stream=None):
+        import torch
+
+        self.n = tuple(int(v) for v in n)
+        self.cell = tuple(float(v) for v in cell)
+        self.n_r = int(np.prod(self.n))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = isdf_create(self.n, self.cell, self.stream.cuda_stream)
+        self.n_mu = 0
+        self.rank = 0
+
+    def close(self):
+        if self.ctx is not None:
+            isdf_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fit(self, phi, n_v, n_c, mu_idx, theta=None, prec=ISDF_PREC_FP64):
+        mu = np.asarray(mu_idx, dtype=np.int64)
+        if theta is None:
+            theta = fortran_empty(self.n_r, mu.shape[0], phi.device)
+        self.rank = isdf_fit(self.ctx, phi, n_v, n_c, mu, theta, self.n_r, prec)
+        self.n_mu = mu.shape[0]
+        self.theta = theta
+        return theta, self.rank
+
+    def polarizability(self, energies, omega=(0.0,), want_D=False, want_G=False):
+        import torch
+
+        w = np.atleast_1d(np.asarray(omega, dtype=np.float64))
+        dev = self.theta.device
+        D = torch.empty((w.shape[0], self.n_mu, self.n_mu), dtype=torch.float64, device=dev) if want_D else None
+        G = torch.empty((self.n_mu, self.n_mu), dtype=torch.float64, device=dev) if want_G else None
+        build_polarizability(self.ctx, energies, w, D, G)
+        return D, G
+
+    def smw(self, omega_index=0, want_K=False):
+        import torch
+
+        K = torch.empty((self.n_mu, self.n_mu), dtype=torch.float64, device=self.theta.device) if want_K else None
+        smw_inverse(self.ctx, omega_index, K)
+        return K
+
+    def apply(self, X, omega_index=0, Y=None):
+        if Y is None:
+            Y = fortran_empty(self.n_r, X.shape[1], X.device)
+        apply_eps_inv(self.ctx, omega_index, X, Y, self.n_r)
+        return Y
+
+    def factor(self, want_L=False):
+        import torch
+
+        L = torch.empty((self.n_mu, self.n_mu), dtype=torch.float64, device=self.theta.device) if want_L else None
+        piv = isdf_fit_factor(self.ctx, self.n_mu, L)
+        # the library writes L column-major; the transposed view is L itself
+        return piv, (L.t() if L is not None else None)

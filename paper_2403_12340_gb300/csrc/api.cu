@@ -1,0 +1,584 @@
+// C ABI of the ISDF-SMW library: context, argument checks and the order of
+// kernel launches for isdf_fit / build_polarizability / smw_inverse /
+// apply_eps_inv (declared and documented in include/isdf_smw.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/isdf_smw.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace isdf;
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bound on any device-side wait
+constexpr int kMaxGrid = 512;
+
+struct DevBuf {
+  double* p = nullptr;
+  size_t cap = 0;  // doubles
+};
+
+}  // namespace
+
+struct isdf_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  int n[3] = {0, 0, 0};
+  double L[3] = {0, 0, 0};
+  long long n_r = 0;
+  double dv = 0;
+  FftGrid fft{};
+  long long n_half = 0;  // h n2 n3 complex entries of a half spectrum
+  size_t smem_xy = 0, smem_z = 0;
+  double* d_tables = nullptr;  // twiddles x, y, z | sqrt SYRK weights | convolution weights
+  const double* d_wsyrk = nullptr;
+  const double* d_wconv = nullptr;
+  unsigned* d_status = nullptr;
+  unsigned* d_bar = nullptr;
+  int* d_ints = nullptr;  // [0] rank
+  std::string err;
+
+  // fit state
+  bool fitted = false;
+  const double* phi = nullptr;
+  double* theta = nullptr;
+  int n_v = 0, n_c = 0, n_mu = 0, rank = 0;
+  std::vector<int> perm;  // host copy, n_mu
+  int* d_idx = nullptr;
+  int* d_perm = nullptr;   // pivot order of the fit
+  int* d_perm2 = nullptr;  // scratch order of the unpivoted factorisations
+  size_t cap_idx = 0;
+  DevBuf phimu, phimu_p, A, Lr, Lc, Bf, chol_d, chol_part, spec, G, D, K, R, T, W1, Q, partial, tmp1,
+      tmp2, tmp3, sw;
+  int* d_used = nullptr;
+  int* d_part_idx = nullptr;
+  size_t cap_used = 0;
+
+  // polarizability / SMW state
+  bool polar_ready = false;
+  int n_omega = 0;
+  std::vector<double> omega;
+  std::vector<char> k_ready;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(isdf_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+static int cuda_fail(isdf_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, ISDF_ERR_CUDA, m);
+}
+
+#define CK(expr)                                             \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);   \
+  } while (0)
+
+static cudaError_t ensure(DevBuf& b, size_t n) {
+  if (n <= b.cap) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(n, 1) * sizeof(double));
+  if (e == cudaSuccess) b.cap = n;
+  return e;
+}
+
+static void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+static bool factorize(int n, FftAxis& ax) {
+  ax.n = n;
+  ax.nf = 0;
+  int m = n;
+  while (m % 4 == 0 && ax.nf < FFT_MAX_FACTORS) {
+    ax.f[ax.nf++] = 4;
+    m /= 4;
+  }
+  const int primes[] = {2, 3, 5, 7, 11, 13};
+  for (int p : primes)
+    while (m % p == 0 && ax.nf < FFT_MAX_FACTORS) {
+      ax.f[ax.nf++] = p;
+      m /= p;
+    }
+  return m == 1;
+}
+
+static int signed_freq(int k, int n) { return (2 * k < n) ? k : (2 * k == n ? k : k - n); }
+
+// Reads back the device status word (the stream must be synchronised).
+static int check_status(isdf_ctx* c, const char* where) {
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  if (st & ST_TIMEOUT) return fail(c, ISDF_ERR_TIMEOUT, std::string(where) + ": device wait timed out");
+  if (st & ST_NONFINITE) return fail(c, ISDF_ERR_NONFINITE, std::string(where) + ": NaN or Inf in input");
+  if (st & ST_NOT_SPD)
+    return fail(c, ISDF_ERR_NOT_SPD, std::string(where) + ": matrix not positive definite");
+  if (st & ST_BADINDEX) return fail(c, ISDF_ERR_INDEX, std::string(where) + ": index out of range");
+  return ISDF_OK;
+}
+
+extern "C" const char* isdf_version(void) { return "isdf-smw-gb300 0.1 (fp64, sm_103a)"; }
+
+extern "C" const char* isdf_last_error(isdf_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" int isdf_create(isdf_ctx** out, int n1, int n2, int n3, double L1, double L2, double L3,
+                           void* stream) {
+  g_create_err.clear();
+  if (!out) {
+    g_create_err = "isdf_create: ctx is NULL";
+    return ISDF_ERR_ARG;
+  }
+  *out = nullptr;
+  int nn[3] = {n1, n2, n3};
+  double ll[3] = {L1, L2, L3};
+  for (int i = 0; i < 3; ++i) {
+    if (nn[i] < 2 || nn[i] > 512) {
+      g_create_err = "isdf_create: grid sizes must be in [2, 512]";
+      return ISDF_ERR_SHAPE;
+    }
+    if (!(ll[i] > 0.0) || !std::isfinite(ll[i])) {
+      g_create_err = "isdf_create: cell lengths must be positive and finite";
+      return ISDF_ERR_SHAPE;
+    }
+  }
+  isdf_ctx* c = new isdf_ctx();
+  c->stream = (cudaStream_t)stream;
+  for (int i = 0; i < 3; ++i) {
+    c->n[i] = nn[i];
+    c->L[i] = ll[i];
+    if (!factorize(nn[i], c->fft.ax[i])) {
+      delete c;
+      g_create_err = "isdf_create: grid sizes must be products of primes <= 13";
+      return ISDF_ERR_SHAPE;
+    }
+  }
+  c->fft.h = n1 / 2 + 1;
+  c->n_r = (long long)n1 * n2 * n3;
+  c->n_half = (long long)c->fft.h * n2 * n3;
+  c->dv = L1 * L2 * L3 / (double)c->n_r;
+  auto bail = [&](cudaError_t e, const char* w) {
+    g_create_err = std::string("isdf_create: ") + w + ": " + cudaGetErrorString(e);
+    if (c->d_tables) cudaFree(c->d_tables);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return ISDF_ERR_CUDA;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) return bail(e, "cudaDeviceGetAttribute");
+  int smem_optin = 0;
+  e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e != cudaSuccess) return bail(e, "cudaDeviceGetAttribute");
+  c->smem_xy = fft_smem_xy(c->fft);
+  c->smem_z = fft_smem_z(c->fft);
+  if (c->smem_xy > (size_t)smem_optin || c->smem_z > (size_t)smem_optin) {
+    delete c;
+    g_create_err = "isdf_create: an xy plane or z pencil of this grid does not fit in shared memory";
+    return ISDF_ERR_SHAPE;
+  }
+  e = fft_configure(c->smem_xy, c->smem_z);
+  if (e != cudaSuccess) return bail(e, "fft_configure");
+  // host tables: twiddles (float64 host cos / sin) and Coulomb weights
+  size_t ntw = 2 * (size_t)(n1 + n2 + n3);
+  size_t nh = (size_t)c->n_half;
+  std::vector<double> tab(ntw + 2 * nh);
+  size_t off = 0;
+  size_t tw_off[3];
+  for (int a = 0; a < 3; ++a) {
+    tw_off[a] = off;
+    for (int t = 0; t < nn[a]; ++t) {
+      double ang = 2.0 * M_PI * (double)t / (double)nn[a];
+      tab[off + 2 * t] = std::cos(ang);
+      tab[off + 2 * t + 1] = -std::sin(ang);
+    }
+    off += 2 * (size_t)nn[a];
+  }
+  const int h = c->fft.h;
+  for (int kz = 0; kz < n3; ++kz)
+    for (int ky = 0; ky < n2; ++ky)
+      for (int kx = 0; kx < h; ++kx) {
+        size_t q = ((size_t)kz * n2 + ky) * h + kx;
+        double g1 = 2.0 * M_PI * signed_freq(kx, n1) / L1;
+        double g2 = 2.0 * M_PI * signed_freq(ky, n2) / L2;
+        double g3 = 2.0 * M_PI * signed_freq(kz, n3) / L3;
+        double gg = g1 * g1 + g2 * g2 + g3 * g3;
+        double vg = gg > 0.0 ? 4.0 * M_PI / gg : 0.0;
+        // half spectrum: kx = 0 (and kx = n1/2 for even n1) stand for themselves only
+        double wx = (kx == 0 || 2 * kx == n1) ? 1.0 : 2.0;
+        tab[ntw + q] = std::sqrt(wx * vg / ((double)c->n_r * c->dv));
+        tab[ntw + nh + q] = vg / (c->dv * (double)c->n_r);
+      }
+  e = cudaMalloc(&c->d_tables, tab.size() * sizeof(double));
+  if (e != cudaSuccess) return bail(e, "cudaMalloc tables");
+  e = cudaMemcpy(c->d_tables, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(e, "cudaMemcpy tables");
+  for (int a = 0; a < 3; ++a) c->fft.ax[a].tw = c->d_tables + tw_off[a];
+  c->d_wsyrk = c->d_tables + ntw;
+  c->d_wconv = c->d_tables + ntw + nh;
+  e = cudaMalloc(&c->d_status, 64 * sizeof(unsigned));
+  if (e != cudaSuccess) return bail(e, "cudaMalloc status");
+  c->d_bar = c->d_status + 8;
+  c->d_ints = (int*)(c->d_status + 16);
+  e = cudaMemset(c->d_status, 0, 64 * sizeof(unsigned));
+  if (e != cudaSuccess) return bail(e, "cudaMemset status");
+  *out = c;
+  return ISDF_OK;
+}
+
+extern "C" int isdf_destroy(isdf_ctx* c) {
+  if (!c) return ISDF_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->phimu, &c->phimu_p, &c->A, &c->Lr, &c->Lc, &c->Bf, &c->chol_d, &c->chol_part,
+                    &c->spec, &c->G, &c->D, &c->K, &c->R, &c->T, &c->W1, &c->Q, &c->partial,
+                    &c->tmp1, &c->tmp2, &c->tmp3, &c->sw};
+  for (DevBuf* b : bufs) release(*b);
+  if (c->d_idx) cudaFree(c->d_idx);  // d_perm and d_perm2 point into this allocation
+  if (c->d_used) cudaFree(c->d_used);
+  if (c->d_part_idx) cudaFree(c->d_part_idx);
+  if (c->d_tables) cudaFree(c->d_tables);
+  if (c->d_status) cudaFree(c->d_status);  // d_bar and d_ints point into this allocation
+  delete c;
+  return ISDF_OK;
+}
+
+static cudaError_t ensure_ints(int*& p, size_t& cap, size_t n) {
+  if (n <= cap) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(int));
+  if (e == cudaSuccess) cap = n;
+  return e;
+}
+
+// Cholesky of the n x n matrix W (ld = ldw) into the column-major factor
+// Lout (ld = n); pivoted or not; rank -> c->d_ints[0], pivots -> c->d_perm.
+static int cholesky(isdf_ctx* c, const double* W, long long ldw, int n, int pivot, double tol_rel,
+                    double* Lout, int* d_perm) {
+  CK(ensure(c->Lr, (size_t)n * n));
+  CK(ensure(c->chol_d, (size_t)n));
+  CK(ensure(c->chol_part, (size_t)2 * kMaxGrid));
+  size_t cap_used = c->cap_used;
+  CK(ensure_ints(c->d_used, cap_used, (size_t)n));
+  c->cap_used = cap_used;
+  if (!c->d_part_idx) CK(cudaMalloc(&c->d_part_idx, 2 * kMaxGrid * sizeof(int)));
+  CholWork w{c->chol_d.p, c->chol_part.p, c->d_part_idx, c->d_used, c->d_bar, kMaxGrid};
+  CK(cudaMemsetAsync(c->d_ints, 0, sizeof(int), c->stream));
+  CK(launch_cholesky(W, ldw, n, pivot, tol_rel, c->Lr.p, d_perm, c->d_ints, c->d_status, w,
+                     std::min(c->num_sms, kMaxGrid), kWaitLimitNs, c->stream));
+  CK(launch_factor_to_colmajor(c->Lr.p, n, d_perm, c->d_ints, Lout, n, n, c->stream));
+  return ISDF_OK;
+}
+
+extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const int64_t* mu_idx,
+                        int n_mu, int prec, double* theta, int* rank_out) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  c->fitted = false;
+  c->polar_ready = false;
+  if (!phi || !theta || !mu_idx) return fail(c, ISDF_ERR_ARG, "isdf_fit: null pointer argument");
+  if (prec != ISDF_PREC_FP64) return fail(c, ISDF_ERR_ARG, "isdf_fit: unknown precision mode");
+  if (n_v < 1 || n_c < 1) return fail(c, ISDF_ERR_SHAPE, "isdf_fit: n_v and n_c must be >= 1");
+  if (n_mu < 1 || (long long)n_mu > c->n_r)
+    return fail(c, ISDF_ERR_SHAPE, "isdf_fit: n_mu must be in [1, N_r]");
+  if ((long long)n_v * n_c > (1ll << 31) - 1 || n_mu > 65536)
+    return fail(c, ISDF_ERR_SHAPE, "isdf_fit: problem too large");
+  const double* tend = theta + c->n_r * n_mu;
+  const double* pend = phi + c->n_r * (long long)(n_v + n_c);
+  if (theta < pend && phi < tend) return fail(c, ISDF_ERR_ARG, "isdf_fit: theta overlaps phi");
+  std::vector<int64_t> sorted(mu_idx, mu_idx + n_mu);
+  std::sort(sorted.begin(), sorted.end());
+  if (sorted.front() < 0 || sorted.back() >= c->n_r)
+    return fail(c, ISDF_ERR_INDEX, "isdf_fit: interpolation index out of range");
+  for (int i = 1; i < n_mu; ++i)
+    if (sorted[i] == sorted[i - 1]) return fail(c, ISDF_ERR_INDEX, "isdf_fit: repeated interpolation index");
+  const int n_e = n_v + n_c;
+  std::vector<int> idx32(mu_idx, mu_idx + n_mu);
+  CK(cudaStreamSynchronize(c->stream));  // earlier work may still read workspace that is resized below
+  CK(ensure_ints(c->d_idx, c->cap_idx, (size_t)3 * n_mu));
+  c->d_perm = c->d_idx + n_mu;
+  c->d_perm2 = c->d_idx + 2 * n_mu;
+  CK(cudaMemcpyAsync(c->d_idx, idx32.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+  CK(launch_check_finite(phi, c->n_r * n_e, c->d_status, c->stream));
+  // orbitals at the points, C C^T (face-split Gram of the point block), its pivoted Cholesky
+  CK(ensure(c->phimu, (size_t)n_mu * n_e));
+  CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
+  CK(ensure(c->A, (size_t)n_mu * n_mu));
+  CK(launch_facesplit_gram(c->phimu.p, n_mu, n_mu, c->phimu.p, n_mu, n_mu, n_v, n_e, c->A.p, n_mu,
+                           c->stream));
+  CK(ensure(c->Lc, (size_t)n_mu * n_mu));
+  const double tol = (double)n_mu * 2.220446049250313e-16;
+  int rc = cholesky(c, c->A.p, n_mu, n_mu, 1, tol, c->Lc.p, c->d_perm);
+  if (rc != ISDF_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  rc = check_status(c, "isdf_fit");
+  if (rc != ISDF_OK) return rc;
+  int rank = 0;
+  CK(cudaMemcpy(&rank, c->d_ints, sizeof(int), cudaMemcpyDeviceToHost));
+  c->perm.assign(n_mu, 0);
+  if (rank > 0) CK(cudaMemcpy(c->perm.data(), c->d_perm, rank * sizeof(int), cudaMemcpyDeviceToHost));
+  {  // complete the pivot list with the unused points in increasing order
+    std::vector<char> used(n_mu, 0);
+    for (int j = 0; j < rank; ++j) used[c->perm[j]] = 1;
+    int j = rank;
+    for (int i = 0; i < n_mu; ++i)
+      if (!used[i]) c->perm[j++] = i;
+  }
+  // Lc was written with ld = n_mu; repack the leading rank x rank block with ld = rank
+  const int r = rank;
+  if (r > 0) {
+    CK(ensure(c->Bf, (size_t)r * r));
+    CK(cudaMemcpy2DAsync(c->Bf.p, r * sizeof(double), c->Lc.p, n_mu * sizeof(double), r * sizeof(double),
+                         r, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->Lc.p, c->Bf.p, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    // orbitals at the pivot points, in pivot order
+    CK(ensure(c->phimu_p, (size_t)r * n_e));
+    CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
+    // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
+    CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
+                             c->stream));
+    CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+    CK(launch_trsm_right_lt(theta, c->n_r, (int)c->n_r, c->Bf.p, r, r, c->stream));
+  }
+  if (r < n_mu)
+    CK(cudaMemsetAsync(theta + c->n_r * r, 0, (size_t)c->n_r * (n_mu - r) * sizeof(double), c->stream));
+  c->phi = phi;
+  c->theta = theta;
+  c->n_v = n_v;
+  c->n_c = n_c;
+  c->n_mu = n_mu;
+  c->rank = r;
+  c->fitted = true;
+  if (rank_out) *rank_out = r;
+  return ISDF_OK;
+}
+
+extern "C" int isdf_fit_factor(isdf_ctx* c, int* piv_out, double* L_out) {
+  if (!c) return ISDF_ERR_ARG;
+  if (!c->fitted) return fail(c, ISDF_ERR_STATE, "isdf_fit_factor: no fit");
+  if (piv_out) std::memcpy(piv_out, c->perm.data(), c->n_mu * sizeof(int));
+  if (L_out) {
+    const int r = c->rank, m = c->n_mu;
+    CK(cudaMemsetAsync(L_out, 0, (size_t)m * m * sizeof(double), c->stream));
+    if (r > 0)
+      CK(cudaMemcpy2DAsync(L_out, m * sizeof(double), c->Lc.p, r * sizeof(double), r * sizeof(double), r,
+                           cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return ISDF_OK;
+}
+
+// copy a dense r x r matrix (ld r) into an m x m output with zero padding
+static int copy_padded(isdf_ctx* c, double* dst, const double* src, int r, int m) {
+  CK(cudaMemsetAsync(dst, 0, (size_t)m * m * sizeof(double), c->stream));
+  if (r > 0)
+    CK(cudaMemcpy2DAsync(dst, m * sizeof(double), src, r * sizeof(double), r * sizeof(double), r,
+                         cudaMemcpyDeviceToDevice, c->stream));
+  return ISDF_OK;
+}
+
+static int split_for(long long tiles, long long K, int num_sms) {
+  long long want = (2ll * num_sms + tiles - 1) / tiles;
+  long long maxs = std::max(1ll, K / 1024);
+  return (int)std::max(1ll, std::min(want, std::min(maxs, 64ll)));
+}
+
+extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const double* omega, int n_omega,
+                                    double* D_out, double* G_out) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  if (!c->fitted) return fail(c, ISDF_ERR_STATE, "build_polarizability: call isdf_fit first");
+  if (!energies || !omega) return fail(c, ISDF_ERR_ARG, "build_polarizability: null pointer argument");
+  if (n_omega < 1 || n_omega > 4096) return fail(c, ISDF_ERR_SHAPE, "build_polarizability: n_omega in [1, 4096]");
+  const int n_v = c->n_v, n_c = c->n_c, n_e = n_v + n_c, r = c->rank, m = c->n_mu;
+  for (int i = 0; i < n_e; ++i)
+    if (!std::isfinite(energies[i])) return fail(c, ISDF_ERR_NONFINITE, "build_polarizability: energy not finite");
+  double emax_v = energies[0], emin_c = energies[n_v];
+  for (int i = 0; i < n_v; ++i) emax_v = std::max(emax_v, energies[i]);
+  for (int j = n_v; j < n_e; ++j) emin_c = std::min(emin_c, energies[j]);
+  if (!(emax_v < emin_c)) return fail(c, ISDF_ERR_ORDER, "build_polarizability: occupied energies must lie below unoccupied ones");
+  for (int k = 0; k < n_omega; ++k)
+    if (!std::isfinite(omega[k]) || omega[k] < 0.0)
+      return fail(c, ISDF_ERR_ARG, "build_polarizability: frequencies must be finite and >= 0");
+  c->polar_ready = false;
+  const size_t rr = (size_t)r * r;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(ensure(c->G, std::max<size_t>(rr, 1)));
+  CK(ensure(c->D, std::max<size_t>(rr * n_omega, 1)));
+  CK(ensure(c->K, std::max<size_t>(rr * n_omega, 1)));
+  if (r > 0) {
+    // G = theta^T V theta = S^T S with S the weighted half spectrum (Parseval)
+    const long long lds = 2 * c->n_half;
+    const size_t npair = (size_t)n_v * n_c;
+    long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
+    int sp = split_for(tiles, lds, c->num_sms);
+    int spd = split_for(tiles, (long long)npair, c->num_sms);
+    // size all workspace before the first launch (a resize frees memory)
+    CK(cudaStreamSynchronize(c->stream));
+    CK(ensure(c->spec, (size_t)lds * r));
+    CK(ensure(c->partial, (size_t)std::max(sp, spd) * rr));
+    CK(ensure(c->sw, npair * n_omega));
+    CK(ensure(c->tmp1, rr));
+    // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
+    std::vector<double> sw(npair * n_omega);
+    for (int k = 0; k < n_omega; ++k) {
+      const double w2 = omega[k] * omega[k];
+      for (int i = 0; i < n_v; ++i)
+        for (int j = 0; j < n_c; ++j) {
+          double d = energies[i] - energies[n_v + j];
+          sw[npair * k + (size_t)i * n_c + j] = std::sqrt(-2.0 * d / (d * d + w2));
+        }
+    }
+    CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_fft_forward(c->fft, c->theta, c->n_r, r, c->spec.p, lds, c->d_wsyrk, c->smem_xy, c->smem_z,
+                          c->stream));
+    CK(launch_gemm(c->spec.p, lds, true, c->spec.p, lds, true, r, r, (int)lds, 1.0, 0.0, c->G.p, r, true,
+                   sp, c->partial.p, false, c->stream));
+    // D(w) = L_r^-1 (-2 C_r Omega(iw)^-1 C_r^T) L_r^-T
+    for (int k = 0; k < n_omega; ++k) {
+      double* Dk = c->D.p + rr * k;
+      CK(launch_polarizability(c->phimu_p.p, r, r, n_v, n_c, c->sw.p + npair * k, Dk, r, spd, c->partial.p,
+                               c->stream));
+      CK(launch_trsm_right_lt(Dk, r, r, c->Bf.p, r, r, c->stream));
+      CK(launch_transpose(Dk, r, r, r, c->tmp1.p, r, c->stream));
+      CK(launch_trsm_right_lt(c->tmp1.p, r, r, c->Bf.p, r, r, c->stream));
+      CK(launch_symmetrize(c->tmp1.p, r, r, c->stream));
+      CK(cudaMemcpyAsync(Dk, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
+  if (G_out) {
+    int rc = copy_padded(c, G_out, c->G.p, r, m);
+    if (rc != ISDF_OK) return rc;
+  }
+  if (D_out) {
+    for (int k = 0; k < n_omega; ++k) {
+      int rc = copy_padded(c, D_out + (size_t)m * m * k, c->D.p + rr * k, r, m);
+      if (rc != ISDF_OK) return rc;
+    }
+  }
+  c->n_omega = n_omega;
+  c->omega.assign(omega, omega + n_omega);
+  c->k_ready.assign(n_omega, 0);
+  c->polar_ready = true;
+  return ISDF_OK;
+}
+
+extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  if (!c->polar_ready) return fail(c, ISDF_ERR_STATE, "smw_inverse: call build_polarizability first");
+  if (k < 0 || k >= c->n_omega) return fail(c, ISDF_ERR_ARG, "smw_inverse: omega_index out of range");
+  const int r = c->rank, m = c->n_mu;
+  const size_t rr = (size_t)r * r;
+  double* Kk = c->K.p + rr * k;
+  c->k_ready[k] = 0;
+  long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
+  int sp = split_for(tiles, std::max(r, 1), c->num_sms);
+  if (r > 0) {
+    if (c->R.cap < rr || c->T.cap < rr || c->W1.cap < rr || c->Q.cap < rr || c->partial.cap < sp * rr)
+      CK(cudaStreamSynchronize(c->stream));  // a resize frees memory that earlier work may read
+    CK(ensure(c->R, rr));
+    CK(ensure(c->T, rr));
+    CK(ensure(c->W1, rr));
+    CK(ensure(c->Q, rr));
+    CK(ensure(c->partial, (size_t)sp * rr));
+    CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+    // D = R R^T
+    int rc = cholesky(c, c->D.p + rr * k, r, r, 0, 0.0, c->R.p, c->d_perm2);
+    if (rc != ISDF_OK) return rc;
+    // T = I + R^T G R
+    CK(launch_gemm(c->G.p, r, false, c->R.p, r, true, r, r, r, 1.0, 0.0, c->W1.p, r, false, 1, nullptr,
+                   false, c->stream));
+    CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
+    CK(launch_add_identity(c->T.p, r, r, 1.0, c->stream));
+    CK(launch_gemm(c->R.p, r, true, c->W1.p, r, true, r, r, r, 1.0, 1.0, c->T.p, r, false, 1, nullptr,
+                   false, c->stream));
+    CK(launch_symmetrize(c->T.p, r, r, c->stream));
+    // T = U U^T; Q = R U^-T; K = -Q Q^T
+    rc = cholesky(c, c->T.p, r, r, 0, 0.0, c->W1.p, c->d_perm2);
+    if (rc != ISDF_OK) return rc;
+    CK(launch_trsm_prep(c->W1.p, r, r, c->Bf.p + 0, r, c->stream));
+    CK(cudaMemcpyAsync(c->Q.p, c->R.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_trsm_right_lt(c->Q.p, r, r, c->Bf.p, r, r, c->stream));
+    CK(launch_gemm(c->Q.p, r, false, c->Q.p, r, false, r, r, r, -1.0, 0.0, Kk, r, true, sp, c->partial.p,
+                   false, c->stream));
+    // restore the fit's TRSM table (Bf held L_r^-1 blocks for D(w) of later calls)
+    CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+  }
+  if (K_out) {
+    int rc = copy_padded(c, K_out, Kk, r, m);
+    if (rc != ISDF_OK) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  int rc = check_status(c, "smw_inverse");
+  if (rc != ISDF_OK) return rc;
+  c->k_ready[k] = 1;
+  return ISDF_OK;
+}
+
+extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, double* Y) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  if (!c->polar_ready || k < 0 || k >= c->n_omega || !c->k_ready[k])
+    return fail(c, ISDF_ERR_STATE, "apply_eps_inv: call smw_inverse for this omega_index first");
+  if (!X || !Y) return fail(c, ISDF_ERR_ARG, "apply_eps_inv: null pointer argument");
+  if (n_rhs < 1) return fail(c, ISDF_ERR_SHAPE, "apply_eps_inv: n_rhs must be >= 1");
+  const int r = c->rank;
+  const long long nr = c->n_r;
+  const size_t rr = (size_t)r * r;
+  const double* Kk = c->K.p + rr * k;
+  const int chunk = 64;
+  const long long lds = 2 * c->n_half;
+  const int nc0 = std::min(n_rhs, chunk);
+  const long long tiles0 = (long long)((r + 127) / 128) * ((nc0 + 15) / 16);
+  const int sp0 = split_for(std::max(tiles0, 1ll), nr, c->num_sms);
+  if (c->tmp1.cap < (size_t)r * nc0 || c->tmp2.cap < (size_t)r * nc0 || c->tmp3.cap < (size_t)nr * nc0 ||
+      c->spec.cap < (size_t)lds * nc0 || c->partial.cap < (size_t)sp0 * r * nc0)
+    CK(cudaStreamSynchronize(c->stream));  // a resize frees memory that earlier work may read
+  CK(ensure(c->tmp1, std::max<size_t>((size_t)r * nc0, 1)));
+  CK(ensure(c->tmp2, std::max<size_t>((size_t)r * nc0, 1)));
+  CK(ensure(c->tmp3, (size_t)nr * nc0));
+  CK(ensure(c->spec, (size_t)lds * nc0));
+  CK(ensure(c->partial, std::max<size_t>((size_t)sp0 * r * nc0, 1)));
+  for (int c0 = 0; c0 < n_rhs; c0 += chunk) {
+    const int nc = std::min(chunk, n_rhs - c0);
+    const double* Xc = X + nr * c0;
+    double* Yc = Y + nr * c0;
+    if (r == 0) {
+      if (Yc != Xc) CK(cudaMemcpyAsync(Yc, Xc, (size_t)nr * nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      continue;
+    }
+    // T1 = theta^T X (split over the grid), T2 = K T1, T3 = theta T2, Y = X + V T3
+    int sp = sp0;  // nc <= nc0: the same split fits the partial buffer
+    CK(launch_gemm(c->theta, nr, true, Xc, nr, true, r, nc, (int)nr, 1.0, 0.0, c->tmp1.p, r, false, sp,
+                   c->partial.p, true, c->stream));
+    CK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 1, nullptr,
+                   true, c->stream));
+    CK(launch_gemm(c->theta, nr, false, c->tmp2.p, r, true, (int)nr, nc, r, 1.0, 0.0, c->tmp3.p, nr,
+                   false, 1, nullptr, true, c->stream));
+    CK(launch_fft_convolve(c->fft, c->tmp3.p, nr, nc, c->spec.p, lds, c->d_wconv, Xc, nr, Yc, nr,
+                           c->smem_xy, c->smem_z, c->stream));
+  }
+  return ISDF_OK;
+}

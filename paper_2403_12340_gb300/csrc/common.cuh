@@ -1,0 +1,190 @@
+// Shared device helpers for the ISDF-SMW kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isdf {
+
+// Device status bits, OR-ed into a status word by kernels.
+enum : unsigned {
+  ST_NONFINITE = 1u,   // a NaN / Inf was seen in an input
+  ST_NOT_SPD = 2u,     // non-positive pivot in an unpivoted Cholesky
+  ST_TIMEOUT = 4u,     // a bounded device-side wait gave up
+  ST_BADINDEX = 8u,    // an index failed a device-side bounds check
+};
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier for cooperative launches (all blocks co-resident).
+// A block records the generation before arriving; the last arriver resets
+// the counter and bumps the generation.  The wait is bounded by `limit_ns`
+// of wall time: on expiry the status word gets ST_TIMEOUT and the barrier
+// returns false, so the caller leaves the kernel instead of hanging.
+struct GridBarrier {
+  unsigned* count;
+  unsigned* gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier b, unsigned* status, uint64_t limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned my_gen = ld_acquire(b.gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(b.count, 1u);
+    if (arrived == gridDim.x * gridDim.y * gridDim.z - 1u) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (ld_acquire(b.gen) == my_gen) {
+        if ((++spins & 255u) == 0u) {
+          if (global_ns() - t0 > limit_ns || (ld_acquire(status) & ST_TIMEOUT)) {
+            atomicOr(status, ST_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    s_ok = ok && !(ld_acquire(status) & ST_TIMEOUT);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 tiled GEMM engine: acc(m, n) += sum_k A(m, k) B(n, k) on a BM x BN
+// output tile, 16-deep k slices staged in padded shared memory, a TM x TN
+// register tile per thread.  Thread t owns rows m0 + tx + (BM/TM) i and
+// columns n0 + ty + (BN/TN) j with tx = t % (BM/TM), ty = t / (BM/TM), so
+// column-major stores of a tile are coalesced along m.  FP64 on GB300 is
+// bound by the DFMA pipe (measured 1.2 TFLOP/s per GPU); one shared-memory
+// load feeds TN (resp. TM) DFMAs, which keeps that pipe saturated.
+// ---------------------------------------------------------------------------
+constexpr int GT_BK = 16;
+
+// Operand accessor: element (row, k) of a matrix operand with `rows` rows.
+// KCONTIG = false: row index contiguous, address p[row + ld * k].
+// KCONTIG = true : k index contiguous,   address p[k + ld * row].
+template <bool KCONTIG>
+struct Operand {
+  static constexpr bool kcontig = KCONTIG;
+  const double* p;
+  long long ld;
+  int rows;
+  __device__ __forceinline__ double get(int row, int k) const {
+    return KCONTIG ? p[(long long)row * ld + k] : p[row + ld * (long long)k];
+  }
+};
+
+template <int BM, int BN, int TM, int TN>
+struct Tile {
+  static constexpr int kBM = BM, kBN = BN, kTM = TM, kTN = TN;
+  static constexpr int XT = BM / TM, YT = BN / TN, NT = XT * YT;
+  struct Smem {
+    double a[GT_BK][BM + 1];
+    double b[GT_BK][BN + 1];
+  };
+};
+
+using TileSq = Tile<64, 64, 4, 4>;       // 256 threads, square tiles
+using TileNarrow = Tile<128, 16, 4, 2>;  // 256 threads, tall-skinny (probe blocks)
+
+// sm[k][row] = op(row0 + row, k0 + k), zero outside [0, rows) x [k0, kend).
+template <int NT, int ROWS, class Op>
+__device__ __forceinline__ void load_slice(double (*sm)[ROWS + 1], const Op& op, int row0, int k0,
+                                           int kend) {
+  const int t = threadIdx.x;
+  constexpr int PER = (ROWS * GT_BK + NT - 1) / NT;
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    int idx = t + s * NT;
+    if (idx >= ROWS * GT_BK) break;
+    int r, k;
+    if (!Op::kcontig) {
+      r = idx % ROWS;
+      k = idx / ROWS;
+    } else {
+      k = idx % GT_BK;
+      r = idx / GT_BK;
+    }
+    int gr = row0 + r, gk = k0 + k;
+    sm[k][r] = (gr < op.rows && gk < kend) ? op.get(gr, gk) : 0.0;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void mma_slice(double (&acc)[T::kTM][T::kTN], const typename T::Smem& s) {
+  const int tx = threadIdx.x % T::XT, ty = threadIdx.x / T::XT;
+#pragma unroll
+  for (int kk = 0; kk < GT_BK; ++kk) {
+    double a[T::kTM], b[T::kTN];
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i) a[i] = s.a[kk][tx + T::XT * i];
+#pragma unroll
+    for (int j = 0; j < T::kTN; ++j) b[j] = s.b[kk][ty + T::YT * j];
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i)
+#pragma unroll
+      for (int j = 0; j < T::kTN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
+// acc += sum_{k in [kbeg, kend)} A(m0 + ., k) B(n0 + ., k)
+template <class T, class OpA, class OpB>
+__device__ __forceinline__ void gemm_mainloop(double (&acc)[T::kTM][T::kTN], typename T::Smem& s,
+                                              const OpA& A, const OpB& B, int m0, int n0, int kbeg,
+                                              int kend) {
+  for (int k0 = kbeg; k0 < kend; k0 += GT_BK) {
+    load_slice<T::NT, T::kBM>(s.a, A, m0, k0, kend);
+    load_slice<T::NT, T::kBN>(s.b, B, n0, k0, kend);
+    __syncthreads();
+    mma_slice<T>(acc, s);
+    __syncthreads();
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void zero_acc(double (&acc)[T::kTM][T::kTN]) {
+#pragma unroll
+  for (int i = 0; i < T::kTM; ++i)
+#pragma unroll
+    for (int j = 0; j < T::kTN; ++j) acc[i][j] = 0.0;
+}
+
+// (row, col) of register element (i, j) of this thread in tile (m0, n0).
+template <class T>
+__device__ __forceinline__ int tile_row(int m0, int i) {
+  return m0 + (int)(threadIdx.x % T::XT) + T::XT * i;
+}
+template <class T>
+__device__ __forceinline__ int tile_col(int n0, int j) {
+  return n0 + (int)(threadIdx.x / T::XT) + T::YT * j;
+}
+
+// Map a linear block index onto lower-triangular tile coordinates (mt >= nt).
+__device__ __forceinline__ void lower_tile(int lin, int& mt, int& nt) {
+  int m = (int)((sqrt(8.0 * (double)lin + 1.0) - 1.0) * 0.5);
+  while ((m + 1) * (m + 2) / 2 <= lin) ++m;
+  while (m * (m + 1) / 2 > lin) --m;
+  mt = m;
+  nt = lin - m * (m + 1) / 2;
+}
+
+}  // namespace isdf

@@ -1,0 +1,449 @@
+// Dense FP64 kernels of the ISDF-SMW path: gather, face-split Gram (ISDF
+// fit right-hand side M C^T), generic GEMM / SYRK with deterministic split-K,
+// polarizability C Omega^-1 C^T with on-the-fly pair operands, and a blocked
+// in-place right triangular solve.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace isdf {
+
+// ---------------------------------------------------------------- utilities
+
+__global__ void k_check_finite(const double* __restrict__ p, long long n, unsigned* status) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (; i < n; i += stride) bad |= !isfinite(p[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+}
+
+cudaError_t launch_check_finite(const double* p, long long n, unsigned* status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_check_finite<<<(int)blocks, 256, 0, s>>>(p, n, status);
+  return cudaGetLastError();
+}
+
+// dst(a, e) = src(idx[a], e)
+__global__ void k_gather_rows(const double* __restrict__ src, long long lds, const int* __restrict__ idx,
+                              int nrows, int ncols, double* __restrict__ dst, long long ldd) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = blockIdx.y;
+  if (a < nrows && e < ncols) dst[a + ldd * e] = src[(long long)idx[a] + lds * e];
+}
+
+cudaError_t launch_gather_rows(const double* src, long long lds, const int* idx, int nrows, int ncols,
+                               double* dst, long long ldd, cudaStream_t s) {
+  if (nrows <= 0 || ncols <= 0) return cudaSuccess;
+  dim3 grid((nrows + 127) / 128, ncols);
+  k_gather_rows<<<grid, 128, 0, s>>>(src, lds, idx, nrows, ncols, dst, ldd);
+  return cudaGetLastError();
+}
+
+__global__ void k_transpose(const double* __restrict__ src, long long lds, int M, int N,
+                            double* __restrict__ dst, long long ldd) {
+  __shared__ double t[32][33];
+  int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int i = i0 + threadIdx.x, j = j0 + k;
+    if (i < M && j < N) t[k][threadIdx.x] = src[i + lds * j];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int j = j0 + threadIdx.x, i = i0 + k;
+    if (i < M && j < N) dst[j + ldd * i] = t[threadIdx.x][k];
+  }
+}
+
+cudaError_t launch_transpose(const double* src, long long lds, int M, int N, double* dst,
+                             long long ldd, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((M + 31) / 32, (N + 31) / 32), block(32, 8);
+  k_transpose<<<grid, block, 0, s>>>(src, lds, M, N, dst, ldd);
+  return cudaGetLastError();
+}
+
+__global__ void k_symmetrize(double* A, long long lda, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i < n && j < i) {
+    double v = 0.5 * (A[i + lda * j] + A[j + lda * i]);
+    A[i + lda * j] = v;
+    A[j + lda * i] = v;
+  }
+}
+
+cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  dim3 grid((n + 127) / 128, n);
+  k_symmetrize<<<grid, 128, 0, s>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_add_identity(double* A, long long lda, int n, double v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + lda * i] += v;
+}
+
+cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_add_identity<<<(n + 127) / 128, 128, 0, s>>>(A, lda, n, v);
+  return cudaGetLastError();
+}
+
+// L(a, c) = Lr[perm[a] * n + c] for c <= a < rank, zero elsewhere in n_full x n_full.
+__global__ void k_factor_to_colmajor(const double* __restrict__ Lr, int n, const int* __restrict__ perm,
+                                     const int* __restrict__ rank_p, double* __restrict__ L,
+                                     long long ldl, int n_full) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (a >= n_full || c >= n_full) return;
+  int rank = min(*rank_p, n);  // a failed factorisation may leave rank stale: never trust it past n
+  double v = 0.0;
+  if (a < rank && c < rank && c <= a) {
+    int pa = perm[a];
+    if (pa >= 0 && pa < n) v = __ldcg(&Lr[(long long)pa * n + c]);
+  }
+  L[a + ldl * c] = v;
+}
+
+cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
+                                      double* L, long long ldl, int n_full, cudaStream_t s) {
+  dim3 grid((n_full + 127) / 128, n_full);
+  k_factor_to_colmajor<<<grid, 128, 0, s>>>(Lr, n, perm, rank, L, ldl, n_full);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- face-split Gram (ISDF fit)
+// C(m, n) = (sum_{k < n_v} A(m,k) B(n,k)) * (sum_{n_v <= k < n_e} A(m,k) B(n,k)):
+// with A = Phi and B = Phi at the points this is M C^T (Hadamard identity,
+// Eq. Hadamard), with A = B = Phi at the points it is C C^T.
+__global__ void __launch_bounds__(256) k_facesplit_gram(Operand<false> A, Operand<false> B, int n_v,
+                                                        int n_e, double* __restrict__ C,
+                                                        long long ldc) {
+  using T = TileSq;
+  __shared__ T::Smem s;
+  const int m0 = blockIdx.x * T::kBM, n0 = blockIdx.y * T::kBN;
+  double av[T::kTM][T::kTN], ac[T::kTM][T::kTN];
+  zero_acc<T>(av);
+  zero_acc<T>(ac);
+  gemm_mainloop<T>(av, s, A, B, m0, n0, 0, n_v);
+  gemm_mainloop<T>(ac, s, A, B, m0, n0, n_v, n_e);
+#pragma unroll
+  for (int j = 0; j < T::kTN; ++j) {
+    int n = tile_col<T>(n0, j);
+    if (n >= B.rows) continue;
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i) {
+      int m = tile_row<T>(m0, i);
+      if (m < A.rows) C[m + ldc * n] = av[i][j] * ac[i][j];
+    }
+  }
+}
+
+cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const double* B,
+                                  long long ldb, int N, int n_v, int n_e, double* C, long long ldc,
+                                  cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((M + 63) / 64, (N + 63) / 64);
+  k_facesplit_gram<<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v,
+                                        n_e, C, ldc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ generic GEMM
+
+template <class T>
+__device__ __forceinline__ void store_tile(const double (&acc)[T::kTM][T::kTN], int m0, int n0, int M,
+                                           int N, double alpha, double beta, double* C, long long ldc,
+                                           bool mirror) {
+#pragma unroll
+  for (int j = 0; j < T::kTN; ++j) {
+    int n = tile_col<T>(n0, j);
+    if (n >= N) continue;
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i) {
+      int m = tile_row<T>(m0, i);
+      if (m >= M) continue;
+      double v = alpha * acc[i][j];
+      if (beta != 0.0) v += beta * C[m + ldc * n];
+      C[m + ldc * n] = v;
+      if (mirror) C[n + ldc * m] = v;
+    }
+  }
+}
+
+template <class T, class OpA, class OpB>
+__global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int K, int klen,
+                                                double alpha, double beta, double* C, long long ldc,
+                                                double* partial, int lower_only) {
+  __shared__ typename T::Smem s;
+  int mt, nt;
+  if (lower_only) {
+    lower_tile(blockIdx.x, mt, nt);
+  } else {
+    mt = blockIdx.x;
+    nt = blockIdx.y;
+  }
+  const int m0 = mt * T::kBM, n0 = nt * T::kBN;
+  const int kbeg = blockIdx.z * klen;
+  const int kend = min(K, kbeg + klen);
+  double acc[T::kTM][T::kTN];
+  zero_acc<T>(acc);
+  gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  if (partial) {
+    double* P = partial + (long long)blockIdx.z * M * N;
+    store_tile<T>(acc, m0, n0, M, N, 1.0, 0.0, P, M, false);
+  } else {
+    store_tile<T>(acc, m0, n0, M, N, alpha, beta, C, ldc, lower_only && mt != nt);
+  }
+}
+
+// C = alpha * sum_z partial[z] + beta * C; for lower_only the upper tiles are
+// read mirrored from the lower ones.
+__global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, int M, int N,
+                                double alpha, double beta, double* C, long long ldc, int lower_only,
+                                int tile) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = blockIdx.y;
+  if (m >= M || n >= N) return;
+  int pm = m, pn = n;
+  if (lower_only && (m / tile) < (n / tile)) {
+    pm = n;
+    pn = m;
+  }
+  double v = 0.0;
+  for (int z = 0; z < splits; ++z) v += partial[(long long)z * M * N + pm + (long long)M * pn];
+  v *= alpha;
+  if (beta != 0.0) v += beta * C[m + ldc * n];
+  C[m + ldc * n] = v;
+}
+
+template <class T, bool KA, bool KB>
+static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B, long long ldb, int M,
+                                 int N, int K, double alpha, double beta, double* C, long long ldc,
+                                 bool lower_only, int splits, double* partial, cudaStream_t s) {
+  Operand<KA> oa{A, lda, M};
+  Operand<KB> ob{B, ldb, N};
+  int tm = (M + T::kBM - 1) / T::kBM, tn = (N + T::kBN - 1) / T::kBN;
+  if (splits < 1) splits = 1;
+  int klen = (K + splits - 1) / splits;
+  klen = ((klen + GT_BK - 1) / GT_BK) * GT_BK;
+  splits = (K + klen - 1) / klen;
+  if (splits < 1) splits = 1;
+  bool use_partial = splits > 1;
+  dim3 grid;
+  if (lower_only) {
+    grid = dim3(tm * (tm + 1) / 2, 1, splits);
+  } else {
+    grid = dim3(tm, tn, splits);
+  }
+  k_gemm<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
+                                                            use_partial ? partial : nullptr,
+                                                            lower_only ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !use_partial) return e;
+  dim3 rg((M + 127) / 128, N);
+  k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, M, N, alpha, beta, C, ldc, lower_only ? 1 : 0,
+                                     T::kBM);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const double* A, long long lda, bool ka, const double* B, long long ldb,
+                        bool kb, int M, int N, int K, double alpha, double beta, double* C,
+                        long long ldc, bool lower_only, int splits, double* partial, bool narrow,
+                        cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (splits > 1 && !partial) return cudaErrorInvalidValue;
+  if (lower_only && (M != N || narrow)) return cudaErrorInvalidValue;
+#define ISDF_GEMM_CASE(TT, a, b)                                                                 \
+  if (ka == a && kb == b)                                                                        \
+    return gemm_dispatch<TT, a, b>(A, lda, B, ldb, M, N, K, alpha, beta, C, ldc, lower_only,     \
+                                   splits, partial, s);
+  if (narrow) {
+    ISDF_GEMM_CASE(TileNarrow, false, false)
+    ISDF_GEMM_CASE(TileNarrow, false, true)
+    ISDF_GEMM_CASE(TileNarrow, true, false)
+    ISDF_GEMM_CASE(TileNarrow, true, true)
+  } else {
+    ISDF_GEMM_CASE(TileSq, false, false)
+    ISDF_GEMM_CASE(TileSq, false, true)
+    ISDF_GEMM_CASE(TileSq, true, false)
+    ISDF_GEMM_CASE(TileSq, true, true)
+  }
+#undef ISDF_GEMM_CASE
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ polarizability
+// S(a, ij) = phimu(a, i) phimu(a, n_v + j) sw[i n_c + j]: the columns of the
+// pair matrix at the points (C of Eq. MatrixExpressionISDF) scaled by
+// sqrt(-2 Omega^-1), generated on the fly so C (N_mu x N_v N_c) is never
+// stored.  D = S S^T = -2 C Omega^-1 C^T.
+struct PairOperand {
+  static constexpr bool kcontig = false;
+  const double* p;  // phimu, column-major r x n_e
+  long long ld;
+  int rows;
+  int n_v, n_c;
+  const double* sw;
+  __device__ __forceinline__ double get(int a, int kk) const {
+    int i = kk / n_c;
+    int j = kk - i * n_c;
+    return p[a + ld * i] * p[a + ld * (long long)(n_v + j)] * sw[kk];
+  }
+};
+
+__global__ void __launch_bounds__(256) k_polarizability(PairOperand S, int K, int klen,
+                                                        double* __restrict__ D, long long ldd,
+                                                        double* partial) {
+  using T = TileSq;
+  __shared__ T::Smem s;
+  int mt, nt;
+  lower_tile(blockIdx.x, mt, nt);
+  const int m0 = mt * T::kBM, n0 = nt * T::kBN;
+  const int kbeg = blockIdx.z * klen, kend = min(K, kbeg + klen);
+  double acc[T::kTM][T::kTN];
+  zero_acc<T>(acc);
+  gemm_mainloop<T>(acc, s, S, S, m0, n0, kbeg, kend);
+  if (partial) {
+    store_tile<T>(acc, m0, n0, S.rows, S.rows, 1.0, 0.0, partial + (long long)blockIdx.z * S.rows * S.rows,
+                  S.rows, false);
+  } else {
+    store_tile<T>(acc, m0, n0, S.rows, S.rows, 1.0, 0.0, D, ldd, mt != nt);
+  }
+}
+
+cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int n_v, int n_c,
+                                  const double* sw, double* D, long long ldd, int splits,
+                                  double* partial, cudaStream_t s) {
+  if (r <= 0) return cudaSuccess;
+  PairOperand S{phimu, ldp, r, n_v, n_c, sw};
+  int K = n_v * n_c;
+  if (splits < 1 || !partial) splits = 1;
+  int klen = (K + splits - 1) / splits;
+  klen = ((klen + GT_BK - 1) / GT_BK) * GT_BK;
+  splits = (K + klen - 1) / klen;
+  int tm = (r + 63) / 64;
+  dim3 grid(tm * (tm + 1) / 2, 1, splits);
+  k_polarizability<<<grid, 256, 0, s>>>(S, K, klen, D, ldd, splits > 1 ? partial : nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  dim3 rg((r + 127) / 128, r);
+  k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, r, r, 1.0, 0.0, D, ldd, 1, 64);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ triangular solve
+constexpr int TRSM_NB = 64;
+
+// Inverse of each 64 x 64 diagonal block of the lower-triangular L, written
+// into the diagonal blocks of Bf (lower part; the strict upper part is 0).
+// Thread c solves L_JJ x = e_c by forward substitution.
+__global__ void k_diag_inverse(const double* __restrict__ L, long long ldl, int r, double* __restrict__ Bf,
+                               long long ldb) {
+  __shared__ double Ls[TRSM_NB][TRSM_NB + 1];
+  __shared__ double Xs[TRSM_NB][TRSM_NB + 1];
+  const int j0 = blockIdx.x * TRSM_NB;
+  const int bs = min(TRSM_NB, r - j0);
+  const int c = threadIdx.x;
+  for (int i = 0; i < bs; ++i)
+    if (c < bs) Ls[i][c] = L[(j0 + i) + ldl * (j0 + c)];
+  __syncthreads();
+  if (c < bs) {
+    for (int i = 0; i < c; ++i) Xs[i][c] = 0.0;
+    Xs[c][c] = 1.0 / Ls[c][c];
+    for (int i = c + 1; i < bs; ++i) {
+      double acc = 0.0;
+      for (int k = c; k < i; ++k) acc = fma(Ls[i][k], Xs[k][c], acc);
+      Xs[i][c] = -acc / Ls[i][i];
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < bs; ++i)
+    if (c < bs) Bf[(j0 + i) + ldb * (j0 + c)] = Xs[i][c];
+}
+
+// Bf[J, I] = -L_JJ^-1 L_JI for I < J (64 x 64 blocks), the diagonal
+// inverses already in Bf.
+__global__ void __launch_bounds__(256) k_trsm_offdiag(const double* __restrict__ L, long long ldl, int r,
+                                                      double* __restrict__ Bf, long long ldb) {
+  using T = TileSq;
+  __shared__ T::Smem s;
+  const int J = blockIdx.y + 1;
+  const int It = blockIdx.x;
+  if (It >= J) return;
+  const int j0 = J * TRSM_NB;
+  const int bs = min(TRSM_NB, r - j0);
+  // A(m, k) = Dinv_J(m, k) = Bf[j0 + m, j0 + k]; B(n, k) = L[j0 + k, n] (n < j0)
+  Operand<false> A{Bf + j0 + ldb * (long long)j0, ldb, bs};
+  Operand<true> B{L + j0, ldl, j0};
+  double acc[T::kTM][T::kTN];
+  zero_acc<T>(acc);
+  gemm_mainloop<T>(acc, s, A, B, 0, It * T::kBN, 0, bs);
+#pragma unroll
+  for (int j = 0; j < T::kTN; ++j) {
+    int n = tile_col<T>(It * T::kBN, j);
+    if (n >= j0) continue;
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i) {
+      int m = tile_row<T>(0, i);
+      if (m < bs) Bf[(j0 + m) + ldb * n] = -acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_trsm_prep(const double* L, long long ldl, int r, double* Bf, long long ldb,
+                             cudaStream_t s) {
+  if (r <= 0) return cudaSuccess;
+  int nb = (r + TRSM_NB - 1) / TRSM_NB;
+  k_diag_inverse<<<nb, TRSM_NB, 0, s>>>(L, ldl, r, Bf, ldb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nb == 1) return e;
+  dim3 grid(nb - 1, nb - 1);
+  k_trsm_offdiag<<<grid, 256, 0, s>>>(L, ldl, r, Bf, ldb);
+  return cudaGetLastError();
+}
+
+// One block column of X <- X L^-T: X[:, J] = X[:, 0 : j0 + bs] Bf[J, 0 : j0 + bs]^T.
+// Columns < j0 are already solved; columns J still hold the right-hand side.
+// Each thread block owns 64 full rows of the block column, and reads all of
+// them before it writes, so the update is safe in place.
+__global__ void __launch_bounds__(256) k_trsm_step(double* X, long long ldx, int M,
+                                                   const double* __restrict__ Bf, long long ldb, int j0,
+                                                   int bs) {
+  using T = TileSq;
+  __shared__ T::Smem s;
+  const int m0 = blockIdx.x * T::kBM;
+  Operand<false> A{X, ldx, M};
+  Operand<false> B{Bf + j0, ldb, bs};
+  double acc[T::kTM][T::kTN];
+  zero_acc<T>(acc);
+  gemm_mainloop<T>(acc, s, A, B, m0, 0, 0, j0 + bs);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < T::kTN; ++j) {
+    int n = tile_col<T>(0, j);
+    if (n >= bs) continue;
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i) {
+      int m = tile_row<T>(m0, i);
+      if (m < M) X[m + ldx * (long long)(j0 + n)] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* Bf, long long ldb,
+                                 int r, cudaStream_t s) {
+  if (M <= 0 || r <= 0) return cudaSuccess;
+  for (int j0 = 0; j0 < r; j0 += TRSM_NB) {
+    int bs = min(TRSM_NB, r - j0);
+    k_trsm_step<<<(M + 63) / 64, 256, 0, s>>>(X, ldx, M, Bf, ldb, j0, bs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace isdf

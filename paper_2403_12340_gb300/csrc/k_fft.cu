@@ -1,0 +1,350 @@
+// Batched 3-D real FFTs on the periodic grid, written for the Coulomb
+// operator of the ISDF-SMW path (V = F^-1 diag(v_G / dV) F; Algorithm 3
+// step 2 applies it to the interpolation vectors).  No cuFFT.
+//
+// Two kernels per direction:
+//   xy kernel: one thread block per (column, z plane).  The real n1 x n2
+//     plane is loaded into shared memory with lines y = 2t and 2t+1 packed
+//     as one complex line, transformed along x, unpacked to the half
+//     spectrum kx = 0..n1/2 (Hermitian symmetry of a real line), then
+//     transformed along y.  The inverse runs the same steps backwards.
+//   z kernel: one thread block per (column, 32 consecutive (ky, kx)
+//     positions); transforms along z and multiplies by a real weight table
+//     (for the convolution: forward, weight, inverse in one pass).
+// 1-D transforms are Stockham auto-sort passes with radices 4, 2, 3, 5 (and
+// a direct DFT for 7, 11, 13), ping-ponging between two shared buffers.
+// Twiddles exp(-2 pi i t / n) come from a per-axis table computed on the
+// host in float64.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace isdf {
+
+constexpr int FFT_THREADS = 256;
+constexpr int FFT_ZCHUNK = 32;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// twiddle exp(DIR 2 pi i t / n) with DIR = -1 forward, +1 inverse
+template <int DIR>
+__device__ __forceinline__ double2 twid(const double2* tw, int t) {
+  double2 w = tw[t];
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+template <int DIR>
+__device__ __forceinline__ void bfly2(double2* v) {
+  double2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void bfly3(double2* v) {
+  const double s3 = 0.86602540378443864676;  // sqrt(3) / 2
+  double2 t1 = cadd(v[1], v[2]);
+  double2 t2 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
+  double2 m = make_double2(s3 * (v[1].x - v[2].x), s3 * (v[1].y - v[2].y));
+  v[0] = cadd(v[0], t1);
+  if (DIR < 0) {  // X1 = t2 - i m, X2 = t2 + i m
+    v[1] = make_double2(t2.x + m.y, t2.y - m.x);
+    v[2] = make_double2(t2.x - m.y, t2.y + m.x);
+  } else {
+    v[1] = make_double2(t2.x - m.y, t2.y + m.x);
+    v[2] = make_double2(t2.x + m.y, t2.y - m.x);
+  }
+}
+
+template <int DIR>
+__device__ __forceinline__ void bfly4(double2* v) {
+  double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  double2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  if (DIR < 0) {  // X1 = b - i d, X3 = b + i d
+    v[1] = make_double2(b.x + d.y, b.y - d.x);
+    v[3] = make_double2(b.x - d.y, b.y + d.x);
+  } else {
+    v[1] = make_double2(b.x - d.y, b.y + d.x);
+    v[3] = make_double2(b.x + d.y, b.y - d.x);
+  }
+}
+
+// direct R-point DFT with table twiddles (w_R^m = tw[(m mod R) n / R])
+template <int R, int DIR>
+__device__ __forceinline__ void bfly_direct(double2* v, const double2* tw, int n) {
+  double2 out[R];
+  const int step = n / R;
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    double2 acc = v[0];
+#pragma unroll
+    for (int b = 1; b < R; ++b) acc = cadd(acc, cmul(v[b], twid<DIR>(tw, ((a * b) % R) * step)));
+    out[a] = acc;
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a) v[a] = out[a];
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void bfly(double2* v, const double2* tw, int n) {
+  if constexpr (R == 2) bfly2<DIR>(v);
+  else if constexpr (R == 3) bfly3<DIR>(v);
+  else if constexpr (R == 4) bfly4<DIR>(v);
+  else bfly_direct<R, DIR>(v, tw, n);
+}
+
+// One Stockham pass of radix R over `nlines` lines of length n (element e of
+// line l at buf[l * sl + e * se]); Ns = product of the radices done so far.
+template <int R, int DIR>
+__device__ void stockham_pass(const double2* __restrict__ src, double2* __restrict__ dst, int n, int Ns,
+                              int nlines, int se, int sl, const double2* tw) {
+  const int nR = n / R;
+  const int tstep = n / (Ns * R);
+  for (int idx = threadIdx.x; idx < nlines * nR; idx += blockDim.x) {
+    int line = idx / nR, j = idx - line * nR;
+    int k = j % Ns;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[line * sl + (j + r * nR) * se];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(tw, r * k * tstep));
+    }
+    bfly<R, DIR>(v, tw, n);
+    int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[line * sl + (base + r * Ns) * se] = v[r];
+  }
+}
+
+// 1-D transforms of all lines; returns the buffer holding the result.
+template <int DIR>
+__device__ double2* fft_lines(double2* src, double2* dst, const FftAxis& ax, const double2* tw, int nlines,
+                              int se, int sl) {
+  int Ns = 1;
+  const int n = ax.n;
+  for (int f = 0; f < ax.nf; ++f) {
+    int R = ax.f[f];
+    switch (R) {
+      case 2: stockham_pass<2, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+      case 3: stockham_pass<3, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+      case 4: stockham_pass<4, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+      case 5: stockham_pass<5, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+      case 7: stockham_pass<7, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+      case 11: stockham_pass<11, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+      default: stockham_pass<13, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
+    }
+    __syncthreads();
+    double2* t = src;
+    src = dst;
+    dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+struct XYShape {
+  int n1, n2, h, npair, buf;  // buf = complex elements per ping-pong buffer
+};
+
+__device__ __forceinline__ XYShape xy_shape(const FftGrid& g) {
+  XYShape s;
+  s.n1 = g.ax[0].n;
+  s.n2 = g.ax[1].n;
+  s.h = g.h;
+  s.npair = (s.n2 + 1) / 2;
+  s.buf = max(s.npair * s.n1, s.h * s.n2);
+  return s;
+}
+
+// Forward xy: real plane -> half spectrum plane P[ky][kx] (h x n2).
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd(FftGrid g, const double* __restrict__ X,
+                                                            long long ldx, double* __restrict__ S,
+                                                            long long lds) {
+  extern __shared__ double2 sm[];
+  const XYShape sh = xy_shape(g);
+  double2* twx = sm;
+  double2* twy = twx + sh.n1;
+  double2* b0 = twy + sh.n2;
+  double2* b1 = b0 + sh.buf;
+  const int z = blockIdx.x, col = blockIdx.y;
+  for (int t = threadIdx.x; t < sh.n1; t += blockDim.x) twx[t] = ((const double2*)g.ax[0].tw)[t];
+  for (int t = threadIdx.x; t < sh.n2; t += blockDim.x) twy[t] = ((const double2*)g.ax[1].tw)[t];
+  const double* plane = X + ldx * (long long)col + (long long)z * sh.n1 * sh.n2;
+  for (int idx = threadIdx.x; idx < sh.npair * sh.n1; idx += blockDim.x) {
+    int t = idx / sh.n1, x = idx - t * sh.n1;
+    int y0 = 2 * t, y1 = 2 * t + 1;
+    double re = plane[x + sh.n1 * y0];
+    double im = y1 < sh.n2 ? plane[x + sh.n1 * y1] : 0.0;
+    b0[t * sh.n1 + x] = make_double2(re, im);
+  }
+  __syncthreads();
+  double2* res = fft_lines<-1>(b0, b1, g.ax[0], twx, sh.npair, 1, sh.n1);
+  double2* P = (res == b0) ? b1 : b0;
+  // unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
+  for (int idx = threadIdx.x; idx < sh.npair * sh.h; idx += blockDim.x) {
+    int t = idx / sh.h, k = idx - t * sh.h;
+    double2 zk = res[t * sh.n1 + k];
+    double2 zm = res[t * sh.n1 + (k == 0 ? 0 : sh.n1 - k)];
+    double2 A = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
+    double2 B = make_double2(0.5 * (zk.y + zm.y), -0.5 * (zk.x - zm.x));
+    P[(2 * t) * sh.h + k] = A;
+    if (2 * t + 1 < sh.n2) P[(2 * t + 1) * sh.h + k] = B;
+  }
+  __syncthreads();
+  double2* other = (P == b0) ? b1 : b0;
+  double2* Q = fft_lines<-1>(P, other, g.ax[1], twy, sh.h, sh.h, 1);
+  double2* out = (double2*)(S + lds * (long long)col) + (long long)z * sh.n2 * sh.h;
+  for (int idx = threadIdx.x; idx < sh.n2 * sh.h; idx += blockDim.x) out[idx] = Q[idx];
+}
+
+// Inverse xy: half spectrum plane -> real plane, Y = X + result (X may be null).
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_inv(FftGrid g, const double* __restrict__ S,
+                                                            long long lds, const double* X, long long ldx,
+                                                            double* Y, long long ldy) {
+  extern __shared__ double2 sm[];
+  const XYShape sh = xy_shape(g);
+  double2* twx = sm;
+  double2* twy = twx + sh.n1;
+  double2* b0 = twy + sh.n2;
+  double2* b1 = b0 + sh.buf;
+  const int z = blockIdx.x, col = blockIdx.y;
+  for (int t = threadIdx.x; t < sh.n1; t += blockDim.x) twx[t] = ((const double2*)g.ax[0].tw)[t];
+  for (int t = threadIdx.x; t < sh.n2; t += blockDim.x) twy[t] = ((const double2*)g.ax[1].tw)[t];
+  const double2* in = (const double2*)(S + lds * (long long)col) + (long long)z * sh.n2 * sh.h;
+  for (int idx = threadIdx.x; idx < sh.n2 * sh.h; idx += blockDim.x) b0[idx] = in[idx];
+  __syncthreads();
+  double2* P = fft_lines<1>(b0, b1, g.ax[1], twy, sh.h, sh.h, 1);
+  double2* Zb = (P == b0) ? b1 : b0;
+  // repack pairs of lines: Z_k = A_k + i B_k over the full k range
+  for (int idx = threadIdx.x; idx < sh.npair * sh.n1; idx += blockDim.x) {
+    int t = idx / sh.n1, k = idx - t * sh.n1;
+    bool lo = k < sh.h;
+    int kk = lo ? k : sh.n1 - k;
+    double2 A = P[(2 * t) * sh.h + kk];
+    double2 B = (2 * t + 1 < sh.n2) ? P[(2 * t + 1) * sh.h + kk] : make_double2(0.0, 0.0);
+    if (!lo) {
+      A.y = -A.y;
+      B.y = -B.y;
+    }
+    Zb[t * sh.n1 + k] = make_double2(A.x - B.y, A.y + B.x);
+  }
+  __syncthreads();
+  double2* other = (Zb == b0) ? b1 : b0;
+  double2* R = fft_lines<1>(Zb, other, g.ax[0], twx, sh.npair, 1, sh.n1);
+  const long long off = (long long)z * sh.n1 * sh.n2;
+  for (int idx = threadIdx.x; idx < sh.npair * sh.n1; idx += blockDim.x) {
+    int t = idx / sh.n1, x = idx - t * sh.n1;
+    double2 v = R[t * sh.n1 + x];
+    long long r0 = off + x + (long long)sh.n1 * (2 * t);
+    double a0 = X ? X[ldx * (long long)col + r0] : 0.0;
+    Y[ldy * (long long)col + r0] = a0 + v.x;
+    if (2 * t + 1 < sh.n2) {
+      long long r1 = r0 + sh.n1;
+      double a1 = X ? X[ldx * (long long)col + r1] : 0.0;
+      Y[ldy * (long long)col + r1] = a1 + v.y;
+    }
+  }
+}
+
+// z transforms of FFT_ZCHUNK consecutive (ky, kx) positions of one column.
+// MODE 0: forward then multiply by wt.  MODE 1: forward, multiply, inverse.
+template <int MODE>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, double* S, long long lds,
+                                                       const double* __restrict__ wt) {
+  extern __shared__ double2 sm[];
+  const int n3 = g.ax[2].n;
+  const int plane = g.ax[1].n * g.h;
+  double2* twz = sm;
+  double2* b0 = twz + n3;
+  double2* b1 = b0 + n3 * FFT_ZCHUNK;
+  const int q0 = blockIdx.x * FFT_ZCHUNK, col = blockIdx.y;
+  const int nq = min(FFT_ZCHUNK, plane - q0);
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) twz[t] = ((const double2*)g.ax[2].tw)[t];
+  double2* base = (double2*)(S + lds * (long long)col);
+  for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
+    int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
+    b0[idx] = c < nq ? base[(long long)z * plane + q0 + c] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  double2* R = fft_lines<-1>(b0, b1, g.ax[2], twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
+  if (wt) {
+    for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
+      int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
+      double w = c < nq ? wt[(long long)z * plane + q0 + c] : 0.0;
+      R[idx] = make_double2(R[idx].x * w, R[idx].y * w);
+    }
+    __syncthreads();
+  }
+  if (MODE == 1) {
+    double2* other = (R == b0) ? b1 : b0;
+    R = fft_lines<1>(R, other, g.ax[2], twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
+  }
+  for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
+    int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
+    if (c < nq) base[(long long)z * plane + q0 + c] = R[idx];
+  }
+}
+
+size_t fft_smem_xy(const FftGrid& g) {
+  int n1 = g.ax[0].n, n2 = g.ax[1].n, h = g.h;
+  int npair = (n2 + 1) / 2;
+  int buf = npair * n1 > h * n2 ? npair * n1 : h * n2;
+  return sizeof(double2) * (size_t)(n1 + n2 + 2 * buf);
+}
+
+size_t fft_smem_z(const FftGrid& g) {
+  int n3 = g.ax[2].n;
+  return sizeof(double2) * (size_t)(n3 + 2 * n3 * FFT_ZCHUNK);
+}
+
+cudaError_t fft_configure(size_t smem_xy, size_t smem_z) {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_fft_xy_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fft_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fft_z<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fft_z<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+}
+
+cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx, int ncols, double* S,
+                               long long lds, const double* wt, size_t smem_xy, size_t smem_z,
+                               cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  dim3 gxy(g.ax[2].n, ncols);
+  k_fft_xy_fwd<<<gxy, FFT_THREADS, smem_xy, s>>>(g, X, ldx, S, lds);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int plane = g.ax[1].n * g.h;
+  dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+  k_fft_z<0><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ldin, int ncols, double* S,
+                                long long lds, const double* wt, const double* Add, long long ldadd,
+                                double* Y, long long ldy, size_t smem_xy, size_t smem_z,
+                                cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  dim3 gxy(g.ax[2].n, ncols);
+  k_fft_xy_fwd<<<gxy, FFT_THREADS, smem_xy, s>>>(g, In, ldin, S, lds);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int plane = g.ax[1].n * g.h;
+  dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+  k_fft_z<1><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fft_xy_inv<<<gxy, FFT_THREADS, smem_xy, s>>>(g, S, lds, Add, ldadd, Y, ldy);
+  return cudaGetLastError();
+}
+
+}  // namespace isdf

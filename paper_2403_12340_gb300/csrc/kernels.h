@@ -1,0 +1,93 @@
+// Host-side launchers of the ISDF-SMW kernels (internal C++ interface of the
+// library; the public boundary is include/isdf_smw.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isdf {
+
+// ---- k_dense.cu -----------------------------------------------------------
+cudaError_t launch_check_finite(const double* p, long long n, unsigned* status, cudaStream_t s);
+cudaError_t launch_gather_rows(const double* src, long long lds, const int* idx, int nrows, int ncols,
+                               double* dst, long long ldd, cudaStream_t s);
+// C (M x N) = (A_v B_v^T) .* (A_c B_c^T); A: M x n_e, B: N x n_e, both
+// column-major; the first n_v columns form the v part.
+cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const double* B,
+                                  long long ldb, int N, int n_v, int n_e, double* C, long long ldc,
+                                  cudaStream_t s);
+// C = alpha * op(A) op(B)^T + beta * C with op(A)(m, k), op(B)(n, k):
+// ka / kb false -> element (row, k) at p[row + ld k]; true -> p[k + ld row].
+// lower_only: M == N, only lower tiles are computed and mirrored (SYRK).
+// splits > 1 needs `partial` of splits * M * N doubles (deterministic reduce).
+// narrow: 128 x 16 tiles (N small) instead of 64 x 64.
+cudaError_t launch_gemm(const double* A, long long lda, bool ka, const double* B, long long ldb,
+                        bool kb, int M, int N, int K, double alpha, double beta, double* C,
+                        long long ldc, bool lower_only, int splits, double* partial, bool narrow,
+                        cudaStream_t s);
+// D (r x r, symmetric) = sum_{i<n_v, j<n_c} S(:, ij) S(:, ij)^T with
+// S(a, ij) = phimu(a, i) phimu(a, n_v + j) sw[i n_c + j]; phimu r x n_e.
+cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int n_v, int n_c,
+                                  const double* sw, double* D, long long ldd, int splits,
+                                  double* partial, cudaStream_t s);
+// Blocked right solve X <- X L^-T in place (L lower r x r, X M x r).
+// trsm_prep builds Bf: diagonal blocks L_JJ^-1, off-diagonal -L_JJ^-1 L_JI.
+cudaError_t launch_trsm_prep(const double* L, long long ldl, int r, double* Bf, long long ldb,
+                             cudaStream_t s);
+cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* Bf, long long ldb,
+                                 int r, cudaStream_t s);
+cudaError_t launch_transpose(const double* src, long long lds, int M, int N, double* dst,
+                             long long ldd, cudaStream_t s);
+cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s);
+cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s);
+// L (n_full x n_full column-major) from the row-major pivoted factor Lr.
+cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
+                                      double* L, long long ldl, int n_full, cudaStream_t s);
+
+// ---- k_chol.cu ------------------------------------------------------------
+struct CholWork {
+  double* d;         // n
+  double* part_val;  // 2 * max_blocks
+  int* part_idx;     // 2 * max_blocks
+  int* used;         // n
+  unsigned* bar;     // 2 (count, generation)
+  int max_blocks;
+};
+// Cholesky of the symmetric n x n matrix W (column-major, full storage):
+// P^T W P = L L^T.  pivot = 1: diagonal pivoting, stops when the largest
+// remaining diagonal is <= tol_rel * max(diag W); pivot = 0: natural order,
+// stops (ST_NOT_SPD) at a non-positive pivot.  Writes Lr (row-major n x n,
+// row index = original index), perm (n), *rank.
+cudaError_t launch_cholesky(const double* W, long long ldw, int n, int pivot, double tol_rel,
+                            double* Lr, int* perm, int* rank, unsigned* status, const CholWork& w,
+                            int num_sms, uint64_t limit_ns, cudaStream_t s);
+
+// ---- k_fft.cu -------------------------------------------------------------
+constexpr int FFT_MAX_FACTORS = 16;
+struct FftAxis {
+  int n;
+  int nf;
+  int f[FFT_MAX_FACTORS];
+  const double* tw;  // device, 2 n doubles: exp(-2 pi i t / n), t = 0..n-1
+};
+struct FftGrid {
+  FftAxis ax[3];  // x, y, z
+  int h;          // n1 / 2 + 1
+};
+// Forward real-to-complex transform of ncols real columns (each n1 n2 n3,
+// ld = ldx) into the half spectrum (h n2 n3 complex per column, ld = lds
+// doubles), multiplied by the real weight table wt (h n2 n3) if non-null.
+cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx, int ncols,
+                               double* S, long long lds, const double* wt, size_t smem_xy,
+                               size_t smem_z, cudaStream_t s);
+// Y = Add + F^-1 diag(wt) F In for ncols columns (wt includes 1 / N_r; Add
+// may be null, then Y = F^-1 diag(wt) F In); S is half-spectrum scratch
+// (ncols * lds doubles).  Y may alias Add (element-wise update).
+cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ldin, int ncols,
+                                double* S, long long lds, const double* wt, const double* Add,
+                                long long ldadd, double* Y, long long ldy, size_t smem_xy,
+                                size_t smem_z, cudaStream_t s);
+size_t fft_smem_xy(const FftGrid& g);
+size_t fft_smem_z(const FftGrid& g);
+cudaError_t fft_configure(size_t smem_xy, size_t smem_z);
+
+}  // namespace isdf
