@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput of the ISDF-SMW inverse dielectric matrix on GB300.
+
+One step = one full solve of the hot path on one synthetic system: ISDF fit
+(isdf_fit), polarizability and Coulomb operators in the ISDF basis
+(build_polarizability, static w = 0), SMW capacitance (smw_inverse) and the
+application of eps^-1 to 16 probe vectors (apply_eps_inv), all through the C
+ABI.  Workload: the 48^3 grid (N_r = 110592), N_v = 64, N_c = 448,
+N_mu = 1536 system of the synthetic generator (random combinations of the
+lowest 1024 real plane waves, Lowdin-orthonormalised; occupied energies
+uniform in [-10, -2] eV, unoccupied in [0, 20] eV; QRCP points).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the system on its
+own GPU (independent replicas, no data-path collective; barrier and
+max-over-ranks timing only), so `value` is the whole-job solves/s.
+`--impl reference` times the FP64 CPU oracle (the only reference there is:
+the paper ships no code) on this host's cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ε^-1 (ISDF-SMW) solves/s and TFLOP/s vs plain FP64 GPU path at stated error"
+WORKLOAD = "isdf48"
+N_RHS = 16
+
+# Peak of the FP64 pipe (the FP64 path has no tensor-core form on GB300):
+# 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2070 MHz maximum SM clock.  A DFMA
+# throughput microbenchmark on this machine measured 1.20 TFLOP/s at ~1.97 GHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+# DRAM traffic per launch of the dominant kernels, from one ncu capture of
+# this workload (profiles/fp64_kernels_isdf48.md); None until captured or
+# once the kernel has changed since.
+NCU_DRAM_BYTES = {
+    # k_gemm<Tile<64,64,4,4>, K-contiguous x2> (G = S^T S): read 2.829616 GB + write 0.021971 GB
+    "coulomb_syrk": 2.851587e9,
+}
+
+
+def algorithmic_flops(n_r, n_e, pairs, r, n_rhs, n_half2):
+    """Flops each phase performs by the arithmetic of the method (not counting
+    padding or wasted tile work): GEMM 2mnk, SYRK mnk... see the design doc."""
+    log2nr = math.log2(n_r)
+    return {
+        "points_chol": 2.0 * r * r * n_e + r ** 3 / 3.0,
+        "fit_gram": 2.0 * n_r * r * n_e,
+        "fit_trsm": float(n_r) * r * r,
+        "coulomb_fft": 2.5 * n_r * log2nr * r,
+        "coulomb_syrk": float(n_half2) * r * r,
+        "polar_d": float(pairs) * r * r,
+        "whiten_d": 2.0 * r ** 3,
+        "smw": (2.0 / 3.0 + 4.0 + 1.0 + 1.0) * r ** 3,
+        "apply": 4.0 * n_r * r * n_rhs + 2.0 * r * r * n_rhs + 5.0 * n_r * log2nr * n_rhs,
+    }
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [ln.strip().split(",") for ln in self.tmp.read().splitlines() if ln.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in rows:
+            row = [c.strip() for c in row]
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax = float(row[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_system():
+    import synth
+
+    return synth.workload(WORKLOAD)
+
+
+def oracle_solve(s, x):
+    import oracle
+
+    t0 = time.perf_counter()
+    res = oracle.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x)
+    return res, time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def workload_config(s, extra=None):
+    cfg = {
+        "workload": (f"{WORKLOAD}: {s.n[0]}^3 grid (N_r={s.n_r}), N_v={s.n_v}, N_c={s.n_c}, "
+                     f"N_mu={s.n_mu}, static omega=0, {N_RHS} probe vectors"),
+        "n_r": s.n_r, "n_v": s.n_v, "n_c": s.n_c, "n_mu": s.n_mu, "n_rhs": N_RHS,
+        "precision": "fp64",
+        "l2": "inputs larger than L2 (phi 453 MB, theta 1.36 GB per solve)",
+        "data": "seeded synthetic Gamma-point orbitals (stand-in for the paper's KSSOLV systems)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------- native arm
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2403_12340_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    s = make_system()
+    import synth
+
+    x = synth.probe_block(s.n_r, N_RHS)
+
+    # CPU baseline first (rank 0, one GPU): the oracle as it stands, one full solve
+    cpu = None
+    ref_y = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        res, t = oracle_solve(s, x)
+        ref_y = res.y
+        cpu = {"value": 1.0 / t, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"one full {WORKLOAD} solve (fit, B, G, K, eps^-1 on {N_RHS} probes), "
+                         f"{t:.1f} s, numpy/scipy FP64 with BLAS on all host cores"}
+
+    pkg.load_library()
+    stream = torch.cuda.current_stream(dev)
+    phi = pkg.to_fortran(s.phi, dev)
+    X = pkg.to_fortran(x, dev)
+    theta = pkg.fortran_empty(s.n_r, s.n_mu, dev)
+    Y = pkg.fortran_empty(s.n_r, N_RHS, dev)
+    ctx = pkg.IsdfSmw(s.n, s.cell, stream)
+
+    def step(phi_d, X_d, Y_d):
+        ctx.fit(phi_d, s.n_v, s.n_c, s.mu_idx, theta)
+        ctx.polarizability(s.energies, [0.0])
+        ctx.smw(0)
+        ctx.apply(X_d, 0, Y_d)
+
+    for _ in range(args.warmup):
+        step(phi, X, Y)
+    torch.cuda.synchronize(dev)
+    err = None
+    if ref_y is not None:
+        y = Y.cpu().numpy()
+        err = float(np.linalg.norm(y - ref_y) / np.linalg.norm(ref_y))
+
+    # ---- device-timed region: inputs resident in HBM
+    sampler = None
+    if rank == 0:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    pkg.isdf_set_profiling(ctx.ctx, True)
+    pkg.isdf_read_profile(ctx.ctx)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    n0 = pkg.isdf_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(phi, X, Y)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = pkg.isdf_launch_count() - n0
+    clocks = sampler.stop() if sampler else None
+    prof = pkg.isdf_read_profile(ctx.ctx)
+    pkg.isdf_set_profiling(ctx.ctx, False)
+    rank_r = ctx.rank
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / args.steps
+    value = ws * args.steps / (ms_total / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        phi_h = torch.from_numpy(np.ascontiguousarray(s.phi.T)).pin_memory()   # (N_e, N_r) = column-major phi
+        x_h = torch.from_numpy(np.ascontiguousarray(x.T)).pin_memory()
+        y_h = torch.empty((N_RHS, s.n_r), dtype=torch.float64).pin_memory()
+        phi_t = torch.empty((s.n_e, s.n_r), dtype=torch.float64, device=dev)
+        x_t = torch.empty((N_RHS, s.n_r), dtype=torch.float64, device=dev)
+        k_e2e = max(1, min(args.steps, args.e2e_steps))
+
+        def e2e_step():
+            phi_t.copy_(phi_h, non_blocking=True)
+            x_t.copy_(x_h, non_blocking=True)
+            step(phi_t.t(), x_t.t(), Y)
+            y_h.copy_(Y.t(), non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(k_e2e):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_e2e = a0.elapsed_time(a1)
+        if ws > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": ws * k_e2e / (ms_e2e / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(phi_h.numel() * 8 + x_h.numel() * 8 + s.mu_idx.nbytes + s.energies.nbytes + 8),
+               "d2h_bytes_per_step": int(y_h.numel() * 8), "steps": k_e2e}
+
+    # ---- roofline of the dominant phase (FP64 pipe bound)
+    n_half2 = 2 * (s.n[0] // 2 + 1) * s.n[1] * s.n[2]
+    fl = algorithmic_flops(s.n_r, s.n_e, s.n_v * s.n_c, rank_r, N_RHS, n_half2)
+    phases = {}
+    for name, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        per = ms / cnt
+        achieved = fl[name] / (per / 1e3) / 1e12
+        phases[name] = {"ms": round(per, 3), "tflops": round(achieved, 4),
+                        "frac_fp64": round(achieved / FP64_PEAK_TFLOPS, 3)}
+    flops_step = sum(fl.values())
+    dom = max(phases, key=lambda k: phases[k]["ms"]) if phases else None
+    roof = None
+    if dom:
+        ach = phases[dom]["tflops"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; no FP64 tensor path)",
+                "traffic": NCU_DRAM_BYTES.get(dom)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(s, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                          "rank": rank_r}),
+            "tflops": round(flops_step * value / 1e12, 4),
+            "flops_per_step": flops_step,
+            "rel_err_vs_oracle": err,
+            "roofline": roof, "phases_ms": phases,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return  # rank 0 alone runs the CPU oracle; the other ranks exit without work
+    import synth
+
+    s = make_system()
+    x = synth.probe_block(s.n_r, N_RHS)
+    for _ in range(args.warmup):
+        oracle_solve(s, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_solve(s, x)
+    t = time.perf_counter() - t0
+    value = args.steps / t
+    sample = (f"each step one full {WORKLOAD} solve (fit, B, G, K, eps^-1 on {N_RHS} probes) by the "
+              f"FP64 numpy/scipy oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(s, {"parallelism": "host cores, rank 0 only"}),
+        "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,34 @@ ISDF_API int apply_eps_inv(isdf_ctx* ctx, int omega_index, const double* X, int 
  *            r x r block (lower triangular), zero elsewhere. */
 ISDF_API int isdf_fit_factor(isdf_ctx* ctx, int* piv_out, double* L_out);
 
+/* Phase timing (CUDA events on the context stream, off by default).  The
+ * paper has no counterpart; it reports wall times only.  Phases:           */
+enum {
+  ISDF_PH_POINTS = 0,      /* C C^T of the points and its pivoted Cholesky */
+  ISDF_PH_FIT_GRAM = 1,    /* face-split Gram M C_r^T over the grid */
+  ISDF_PH_FIT_TRSM = 2,    /* triangular solve to the whitened basis */
+  ISDF_PH_FFT = 3,         /* batched r2c FFT of theta with Coulomb weights */
+  ISDF_PH_SYRK_G = 4,      /* G = S^T S over the half spectrum */
+  ISDF_PH_POLAR_D = 5,     /* -2 C Omega^-1 C^T at the pivot points */
+  ISDF_PH_WHITEN_D = 6,    /* D = L^-1 (.) L^-T */
+  ISDF_PH_SMW = 7,         /* capacitance K */
+  ISDF_PH_APPLY = 8,       /* eps^-1 X */
+  ISDF_NUM_PHASES = 9
+};
+/* on != 0 starts recording (events are recorded around every phase of every
+ * later call); on == 0 stops. */
+ISDF_API int isdf_set_profiling(isdf_ctx* ctx, int on);
+/* Synchronises the stream, then writes the summed milliseconds and the
+ * number of recorded intervals of every phase since the last read into
+ * ms[ISDF_NUM_PHASES] and counts[ISDF_NUM_PHASES] (host; either may be
+ * NULL) and clears the record. */
+ISDF_API int isdf_read_profile(isdf_ctx* ctx, double* ms, int* counts);
+/* Short name of a phase, or NULL. */
+ISDF_API const char* isdf_phase_name(int phase);
+/* Number of kernel launches issued by this library in this process so far
+ * (all contexts). */
+ISDF_API long long isdf_launch_count(void);
+
 /* Message for the last error on this context ("" if none).  With ctx NULL,
  * the last error of isdf_create on this thread. */
 ISDF_API const char* isdf_last_error(isdf_ctx* ctx);

@@ -29,7 +29,9 @@ ERRORS = {
 ISDF_PREC_FP64 = 0
 
 EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
-            "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version"]
+            "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version",
+            "isdf_set_profiling", "isdf_read_profile", "isdf_phase_name", "isdf_launch_count"]
+NUM_PHASES = 9
 
 
 class IsdfError(RuntimeError):
@@ -63,8 +65,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_last_error.restype = ctypes.c_char_p
     lib.isdf_version.argtypes = []
     lib.isdf_version.restype = ctypes.c_char_p
+    lib.isdf_set_profiling.argtypes = [P, I]
+    lib.isdf_read_profile.argtypes = [P, P, P]
+    lib.isdf_phase_name.argtypes = [I]
+    lib.isdf_phase_name.restype = ctypes.c_char_p
+    lib.isdf_launch_count.argtypes = []
+    lib.isdf_launch_count.restype = ctypes.c_longlong
     for name in ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
-                 "apply_eps_inv", "isdf_fit_factor"]:
+                 "apply_eps_inv", "isdf_fit_factor", "isdf_set_profiling", "isdf_read_profile"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -179,6 +187,23 @@ def isdf_fit_factor(ctx, n_mu: int, L_out=None):
     pl = 0 if L_out is None else _dev_ptr(L_out.reshape(-1), name="L_out")
     _check(load_library().isdf_fit_factor(ctx, piv.ctypes.data, pl), ctx)
     return piv
+
+
+def isdf_set_profiling(ctx, on: bool) -> None:
+    _check(load_library().isdf_set_profiling(ctx, 1 if on else 0), ctx)
+
+
+def isdf_read_profile(ctx):
+    """{phase name: (milliseconds, intervals)} since the last read (syncs the stream)."""
+    ms = np.zeros(NUM_PHASES, dtype=np.float64)
+    cnt = np.zeros(NUM_PHASES, dtype=np.int32)
+    _check(load_library().isdf_read_profile(ctx, ms.ctypes.data, cnt.ctypes.data), ctx)
+    lib = load_library()
+    return {lib.isdf_phase_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(NUM_PHASES)}
+
+
+def isdf_launch_count() -> int:
+    return int(load_library().isdf_launch_count())
 
 
 class IsdfSmw:

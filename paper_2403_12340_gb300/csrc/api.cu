@@ -61,6 +61,11 @@ struct isdf_ctx {
   int* d_part_idx = nullptr;
   size_t cap_used = 0;
 
+  // phase profiling
+  bool prof_on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
+
   // polarizability / SMW state
   bool polar_ready = false;
   int n_omega = 0;
@@ -69,6 +74,40 @@ struct isdf_ctx {
 };
 
 static thread_local std::string g_create_err;
+
+static cudaEvent_t take_event(isdf_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Records a start event now and an end event when it goes out of scope
+// (only while profiling is on).
+struct PhaseScope {
+  isdf_ctx* c;
+  int ph;
+  cudaEvent_t e0 = nullptr;
+  PhaseScope(isdf_ctx* ctx, int phase) : c(ctx), ph(phase) {
+    if (!c->prof_on) return;
+    e0 = take_event(c);
+    if (e0) cudaEventRecord(e0, c->stream);
+  }
+  ~PhaseScope() {
+    if (!e0) return;
+    cudaEvent_t e1 = take_event(c);
+    if (!e1) {
+      c->ev_pool.push_back(e0);
+      return;
+    }
+    cudaEventRecord(e1, c->stream);
+    c->prof_ev.push_back({ph, {e0, e1}});
+  }
+};
 
 static int fail(isdf_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -252,6 +291,11 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->spec, &c->G, &c->D, &c->K, &c->R, &c->T, &c->W1, &c->Q, &c->partial,
                     &c->tmp1, &c->tmp2, &c->tmp3, &c->sw};
   for (DevBuf* b : bufs) release(*b);
+  for (auto& pe : c->prof_ev) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->d_idx) cudaFree(c->d_idx);  // d_perm and d_perm2 point into this allocation
   if (c->d_used) cudaFree(c->d_used);
   if (c->d_part_idx) cudaFree(c->d_part_idx);
@@ -323,15 +367,19 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   CK(launch_check_finite(phi, c->n_r * n_e, c->d_status, c->stream));
   // orbitals at the points, C C^T (face-split Gram of the point block), its pivoted Cholesky
   CK(ensure(c->phimu, (size_t)n_mu * n_e));
-  CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
   CK(ensure(c->A, (size_t)n_mu * n_mu));
+  CK(ensure(c->Lc, (size_t)n_mu * n_mu));
+  {
+  PhaseScope ph(c, ISDF_PH_POINTS);
+  CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
   CK(launch_facesplit_gram(c->phimu.p, n_mu, n_mu, c->phimu.p, n_mu, n_mu, n_v, n_e, c->A.p, n_mu,
                            c->stream));
-  CK(ensure(c->Lc, (size_t)n_mu * n_mu));
   const double tol = (double)n_mu * 2.220446049250313e-16;
-  int rc = cholesky(c, c->A.p, n_mu, n_mu, 1, tol, c->Lc.p, c->d_perm);
-  if (rc != ISDF_OK) return rc;
+  int rc0 = cholesky(c, c->A.p, n_mu, n_mu, 1, tol, c->Lc.p, c->d_perm);
+  if (rc0 != ISDF_OK) return rc0;
+  }
   CK(cudaStreamSynchronize(c->stream));
+  int rc;
   rc = check_status(c, "isdf_fit");
   if (rc != ISDF_OK) return rc;
   int rank = 0;
@@ -357,8 +405,12 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     CK(ensure(c->phimu_p, (size_t)r * n_e));
     CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
     // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
-    CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
-                             c->stream));
+    {
+      PhaseScope ph(c, ISDF_PH_FIT_GRAM);
+      CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
+                               c->stream));
+    }
+    PhaseScope ph(c, ISDF_PH_FIT_TRSM);
     CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
     CK(launch_trsm_right_lt(theta, c->n_r, (int)c->n_r, c->Bf.p, r, r, c->stream));
   }
@@ -451,15 +503,25 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
         }
     }
     CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(launch_fft_forward(c->fft, c->theta, c->n_r, r, c->spec.p, lds, c->d_wsyrk, c->smem_xy, c->smem_z,
-                          c->stream));
-    CK(launch_gemm(c->spec.p, lds, true, c->spec.p, lds, true, r, r, (int)lds, 1.0, 0.0, c->G.p, r, true,
-                   sp, c->partial.p, false, c->stream));
+    {
+      PhaseScope ph(c, ISDF_PH_FFT);
+      CK(launch_fft_forward(c->fft, c->theta, c->n_r, r, c->spec.p, lds, c->d_wsyrk, c->smem_xy,
+                            c->smem_z, c->stream));
+    }
+    {
+      PhaseScope ph(c, ISDF_PH_SYRK_G);
+      CK(launch_gemm(c->spec.p, lds, true, c->spec.p, lds, true, r, r, (int)lds, 1.0, 0.0, c->G.p, r,
+                     true, sp, c->partial.p, false, c->stream));
+    }
     // D(w) = L_r^-1 (-2 C_r Omega(iw)^-1 C_r^T) L_r^-T
     for (int k = 0; k < n_omega; ++k) {
       double* Dk = c->D.p + rr * k;
-      CK(launch_polarizability(c->phimu_p.p, r, r, n_v, n_c, c->sw.p + npair * k, Dk, r, spd, c->partial.p,
-                               c->stream));
+      {
+        PhaseScope ph(c, ISDF_PH_POLAR_D);
+        CK(launch_polarizability(c->phimu_p.p, r, r, n_v, n_c, c->sw.p + npair * k, Dk, r, spd,
+                                 c->partial.p, c->stream));
+      }
+      PhaseScope ph(c, ISDF_PH_WHITEN_D);
       CK(launch_trsm_right_lt(Dk, r, r, c->Bf.p, r, r, c->stream));
       CK(launch_transpose(Dk, r, r, r, c->tmp1.p, r, c->stream));
       CK(launch_trsm_right_lt(c->tmp1.p, r, r, c->Bf.p, r, r, c->stream));
@@ -504,6 +566,7 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
     CK(ensure(c->Q, rr));
     CK(ensure(c->partial, (size_t)sp * rr));
     CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+    PhaseScope ph(c, ISDF_PH_SMW);
     // D = R R^T
     int rc = cholesky(c, c->D.p + rr * k, r, r, 0, 0.0, c->R.p, c->d_perm2);
     if (rc != ISDF_OK) return rc;
@@ -561,6 +624,7 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
   CK(ensure(c->tmp3, (size_t)nr * nc0));
   CK(ensure(c->spec, (size_t)lds * nc0));
   CK(ensure(c->partial, std::max<size_t>((size_t)sp0 * r * nc0, 1)));
+  PhaseScope ph(c, ISDF_PH_APPLY);
   for (int c0 = 0; c0 < n_rhs; c0 += chunk) {
     const int nc = std::min(chunk, n_rhs - c0);
     const double* Xc = X + nr * c0;
@@ -579,6 +643,43 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
                    false, 1, nullptr, true, c->stream));
     CK(launch_fft_convolve(c->fft, c->tmp3.p, nr, nc, c->spec.p, lds, c->d_wconv, Xc, nr, Yc, nr,
                            c->smem_xy, c->smem_z, c->stream));
+  }
+  return ISDF_OK;
+}
+
+static const char* kPhaseNames[ISDF_NUM_PHASES] = {"points_chol", "fit_gram", "fit_trsm", "coulomb_fft",
+                                                   "coulomb_syrk", "polar_d", "whiten_d", "smw", "apply"};
+
+extern "C" const char* isdf_phase_name(int phase) {
+  return (phase >= 0 && phase < ISDF_NUM_PHASES) ? kPhaseNames[phase] : nullptr;
+}
+
+extern "C" long long isdf_launch_count(void) { return launch_count(); }
+
+extern "C" int isdf_set_profiling(isdf_ctx* c, int on) {
+  if (!c) return ISDF_ERR_ARG;
+  c->prof_on = on != 0;
+  return ISDF_OK;
+}
+
+extern "C" int isdf_read_profile(isdf_ctx* c, double* ms, int* counts) {
+  if (!c) return ISDF_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  double acc[ISDF_NUM_PHASES] = {0};
+  int cnt[ISDF_NUM_PHASES] = {0};
+  for (auto& pe : c->prof_ev) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pe.second.first, pe.second.second) == cudaSuccess) {
+      acc[pe.first] += t;
+      cnt[pe.first] += 1;
+    }
+    c->ev_pool.push_back(pe.second.first);
+    c->ev_pool.push_back(pe.second.second);
+  }
+  c->prof_ev.clear();
+  for (int i = 0; i < ISDF_NUM_PHASES; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (counts) counts[i] = cnt[i];
   }
   return ISDF_OK;
 }

@@ -218,6 +218,7 @@ cudaError_t launch_cholesky(const double* W, long long ldw, int n, int pivot, do
   a.bar = GridBarrier{w.bar, w.bar + 1};
   a.limit_ns = limit_ns;
   void* args[] = {&a};
+  note_launch();
   return cudaLaunchCooperativeKernel((const void*)k_cholesky, dim3(blocks), dim3(256), args, 0, s);
 }
 

@@ -2,10 +2,16 @@
 // fit right-hand side M C^T), generic GEMM / SYRK with deterministic split-K,
 // polarizability C Omega^-1 C^T with on-the-fly pair operands, and a blocked
 // in-place right triangular solve.
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace isdf {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- utilities
 
@@ -21,6 +27,7 @@ cudaError_t launch_check_finite(const double* p, long long n, unsigned* status, 
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  note_launch();
   k_check_finite<<<(int)blocks, 256, 0, s>>>(p, n, status);
   return cudaGetLastError();
 }
@@ -37,6 +44,7 @@ cudaError_t launch_gather_rows(const double* src, long long lds, const int* idx,
                                double* dst, long long ldd, cudaStream_t s) {
   if (nrows <= 0 || ncols <= 0) return cudaSuccess;
   dim3 grid((nrows + 127) / 128, ncols);
+  note_launch();
   k_gather_rows<<<grid, 128, 0, s>>>(src, lds, idx, nrows, ncols, dst, ldd);
   return cudaGetLastError();
 }
@@ -60,6 +68,7 @@ cudaError_t launch_transpose(const double* src, long long lds, int M, int N, dou
                              long long ldd, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + 31) / 32, (N + 31) / 32), block(32, 8);
+  note_launch();
   k_transpose<<<grid, block, 0, s>>>(src, lds, M, N, dst, ldd);
   return cudaGetLastError();
 }
@@ -77,6 +86,7 @@ __global__ void k_symmetrize(double* A, long long lda, int n) {
 cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
   dim3 grid((n + 127) / 128, n);
+  note_launch();
   k_symmetrize<<<grid, 128, 0, s>>>(A, lda, n);
   return cudaGetLastError();
 }
@@ -88,6 +98,7 @@ __global__ void k_add_identity(double* A, long long lda, int n, double v) {
 
 cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  note_launch();
   k_add_identity<<<(n + 127) / 128, 128, 0, s>>>(A, lda, n, v);
   return cudaGetLastError();
 }
@@ -111,6 +122,7 @@ __global__ void k_factor_to_colmajor(const double* __restrict__ Lr, int n, const
 cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
                                       double* L, long long ldl, int n_full, cudaStream_t s) {
   dim3 grid((n_full + 127) / 128, n_full);
+  note_launch();
   k_factor_to_colmajor<<<grid, 128, 0, s>>>(Lr, n, perm, rank, L, ldl, n_full);
   return cudaGetLastError();
 }
@@ -147,6 +159,7 @@ cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const d
                                   cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + 63) / 64, (N + 63) / 64);
+  note_launch();
   k_facesplit_gram<<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v,
                                         n_e, C, ldc);
   return cudaGetLastError();
@@ -239,12 +252,14 @@ static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B
   } else {
     grid = dim3(tm, tn, splits);
   }
+  note_launch();
   k_gemm<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
                                                             use_partial ? partial : nullptr,
                                                             lower_only ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !use_partial) return e;
   dim3 rg((M + 127) / 128, N);
+  note_launch();
   k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, M, N, alpha, beta, C, ldc, lower_only ? 1 : 0,
                                      T::kBM);
   return cudaGetLastError();
@@ -327,10 +342,12 @@ cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int
   splits = (K + klen - 1) / klen;
   int tm = (r + 63) / 64;
   dim3 grid(tm * (tm + 1) / 2, 1, splits);
+  note_launch();
   k_polarizability<<<grid, 256, 0, s>>>(S, K, klen, D, ldd, splits > 1 ? partial : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   dim3 rg((r + 127) / 128, r);
+  note_launch();
   k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, r, r, 1.0, 0.0, D, ldd, 1, 64);
   return cudaGetLastError();
 }
@@ -398,10 +415,12 @@ cudaError_t launch_trsm_prep(const double* L, long long ldl, int r, double* Bf, 
                              cudaStream_t s) {
   if (r <= 0) return cudaSuccess;
   int nb = (r + TRSM_NB - 1) / TRSM_NB;
+  note_launch();
   k_diag_inverse<<<nb, TRSM_NB, 0, s>>>(L, ldl, r, Bf, ldb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nb == 1) return e;
   dim3 grid(nb - 1, nb - 1);
+  note_launch();
   k_trsm_offdiag<<<grid, 256, 0, s>>>(L, ldl, r, Bf, ldb);
   return cudaGetLastError();
 }
@@ -439,6 +458,7 @@ cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* 
   if (M <= 0 || r <= 0) return cudaSuccess;
   for (int j0 = 0; j0 < r; j0 += TRSM_NB) {
     int bs = min(TRSM_NB, r - j0);
+    note_launch();
     k_trsm_step<<<(M + 63) / 64, 256, 0, s>>>(X, ldx, M, Bf, ldb, j0, bs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

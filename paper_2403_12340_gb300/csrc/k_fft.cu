@@ -320,11 +320,13 @@ cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx,
                                cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
   dim3 gxy(g.ax[2].n, ncols);
+  note_launch();
   k_fft_xy_fwd<<<gxy, FFT_THREADS, smem_xy, s>>>(g, X, ldx, S, lds);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int plane = g.ax[1].n * g.h;
   dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+  note_launch();
   k_fft_z<0><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt);
   return cudaGetLastError();
 }
@@ -335,14 +337,17 @@ cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ld
                                 cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
   dim3 gxy(g.ax[2].n, ncols);
+  note_launch();
   k_fft_xy_fwd<<<gxy, FFT_THREADS, smem_xy, s>>>(g, In, ldin, S, lds);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int plane = g.ax[1].n * g.h;
   dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+  note_launch();
   k_fft_z<1><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launch();
   k_fft_xy_inv<<<gxy, FFT_THREADS, smem_xy, s>>>(g, S, lds, Add, ldadd, Y, ldy);
   return cudaGetLastError();
 }

@@ -6,6 +6,10 @@
 
 namespace isdf {
 
+// Count of kernel launches issued by this library (all contexts, all threads).
+void note_launch();
+long long launch_count();
+
 // ---- k_dense.cu -----------------------------------------------------------
 cudaError_t launch_check_finite(const double* p, long long n, unsigned* status, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* src, long long lds, const int* idx, int nrows, int ncols,
