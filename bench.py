@@ -28,7 +28,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -131,6 +130,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """Largest value over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, steps: int, ms_total_max: float) -> float:
+    """Whole-job solves/s: every rank solved `steps` systems in at most ms_total_max."""
+    return world_size * steps / (ms_total_max / 1e3)
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -250,14 +266,11 @@ def run_native(args):
     prof = pkg.isdf_read_profile(ctx.ctx)
     pkg.isdf_set_profiling(ctx.ctx, False)
     rank_r = ctx.rank
-    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dev)
     if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / args.steps
-    value = ws * args.steps / (ms_total / 1e3)
+    value = job_throughput(ws, args.steps, ms_total)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -286,12 +299,8 @@ def run_native(args):
             e2e_step()
         a1.record(stream)
         torch.cuda.synchronize(dev)
-        ms_e2e = a0.elapsed_time(a1)
-        if ws > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": ws * k_e2e / (ms_e2e / 1e3), "unit": "solves/s",
+        ms_e2e = max_over_ranks(a0.elapsed_time(a1), dev)
+        e2e = {"value": job_throughput(ws, k_e2e, ms_e2e), "unit": "solves/s",
                "h2d_bytes_per_step": int(phi_h.numel() * 8 + x_h.numel() * 8 + s.mu_idx.nbytes + s.energies.nbytes + 8),
                "d2h_bytes_per_step": int(y_h.numel() * 8), "steps": k_e2e}
 
