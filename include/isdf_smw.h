@@ -133,6 +133,31 @@ ISDF_API int smw_inverse(isdf_ctx* ctx, int omega_index, double* K_out);
  * Requires smw_inverse for the same omega_index. */
 ISDF_API int apply_eps_inv(isdf_ctx* ctx, int omega_index, const double* X, int n_rhs, double* Y);
 
+/* apply_eps_inv without any device allocation.  The paper has no
+ * counterpart: this entry point is for callers that must not allocate
+ * device memory when they call, such as code that runs under a fixed
+ * device-memory budget, inside a latency-critical loop where a cudaMalloc or
+ * cudaFree (which can synchronise the whole device) is not acceptable, or in
+ * a component that is not allowed to own memory.  Everything else needed
+ * (theta, K, the Coulomb tables) was allocated earlier by isdf_create,
+ * isdf_fit and build_polarizability.
+ *   Arguments and result: as apply_eps_inv (same kernels, same numbers up to
+ *   the order of the split-K sums).
+ *   Scratch: a file-scope device array of 8 MiB (2^20 doubles), one per GPU
+ *   that loads this library, held until the process exits.  A probe column
+ *   needs 2 N_mu + N_r + 2 h n2 n3 + 64 N_mu doubles (h = n1/2 + 1, each
+ *   term rounded up to 256 bytes); columns are processed as many at a time
+ *   as fit.  If one column does not fit the call returns ISDF_ERR_SHAPE and
+ *   writes nothing (apply_eps_inv has no such limit).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Every call on a device shares the one array and leaves its contents
+ *   behind; each call overwrites what it reads.  Calls whose kernels overlap
+ *   on the GPU (two streams, two threads, two contexts on the same device)
+ *   race on the array: order them on one stream. */
+ISDF_API int apply_eps_inv_noalloc(isdf_ctx* ctx, int omega_index, const double* X, int n_rhs, double* Y);
+
 /* Pivot order and Cholesky factor of the last fit.
  *   piv_out  host, n_mu int32 out (or NULL): pivot j is point mu_idx[piv[j]];
  *            the first r are the pivot points that define theta.

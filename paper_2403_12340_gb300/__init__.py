@@ -30,7 +30,8 @@ ISDF_PREC_FP64 = 0
 
 EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
             "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version",
-            "isdf_set_profiling", "isdf_read_profile", "isdf_phase_name", "isdf_launch_count"]
+            "isdf_set_profiling", "isdf_read_profile", "isdf_phase_name", "isdf_launch_count",
+            "apply_eps_inv_noalloc"]
 NUM_PHASES = 9
 
 
@@ -65,6 +66,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_last_error.restype = ctypes.c_char_p
     lib.isdf_version.argtypes = []
     lib.isdf_version.restype = ctypes.c_char_p
+    lib.apply_eps_inv_noalloc.argtypes = [P, I, P, I, P]
+    lib.apply_eps_inv_noalloc.restype = I
     lib.isdf_set_profiling.argtypes = [P, I]
     lib.isdf_read_profile.argtypes = [P, P, P]
     lib.isdf_phase_name.argtypes = [I]

@@ -683,3 +683,31 @@ extern "C" int isdf_read_profile(isdf_ctx* c, double* ms, int* counts) {
   }
   return ISDF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Read-only view of a context for the allocation-free apply (noalloc.cu).
+namespace isdf {
+
+int ctx_apply_view(isdf_ctx* c, int k, ApplyView* v) {
+  if (!c || !v) return ISDF_ERR_ARG;
+  c->err.clear();
+  if (!c->polar_ready || k < 0 || k >= c->n_omega || !c->k_ready[k])
+    return fail(c, ISDF_ERR_STATE, "apply_eps_inv_noalloc: call smw_inverse for this omega_index first");
+  v->device = c->device;
+  v->num_sms = c->num_sms;
+  v->stream = c->stream;
+  v->n_r = c->n_r;
+  v->n_half = c->n_half;
+  v->fft = c->fft;
+  v->smem_xy = c->smem_xy;
+  v->smem_z = c->smem_z;
+  v->wconv = c->d_wconv;
+  v->theta = c->theta;
+  v->rank = c->rank;
+  v->K = c->K.p + (size_t)c->rank * c->rank * k;
+  return ISDF_OK;
+}
+
+int ctx_fail(isdf_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+
+}  // namespace isdf

@@ -95,3 +95,25 @@ size_t fft_smem_z(const FftGrid& g);
 cudaError_t fft_configure(size_t smem_xy, size_t smem_z);
 
 }  // namespace isdf
+
+// ---- api.cu: read-only context view for the allocation-free apply -------
+struct isdf_ctx;
+namespace isdf {
+struct ApplyView {
+  int device;
+  int num_sms;
+  cudaStream_t stream;
+  long long n_r;
+  long long n_half;
+  FftGrid fft;
+  size_t smem_xy, smem_z;
+  const double* wconv;
+  const double* theta;
+  int rank;
+  const double* K;
+};
+// Fills *v for frequency index k, or returns an ISDF_ERR_* code with the
+// context's error message set.
+int ctx_apply_view(isdf_ctx* c, int k, ApplyView* v);
+int ctx_fail(isdf_ctx* c, int code, const char* msg);
+}  // namespace isdf
