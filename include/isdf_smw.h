@@ -158,6 +158,23 @@ ISDF_API int apply_eps_inv(isdf_ctx* ctx, int omega_index, const double* X, int 
  *   race on the array: order them on one stream. */
 ISDF_API int apply_eps_inv_noalloc(isdf_ctx* ctx, int omega_index, const double* X, int n_rhs, double* Y);
 
+/* Split-precision DGEMM on the tensor cores, the building block of the
+ * mixed-precision path (the paper has no counterpart; it is a GB300 means
+ * of running FP64 contractions at tensor-core rates).
+ *   C = alpha A B^T + beta C, A: M x K, B: N x K, C: M x N, all float64,
+ *   column-major, device pointers (lda >= M, ldb >= N, ldc >= M).
+ *   Each operand is cut into nslices (1..3) BF16 slices, x ~ x0 + x1 + x2;
+ *   the products x_i y_j with i + j < nslices are accumulated in FP32 by
+ *   tcgen05.mma and long K is summed in FP64 over K blocks.  nslices = 3
+ *   gives errors of a few 1e-7 relative to |A| |B|.
+ *   Allocates and frees its temporaries on the stream (cudaMallocAsync) and
+ *   synchronises the stream before it returns.  Errors: ISDF_ERR_SHAPE,
+ *   ISDF_ERR_ARG, ISDF_ERR_CUDA, ISDF_ERR_TIMEOUT; message from
+ *   isdf_dgemm_split_error(). */
+ISDF_API int isdf_dgemm_split(int M, int N, int K, double alpha, const double* A, long long lda, const double* B,
+                              long long ldb, double beta, double* C, long long ldc, int nslices, void* cuda_stream);
+ISDF_API const char* isdf_dgemm_split_error(void);
+
 /* Pivot order and Cholesky factor of the last fit.
  *   piv_out  host, n_mu int32 out (or NULL): pivot j is point mu_idx[piv[j]];
  *            the first r are the pivot points that define theta.

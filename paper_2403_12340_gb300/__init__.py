@@ -31,7 +31,7 @@ ISDF_PREC_FP64 = 0
 EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
             "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version",
             "isdf_set_profiling", "isdf_read_profile", "isdf_phase_name", "isdf_launch_count",
-            "apply_eps_inv_noalloc"]
+            "apply_eps_inv_noalloc", "isdf_dgemm_split", "isdf_dgemm_split_error"]
 NUM_PHASES = 9
 
 
@@ -66,6 +66,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_last_error.restype = ctypes.c_char_p
     lib.isdf_version.argtypes = []
     lib.isdf_version.restype = ctypes.c_char_p
+    LL = ctypes.c_longlong
+    lib.isdf_dgemm_split.argtypes = [I, I, I, D, P, LL, P, LL, D, P, LL, I, P]
+    lib.isdf_dgemm_split.restype = I
+    lib.isdf_dgemm_split_error.argtypes = []
+    lib.isdf_dgemm_split_error.restype = ctypes.c_char_p
     lib.apply_eps_inv_noalloc.argtypes = [P, I, P, I, P]
     lib.apply_eps_inv_noalloc.restype = I
     lib.isdf_set_profiling.argtypes = [P, I]
@@ -203,6 +208,24 @@ def isdf_read_profile(ctx):
     _check(load_library().isdf_read_profile(ctx, ms.ctypes.data, cnt.ctypes.data), ctx)
     lib = load_library()
     return {lib.isdf_phase_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(NUM_PHASES)}
+
+
+def isdf_dgemm_split(A, B, C, alpha=1.0, beta=0.0, nslices=3, stream=None) -> None:
+    """C = alpha A B^T + beta C on the tensor cores (float64 CUDA tensors,
+    column-major: A M x K, B N x K, C M x N)."""
+    import torch
+
+    M, K = A.shape
+    N = B.shape[0]
+    pa = _dev_ptr(A, M, K, "A")
+    pb = _dev_ptr(B, N, K, "B")
+    pc = _dev_ptr(C, M, N, "C")
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    lib = load_library()
+    rc = lib.isdf_dgemm_split(M, N, K, float(alpha), pa, max(M, 1), pb, max(N, 1), float(beta), pc, max(M, 1),
+                              int(nslices), ctypes.c_void_p(s))
+    if rc != ISDF_OK:
+        raise IsdfError(rc, lib.isdf_dgemm_split_error().decode())
 
 
 def isdf_launch_count() -> int:

@@ -233,6 +233,15 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, 
   C[m + ldc * n] = v;
 }
 
+cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
+                                 double* C, long long ldc, bool lower_only, int tile, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 rg((M + 127) / 128, N);
+  note_launch();
+  k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, M, N, alpha, beta, C, ldc, lower_only ? 1 : 0, tile);
+  return cudaGetLastError();
+}
+
 template <class T, bool KA, bool KB>
 static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B, long long ldb, int M,
                                  int N, int K, double alpha, double beta, double* C, long long ldc,

@@ -1,0 +1,412 @@
+// Split-precision GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// An FP64 operand x is represented by s BF16 slices, x ~ x0 + x1 + x2 with
+// x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1) (s <= 3), stored
+// K-major ("slice matrices": slice l of a R x K operand occupies rows
+// [l Rp, l Rp + R) of a row-major (s Rp) x Kp BF16 array, zero padded).
+// C = sum over slice pairs (i, j) with i + j < s of A_i B_j^T, accumulated in
+// FP32 in tensor memory; dropping the pairs with i + j >= s costs about
+// 2^-8s relative, so s = 3 gives FP32-grade products from six BF16 MMAs.
+// Long K is split across thread blocks whose FP32 partial tiles are summed
+// in FP64 (deterministically) afterwards.
+//
+// Kernel structure, one 128 x BN output tile per block (BN = 128):
+//   warp 0  : TMA producer, s A-slice and s B-slice tiles (128 B rows,
+//             128-byte swizzle) per 64-wide k chunk into a 2-4 stage ring;
+//   warp 1  : allocates TMEM, issues tcgen05.mma (one thread), commits to
+//             the ring's empty barriers and finally to the done barrier;
+//   warps 2-5: epilogue, tcgen05.ld of the FP32 accumulator rows (TMEM lane
+//             = tile row), FP64 conversion and the store.
+// NACC = 2 runs two accumulators over two K ranges (the occupied and the
+// unoccupied part of the orbital index) and multiplies them in the epilogue:
+// the face-split Gram (Phi_v Phi_v,mu^T) .* (Phi_c Phi_c,mu^T) of the ISDF fit.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace isdf {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;             // BF16 elements per 128-byte row
+constexpr int TC_THREADS = 192;
+constexpr int TC_SMEM_LIMIT = 227 * 1024;
+
+__host__ __device__ inline int tc_stage_bytes(int s, int bn) { return s * (TC_BM + bn) * TC_BK * 2; }
+
+__host__ __device__ inline int tc_stages(int s, int bn) {
+  int per = tc_stage_bytes(s, bn);
+  int st = (TC_SMEM_LIMIT - 2048) / per;
+  return st > 4 ? 4 : st;
+}
+
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(a);
+  b = __double2bfloat16(r);
+  r -= (double)__bfloat162float(b);
+  c = __double2bfloat16(r);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- slicing
+
+// Column-major FP64 source (element (row, col) at src[row + lds col]) ->
+// slices dst[(l Rp + row) Kp + kmap(col)], kmap(col) = col for col < kv,
+// col - kv + kvp otherwise (kv = kvp = 0: identity).  Transposes through a
+// 32 x 32 shared tile so that both sides are coalesced.
+__global__ void k_slice_cm(const double* __restrict__ src, long long lds, int R, int C, int kv, int kvp,
+                           __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+  __shared__ double t[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int r = r0 + threadIdx.x, c = c0 + k;
+    t[k][threadIdx.x] = (r < R && c < C) ? src[r + lds * (long long)c] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int r = r0 + k, c = c0 + threadIdx.x;
+    if (r >= R || c >= C) continue;
+    int kc = (c < kv) ? c : c - kv + kvp;
+    __nv_bfloat16 a, b, d;
+    split3(t[threadIdx.x][k], a, b, d);
+    long long base = (long long)r * Kp + kc;
+    dst[base] = a;
+    if (s > 1) dst[base + (long long)Rp * Kp] = b;
+    if (s > 2) dst[base + 2ll * Rp * Kp] = d;
+  }
+}
+
+// Row-major FP64 source (element (row, k) at src[k + lds row]) -> slices.
+__global__ void k_slice_rm(const double* __restrict__ src, long long lds, int R, int K,
+                           __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+  const int row = blockIdx.y;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    __nv_bfloat16 a, b, d;
+    split3(src[k + lds * (long long)row], a, b, d);
+    long long base = (long long)row * Kp + k;
+    dst[base] = a;
+    if (s > 1) dst[base + (long long)Rp * Kp] = b;
+    if (s > 2) dst[base + 2ll * Rp * Kp] = d;
+  }
+}
+
+cudaError_t launch_slice_colmajor(const double* src, long long lds, int R, int C, int kv, int kvp,
+                                  __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st) {
+  if (R <= 0 || C <= 0) return cudaSuccess;
+  dim3 grid((R + 31) / 32, (C + 31) / 32), block(32, 8);
+  note_launch();
+  k_slice_cm<<<grid, block, 0, st>>>(src, lds, R, C, kv, kvp, dst, Rp, Kp, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K, __nv_bfloat16* dst, int Rp,
+                                  int Kp, int s, cudaStream_t st) {
+  if (R <= 0 || K <= 0) return cudaSuccess;
+  int bx = (K + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, R);
+  note_launch();
+  k_slice_rm<<<grid, 256, 0, st>>>(src, lds, R, K, dst, Rp, Kp, s);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ the GEMM
+
+struct TcArgs {
+  int M, N;
+  int a_rows_pad, b_rows_pad;  // slice stride (rows) of the A / B slice matrices
+  int s;                       // slices per operand (1..3)
+  int k_iters;                 // Kp / 64
+  int k_per_split;             // k chunks per blockIdx.z
+  int kv_iters;                // NACC == 2: chunks of the first accumulator
+  int lower_only;              // M == N; only tiles with n-tile <= m-tile
+  int tri_b;                   // B(n, k) == 0 for k > n: skip chunks beyond the tile's last n
+  int tiles_n;                 // number of n tiles (grid.x when !lower_only)
+  double alpha, beta;
+  double* C;
+  long long ldc;
+  double* partial;             // raw FP64 partial tiles [z][M N] (column-major M x N)
+  __nv_bfloat16* zs;           // EPI_HAD_SLICES output slices (row-major)
+  int zs_rows_pad, zs_kp;
+  unsigned* status;
+};
+
+enum { EPI_F64 = 0, EPI_HAD_F64 = 1, EPI_HAD_SLICES = 2 };
+
+template <int BN, int NACC, int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb, TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  // 1024-byte aligned ring of stages, then the barriers
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = tc_stages(a.s, BN);
+  const int stage_bytes = tc_stage_bytes(a.s, BN);
+  uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
+  uint64_t* empty = full + 4;
+  uint64_t* done = empty + 4;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int mt, nt;
+  if (a.lower_only) {
+    lower_tile(blockIdx.x, mt, nt);
+  } else {
+    nt = blockIdx.x;  // n fastest: consecutive blocks share the A tile (L2 reuse)
+    mt = blockIdx.y;
+  }
+  const int m0 = mt * TC_BM, n0 = nt * BN;
+  int kb = blockIdx.z * a.k_per_split;
+  int ke = min(a.k_iters, kb + a.k_per_split);
+  if (a.tri_b) ke = min(ke, (n0 + BN + TC_BK - 1) / TC_BK);
+  const int nk = ke > kb ? ke - kb : 0;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int i = 0; i < S; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, NACC * BN);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    tc::prefetch_tmap(&tma);
+    tc::prefetch_tmap(&tmb);
+    const uint32_t bytes = (uint32_t)stage_bytes;
+    for (int it = 0; it < nk; ++it) {
+      const int st = it % S;
+      const uint32_t ph = (uint32_t)(it / S) & 1u;
+      if (!tc::mbar_wait(&empty[st], ph ^ 1u, a.status)) {
+        s_abort = 1;
+        break;
+      }
+      tc::mbar_expect_tx(&full[st], bytes);
+      uint8_t* sa = smem + st * stage_bytes;
+      uint8_t* sb = sa + a.s * TC_BM * TC_BK * 2;
+      const int kx = (kb + it) * TC_BK;
+      for (int l = 0; l < a.s; ++l) {
+        tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, l * a.a_rows_pad + m0);
+        tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, l * a.b_rows_pad + n0);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_BM, BN);
+    bool first[2] = {true, true};
+    for (int it = 0; it < nk; ++it) {
+      const int st = it % S;
+      const uint32_t ph = (uint32_t)(it / S) & 1u;
+      if (!tc::mbar_wait(&full[st], ph, a.status)) {
+        s_abort = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      const int acc = (NACC == 2 && (kb + it) >= a.kv_iters) ? 1 : 0;
+      const uint32_t d = tmem + (uint32_t)(acc * BN);
+      const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
+      const uint32_t sb = sa + (uint32_t)(a.s * TC_BM * TC_BK * 2);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        for (int i = 0; i < a.s; ++i) {
+          for (int j = 0; i + j < a.s; ++j) {
+            const uint64_t ad = tc::desc_kmajor_sw128(sa + (uint32_t)(i * TC_BM * TC_BK * 2 + kk * 32));
+            const uint64_t bd = tc::desc_kmajor_sw128(sb + (uint32_t)(j * BN * TC_BK * 2 + kk * 32));
+            tc::mma_bf16(d, ad, bd, idesc, first[acc] ? 0u : 1u);
+            first[acc] = false;
+          }
+        }
+      }
+      tc::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
+    }
+    if (nk > 0) {
+      tc::mma_commit(done);
+    } else {
+      tc::mbar_arrive(done);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: thread <-> tile row (TMEM lane)
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    const int m = m0 + row;
+    const bool ok = tc::mbar_wait(done, 0u, a.status);
+    tc::fence_after_sync();
+    const bool have = ok && nk > 0;
+    const bool have1 = NACC == 2 && have && ke > a.kv_iters;
+    const bool have0 = have && (NACC == 1 || kb < a.kv_iters);
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    for (int c = 0; c < BN; c += 16) {
+      float v0[16], v1[16];
+      if (have0) tc::tmem_ld16(lane_addr + (uint32_t)c, v0);
+      else
+        for (int i = 0; i < 16; ++i) v0[i] = 0.f;
+      if (NACC == 2) {
+        if (have1) tc::tmem_ld16(lane_addr + (uint32_t)(BN + c), v1);
+        else
+          for (int i = 0; i < 16; ++i) v1[i] = 0.f;
+      }
+      if (m >= a.M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c + i;
+        if (n >= a.N) break;
+        double v = (NACC == 2) ? (double)v0[i] * (double)v1[i] : (double)v0[i];
+        if (EPI == EPI_HAD_SLICES) {
+          __nv_bfloat16 x0, x1, x2;
+          split3(v, x0, x1, x2);
+          long long base = (long long)m * a.zs_kp + n;
+          long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
+          a.zs[base] = x0;
+          if (a.s > 1) a.zs[base + sstr] = x1;
+          if (a.s > 2) a.zs[base + 2 * sstr] = x2;
+        } else if (a.partial) {
+          a.partial[(long long)blockIdx.z * a.M * a.N + m + (long long)a.M * n] = v;
+        } else {
+          double o = a.alpha * v;
+          if (a.beta != 0.0) o += a.beta * a.C[m + a.ldc * n];
+          a.C[m + a.ldc * n] = o;
+          if (a.lower_only && mt != nt) a.C[n + a.ldc * m] = o;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, NACC * BN);
+}
+
+// ------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D map over a row-major BF16 array (rows x kp), box 64 x box_rows, 128B swizzle.
+static cudaError_t make_map(CUtensorMap* m, const __nv_bfloat16* base, int kp, long long rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || (kp % 8)) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int NACC, int EPI>
+static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, int splits, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  cudaError_t e = make_map(&ma, A.p, A.kp, (long long)A.rows_pad * a.s, TC_BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&mb, B.p, B.kp, (long long)B.rows_pad * a.s, BN);
+  if (e != cudaSuccess) return e;
+  const int smem = tc_stages(a.s, BN) * tc_stage_bytes(a.s, BN) + 1024 + 256;
+  static bool configured = false;
+  if (!configured) {
+    e = cudaFuncSetAttribute(k_tc_gemm<BN, NACC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM_LIMIT - 2048);  // leaves room for the static shared variables
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (smem > TC_SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
+  const int tm = (a.M + TC_BM - 1) / TC_BM, tn = (a.N + BN - 1) / BN;
+  a.tiles_n = tn;
+  dim3 grid = a.lower_only ? dim3(tm * (tm + 1) / 2, 1, splits) : dim3(tn, tm, splits);
+  note_launch();
+  k_tc_gemm<BN, NACC, EPI><<<grid, TC_THREADS, smem, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+static void split_k(int k_iters, int tiles, int num_sms, int max_split, int& splits, int& per) {
+  int want = (2 * num_sms + tiles - 1) / tiles;
+  if (want > max_split) want = max_split;
+  if (want > k_iters) want = k_iters;
+  if (want < 1) want = 1;
+  per = (k_iters + want - 1) / want;
+  splits = (k_iters + per - 1) / per;
+}
+
+cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta, double* C,
+                        long long ldc, bool lower_only, bool tri_b, double* partial, int max_split, int num_sms,
+                        unsigned* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (A.s != B.s || A.kp != B.kp || A.kp % TC_BK) return cudaErrorInvalidValue;
+  if (lower_only && M != N) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.a_rows_pad = A.rows_pad;
+  a.b_rows_pad = B.rows_pad;
+  a.s = A.s;
+  a.k_iters = A.kp / TC_BK;
+  a.lower_only = lower_only ? 1 : 0;
+  a.tri_b = tri_b ? 1 : 0;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.status = status;
+  const int tm = (M + TC_BM - 1) / TC_BM, tn = (N + 127) / 128;
+  const int tiles = lower_only ? tm * (tm + 1) / 2 : tm * tn;
+  int splits = 1, per = a.k_iters;
+  if (partial && !tri_b) split_k(a.k_iters, tiles, num_sms, max_split, splits, per);
+  a.k_per_split = per;
+  if (splits > 1) {
+    a.partial = partial;
+    cudaError_t e = tc_launch<128, 1, EPI_F64>(A, B, a, splits, st);
+    if (e != cudaSuccess) return e;
+    return launch_splitk_reduce(partial, splits, M, N, alpha, beta, C, ldc, lower_only, TC_BM, st);
+  }
+  return tc_launch<128, 1, EPI_F64>(A, B, a, 1, st);
+}
+
+cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, int kv_iters, double* C,
+                         long long ldc, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, unsigned* status,
+                         cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (A.s != B.s || A.kp != B.kp || A.kp % TC_BK) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.a_rows_pad = A.rows_pad;
+  a.b_rows_pad = B.rows_pad;
+  a.s = A.s;
+  a.k_iters = A.kp / TC_BK;
+  a.k_per_split = a.k_iters;
+  a.kv_iters = kv_iters;
+  a.alpha = 1.0;
+  a.C = C;
+  a.ldc = ldc;
+  a.zs = zs;
+  a.zs_rows_pad = zs_rows_pad;
+  a.zs_kp = zs_kp;
+  a.status = status;
+  if (zs) return tc_launch<128, 2, EPI_HAD_SLICES>(A, B, a, 1, st);
+  return tc_launch<128, 2, EPI_HAD_F64>(A, B, a, 1, st);
+}
+
+}  // namespace isdf

@@ -1,6 +1,7 @@
 // Host-side launchers of the ISDF-SMW kernels (internal C++ interface of the
 // library; the public boundary is include/isdf_smw.h).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,6 +47,11 @@ cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaS
 // L (n_full x n_full column-major) from the row-major pivoted factor Lr.
 cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
                                       double* L, long long ldl, int n_full, cudaStream_t s);
+
+// C = alpha * sum_z partial[z] + beta * C (partials column-major M x N);
+// lower_only: tiles above the diagonal (tile size `tile`) are read mirrored.
+cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
+                                 double* C, long long ldc, bool lower_only, int tile, cudaStream_t s);
 
 // ---- k_chol.cu ------------------------------------------------------------
 struct CholWork {
@@ -93,6 +99,37 @@ cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ld
 size_t fft_smem_xy(const FftGrid& g);
 size_t fft_smem_z(const FftGrid& g);
 cudaError_t fft_configure(size_t smem_xy, size_t smem_z);
+
+// ---- k_tc_gemm.cu: split-precision GEMMs on tcgen05 -----------------------
+// A "slice matrix": s BF16 slices of an R x K FP64 operand, row-major with
+// K contiguous; slice l occupies rows [l rows_pad, l rows_pad + R) of a
+// (s rows_pad) x kp array.  rows_pad % 128 == 0, kp % 64 == 0, zero padded.
+struct TcOperand {
+  const __nv_bfloat16* p;
+  int rows_pad;
+  int kp;
+  int s;
+};
+// slices of a column-major FP64 matrix (R x C, element (r, c) at src[r + lds c]);
+// columns c >= kv are shifted to c - kv + kvp (kv = kvp = 0: no shift)
+cudaError_t launch_slice_colmajor(const double* src, long long lds, int R, int C, int kv, int kvp,
+                                  __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st);
+// slices of a row-major FP64 matrix (R x K, element (r, k) at src[k + lds r])
+cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K, __nv_bfloat16* dst, int Rp,
+                                  int Kp, int s, cudaStream_t st);
+// C (M x N, column-major FP64) = alpha sum_{i+j<s} A_i B_j^T + beta C.  With
+// `partial` (max_split * M * N doubles) long K is split over blocks and
+// reduced in FP64.  lower_only: SYRK-style (M == N, mirrored).  tri_b: B is
+// lower triangular as B(n, k), chunks past the tile's last n are skipped.
+cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
+                        double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
+                        int num_sms, unsigned* status, cudaStream_t st);
+// Face-split Gram (A_v B_v^T) .* (A_c B_c^T): chunks [0, kv_iters) feed the
+// first accumulator, the rest the second.  Output FP64 column-major (C) or,
+// with zs non-null, BF16 slices (row-major M x N, zs_rows_pad x zs_kp).
+cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, int kv_iters, double* C,
+                         long long ldc, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, unsigned* status,
+                         cudaStream_t st);
 
 }  // namespace isdf
 
