@@ -75,7 +75,15 @@ enum {
   ISDF_ERR_NOMEM = -10      /* workspace allocation failed */
 };
 
-enum { ISDF_PREC_FP64 = 0 };
+/* Precision of the path.  FP64: every step in float64 on the FP64 pipe.
+ * MIXED: every large contraction (face-split Gram, the triangular solve of
+ * the fit as a GEMM with the FP64 inverse factor, G, D and the capacitance
+ * products, theta^T X and theta T) on the tensor cores with operands cut into
+ * three BF16 slices and FP32 accumulation, the Coulomb transform of theta
+ * in FP32; the Cholesky factorisations, triangular inverses and the FFT of
+ * the probe block stay in FP64.  Results agree with FP64 to about 1e-6
+ * relative on well-conditioned systems. */
+enum { ISDF_PREC_FP64 = 0, ISDF_PREC_MIXED = 1 };
 
 /* Create a context for one periodic grid n1 x n2 x n3 with cell lengths
  * L1, L2, L3 (Bohr).  cuda_stream is a cudaStream_t (NULL = legacy default
@@ -96,7 +104,7 @@ ISDF_API int isdf_destroy(isdf_ctx* ctx);
  *   n_v,n_c  numbers of occupied / unoccupied orbitals (>= 1 each).
  *   mu_idx   host, n_mu int64 grid indices in [0, N_r), distinct.
  *   n_mu     number of interpolation points, 1 <= n_mu <= N_r.
- *   prec     ISDF_PREC_FP64.
+ *   prec     ISDF_PREC_FP64 or ISDF_PREC_MIXED; later calls use the same mode.
  *   theta    device, N_r x n_mu float64 out (ld = N_r); must not alias phi.
  *            Later calls read it: keep it until the next fit.
  *   rank_out host int out (may be NULL): numerical rank r of C C^T.  The

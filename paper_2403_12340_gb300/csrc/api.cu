@@ -14,100 +14,17 @@
 
 using namespace isdf;
 
-namespace {
+#include "ctx.h"
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bound on any device-side wait
-constexpr int kMaxGrid = 512;
-
-struct DevBuf {
-  double* p = nullptr;
-  size_t cap = 0;  // doubles
-};
-
-}  // namespace
-
-struct isdf_ctx {
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  int n[3] = {0, 0, 0};
-  double L[3] = {0, 0, 0};
-  long long n_r = 0;
-  double dv = 0;
-  FftGrid fft{};
-  long long n_half = 0;  // h n2 n3 complex entries of a half spectrum
-  size_t smem_xy = 0, smem_z = 0;
-  double* d_tables = nullptr;  // twiddles x, y, z | sqrt SYRK weights | convolution weights
-  const double* d_wsyrk = nullptr;
-  const double* d_wconv = nullptr;
-  unsigned* d_status = nullptr;
-  unsigned* d_bar = nullptr;
-  int* d_ints = nullptr;  // [0] rank
-  std::string err;
-
-  // fit state
-  bool fitted = false;
-  const double* phi = nullptr;
-  double* theta = nullptr;
-  int n_v = 0, n_c = 0, n_mu = 0, rank = 0;
-  std::vector<int> perm;  // host copy, n_mu
-  int* d_idx = nullptr;
-  int* d_perm = nullptr;   // pivot order of the fit
-  int* d_perm2 = nullptr;  // scratch order of the unpivoted factorisations
-  size_t cap_idx = 0;
-  DevBuf phimu, phimu_p, A, Lr, Lc, Bf, chol_d, chol_part, spec, G, D, K, R, T, W1, Q, partial, tmp1,
-      tmp2, tmp3, sw;
-  int* d_used = nullptr;
-  int* d_part_idx = nullptr;
-  size_t cap_used = 0;
-
-  // phase profiling
-  bool prof_on = false;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
-  std::vector<cudaEvent_t> ev_pool;
-
-  // polarizability / SMW state
-  bool polar_ready = false;
-  int n_omega = 0;
-  std::vector<double> omega;
-  std::vector<char> k_ready;
-};
+using isdf::DevBuf;
+using isdf::kMaxGrid;
+using isdf::kWaitLimitNs;
+using isdf::ensure;
+using isdf::release;
 
 static thread_local std::string g_create_err;
 
-static cudaEvent_t take_event(isdf_ctx* c) {
-  if (!c->ev_pool.empty()) {
-    cudaEvent_t e = c->ev_pool.back();
-    c->ev_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  return e;
-}
-
-// Records a start event now and an end event when it goes out of scope
-// (only while profiling is on).
-struct PhaseScope {
-  isdf_ctx* c;
-  int ph;
-  cudaEvent_t e0 = nullptr;
-  PhaseScope(isdf_ctx* ctx, int phase) : c(ctx), ph(phase) {
-    if (!c->prof_on) return;
-    e0 = take_event(c);
-    if (e0) cudaEventRecord(e0, c->stream);
-  }
-  ~PhaseScope() {
-    if (!e0) return;
-    cudaEvent_t e1 = take_event(c);
-    if (!e1) {
-      c->ev_pool.push_back(e0);
-      return;
-    }
-    cudaEventRecord(e1, c->stream);
-    c->prof_ev.push_back({ph, {e0, e1}});
-  }
-};
+using PhaseScope = isdf::PhaseTimer;
 
 static int fail(isdf_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -125,7 +42,7 @@ static int cuda_fail(isdf_ctx* c, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);   \
   } while (0)
 
-static cudaError_t ensure(DevBuf& b, size_t n) {
+cudaError_t isdf::ensure(DevBuf& b, size_t n) {
   if (n <= b.cap) return cudaSuccess;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -135,7 +52,7 @@ static cudaError_t ensure(DevBuf& b, size_t n) {
   return e;
 }
 
-static void release(DevBuf& b) {
+void isdf::release(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;
@@ -289,7 +206,9 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
   cudaStreamSynchronize(c->stream);
   DevBuf* bufs[] = {&c->phimu, &c->phimu_p, &c->A, &c->Lr, &c->Lc, &c->Bf, &c->chol_d, &c->chol_part,
                     &c->spec, &c->G, &c->D, &c->K, &c->R, &c->T, &c->W1, &c->Q, &c->partial,
-                    &c->tmp1, &c->tmp2, &c->tmp3, &c->sw};
+                    &c->tmp1, &c->tmp2, &c->tmp3, &c->sw, &c->m_phis, &c->m_phimus, &c->m_zs, &c->m_linv,
+                    &c->m_linvs, &c->m_work, &c->m_thetas_t, &c->m_s32, &c->m_ss, &c->m_pairs, &c->m_sa,
+                    &c->m_sb, &c->m_xs};
   for (DevBuf* b : bufs) release(*b);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
@@ -341,7 +260,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   c->fitted = false;
   c->polar_ready = false;
   if (!phi || !theta || !mu_idx) return fail(c, ISDF_ERR_ARG, "isdf_fit: null pointer argument");
-  if (prec != ISDF_PREC_FP64) return fail(c, ISDF_ERR_ARG, "isdf_fit: unknown precision mode");
+  if (prec != ISDF_PREC_FP64 && prec != ISDF_PREC_MIXED)
+    return fail(c, ISDF_ERR_ARG, "isdf_fit: unknown precision mode");
   if (n_v < 1 || n_c < 1) return fail(c, ISDF_ERR_SHAPE, "isdf_fit: n_v and n_c must be >= 1");
   if (n_mu < 1 || (long long)n_mu > c->n_r)
     return fail(c, ISDF_ERR_SHAPE, "isdf_fit: n_mu must be in [1, N_r]");
@@ -404,20 +324,26 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     // orbitals at the pivot points, in pivot order
     CK(ensure(c->phimu_p, (size_t)r * n_e));
     CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
-    // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
-    {
-      PhaseScope ph(c, ISDF_PH_FIT_GRAM);
-      CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
-                               c->stream));
+    if (prec == ISDF_PREC_MIXED) {
+      CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+      CK(isdf::mixed_fit(c, phi, theta, n_v, n_c, r));
+    } else {
+      // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
+      {
+        PhaseScope ph(c, ISDF_PH_FIT_GRAM);
+        CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
+                                 c->stream));
+      }
+      PhaseScope ph(c, ISDF_PH_FIT_TRSM);
+      CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+      CK(launch_trsm_right_lt(theta, c->n_r, (int)c->n_r, c->Bf.p, r, r, c->stream));
     }
-    PhaseScope ph(c, ISDF_PH_FIT_TRSM);
-    CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
-    CK(launch_trsm_right_lt(theta, c->n_r, (int)c->n_r, c->Bf.p, r, r, c->stream));
   }
   if (r < n_mu)
     CK(cudaMemsetAsync(theta + c->n_r * r, 0, (size_t)c->n_r * (n_mu - r) * sizeof(double), c->stream));
   c->phi = phi;
   c->theta = theta;
+  c->prec = prec;
   c->n_v = n_v;
   c->n_c = n_c;
   c->n_mu = n_mu;
@@ -503,6 +429,9 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
         }
     }
     CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (c->prec == ISDF_PREC_MIXED) {
+      CK(isdf::mixed_polar(c, c->sw.p, n_omega));
+    } else {
     {
       PhaseScope ph(c, ISDF_PH_FFT);
       CK(launch_fft_forward(c->fft, c->theta, c->n_r, r, c->spec.p, lds, c->d_wsyrk, c->smem_xy,
@@ -527,6 +456,7 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
       CK(launch_trsm_right_lt(c->tmp1.p, r, r, c->Bf.p, r, r, c->stream));
       CK(launch_symmetrize(c->tmp1.p, r, r, c->stream));
       CK(cudaMemcpyAsync(Dk, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
     }
   }
   if (G_out) {
@@ -571,16 +501,23 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
     int rc = cholesky(c, c->D.p + rr * k, r, r, 0, 0.0, c->R.p, c->d_perm2);
     if (rc != ISDF_OK) return rc;
     // T = I + R^T G R
-    CK(launch_gemm(c->G.p, r, false, c->R.p, r, true, r, r, r, 1.0, 0.0, c->W1.p, r, false, 1, nullptr,
-                   false, c->stream));
     CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
     CK(launch_add_identity(c->T.p, r, r, 1.0, c->stream));
-    CK(launch_gemm(c->R.p, r, true, c->W1.p, r, true, r, r, r, 1.0, 1.0, c->T.p, r, false, 1, nullptr,
-                   false, c->stream));
-    CK(launch_symmetrize(c->T.p, r, r, c->stream));
+    if (c->prec == ISDF_PREC_MIXED) {
+      CK(isdf::mixed_smw_products_T(c));
+    } else {
+      CK(launch_gemm(c->G.p, r, false, c->R.p, r, true, r, r, r, 1.0, 0.0, c->W1.p, r, false, 1, nullptr,
+                     false, c->stream));
+      CK(launch_gemm(c->R.p, r, true, c->W1.p, r, true, r, r, r, 1.0, 1.0, c->T.p, r, false, 1, nullptr,
+                     false, c->stream));
+      CK(launch_symmetrize(c->T.p, r, r, c->stream));
+    }
     // T = U U^T; Q = R U^-T; K = -Q Q^T
     rc = cholesky(c, c->T.p, r, r, 0, 0.0, c->W1.p, c->d_perm2);
     if (rc != ISDF_OK) return rc;
+    if (c->prec == ISDF_PREC_MIXED) {
+      CK(isdf::mixed_smw_products_K(c, Kk));
+    } else {
     CK(launch_trsm_prep(c->W1.p, r, r, c->Bf.p + 0, r, c->stream));
     CK(cudaMemcpyAsync(c->Q.p, c->R.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CK(launch_trsm_right_lt(c->Q.p, r, r, c->Bf.p, r, r, c->stream));
@@ -588,6 +525,7 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
                    false, c->stream));
     // restore the fit's TRSM table (Bf held L_r^-1 blocks for D(w) of later calls)
     CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+    }
   }
   if (K_out) {
     int rc = copy_padded(c, K_out, Kk, r, m);
@@ -631,6 +569,10 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
     double* Yc = Y + nr * c0;
     if (r == 0) {
       if (Yc != Xc) CK(cudaMemcpyAsync(Yc, Xc, (size_t)nr * nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      continue;
+    }
+    if (c->prec == ISDF_PREC_MIXED) {
+      CK(isdf::mixed_apply_chunk(c, Kk, Xc, Yc, nc));
       continue;
     }
     // T1 = theta^T X (split over the grid), T2 = K T1, T3 = theta T2, Y = X + V T3

@@ -1,0 +1,126 @@
+// Internal: the ISDF-SMW context (opaque in the public header).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kernels.h"
+
+namespace isdf {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bound on any device-side wait
+constexpr int kMaxGrid = 512;
+
+struct DevBuf {
+  double* p = nullptr;
+  size_t cap = 0;  // doubles
+  __nv_bfloat16* bf() const { return reinterpret_cast<__nv_bfloat16*>(p); }
+};
+
+cudaError_t ensure(DevBuf& b, size_t n_doubles);
+inline cudaError_t ensure_bf16(DevBuf& b, size_t n_elems) { return ensure(b, (n_elems + 3) / 4); }
+void release(DevBuf& b);
+
+}  // namespace isdf
+
+using isdf::DevBuf;
+using isdf::FftGrid;
+
+struct isdf_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  int n[3] = {0, 0, 0};
+  double L[3] = {0, 0, 0};
+  long long n_r = 0;
+  double dv = 0;
+  FftGrid fft{};
+  long long n_half = 0;  // h n2 n3 complex entries of a half spectrum
+  size_t smem_xy = 0, smem_z = 0;
+  double* d_tables = nullptr;  // twiddles x, y, z | sqrt SYRK weights | convolution weights
+  const double* d_wsyrk = nullptr;
+  const double* d_wconv = nullptr;
+  unsigned* d_status = nullptr;
+  unsigned* d_bar = nullptr;
+  int* d_ints = nullptr;  // [0] rank
+  std::string err;
+
+  // fit state
+  bool fitted = false;
+  const double* phi = nullptr;
+  double* theta = nullptr;
+  int n_v = 0, n_c = 0, n_mu = 0, rank = 0;
+  std::vector<int> perm;  // host copy, n_mu
+  int* d_idx = nullptr;
+  int* d_perm = nullptr;   // pivot order of the fit
+  int* d_perm2 = nullptr;  // scratch order of the unpivoted factorisations
+  size_t cap_idx = 0;
+  DevBuf phimu, phimu_p, A, Lr, Lc, Bf, chol_d, chol_part, spec, G, D, K, R, T, W1, Q, partial, tmp1,
+      tmp2, tmp3, sw;
+  int* d_used = nullptr;
+  int* d_part_idx = nullptr;
+  size_t cap_used = 0;
+
+  // mixed precision (ISDF_PREC_MIXED): BF16 slice matrices and FP64 helpers
+  int prec = 0;
+  DevBuf m_phis, m_phimus, m_zs, m_linv, m_linvs, m_work, m_thetas_t, m_s32, m_ss, m_pairs, m_sa, m_sb, m_xs;
+
+  // phase profiling
+  bool prof_on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
+
+  // polarizability / SMW state
+  bool polar_ready = false;
+  int n_omega = 0;
+  std::vector<double> omega;
+  std::vector<char> k_ready;
+};
+
+namespace isdf {
+
+inline cudaEvent_t take_event(isdf_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Records a start event now and an end event when it goes out of scope
+// (only while profiling is on).
+struct PhaseTimer {
+  isdf_ctx* c;
+  int ph;
+  cudaEvent_t e0 = nullptr;
+  PhaseTimer(isdf_ctx* ctx, int phase) : c(ctx), ph(phase) {
+    if (!c->prof_on) return;
+    e0 = take_event(c);
+    if (e0) cudaEventRecord(e0, c->stream);
+  }
+  ~PhaseTimer() {
+    if (!e0) return;
+    cudaEvent_t e1 = take_event(c);
+    if (!e1) {
+      c->ev_pool.push_back(e0);
+      return;
+    }
+    cudaEventRecord(e1, c->stream);
+    c->prof_ev.push_back({ph, {e0, e1}});
+  }
+};
+
+// mixed.cu
+cudaError_t mixed_fit(isdf_ctx* c, const double* phi, double* theta, int n_v, int n_c, int r);
+cudaError_t mixed_polar(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_smw_products_T(isdf_ctx* c);
+cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk);
+cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc);
+
+}  // namespace isdf

@@ -476,3 +476,38 @@ cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* 
 }
 
 }  // namespace isdf
+
+namespace isdf {
+
+// Inverse of a lower-triangular r x r matrix L, in FP64: the 64 x 64
+// diagonal blocks are inverted directly (k_diag_inverse), then blocks are
+// merged pairwise, [[A, 0], [C, B]]^-1 = [[A^-1, 0], [-B^-1 C A^-1, B^-1]],
+// for block sizes 64, 128, 256, ... (two GEMMs per merge, all merges of one
+// level independent).  work: (r/2 + 64)^2 doubles.
+cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li, long long ldi, double* work,
+                               cudaStream_t s) {
+  if (r <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, r * sizeof(double), r, s);
+  if (e != cudaSuccess) return e;
+  int nb = (r + TRSM_NB - 1) / TRSM_NB;
+  note_launch();
+  k_diag_inverse<<<nb, TRSM_NB, 0, s>>>(L, ldl, r, Li, ldi);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int bs = TRSM_NB; bs < r; bs *= 2) {
+    for (int b = 0; b + bs < r; b += 2 * bs) {
+      const int sa = bs;                       // size of the inverted upper-left block A
+      const int sb = min(bs, r - (b + bs));    // size of the lower-right block B
+      // X (sb x sa) = C A^-1 with C = L[b+bs .., b ..]
+      e = launch_gemm(L + (b + bs) + ldl * (long long)b, ldl, false, Li + b + ldi * (long long)b, ldi, true, sb,
+                      sa, sa, 1.0, 0.0, work, sb, false, 1, nullptr, false, s);
+      if (e != cudaSuccess) return e;
+      // Li[B, A] = -B^-1 X
+      e = launch_gemm(Li + (b + bs) + ldi * (long long)(b + bs), ldi, false, work, sb, true, sb, sa, sb, -1.0, 0.0,
+                      Li + (b + bs) + ldi * (long long)b, ldi, false, 1, nullptr, false, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace isdf

@@ -15,6 +15,8 @@
 // a direct DFT for 7, 11, 13), ping-ponging between two shared buffers.
 // Twiddles exp(-2 pi i t / n) come from a per-axis table computed on the
 // host in float64.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -23,66 +25,98 @@ namespace isdf {
 constexpr int FFT_THREADS = 256;
 constexpr int FFT_ZCHUNK = 32;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+// Complex arithmetic for both precisions (double2 for the FP64 path, float2
+// for the mixed path); twiddle tables are float64 and are rounded on load.
+template <class C>
+struct Real;
+template <>
+struct Real<double2> {
+  using T = double;
+};
+template <>
+struct Real<float2> {
+  using T = float;
+};
+template <class C>
+__device__ __forceinline__ C mk(typename Real<C>::T x, typename Real<C>::T y) {
+  C c;
+  c.x = x;
+  c.y = y;
+  return c;
 }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <class C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+template <class C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  return mk<C>(a.x + b.x, a.y + b.y);
+}
+template <class C>
+__device__ __forceinline__ C csub(C a, C b) {
+  return mk<C>(a.x - b.x, a.y - b.y);
+}
+template <class C>
+__device__ __forceinline__ C from_tw(const double2 w) {
+  return mk<C>((typename Real<C>::T)w.x, (typename Real<C>::T)w.y);
+}
 
 // twiddle exp(DIR 2 pi i t / n) with DIR = -1 forward, +1 inverse
-template <int DIR>
-__device__ __forceinline__ double2 twid(const double2* tw, int t) {
-  double2 w = tw[t];
+template <int DIR, class C>
+__device__ __forceinline__ C twid(const C* tw, int t) {
+  C w = tw[t];
   if (DIR > 0) w.y = -w.y;
   return w;
 }
 
-template <int DIR>
-__device__ __forceinline__ void bfly2(double2* v) {
-  double2 a = v[0], b = v[1];
+template <int DIR, class C>
+__device__ __forceinline__ void bfly2(C* v) {
+  C a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
 }
 
-template <int DIR>
-__device__ __forceinline__ void bfly3(double2* v) {
-  const double s3 = 0.86602540378443864676;  // sqrt(3) / 2
-  double2 t1 = cadd(v[1], v[2]);
-  double2 t2 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
-  double2 m = make_double2(s3 * (v[1].x - v[2].x), s3 * (v[1].y - v[2].y));
+template <int DIR, class C>
+__device__ __forceinline__ void bfly3(C* v) {
+  using T = typename Real<C>::T;
+  const T s3 = (T)0.86602540378443864676;  // sqrt(3) / 2
+  const T h = (T)0.5;
+  C t1 = cadd(v[1], v[2]);
+  C t2 = mk<C>(v[0].x - h * t1.x, v[0].y - h * t1.y);
+  C m = mk<C>(s3 * (v[1].x - v[2].x), s3 * (v[1].y - v[2].y));
   v[0] = cadd(v[0], t1);
   if (DIR < 0) {  // X1 = t2 - i m, X2 = t2 + i m
-    v[1] = make_double2(t2.x + m.y, t2.y - m.x);
-    v[2] = make_double2(t2.x - m.y, t2.y + m.x);
+    v[1] = mk<C>(t2.x + m.y, t2.y - m.x);
+    v[2] = mk<C>(t2.x - m.y, t2.y + m.x);
   } else {
-    v[1] = make_double2(t2.x - m.y, t2.y + m.x);
-    v[2] = make_double2(t2.x + m.y, t2.y - m.x);
+    v[1] = mk<C>(t2.x - m.y, t2.y + m.x);
+    v[2] = mk<C>(t2.x + m.y, t2.y - m.x);
   }
 }
 
-template <int DIR>
-__device__ __forceinline__ void bfly4(double2* v) {
-  double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-  double2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+template <int DIR, class C>
+__device__ __forceinline__ void bfly4(C* v) {
+  C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  C c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
   v[0] = cadd(a, c);
   v[2] = csub(a, c);
   if (DIR < 0) {  // X1 = b - i d, X3 = b + i d
-    v[1] = make_double2(b.x + d.y, b.y - d.x);
-    v[3] = make_double2(b.x - d.y, b.y + d.x);
+    v[1] = mk<C>(b.x + d.y, b.y - d.x);
+    v[3] = mk<C>(b.x - d.y, b.y + d.x);
   } else {
-    v[1] = make_double2(b.x - d.y, b.y + d.x);
-    v[3] = make_double2(b.x + d.y, b.y - d.x);
+    v[1] = mk<C>(b.x - d.y, b.y + d.x);
+    v[3] = mk<C>(b.x + d.y, b.y - d.x);
   }
 }
 
 // direct R-point DFT with table twiddles (w_R^m = tw[(m mod R) n / R])
-template <int R, int DIR>
-__device__ __forceinline__ void bfly_direct(double2* v, const double2* tw, int n) {
-  double2 out[R];
+template <int R, int DIR, class C>
+__device__ __forceinline__ void bfly_direct(C* v, const C* tw, int n) {
+  C out[R];
   const int step = n / R;
 #pragma unroll
   for (int a = 0; a < R; ++a) {
-    double2 acc = v[0];
+    C acc = v[0];
 #pragma unroll
     for (int b = 1; b < R; ++b) acc = cadd(acc, cmul(v[b], twid<DIR>(tw, ((a * b) % R) * step)));
     out[a] = acc;
@@ -91,8 +125,8 @@ __device__ __forceinline__ void bfly_direct(double2* v, const double2* tw, int n
   for (int a = 0; a < R; ++a) v[a] = out[a];
 }
 
-template <int R, int DIR>
-__device__ __forceinline__ void bfly(double2* v, const double2* tw, int n) {
+template <int R, int DIR, class C>
+__device__ __forceinline__ void bfly(C* v, const C* tw, int n) {
   if constexpr (R == 2) bfly2<DIR>(v);
   else if constexpr (R == 3) bfly3<DIR>(v);
   else if constexpr (R == 4) bfly4<DIR>(v);
@@ -101,15 +135,15 @@ __device__ __forceinline__ void bfly(double2* v, const double2* tw, int n) {
 
 // One Stockham pass of radix R over `nlines` lines of length n (element e of
 // line l at buf[l * sl + e * se]); Ns = product of the radices done so far.
-template <int R, int DIR>
-__device__ void stockham_pass(const double2* __restrict__ src, double2* __restrict__ dst, int n, int Ns,
-                              int nlines, int se, int sl, const double2* tw) {
+template <int R, int DIR, class C>
+__device__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int n, int Ns, int nlines, int se,
+                              int sl, const C* tw) {
   const int nR = n / R;
   const int tstep = n / (Ns * R);
   for (int idx = threadIdx.x; idx < nlines * nR; idx += blockDim.x) {
     int line = idx / nR, j = idx - line * nR;
     int k = j % Ns;
-    double2 v[R];
+    C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[line * sl + (j + r * nR) * se];
     if (Ns > 1) {
@@ -124,9 +158,8 @@ __device__ void stockham_pass(const double2* __restrict__ src, double2* __restri
 }
 
 // 1-D transforms of all lines; returns the buffer holding the result.
-template <int DIR>
-__device__ double2* fft_lines(double2* src, double2* dst, const FftAxis& ax, const double2* tw, int nlines,
-                              int se, int sl) {
+template <int DIR, class C>
+__device__ C* fft_lines(C* src, C* dst, const FftAxis& ax, const C* tw, int nlines, int se, int sl) {
   int Ns = 1;
   const int n = ax.n;
   for (int f = 0; f < ax.nf; ++f) {
@@ -141,7 +174,7 @@ __device__ double2* fft_lines(double2* src, double2* dst, const FftAxis& ax, con
       default: stockham_pass<13, DIR>(src, dst, n, Ns, nlines, se, sl, tw); break;
     }
     __syncthreads();
-    double2* t = src;
+    C* t = src;
     src = dst;
     dst = t;
     Ns *= R;
@@ -163,44 +196,50 @@ __device__ __forceinline__ XYShape xy_shape(const FftGrid& g) {
   return s;
 }
 
-// Forward xy: real plane -> half spectrum plane P[ky][kx] (h x n2).
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd(FftGrid g, const double* __restrict__ X,
-                                                            long long ldx, double* __restrict__ S,
-                                                            long long lds) {
-  extern __shared__ double2 sm[];
+// Forward xy: real plane -> half spectrum plane P[ky][kx] (h x n2).  The
+// input is float64; the transform runs in the precision of C; the output
+// plane is written as C (interleaved re, im) at S + lds * col (in units of
+// Real<C>::T).
+template <class C>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd(FftGrid g, const double* __restrict__ X, long long ldx,
+                                                            typename Real<C>::T* __restrict__ S, long long lds) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
+  using T = typename Real<C>::T;
   const XYShape sh = xy_shape(g);
-  double2* twx = sm;
-  double2* twy = twx + sh.n1;
-  double2* b0 = twy + sh.n2;
-  double2* b1 = b0 + sh.buf;
+  C* twx = sm;
+  C* twy = twx + sh.n1;
+  C* b0 = twy + sh.n2;
+  C* b1 = b0 + sh.buf;
   const int z = blockIdx.x, col = blockIdx.y;
-  for (int t = threadIdx.x; t < sh.n1; t += blockDim.x) twx[t] = ((const double2*)g.ax[0].tw)[t];
-  for (int t = threadIdx.x; t < sh.n2; t += blockDim.x) twy[t] = ((const double2*)g.ax[1].tw)[t];
+  for (int t = threadIdx.x; t < sh.n1; t += blockDim.x) twx[t] = from_tw<C>(((const double2*)g.ax[0].tw)[t]);
+  for (int t = threadIdx.x; t < sh.n2; t += blockDim.x) twy[t] = from_tw<C>(((const double2*)g.ax[1].tw)[t]);
   const double* plane = X + ldx * (long long)col + (long long)z * sh.n1 * sh.n2;
   for (int idx = threadIdx.x; idx < sh.npair * sh.n1; idx += blockDim.x) {
     int t = idx / sh.n1, x = idx - t * sh.n1;
     int y0 = 2 * t, y1 = 2 * t + 1;
     double re = plane[x + sh.n1 * y0];
     double im = y1 < sh.n2 ? plane[x + sh.n1 * y1] : 0.0;
-    b0[t * sh.n1 + x] = make_double2(re, im);
+    b0[t * sh.n1 + x] = mk<C>((T)re, (T)im);
   }
   __syncthreads();
-  double2* res = fft_lines<-1>(b0, b1, g.ax[0], twx, sh.npair, 1, sh.n1);
-  double2* P = (res == b0) ? b1 : b0;
+  C* res = fft_lines<-1>(b0, b1, g.ax[0], twx, sh.npair, 1, sh.n1);
+  C* P = (res == b0) ? b1 : b0;
   // unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
+  const T half = (T)0.5;
   for (int idx = threadIdx.x; idx < sh.npair * sh.h; idx += blockDim.x) {
     int t = idx / sh.h, k = idx - t * sh.h;
-    double2 zk = res[t * sh.n1 + k];
-    double2 zm = res[t * sh.n1 + (k == 0 ? 0 : sh.n1 - k)];
-    double2 A = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
-    double2 B = make_double2(0.5 * (zk.y + zm.y), -0.5 * (zk.x - zm.x));
+    C zk = res[t * sh.n1 + k];
+    C zm = res[t * sh.n1 + (k == 0 ? 0 : sh.n1 - k)];
+    C A = mk<C>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+    C B = mk<C>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
     P[(2 * t) * sh.h + k] = A;
     if (2 * t + 1 < sh.n2) P[(2 * t + 1) * sh.h + k] = B;
   }
   __syncthreads();
-  double2* other = (P == b0) ? b1 : b0;
-  double2* Q = fft_lines<-1>(P, other, g.ax[1], twy, sh.h, sh.h, 1);
-  double2* out = (double2*)(S + lds * (long long)col) + (long long)z * sh.n2 * sh.h;
+  C* other = (P == b0) ? b1 : b0;
+  C* Q = fft_lines<-1>(P, other, g.ax[1], twy, sh.h, sh.h, 1);
+  C* out = (C*)(S + lds * (long long)col) + (long long)z * sh.n2 * sh.h;
   for (int idx = threadIdx.x; idx < sh.n2 * sh.h; idx += blockDim.x) out[idx] = Q[idx];
 }
 
@@ -208,7 +247,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd(FftGrid g, const dou
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_inv(FftGrid g, const double* __restrict__ S,
                                                             long long lds, const double* X, long long ldx,
                                                             double* Y, long long ldy) {
-  extern __shared__ double2 sm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double2* sm = reinterpret_cast<double2*>(sm_raw);
   const XYShape sh = xy_shape(g);
   double2* twx = sm;
   double2* twy = twx + sh.n1;
@@ -228,12 +268,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_inv(FftGrid g, const dou
     bool lo = k < sh.h;
     int kk = lo ? k : sh.n1 - k;
     double2 A = P[(2 * t) * sh.h + kk];
-    double2 B = (2 * t + 1 < sh.n2) ? P[(2 * t + 1) * sh.h + kk] : make_double2(0.0, 0.0);
+    double2 B = (2 * t + 1 < sh.n2) ? P[(2 * t + 1) * sh.h + kk] : mk<double2>(0.0, 0.0);
     if (!lo) {
       A.y = -A.y;
       B.y = -B.y;
     }
-    Zb[t * sh.n1 + k] = make_double2(A.x - B.y, A.y + B.x);
+    Zb[t * sh.n1 + k] = mk<double2>(A.x - B.y, A.y + B.x);
   }
   __syncthreads();
   double2* other = (Zb == b0) ? b1 : b0;
@@ -254,37 +294,66 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_inv(FftGrid g, const dou
 }
 
 // z transforms of FFT_ZCHUNK consecutive (ky, kx) positions of one column.
-// MODE 0: forward then multiply by wt.  MODE 1: forward, multiply, inverse.
-template <int MODE>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, double* S, long long lds,
-                                                       const double* __restrict__ wt) {
-  extern __shared__ double2 sm[];
+// MODE 0: forward then multiply by wt, in place.
+// MODE 1: forward, multiply, inverse, in place (the Coulomb convolution).
+// MODE 2: forward, multiply, then write BF16 slices of the weighted spectrum
+//         (slice l at out[(l rows_pad + col) kp + 2 q + {0: re, 1: im}], q the
+//         complex index) instead of writing back: the K-major operand of the
+//         tensor-core SYRK G = S^T S.
+template <int MODE, class C>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, typename Real<C>::T* S, long long lds,
+                                                       const double* __restrict__ wt, __nv_bfloat16* out,
+                                                       int rows_pad, int kp, int nsl) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
+  using T = typename Real<C>::T;
   const int n3 = g.ax[2].n;
   const int plane = g.ax[1].n * g.h;
-  double2* twz = sm;
-  double2* b0 = twz + n3;
-  double2* b1 = b0 + n3 * FFT_ZCHUNK;
+  C* twz = sm;
+  C* b0 = twz + n3;
+  C* b1 = b0 + n3 * FFT_ZCHUNK;
   const int q0 = blockIdx.x * FFT_ZCHUNK, col = blockIdx.y;
   const int nq = min(FFT_ZCHUNK, plane - q0);
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) twz[t] = ((const double2*)g.ax[2].tw)[t];
-  double2* base = (double2*)(S + lds * (long long)col);
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) twz[t] = from_tw<C>(((const double2*)g.ax[2].tw)[t]);
+  C* base = (C*)(S + lds * (long long)col);
   for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
     int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
-    b0[idx] = c < nq ? base[(long long)z * plane + q0 + c] : make_double2(0.0, 0.0);
+    b0[idx] = c < nq ? base[(long long)z * plane + q0 + c] : mk<C>((T)0, (T)0);
   }
   __syncthreads();
-  double2* R = fft_lines<-1>(b0, b1, g.ax[2], twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
+  C* R = fft_lines<-1>(b0, b1, g.ax[2], twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
   if (wt) {
     for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
       int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
-      double w = c < nq ? wt[(long long)z * plane + q0 + c] : 0.0;
-      R[idx] = make_double2(R[idx].x * w, R[idx].y * w);
+      T w = c < nq ? (T)wt[(long long)z * plane + q0 + c] : (T)0;
+      R[idx] = mk<C>(R[idx].x * w, R[idx].y * w);
     }
     __syncthreads();
   }
   if (MODE == 1) {
-    double2* other = (R == b0) ? b1 : b0;
+    C* other = (R == b0) ? b1 : b0;
     R = fft_lines<1>(R, other, g.ax[2], twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
+  }
+  if (MODE == 2) {
+    const long long sstr = (long long)rows_pad * kp;
+    for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
+      int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
+      if (c >= nq) continue;
+      long long k = 2ll * ((long long)z * plane + q0 + c);
+      T v[2] = {R[idx].x, R[idx].y};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        __nv_bfloat16 x0 = __float2bfloat16((float)v[h]);
+        float r1 = (float)v[h] - __bfloat162float(x0);
+        __nv_bfloat16 x1 = __float2bfloat16(r1);
+        __nv_bfloat16 x2 = __float2bfloat16(r1 - __bfloat162float(x1));
+        long long o = (long long)col * kp + k + h;
+        out[o] = x0;
+        if (nsl > 1) out[o + sstr] = x1;
+        if (nsl > 2) out[o + 2 * sstr] = x2;
+      }
+    }
+    return;
   }
   for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
     int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
@@ -304,15 +373,21 @@ size_t fft_smem_z(const FftGrid& g) {
   return sizeof(double2) * (size_t)(n3 + 2 * n3 * FFT_ZCHUNK);
 }
 
+// The FP32 kernels use half of these byte counts.
+
 cudaError_t fft_configure(size_t smem_xy, size_t smem_z) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_fft_xy_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+  e = cudaFuncSetAttribute(k_fft_xy_fwd<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fft_xy_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fft_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fft_z<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+  e = cudaFuncSetAttribute(k_fft_z<0, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fft_z<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+  e = cudaFuncSetAttribute(k_fft_z<2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fft_z<1, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
 }
 
 cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx, int ncols, double* S,
@@ -321,13 +396,13 @@ cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx,
   if (ncols <= 0) return cudaSuccess;
   dim3 gxy(g.ax[2].n, ncols);
   note_launch();
-  k_fft_xy_fwd<<<gxy, FFT_THREADS, smem_xy, s>>>(g, X, ldx, S, lds);
+  k_fft_xy_fwd<double2><<<gxy, FFT_THREADS, smem_xy, s>>>(g, X, ldx, S, lds);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int plane = g.ax[1].n * g.h;
   dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
   note_launch();
-  k_fft_z<0><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt);
+  k_fft_z<0, double2><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt, nullptr, 0, 0, 0);
   return cudaGetLastError();
 }
 
@@ -338,17 +413,37 @@ cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ld
   if (ncols <= 0) return cudaSuccess;
   dim3 gxy(g.ax[2].n, ncols);
   note_launch();
-  k_fft_xy_fwd<<<gxy, FFT_THREADS, smem_xy, s>>>(g, In, ldin, S, lds);
+  k_fft_xy_fwd<double2><<<gxy, FFT_THREADS, smem_xy, s>>>(g, In, ldin, S, lds);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int plane = g.ax[1].n * g.h;
   dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
   note_launch();
-  k_fft_z<1><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt);
+  k_fft_z<1, double2><<<gz, FFT_THREADS, smem_z, s>>>(g, S, lds, wt, nullptr, 0, 0, 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   note_launch();
   k_fft_xy_inv<<<gxy, FFT_THREADS, smem_xy, s>>>(g, S, lds, Add, ldadd, Y, ldy);
+  return cudaGetLastError();
+}
+
+}  // namespace isdf
+
+namespace isdf {
+
+cudaError_t launch_fft_forward_slices(const FftGrid& g, const double* X, long long ldx, int ncols, float* S32,
+                                      long long lds32, const double* wt, __nv_bfloat16* out, int rows_pad, int kp,
+                                      int nsl, size_t smem_xy, size_t smem_z, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  dim3 gxy(g.ax[2].n, ncols);
+  note_launch();
+  k_fft_xy_fwd<float2><<<gxy, FFT_THREADS, smem_xy / 2, s>>>(g, X, ldx, S32, lds32);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int plane = g.ax[1].n * g.h;
+  dim3 gz((plane + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+  note_launch();
+  k_fft_z<2, float2><<<gz, FFT_THREADS, smem_z / 2, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
   return cudaGetLastError();
 }
 

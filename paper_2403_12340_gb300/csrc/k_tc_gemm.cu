@@ -115,6 +115,37 @@ cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K
   return cudaGetLastError();
 }
 
+// Slices of the pair operand of the polarizability at the points:
+// S(a, i n_c + j) = phimu(a, i) phimu(a, n_v + j) sw[i n_c + j], a < r
+// (the columns of C, Eq. MatrixExpressionISDF, scaled by sqrt(-2 Omega^-1)).
+__global__ void k_pair_slices(const double* __restrict__ phimu, long long ldp, int r, int n_v, int n_c,
+                              const double* __restrict__ sw, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+  const int a = blockIdx.y;
+  const int K = n_v * n_c;
+  for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk < K; kk += gridDim.x * blockDim.x) {
+    const int i = kk / n_c, j = kk - i * n_c;
+    const double v = phimu[a + ldp * i] * phimu[a + ldp * (long long)(n_v + j)] * sw[kk];
+    __nv_bfloat16 x0, x1, x2;
+    split3(v, x0, x1, x2);
+    long long base = (long long)a * Kp + kk;
+    dst[base] = x0;
+    if (s > 1) dst[base + (long long)Rp * Kp] = x1;
+    if (s > 2) dst[base + 2ll * Rp * Kp] = x2;
+  }
+}
+
+cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
+                               __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st) {
+  if (r <= 0) return cudaSuccess;
+  int K = n_v * n_c;
+  int bx = (K + 255) / 256;
+  if (bx > 128) bx = 128;
+  dim3 grid(bx, r);
+  note_launch();
+  k_pair_slices<<<grid, 256, 0, st>>>(phimu, ldp, r, n_v, n_c, sw, dst, Rp, Kp, s);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ the GEMM
 
 struct TcArgs {

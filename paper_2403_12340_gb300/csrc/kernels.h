@@ -44,6 +44,9 @@ cudaError_t launch_transpose(const double* src, long long lds, int M, int N, dou
                              long long ldd, cudaStream_t s);
 cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s);
 cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s);
+// Li = L^-1 for lower-triangular L (r x r), FP64; work >= (r/2 + 64)^2 doubles.
+cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li, long long ldi, double* work,
+                               cudaStream_t s);
 // L (n_full x n_full column-major) from the row-major pivoted factor Lr.
 cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
                                       double* L, long long ldl, int n_full, cudaStream_t s);
@@ -96,6 +99,13 @@ cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ld
                                 double* S, long long lds, const double* wt, const double* Add,
                                 long long ldadd, double* Y, long long ldy, size_t smem_xy,
                                 size_t smem_z, cudaStream_t s);
+// Mixed path: forward FP32 transform of ncols float64 columns with weights
+// wt, written as nsl BF16 slices (slice l at out[(l rows_pad + col) kp + k],
+// k = 2 q + {0 re, 1 im}); S32 is FP32 scratch (ncols * lds32 floats,
+// lds32 >= 2 h n2 n3).
+cudaError_t launch_fft_forward_slices(const FftGrid& g, const double* X, long long ldx, int ncols, float* S32,
+                                      long long lds32, const double* wt, __nv_bfloat16* out, int rows_pad, int kp,
+                                      int nsl, size_t smem_xy, size_t smem_z, cudaStream_t s);
 size_t fft_smem_xy(const FftGrid& g);
 size_t fft_smem_z(const FftGrid& g);
 cudaError_t fft_configure(size_t smem_xy, size_t smem_z);
@@ -117,6 +127,10 @@ cudaError_t launch_slice_colmajor(const double* src, long long lds, int R, int C
 // slices of a row-major FP64 matrix (R x K, element (r, k) at src[k + lds r])
 cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K, __nv_bfloat16* dst, int Rp,
                                   int Kp, int s, cudaStream_t st);
+// Slices of the pair operand at the points, S(a, i n_c + j) =
+// phimu(a, i) phimu(a, n_v + j) sw[i n_c + j] (r rows, K = n_v n_c).
+cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
+                               __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st);
 // C (M x N, column-major FP64) = alpha sum_{i+j<s} A_i B_j^T + beta C.  With
 // `partial` (max_split * M * N doubles) long K is split over blocks and
 // reduced in FP64.  lower_only: SYRK-style (M == N, mirrored).  tri_b: B is

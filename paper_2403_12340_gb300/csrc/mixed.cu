@@ -1,0 +1,208 @@
+// Mixed-precision ISDF-SMW (ISDF_PREC_MIXED): every large contraction runs
+// on the tensor cores as a three-slice BF16 split-precision GEMM (FP32
+// accumulation in TMEM, FP64 sums across K blocks); the factorisations (the
+// pivoted Cholesky of C C^T, the Cholesky factors of the capacitance, the
+// triangular inverses) and the small products stay in FP64.
+//
+//   fit   : theta = [(Phi_v Phi_v,mu^T) .* (Phi_c Phi_c,mu^T)] L^-T, the
+//           face-split Gram with two TMEM accumulators, then one triangular
+//           GEMM with the FP64 inverse of the Cholesky factor;
+//   polar : G = S^T S with S the FP32 FFT of theta written straight into
+//           BF16 slices; D = L^-1 (S_pair S_pair^T) L^-T with the pair
+//           operand generated into slices;
+//   smw   : K = -Q Q^T, Q = R U^-T, with R, U FP64 Cholesky factors and the
+//           GEMMs around them on the tensor cores;
+//   apply : theta^T X and theta T2 on the tensor cores, the Coulomb
+//           convolution of the n_rhs columns in FP64.
+#include <algorithm>
+#include <string>
+
+#include "../../include/isdf_smw.h"
+#include "ctx.h"
+
+namespace isdf {
+
+namespace {
+
+constexpr int NSL = 3;  // BF16 slices per operand
+
+inline int pad(long long x, int m) { return (int)((x + m - 1) / m * m); }
+
+inline cudaError_t slices_cm(DevBuf& buf, const double* src, long long lds, int R, int C, int rows_pad, int kp,
+                             cudaStream_t st, int kv = 0, int kvp = 0) {
+  const size_t n = (size_t)NSL * rows_pad * kp;
+  cudaError_t e = ensure_bf16(buf, n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(buf.p, 0, n * 2, st);
+  if (e != cudaSuccess) return e;
+  return launch_slice_colmajor(src, lds, R, C, kv, kvp, buf.bf(), rows_pad, kp, NSL, st);
+}
+
+inline cudaError_t slices_rm(DevBuf& buf, const double* src, long long lds, int R, int K, int rows_pad, int kp,
+                             cudaStream_t st) {
+  const size_t n = (size_t)NSL * rows_pad * kp;
+  cudaError_t e = ensure_bf16(buf, n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(buf.p, 0, n * 2, st);
+  if (e != cudaSuccess) return e;
+  return launch_slice_rowmajor(src, lds, R, K, buf.bf(), rows_pad, kp, NSL, st);
+}
+
+inline TcOperand op(const DevBuf& b, int rows_pad, int kp) { return TcOperand{b.bf(), rows_pad, kp, NSL}; }
+
+}  // namespace
+
+#define MK(expr)                                        \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
+    if (_e != cudaSuccess) return _e;                   \
+  } while (0)
+
+// theta (N_r x r, ld N_r) from the pivot-ordered point orbitals (c->phimu_p)
+// and the Cholesky factor c->Lc (r x r, ld r).
+cudaError_t mixed_fit(isdf_ctx* c, const double* phi, double* theta, int n_v, int n_c, int r) {
+  cudaStream_t st = c->stream;
+  const long long nr = c->n_r;
+  const int n_e = n_v + n_c;
+  const int kvp = pad(n_v, 64), kp = kvp + pad(n_c, 64);
+  const int nrp = pad(nr, 128), rp = pad(r, 128), rk = pad(r, 64);
+  {
+    PhaseTimer ph(c, ISDF_PH_FIT_GRAM);
+    MK(slices_cm(c->m_phis, phi, nr, (int)nr, n_e, nrp, kp, st, n_v, kvp));
+    MK(slices_cm(c->m_phimus, c->phimu_p.p, r, r, n_e, rp, kp, st, n_v, kvp));
+    const size_t nz = (size_t)NSL * nrp * rk;
+    MK(ensure_bf16(c->m_zs, nz));
+    MK(cudaMemsetAsync(c->m_zs.p, 0, nz * 2, st));
+    MK(tc_facesplit(op(c->m_phis, nrp, kp), op(c->m_phimus, rp, kp), (int)nr, r, kvp / 64, nullptr, 0,
+                    c->m_zs.bf(), nrp, rk, c->d_status, st));
+  }
+  PhaseTimer ph(c, ISDF_PH_FIT_TRSM);
+  MK(ensure(c->m_linv, (size_t)r * r));
+  MK(ensure(c->m_work, (size_t)(r / 2 + 64) * (r / 2 + 64)));
+  MK(launch_tri_inverse(c->Lc.p, r, r, c->m_linv.p, r, c->m_work.p, st));
+  MK(slices_cm(c->m_linvs, c->m_linv.p, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, 1.0, 0.0, theta, nr, false, true,
+                 nullptr, 1, c->num_sms, c->d_status, st));
+  // slices of theta for the apply: K-major over the grid (theta^T X) and over mu (theta T2)
+  MK(slices_rm(c->m_thetas_t, theta, nr, r, (int)nr, rp, pad(nr, 64), st));
+  MK(slices_cm(c->m_zs, theta, nr, (int)nr, r, nrp, rk, st));
+  return cudaSuccess;
+}
+
+// G (r x r) and D(w_k) for all frequencies, whitened, into c->G and c->D.
+cudaError_t mixed_polar(isdf_ctx* c, const double* sw, int n_omega) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
+  const size_t rr = (size_t)r * r;
+  const int rp = pad(r, 128), rk = pad(r, 64);
+  const long long lds32 = 2 * c->n_half;
+  const int kps = pad(lds32, 64);
+  const int npair = n_v * n_c, kpp = pad(npair, 64);
+  const int max_split = 8;
+  MK(ensure(c->partial, (size_t)max_split * rr));
+  {
+    PhaseTimer ph(c, ISDF_PH_FFT);
+    MK(ensure(c->m_s32, ((size_t)lds32 * r + 1) / 2));
+    const size_t ns = (size_t)NSL * rp * kps;
+    MK(ensure_bf16(c->m_ss, ns));
+    MK(cudaMemsetAsync(c->m_ss.p, 0, ns * 2, st));
+    MK(launch_fft_forward_slices(c->fft, c->theta, c->n_r, r, (float*)c->m_s32.p, lds32, c->d_wsyrk, c->m_ss.bf(),
+                                 rp, kps, NSL, c->smem_xy, c->smem_z, st));
+  }
+  {
+    PhaseTimer ph(c, ISDF_PH_SYRK_G);
+    MK(tc_gemm_f64(op(c->m_ss, rp, kps), op(c->m_ss, rp, kps), r, r, 1.0, 0.0, c->G.p, r, true, false,
+                   c->partial.p, max_split, c->num_sms, c->d_status, st));
+  }
+  MK(ensure(c->tmp1, rr));
+  MK(ensure(c->tmp2, rr));
+  const size_t np = (size_t)NSL * rp * kpp;
+  MK(ensure_bf16(c->m_pairs, np));
+  MK(cudaMemsetAsync(c->m_pairs.p, 0, np * 2, st));
+  for (int k = 0; k < n_omega; ++k) {
+    double* Dk = c->D.p + rr * k;
+    {
+      PhaseTimer ph(c, ISDF_PH_POLAR_D);
+      MK(launch_pair_slices(c->phimu_p.p, r, r, n_v, n_c, sw + (size_t)npair * k, c->m_pairs.bf(), rp, kpp, NSL,
+                            st));
+      MK(tc_gemm_f64(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, c->tmp1.p, r, true, false,
+                     c->partial.p, max_split, c->num_sms, c->d_status, st));
+    }
+    PhaseTimer ph(c, ISDF_PH_WHITEN_D);
+    // X = L^-1 D_pp, then D = X L^-T
+    MK(slices_cm(c->m_sa, c->tmp1.p, r, r, r, rp, rk, st));
+    MK(tc_gemm_f64(op(c->m_linvs, rp, rk), op(c->m_sa, rp, rk), r, r, 1.0, 0.0, c->tmp2.p, r, false, false,
+                   nullptr, 1, c->num_sms, c->d_status, st));
+    MK(slices_cm(c->m_sa, c->tmp2.p, r, r, r, rp, rk, st));
+    MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_linvs, rp, rk), r, r, 1.0, 0.0, Dk, r, false, true, nullptr, 1,
+                   c->num_sms, c->d_status, st));
+    MK(launch_symmetrize(Dk, r, r, st));
+  }
+  return cudaSuccess;
+}
+
+// K = -Q Q^T for frequency k into Kk (r x r).  Needs the unpivoted FP64
+// Cholesky of the host side (passed in as a callback-free sequence: the
+// caller factors D into c->R and T into c->W1).
+cudaError_t mixed_smw_products_T(isdf_ctx* c) {
+  // T = I + R^T (G R), T in c->T (identity already set)
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  MK(slices_cm(c->m_sa, c->G.p, r, r, r, rp, rk, st));
+  MK(slices_rm(c->m_sb, c->R.p, r, r, r, rp, rk, st));  // rows = columns of R
+  MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sb, rp, rk), r, r, 1.0, 0.0, c->W1.p, r, false, false, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  MK(slices_rm(c->m_sa, c->W1.p, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_sb, rp, rk), op(c->m_sa, rp, rk), r, r, 1.0, 1.0, c->T.p, r, false, false, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  return launch_symmetrize(c->T.p, r, r, st);
+}
+
+cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk) {
+  // U in c->W1: Q = R U^-T, K = -Q Q^T
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const size_t rr = (size_t)r * r;
+  const int max_split = 8;
+  MK(ensure(c->m_work, (size_t)(r / 2 + 64) * (r / 2 + 64)));
+  MK(ensure(c->partial, (size_t)max_split * rr));
+  MK(launch_tri_inverse(c->W1.p, r, r, c->Q.p, r, c->m_work.p, st));  // Q <- U^-1
+  MK(slices_cm(c->m_sa, c->R.p, r, r, r, rp, rk, st));
+  MK(slices_cm(c->m_sb, c->Q.p, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sb, rp, rk), r, r, 1.0, 0.0, c->Q.p, r, false, true, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  MK(slices_cm(c->m_sa, c->Q.p, r, r, r, rp, rk, st));
+  return tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 0.0, Kk, r, true, false, c->partial.p,
+                     max_split, c->num_sms, c->d_status, st);
+}
+
+// Y = X + V theta K theta^T X for one chunk of nc columns.
+cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const long long nr = c->n_r;
+  const int nrp = pad(nr, 128), kpg = pad(nr, 64);
+  const int ncp = pad(nc, 128);
+  const int max_split = 64;
+  MK(ensure(c->partial, (size_t)max_split * r * nc));
+  MK(ensure(c->tmp1, (size_t)r * nc));
+  MK(ensure(c->tmp2, (size_t)r * nc));
+  MK(ensure(c->tmp3, (size_t)nr * nc));
+  // T1 = theta^T X
+  MK(slices_rm(c->m_xs, X, nr, nc, (int)nr, ncp, kpg, st));
+  MK(tc_gemm_f64(op(c->m_thetas_t, rp, kpg), op(c->m_xs, ncp, kpg), r, nc, 1.0, 0.0, c->tmp1.p, r, false, false,
+                 c->partial.p, max_split, c->num_sms, c->d_status, st));
+  // T2 = K T1 (FP64, small)
+  MK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 1, nullptr, true, st));
+  // T3 = theta T2
+  MK(slices_rm(c->m_xs, c->tmp2.p, r, nc, r, ncp, rk, st));
+  MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_xs, ncp, rk), (int)nr, nc, 1.0, 0.0, c->tmp3.p, nr, false, false,
+                 nullptr, 1, c->num_sms, c->d_status, st));
+  // Y = X + V T3
+  const long long lds = 2 * c->n_half;
+  MK(ensure(c->spec, (size_t)lds * nc));
+  return launch_fft_convolve(c->fft, c->tmp3.p, nr, nc, c->spec.p, lds, c->d_wconv, X, nr, Y, nr, c->smem_xy,
+                             c->smem_z, st);
+}
+
+}  // namespace isdf

@@ -4,14 +4,14 @@ import numpy as np
 import paper_2403_12340_gb300 as pkg
 
 
-def run_gpu(system, x, omegas=(0.0,), want=False, in_place=False):
+def run_gpu(system, x, omegas=(0.0,), want=False, in_place=False, prec=0):
     """Fit, polarizability, SMW and apply for every frequency; returns host arrays."""
     import torch
 
     out = {}
     with pkg.IsdfSmw(system.n, system.cell) as s:
         phi = pkg.to_fortran(system.phi)
-        theta, rank = s.fit(phi, system.n_v, system.n_c, system.mu_idx)
+        theta, rank = s.fit(phi, system.n_v, system.n_c, system.mu_idx, prec=prec)
         D, G = s.polarizability(system.energies, list(omegas), want_D=want, want_G=want)
         ys, ks = [], []
         X = pkg.to_fortran(x)
