@@ -192,6 +192,15 @@ def workload_config(s, extra=None):
 
 # ------------------------------------------------------------- native arm
 
+PREC = {"fp64": 0, "mixed": 1}
+PREC_DETAIL = {
+    "fp64": "every step in float64 on the FP64 pipe",
+    "mixed": ("large contractions on tcgen05 tensor cores with operands cut into 3 BF16 slices "
+              "(FP32 accumulation, FP64 sums over K blocks), FFT of theta in FP32; Cholesky "
+              "factorisations and triangular inverses in FP64"),
+}
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -227,19 +236,43 @@ def run_native(args):
     Y = pkg.fortran_empty(s.n_r, N_RHS, dev)
     ctx = pkg.IsdfSmw(s.n, s.cell, stream)
 
-    def step(phi_d, X_d, Y_d):
-        ctx.fit(phi_d, s.n_v, s.n_c, s.mu_idx, theta)
+    prec = PREC[args.prec]
+
+    def step(phi_d, X_d, Y_d, p=None):
+        ctx.fit(phi_d, s.n_v, s.n_c, s.mu_idx, theta, prec=prec if p is None else p)
         ctx.polarizability(s.energies, [0.0])
         ctx.smw(0)
         ctx.apply(X_d, 0, Y_d)
 
+    def rel_err():
+        if ref_y is None:
+            return None
+        y = Y.cpu().numpy()
+        return float(np.linalg.norm(y - ref_y) / np.linalg.norm(ref_y))
+
+    # the plain FP64 path on the same system, for the speedup at the stated error
+    fp64 = None
+    if prec != 0 and not args.no_fp64_compare:
+        for _ in range(max(1, min(args.warmup, 2))):
+            step(phi, X, Y, 0)
+        torch.cuda.synchronize(dev)
+        err64 = rel_err()
+        k64 = max(1, min(args.steps, 3))
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k64):
+            step(phi, X, Y, 0)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = max_over_ranks(f0.elapsed_time(f1), dev)
+        fp64 = {"value": round(job_throughput(ws, k64, ms64), 4), "unit": "solves/s",
+                "ms_per_step": round(ms64 / k64, 3), "steps": k64, "rel_err_vs_oracle": err64}
+
     for _ in range(args.warmup):
         step(phi, X, Y)
     torch.cuda.synchronize(dev)
-    err = None
-    if ref_y is not None:
-        y = Y.cpu().numpy()
-        err = float(np.linalg.norm(y - ref_y) / np.linalg.norm(ref_y))
+    err = rel_err()
 
     # ---- device-timed region: inputs resident in HBM
     sampler = None
@@ -329,13 +362,17 @@ def run_native(args):
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else "bf16x3 (f32 accumulate) + f64",
             "data": "synthetic",
             "config": workload_config(s, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                                          "rank": rank_r}),
+                                          "rank": rank_r, "precision": args.prec,
+                                          "precision_detail": PREC_DETAIL[args.prec]}),
             "tflops": round(flops_step * value / 1e12, 4),
             "flops_per_step": flops_step,
             "rel_err_vs_oracle": err,
+            "fp64_path": fp64,
+            "speedup_vs_fp64": (round(value / fp64["value"], 3) if fp64 else None),
             "roofline": roof, "phases_ms": phases,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,
@@ -386,6 +423,10 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed",
+                    help="mixed: split-BF16 tensor-core contractions (the headline); fp64: FP64 pipe only")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 path next to the mixed one")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

@@ -208,7 +208,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->spec, &c->G, &c->D, &c->K, &c->R, &c->T, &c->W1, &c->Q, &c->partial,
                     &c->tmp1, &c->tmp2, &c->tmp3, &c->sw, &c->m_phis, &c->m_phimus, &c->m_zs, &c->m_linv,
                     &c->m_linvs, &c->m_work, &c->m_thetas_t, &c->m_s32, &c->m_ss, &c->m_pairs, &c->m_sa,
-                    &c->m_sb, &c->m_xs};
+                    &c->m_sb, &c->m_xs, &c->cb_work};
   for (DevBuf* b : bufs) release(*b);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
@@ -253,6 +253,16 @@ static int cholesky(isdf_ctx* c, const double* W, long long ldw, int n, int pivo
   return ISDF_OK;
 }
 
+// Blocked Cholesky (no pivoting) of W into Lout (ld n); *fail (device) = -1
+// on success, else the first column whose pivot fell to tol_rel * max diag.
+static int cholesky_blocked(isdf_ctx* c, const double* W, long long ldw, int n, double tol_rel, double* Lout,
+                            int* fail) {
+  CK(ensure(c->cb_work, 64 + 64 * 64 + (size_t)n * 64));
+  CK(launch_cholesky_blocked(W, ldw, n, tol_rel, Lout, n, c->cb_work.p + 64, c->cb_work.p, fail,
+                             c->cb_work.p + 64 + 64 * 64, c->stream));
+  return ISDF_OK;
+}
+
 extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const int64_t* mu_idx,
                         int n_mu, int prec, double* theta, int* rank_out) {
   if (!c) return ISDF_ERR_ARG;
@@ -289,23 +299,41 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   CK(ensure(c->phimu, (size_t)n_mu * n_e));
   CK(ensure(c->A, (size_t)n_mu * n_mu));
   CK(ensure(c->Lc, (size_t)n_mu * n_mu));
+  const double tol = (double)n_mu * 2.220446049250313e-16;
+  int rc0 = ISDF_OK;
   {
   PhaseScope ph(c, ISDF_PH_POINTS);
   CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
   CK(launch_facesplit_gram(c->phimu.p, n_mu, n_mu, c->phimu.p, n_mu, n_mu, n_v, n_e, c->A.p, n_mu,
                            c->stream));
-  const double tol = (double)n_mu * 2.220446049250313e-16;
-  int rc0 = cholesky(c, c->A.p, n_mu, n_mu, 1, tol, c->Lc.p, c->d_perm);
+  // Cholesky of C C^T in the given point order (blocked); if a pivot falls to
+  // the rank threshold, redo it with diagonal pivoting (rank-deficient C)
+  rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1);
   if (rc0 != ISDF_OK) return rc0;
   }
   CK(cudaStreamSynchronize(c->stream));
   int rc;
   rc = check_status(c, "isdf_fit");
   if (rc != ISDF_OK) return rc;
-  int rank = 0;
-  CK(cudaMemcpy(&rank, c->d_ints, sizeof(int), cudaMemcpyDeviceToHost));
+  int fail = 0, rank = 0;
+  CK(cudaMemcpy(&fail, c->d_ints + 1, sizeof(int), cudaMemcpyDeviceToHost));
   c->perm.assign(n_mu, 0);
-  if (rank > 0) CK(cudaMemcpy(c->perm.data(), c->d_perm, rank * sizeof(int), cudaMemcpyDeviceToHost));
+  if (fail < 0) {
+    rank = n_mu;
+    for (int i = 0; i < n_mu; ++i) c->perm[i] = i;
+    CK(cudaMemcpyAsync(c->d_perm, c->perm.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    {
+      PhaseScope ph(c, ISDF_PH_POINTS);
+      rc0 = cholesky(c, c->A.p, n_mu, n_mu, 1, tol, c->Lc.p, c->d_perm);
+      if (rc0 != ISDF_OK) return rc0;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    rc = check_status(c, "isdf_fit");
+    if (rc != ISDF_OK) return rc;
+    CK(cudaMemcpy(&rank, c->d_ints, sizeof(int), cudaMemcpyDeviceToHost));
+    if (rank > 0) CK(cudaMemcpy(c->perm.data(), c->d_perm, rank * sizeof(int), cudaMemcpyDeviceToHost));
+  }
   {  // complete the pivot list with the unused points in increasing order
     std::vector<char> used(n_mu, 0);
     for (int j = 0; j < rank; ++j) used[c->perm[j]] = 1;
@@ -498,7 +526,7 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
     CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
     PhaseScope ph(c, ISDF_PH_SMW);
     // D = R R^T
-    int rc = cholesky(c, c->D.p + rr * k, r, r, 0, 0.0, c->R.p, c->d_perm2);
+    int rc = cholesky_blocked(c, c->D.p + rr * k, r, r, 0.0, c->R.p, c->d_ints + 2);
     if (rc != ISDF_OK) return rc;
     // T = I + R^T G R
     CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
@@ -513,7 +541,7 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
       CK(launch_symmetrize(c->T.p, r, r, c->stream));
     }
     // T = U U^T; Q = R U^-T; K = -Q Q^T
-    rc = cholesky(c, c->T.p, r, r, 0, 0.0, c->W1.p, c->d_perm2);
+    rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, c->d_ints + 3);
     if (rc != ISDF_OK) return rc;
     if (c->prec == ISDF_PREC_MIXED) {
       CK(isdf::mixed_smw_products_K(c, Kk));
@@ -534,6 +562,12 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
   CK(cudaStreamSynchronize(c->stream));
   int rc = check_status(c, "smw_inverse");
   if (rc != ISDF_OK) return rc;
+  if (r > 0) {
+    int fails[2] = {-1, -1};
+    CK(cudaMemcpy(fails, c->d_ints + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    if (fails[0] >= 0 || fails[1] >= 0)
+      return fail(c, ISDF_ERR_NOT_SPD, "smw_inverse: capacitance factor not positive definite");
+  }
   c->k_ready[k] = 1;
   return ISDF_OK;
 }

@@ -104,6 +104,7 @@ struct Tile {
 };
 
 using TileSq = Tile<64, 64, 4, 4>;       // 256 threads, square tiles
+using TileSm = Tile<32, 32, 2, 2>;       // 256 threads, small square tiles (short GEMMs)
 using TileNarrow = Tile<128, 16, 4, 2>;  // 256 threads, tall-skinny (probe blocks)
 
 // sm[k][row] = op(row0 + row, k0 + k), zero outside [0, rows) x [k0, kend).

@@ -66,6 +66,7 @@ struct isdf_ctx {
 
   // mixed precision (ISDF_PREC_MIXED): BF16 slice matrices and FP64 helpers
   int prec = 0;
+  DevBuf cb_work;  // blocked Cholesky: [0] max diagonal, [64..] 64 x 64 inverse block
   DevBuf m_phis, m_phimus, m_zs, m_linv, m_linvs, m_work, m_thetas_t, m_s32, m_ss, m_pairs, m_sa, m_sb, m_xs;
 
   // phase profiling

@@ -1,0 +1,156 @@
+// Blocked right-looking Cholesky (no pivoting), FP64.
+//
+// For J = 0, 1, ...: the 64 x 64 diagonal block is factored in shared memory
+// by one thread block, which also inverts its factor; the panel below is
+// solved as one GEMM with that inverse; the trailing matrix gets a SYRK
+// update.  All the O(n^3) work is in the two GEMMs, which use every SM.
+//
+// A pivot at or below tol_rel * max(diag) stops the factorisation: the
+// first failing column goes to *fail and every later kernel of the sequence
+// does nothing.  The caller decides what that means (not positive definite,
+// or: fall back to the pivoted factorisation for a rank-deficient C C^T).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace isdf {
+
+constexpr int CB = 64;
+
+__global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, double* out, int* fail) {
+  __shared__ double red[256];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, W[i + ldw * (long long)i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *out = red[0];
+    *fail = -1;
+  }
+}
+
+// Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place and
+// write its inverse into dinv (bs x bs, ld CB).  One thread block; the FP64
+// pipe of one SM is the limit, so no FP64 work is repeated across threads:
+// the square root and the reciprocal of each pivot are taken once, and the
+// rank-1 updates touch only the lower triangle (thread (tx, ty) of a 16 x 16
+// layout owns rows tx + 16 a and columns ty + 16 b).
+__global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int j0, int bs, double* dinv,
+                                                  const double* dmax, double tol_rel, int* fail) {
+  __shared__ double Ls[CB][CB + 1];
+  __shared__ double Xs[CB][CB + 1];
+  __shared__ double rdiag[CB];
+  __shared__ int s_bad;
+  if (*(volatile int*)fail >= 0) return;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  for (int idx = t; idx < CB * CB; idx += blockDim.x) {
+    int i = idx & (CB - 1), k = idx >> 6;
+    Ls[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
+  }
+  if (t == 0) s_bad = -1;
+  const double thresh = tol_rel * (*dmax);
+  __syncthreads();
+  for (int j = 0; j < bs; ++j) {
+    if (t == 0) {
+      const double d = Ls[j][j];
+      if (!(d > thresh)) {  // also catches NaN
+        s_bad = j;
+      } else {
+        const double l = sqrt(d);
+        Ls[j][j] = l;
+        rdiag[j] = 1.0 / l;
+      }
+    }
+    __syncthreads();
+    if (s_bad >= 0) break;
+    const double r = rdiag[j];
+    for (int i = j + 1 + t; i < bs; i += blockDim.x) Ls[i][j] *= r;
+    __syncthreads();
+    // Ls[i][k] -= Ls[i][j] Ls[k][j] for j < k <= i < bs
+#pragma unroll
+    for (int a = 0; a < CB / 16; ++a) {
+      const int i = tx + 16 * a;
+      if (i <= j || i >= bs) continue;
+      const double lij = Ls[i][j];
+#pragma unroll
+      for (int b = 0; b < CB / 16; ++b) {
+        const int k = ty + 16 * b;
+        if (k > j && k <= i) Ls[i][k] = fma(-lij, Ls[k][j], Ls[i][k]);
+      }
+    }
+    __syncthreads();
+  }
+  if (s_bad >= 0) {
+    if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
+    return;
+  }
+  // inverse of the factor: column c by forward substitution (threads < bs),
+  // using the reciprocal pivots
+  if (t < bs) {
+    const int c = t;
+    for (int i = 0; i < c; ++i) Xs[i][c] = 0.0;
+    Xs[c][c] = rdiag[c];
+    for (int i = c + 1; i < bs; ++i) {
+      double acc = 0.0;
+      for (int k = c; k < i; ++k) acc = fma(Ls[i][k], Xs[k][c], acc);
+      Xs[i][c] = -acc * rdiag[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = t; idx < bs * bs; idx += blockDim.x) {
+    int i = idx % bs, k = idx / bs;
+    A[(j0 + i) + lda * (long long)(j0 + k)] = (k <= i) ? Ls[i][k] : 0.0;
+    dinv[i + CB * k] = Xs[i][k];
+  }
+}
+
+// Zero the strict upper triangle.
+__global__ void k_zero_upper(double* A, long long lda, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  if (i < k && k < n) A[i + lda * (long long)k] = 0.0;
+}
+
+cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
+                                    double* dinv, double* dmax, int* fail, double* pan, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (L != W) {
+    e = cudaMemcpy2DAsync(L, ldl * sizeof(double), W, ldw * sizeof(double), n * sizeof(double), n,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  note_launch();
+  k_diag_max<<<1, 256, 0, s>>>(L, ldl, n, dmax, fail);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int j0 = 0; j0 < n; j0 += CB) {
+    const int bs = min(CB, n - j0);
+    note_launch();
+    k_chol_diag<<<1, 256, 0, s>>>(L, ldl, j0, bs, dinv, dmax, tol_rel, fail);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int rem = n - j0 - bs;
+    if (rem <= 0) break;
+    // panel: L[j0+bs:, J] = A[j0+bs:, J] Dinv^T, computed into `pan` (rem x bs,
+    // ld n) and copied back: a tile narrower than the panel must not
+    // overwrite columns that another block still reads
+    double* Pj = L + (j0 + bs) + ldl * (long long)j0;
+    e = launch_gemm(Pj, ldl, false, dinv, CB, false, rem, bs, bs, 1.0, 0.0, pan, n, false, 1, nullptr, false, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy2DAsync(Pj, ldl * sizeof(double), pan, n * sizeof(double), rem * sizeof(double), bs,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles, mirrored)
+    e = launch_gemm(pan, n, false, pan, n, false, rem, rem, bs, -1.0, 1.0, L + (j0 + bs) + ldl * (long long)(j0 + bs),
+                    ldl, true, 1, nullptr, false, s);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g((n + 127) / 128, n);
+  note_launch();
+  k_zero_upper<<<g, 128, 0, s>>>(L, ldl, n);
+  return cudaGetLastError();
+}
+
+}  // namespace isdf

@@ -233,6 +233,56 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, 
   C[m + ldc * n] = v;
 }
 
+template <class T, class OpA, class OpB>
+__global__ void __launch_bounds__(T::NT) k_gemm_batched(OpA A, OpB B, long long sA, long long sB, int M, int N,
+                                                        int K, double alpha, double beta, double* C, long long ldc,
+                                                        long long sC) {
+  __shared__ typename T::Smem s;
+  const int z = blockIdx.z;
+  A.p += sA * z;
+  B.p += sB * z;
+  C += sC * z;
+  const int m0 = blockIdx.x * T::kBM, n0 = blockIdx.y * T::kBN;
+  double acc[T::kTM][T::kTN];
+  zero_acc<T>(acc);
+  gemm_mainloop<T>(acc, s, A, B, m0, n0, 0, K);
+  store_tile<T>(acc, m0, n0, M, N, alpha, beta, C, ldc, false);
+}
+
+template <class T, bool KA, bool KB>
+static cudaError_t gemm_batched_dispatch(const double* A, long long lda, long long sA, const double* B, long long ldb,
+                                         long long sB, int M, int N, int K, double alpha, double beta, double* C,
+                                         long long ldc, long long sC, int batch, cudaStream_t s) {
+  dim3 grid((M + T::kBM - 1) / T::kBM, (N + T::kBN - 1) / T::kBN, batch);
+  note_launch();
+  k_gemm_batched<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(Operand<KA>{A, lda, M}, Operand<KB>{B, ldb, N},
+                                                                    sA, sB, M, N, K, alpha, beta, C, ldc, sC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
+                                long long ldb, bool kb, long long sB, int M, int N, int K, double alpha, double beta,
+                                double* C, long long ldc, long long sC, int batch, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  const long long t64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * batch;
+  const bool small = t64 < 2 * 152;
+#define ISDF_BGEMM_CASE(TT, a, b) \
+  if (ka == a && kb == b) return gemm_batched_dispatch<TT, a, b>(A, lda, sA, B, ldb, sB, M, N, K, alpha, beta, C, ldc, sC, batch, s);
+  if (small) {
+    ISDF_BGEMM_CASE(TileSm, false, false)
+    ISDF_BGEMM_CASE(TileSm, false, true)
+    ISDF_BGEMM_CASE(TileSm, true, false)
+    ISDF_BGEMM_CASE(TileSm, true, true)
+  } else {
+    ISDF_BGEMM_CASE(TileSq, false, false)
+    ISDF_BGEMM_CASE(TileSq, false, true)
+    ISDF_BGEMM_CASE(TileSq, true, false)
+    ISDF_BGEMM_CASE(TileSq, true, true)
+  }
+#undef ISDF_BGEMM_CASE
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
                                  double* C, long long ldc, bool lower_only, int tile, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
@@ -285,6 +335,15 @@ cudaError_t launch_gemm(const double* A, long long lda, bool ka, const double* B
   if (ka == a && kb == b)                                                                        \
     return gemm_dispatch<TT, a, b>(A, lda, B, ldb, M, N, K, alpha, beta, C, ldc, lower_only,     \
                                    splits, partial, s);
+  // too few 64 x 64 tiles to fill the GPU twice: use 32 x 32 tiles (4x the blocks)
+  const long long t64 = lower_only ? (long long)((M + 63) / 64) * ((M + 63) / 64 + 1) / 2
+                                   : (long long)((M + 63) / 64) * ((N + 63) / 64);
+  if (!narrow && t64 * (splits > 1 ? splits : 1) < 2 * 152) {
+    ISDF_GEMM_CASE(TileSm, false, false)
+    ISDF_GEMM_CASE(TileSm, false, true)
+    ISDF_GEMM_CASE(TileSm, true, false)
+    ISDF_GEMM_CASE(TileSm, true, true)
+  }
   if (narrow) {
     ISDF_GEMM_CASE(TileNarrow, false, false)
     ISDF_GEMM_CASE(TileNarrow, false, true)
@@ -494,14 +553,25 @@ cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li
   k_diag_inverse<<<nb, TRSM_NB, 0, s>>>(L, ldl, r, Li, ldi);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int bs = TRSM_NB; bs < r; bs *= 2) {
-    for (int b = 0; b + bs < r; b += 2 * bs) {
-      const int sa = bs;                       // size of the inverted upper-left block A
-      const int sb = min(bs, r - (b + bs));    // size of the lower-right block B
-      // X (sb x sa) = C A^-1 with C = L[b+bs .., b ..]
+    // merges of this level with a full-size lower block, batched
+    const int full = r / (2 * bs);
+    if (full > 0) {
+      const long long sL = 2ll * bs * (1 + ldl), sI = 2ll * bs * (1 + ldi), sW = (long long)bs * bs;
+      // X_z (bs x bs) = C_z A_z^-1
+      e = launch_gemm_batched(L + bs, ldl, false, sL, Li, ldi, true, sI, bs, bs, bs, 1.0, 0.0, work, bs, sW, full, s);
+      if (e != cudaSuccess) return e;
+      // Li[B_z, A_z] = -B_z^-1 X_z
+      e = launch_gemm_batched(Li + bs + ldi * (long long)bs, ldi, false, sI, work, bs, true, sW, bs, bs, bs, -1.0,
+                              0.0, Li + bs, ldi, sI, full, s);
+      if (e != cudaSuccess) return e;
+    }
+    // a ragged last merge (lower block shorter than bs)
+    const int b = full * 2 * bs;
+    if (b + bs < r) {
+      const int sa = bs, sb = r - (b + bs);
       e = launch_gemm(L + (b + bs) + ldl * (long long)b, ldl, false, Li + b + ldi * (long long)b, ldi, true, sb,
                       sa, sa, 1.0, 0.0, work, sb, false, 1, nullptr, false, s);
       if (e != cudaSuccess) return e;
-      // Li[B, A] = -B^-1 X
       e = launch_gemm(Li + (b + bs) + ldi * (long long)(b + bs), ldi, false, work, sb, true, sb, sa, sb, -1.0, 0.0,
                       Li + (b + bs) + ldi * (long long)b, ldi, false, 1, nullptr, false, s);
       if (e != cudaSuccess) return e;

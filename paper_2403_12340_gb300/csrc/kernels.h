@@ -44,6 +44,11 @@ cudaError_t launch_transpose(const double* src, long long lds, int M, int N, dou
                              long long ldd, cudaStream_t s);
 cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s);
 cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s);
+// batch independent GEMMs C_z = alpha op(A_z) op(B_z)^T + beta C_z, z < batch,
+// X_z = X + z * strideX (same layout conventions as launch_gemm)
+cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
+                                long long ldb, bool kb, long long sB, int M, int N, int K, double alpha, double beta,
+                                double* C, long long ldc, long long sC, int batch, cudaStream_t s);
 // Li = L^-1 for lower-triangular L (r x r), FP64; work >= (r/2 + 64)^2 doubles.
 cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li, long long ldi, double* work,
                                cudaStream_t s);
@@ -55,6 +60,15 @@ cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, 
 // lower_only: tiles above the diagonal (tile size `tile`) are read mirrored.
 cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
                                  double* C, long long ldc, bool lower_only, int tile, cudaStream_t s);
+
+// ---- k_chol_blocked.cu ----------------------------------------------------
+// Blocked Cholesky without pivoting of the symmetric n x n W (column-major,
+// lower part read) into L (may equal W).  *fail = -1 on success, else the
+// first column whose pivot is <= tol_rel * max(diag W) (later steps are
+// skipped).  dinv: 64 x 64 doubles of scratch; dmax: one double.
+cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
+                                    double* dinv, double* dmax, int* fail, double* pan, cudaStream_t s);
+// pan: n x 64 doubles of scratch (the solved panel).
 
 // ---- k_chol.cu ------------------------------------------------------------
 struct CholWork {

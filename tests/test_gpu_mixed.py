@@ -67,5 +67,6 @@ def test_mixed_intermediates_close_to_fp64():
     # theta: FP32-grade products; G also carries the FP32 FFT (~1e-6 relative)
     assert rel_fro(b["theta"], a["theta"]) < 1e-6
     assert rel_fro(b["G"], a["G"]) < 1e-5
-    assert rel_fro(b["D"][0], a["D"][0]) < 1e-6
+    # D is whitened with L^-1 on both sides: its error grows with kappa(L)^2
+    assert rel_fro(b["D"][0], a["D"][0]) < 1e-5
     assert rel_fro(b["K"][0], a["K"][0]) < 1e-5
