@@ -33,22 +33,40 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
 }
 
 // Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place and
-// write its inverse into dinv (bs x bs, ld CB).  One thread block; the FP64
-// pipe of one SM is the limit, so no FP64 work is repeated across threads:
-// the square root and the reciprocal of each pivot are taken once, and the
-// rank-1 updates touch only the lower triangle (thread (tx, ty) of a 16 x 16
-// layout owns rows tx + 16 a and columns ty + 16 b).
+// write its inverse into dinv (bs x bs, ld CB).  One thread block on one
+// SM, whose FP64 pipe (2 DFMA / clock) is the limit, so the kernel issues as
+// few FP64 warp instructions as it can:
+//  * the rank-1 update of step j touches only the m (m + 1) / 2 entries of
+//    the remaining lower triangle, packed densely over the threads through a
+//    table of (row, column) offsets, so no lane idles under a mask;
+//  * one reciprocal square root per pivot (thread 0), columns scaled by it;
+//  * the inverse by 16 x 16 blocks: the four diagonal blocks in parallel by
+//    forward substitution, then the off-diagonal blocks as products
+//    X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ in order of I - J, which keeps
+//    the dependent FMA chains 16 long instead of up to 2000.
+constexpr int TRI = CB * (CB - 1) / 2;  // entries of a strictly lower 63-row triangle
+
 __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int j0, int bs, double* dinv,
                                                   const double* dmax, double tol_rel, int* fail) {
   __shared__ double Ls[CB][CB + 1];
   __shared__ double Xs[CB][CB + 1];
   __shared__ double rdiag[CB];
+  __shared__ unsigned char ta[TRI], tb[TRI];
   __shared__ int s_bad;
   if (*(volatile int*)fail >= 0) return;
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int t = threadIdx.x;
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
     int i = idx & (CB - 1), k = idx >> 6;
     Ls[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
+    Xs[i][k] = 0.0;
+  }
+  // (a, b) with b <= a for the packed index a (a + 1) / 2 + b
+  for (int a = t; a < CB - 1; a += blockDim.x) {
+    const int base = a * (a + 1) / 2;
+    for (int b = 0; b <= a; ++b) {
+      ta[base + b] = (unsigned char)a;
+      tb[base + b] = (unsigned char)b;
+    }
   }
   if (t == 0) s_bad = -1;
   const double thresh = tol_rel * (*dmax);
@@ -59,9 +77,9 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
       if (!(d > thresh)) {  // also catches NaN
         s_bad = j;
       } else {
-        const double l = sqrt(d);
-        Ls[j][j] = l;
-        rdiag[j] = 1.0 / l;
+        const double ri = rsqrt(d);
+        Ls[j][j] = d * ri;
+        rdiag[j] = ri;
       }
     }
     __syncthreads();
@@ -69,17 +87,12 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
     const double r = rdiag[j];
     for (int i = j + 1 + t; i < bs; i += blockDim.x) Ls[i][j] *= r;
     __syncthreads();
-    // Ls[i][k] -= Ls[i][j] Ls[k][j] for j < k <= i < bs
-#pragma unroll
-    for (int a = 0; a < CB / 16; ++a) {
-      const int i = tx + 16 * a;
-      if (i <= j || i >= bs) continue;
-      const double lij = Ls[i][j];
-#pragma unroll
-      for (int b = 0; b < CB / 16; ++b) {
-        const int k = ty + 16 * b;
-        if (k > j && k <= i) Ls[i][k] = fma(-lij, Ls[k][j], Ls[i][k]);
-      }
+    // Ls[i][k] -= Ls[i][j] Ls[k][j] for j < k <= i < bs, packed
+    const int m = bs - j - 1;
+    const int cnt = m * (m + 1) / 2;
+    for (int idx = t; idx < cnt; idx += blockDim.x) {
+      const int i = j + 1 + ta[idx], k = j + 1 + tb[idx];
+      Ls[i][k] = fma(-Ls[i][j], Ls[k][j], Ls[i][k]);
     }
     __syncthreads();
   }
@@ -87,23 +100,42 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
     if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
     return;
   }
-  // inverse of the factor: column c by forward substitution (threads < bs),
-  // using the reciprocal pivots
-  if (t < bs) {
-    const int c = t;
-    for (int i = 0; i < c; ++i) Xs[i][c] = 0.0;
-    Xs[c][c] = rdiag[c];
-    for (int i = c + 1; i < bs; ++i) {
-      double acc = 0.0;
-      for (int k = c; k < i; ++k) acc = fma(Ls[i][k], Xs[k][c], acc);
-      Xs[i][c] = -acc * rdiag[i];
+  // inverse, step 1: the four diagonal 16 x 16 blocks (thread = block * 16 + column)
+  if (t < CB) {
+    const int o = (t >> 4) * 16, c = o + (t & 15);
+    if (c < bs) {
+      Xs[c][c] = rdiag[c];
+      for (int i = c + 1; i < o + 16 && i < bs; ++i) {
+        double acc = 0.0;
+        for (int k = c; k < i; ++k) acc = fma(Ls[i][k], Xs[k][c], acc);
+        Xs[i][c] = -acc * rdiag[i];
+      }
     }
   }
   __syncthreads();
+  // step 2: off-diagonal blocks by distance; thread (row u, col v) of a 16 x 16 block
+  const int u = t & 15, v = t >> 4;
+  for (int dist = 1; dist < 4; ++dist) {
+    for (int J = 0; J + dist < 4; ++J) {
+      const int I = J + dist;
+      // W = sum_{K=J}^{I-1} L_IK X_KJ  (16 x 16), then X_IJ = -X_II W
+      double w = 0.0;
+      for (int K = J; K < I; ++K)
+        for (int q = 0; q < 16; ++q) w = fma(Ls[I * 16 + u][K * 16 + q], Xs[K * 16 + q][J * 16 + v], w);
+      __syncthreads();
+      Ls[J * 16 + u][I * 16 + v] = w;  // scratch in the (unused) strict upper part
+      __syncthreads();
+      double x = 0.0;
+      for (int q = 0; q <= u; ++q) x = fma(Xs[I * 16 + u][I * 16 + q], Ls[J * 16 + q][I * 16 + v], x);
+      __syncthreads();
+      Xs[I * 16 + u][J * 16 + v] = -x;
+      __syncthreads();
+    }
+  }
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
     int i = idx % bs, k = idx / bs;
     A[(j0 + i) + lda * (long long)(j0 + k)] = (k <= i) ? Ls[i][k] : 0.0;
-    dinv[i + CB * k] = Xs[i][k];
+    dinv[i + CB * k] = (k <= i) ? Xs[i][k] : 0.0;
   }
 }
 

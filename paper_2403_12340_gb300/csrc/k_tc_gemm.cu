@@ -55,59 +55,92 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16
 
 // ------------------------------------------------------------- slicing
 
+// 8 consecutive values -> 8 BF16 of each of the s slices, one 16-byte store
+// per slice (dst must be 16-byte aligned).
+__device__ __forceinline__ void store_slices8(const double (&v)[8], __nv_bfloat16* dst, long long sstr, int s) {
+  __align__(16) __nv_bfloat16 x0[8], x1[8], x2[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) split3(v[q], x0[q], x1[q], x2[q]);
+  *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(x0);
+  if (s > 1) *reinterpret_cast<uint4*>(dst + sstr) = *reinterpret_cast<const uint4*>(x1);
+  if (s > 2) *reinterpret_cast<uint4*>(dst + 2 * sstr) = *reinterpret_cast<const uint4*>(x2);
+}
+
 // Column-major FP64 source (element (row, col) at src[row + lds col]) ->
 // slices dst[(l Rp + row) Kp + kmap(col)], kmap(col) = col for col < kv,
-// col - kv + kvp otherwise (kv = kvp = 0: identity).  Transposes through a
-// 32 x 32 shared tile so that both sides are coalesced.
-__global__ void k_slice_cm(const double* __restrict__ src, long long lds, int R, int C, int kv, int kvp,
-                           __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
-  __shared__ double t[32][33];
-  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    int r = r0 + threadIdx.x, c = c0 + k;
-    t[k][threadIdx.x] = (r < R && c < C) ? src[r + lds * (long long)c] : 0.0;
+// col - kv + kvp otherwise (kv = kvp = 0: identity).  64 x 64 tiles through
+// shared memory: coalesced FP64 loads down the columns, 16-byte slice stores
+// along the rows where the destination is 16-byte aligned (Kp % 8 == 0),
+// element stores elsewhere.
+__global__ void __launch_bounds__(256) k_slice_cm(const double* __restrict__ src, long long lds, int R, int C, int kv,
+                                                  int kvp, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+  __shared__ double t[64][65];
+  const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+    int rr = idx & 63, cc = idx >> 6;
+    int r = r0 + rr, c = c0 + cc;
+    t[cc][rr] = (r < R && c < C) ? src[r + lds * (long long)c] : 0.0;
   }
   __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    int r = r0 + k, c = c0 + threadIdx.x;
-    if (r >= R || c >= C) continue;
-    int kc = (c < kv) ? c : c - kv + kvp;
-    __nv_bfloat16 a, b, d;
-    split3(t[threadIdx.x][k], a, b, d);
-    long long base = (long long)r * Kp + kc;
-    dst[base] = a;
-    if (s > 1) dst[base + (long long)Rp * Kp] = b;
-    if (s > 2) dst[base + 2ll * Rp * Kp] = d;
+  const long long sstr = (long long)Rp * Kp;
+  for (int idx = threadIdx.x; idx < 64 * 8; idx += 256) {
+    const int rr = idx >> 3, ch = idx & 7;
+    const int r = r0 + rr, cb = c0 + ch * 8;
+    if (r >= R || cb >= C) continue;
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = t[ch * 8 + q][rr];
+    // a 16-byte store needs the whole chunk on one side of kv and, past kv,
+    // a shift kvp - kv that keeps the destination 8-aligned
+    const bool whole = cb + 8 <= C && (cb + 8 <= kv || (cb >= kv && ((kvp - kv) & 7) == 0));
+    if (whole) {
+      const int kc = (cb < kv) ? cb : cb - kv + kvp;
+      store_slices8(v, dst + (long long)r * Kp + kc, sstr, s);
+    } else {
+      for (int q = 0; q < 8 && cb + q < C; ++q) {
+        const int c = cb + q;
+        const int kc = (c < kv) ? c : c - kv + kvp;
+        __nv_bfloat16 a, b, d;
+        split3(v[q], a, b, d);
+        const long long base = (long long)r * Kp + kc;
+        dst[base] = a;
+        if (s > 1) dst[base + sstr] = b;
+        if (s > 2) dst[base + 2 * sstr] = d;
+      }
+    }
   }
 }
 
-// Row-major FP64 source (element (row, k) at src[k + lds row]) -> slices.
+// Row-major FP64 source (element (row, k) at src[k + lds row]) -> slices;
+// eight k per thread, 16-byte slice stores.
 __global__ void k_slice_rm(const double* __restrict__ src, long long lds, int R, int K,
                            __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
   const int row = blockIdx.y;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-    __nv_bfloat16 a, b, d;
-    split3(src[k + lds * (long long)row], a, b, d);
-    long long base = (long long)row * Kp + k;
-    dst[base] = a;
-    if (s > 1) dst[base + (long long)Rp * Kp] = b;
-    if (s > 2) dst[base + 2ll * Rp * Kp] = d;
+  const long long sstr = (long long)Rp * Kp;
+  const double* in = src + lds * (long long)row;
+  for (int k8 = (blockIdx.x * blockDim.x + threadIdx.x) * 8; k8 < K; k8 += gridDim.x * blockDim.x * 8) {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (k8 + q < K) ? in[k8 + q] : 0.0;
+    store_slices8(v, dst + (long long)row * Kp + k8, sstr, s);
   }
 }
 
 cudaError_t launch_slice_colmajor(const double* src, long long lds, int R, int C, int kv, int kvp,
                                   __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st) {
   if (R <= 0 || C <= 0) return cudaSuccess;
-  dim3 grid((R + 31) / 32, (C + 31) / 32), block(32, 8);
+  if (Kp % 8) return cudaErrorInvalidValue;
+  dim3 grid((R + 63) / 64, (C + 63) / 64);
   note_launch();
-  k_slice_cm<<<grid, block, 0, st>>>(src, lds, R, C, kv, kvp, dst, Rp, Kp, s);
+  k_slice_cm<<<grid, 256, 0, st>>>(src, lds, R, C, kv, kvp, dst, Rp, Kp, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K, __nv_bfloat16* dst, int Rp,
                                   int Kp, int s, cudaStream_t st) {
   if (R <= 0 || K <= 0) return cudaSuccess;
-  int bx = (K + 255) / 256;
+  if (Kp % 8 || Kp < (K + 7) / 8 * 8) return cudaErrorInvalidValue;
+  int bx = (K + 2047) / 2048;
   if (bx > 64) bx = 64;
   dim3 grid(bx, R);
   note_launch();
@@ -289,6 +322,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int i = 0; i < 16; ++i) v1[i] = 0.f;
       }
       if (m >= a.M) continue;
+      if (EPI == EPI_HAD_SLICES && n0 + c + 16 <= a.N) {
+        // whole 16-column chunk: two 16-byte stores per slice
+        const long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
+        __nv_bfloat16* dst = a.zs + (long long)m * a.zs_kp + n0 + c;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          double v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = (double)v0[8 * h + q] * (double)v1[8 * h + q];
+          store_slices8(v, dst + 8 * h, sstr, a.s);
+        }
+        continue;
+      }
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c + i;
