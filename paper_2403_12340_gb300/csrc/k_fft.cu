@@ -56,6 +56,28 @@ template <class C>
 __device__ __forceinline__ C csub(C a, C b) {
   return mk<C>(a.x - b.x, a.y - b.y);
 }
+// FP64 input to the transform precision; for FP32 by integer operations
+// (no FP64 instruction: GB300's FP64 pipe is 1/64 rate).
+template <class T>
+__device__ __forceinline__ T to_real(double x);
+template <>
+__device__ __forceinline__ double to_real<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float to_real<float>(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int ef = (int)((b >> 52) & 0x7FFull) - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
+  unsigned int bits = ((unsigned int)ef << 23) | (unsigned int)(m >> 29);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) bits += 1u;
+  return __uint_as_float(sign | bits);
+}
+
 template <class C>
 __device__ __forceinline__ C from_tw(const double2 w) {
   return mk<C>((typename Real<C>::T)w.x, (typename Real<C>::T)w.y);
@@ -220,7 +242,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd(FftGrid g, const dou
     int y0 = 2 * t, y1 = 2 * t + 1;
     double re = plane[x + sh.n1 * y0];
     double im = y1 < sh.n2 ? plane[x + sh.n1 * y1] : 0.0;
-    b0[t * sh.n1 + x] = mk<C>((T)re, (T)im);
+    b0[t * sh.n1 + x] = mk<C>(to_real<T>(re), to_real<T>(im));
   }
   __syncthreads();
   C* res = fft_lines<-1>(b0, b1, g.ax[0], twx, sh.npair, 1, sh.n1);
@@ -315,7 +337,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, typename Real<
   const int q0 = blockIdx.x * FFT_ZCHUNK, col = blockIdx.y;
   const int nq = min(FFT_ZCHUNK, plane - q0);
   for (int t = threadIdx.x; t < n3; t += blockDim.x) twz[t] = from_tw<C>(((const double2*)g.ax[2].tw)[t]);
-  C* base = (C*)(S + lds * (long long)col);
+  C* base = (C*)(S + lds * (long long)col);  // (twiddles: n3 conversions per block, negligible)
   for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
     int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
     b0[idx] = c < nq ? base[(long long)z * plane + q0 + c] : mk<C>((T)0, (T)0);
@@ -325,7 +347,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, typename Real<
   if (wt) {
     for (int idx = threadIdx.x; idx < n3 * FFT_ZCHUNK; idx += blockDim.x) {
       int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
-      T w = c < nq ? (T)wt[(long long)z * plane + q0 + c] : (T)0;
+      T w = c < nq ? to_real<T>(wt[(long long)z * plane + q0 + c]) : (T)0;
       R[idx] = mk<C>(R[idx].x * w, R[idx].y * w);
     }
     __syncthreads();
@@ -343,10 +365,11 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, typename Real<
       T v[2] = {R[idx].x, R[idx].y};
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        __nv_bfloat16 x0 = __float2bfloat16((float)v[h]);
-        float r1 = (float)v[h] - __bfloat162float(x0);
-        __nv_bfloat16 x1 = __float2bfloat16(r1);
-        __nv_bfloat16 x2 = __float2bfloat16(r1 - __bfloat162float(x1));
+        const float vf = (float)v[h];  // T is float on this path
+        __nv_bfloat16 x0 = __float2bfloat16_rn(vf);
+        float r1 = vf - __bfloat162float(x0);
+        __nv_bfloat16 x1 = __float2bfloat16_rn(r1);
+        __nv_bfloat16 x2 = __float2bfloat16_rn(r1 - __bfloat162float(x1));
         long long o = (long long)col * kp + k + h;
         out[o] = x0;
         if (nsl > 1) out[o + sstr] = x1;

@@ -43,12 +43,21 @@ __host__ __device__ inline int tc_stages(int s, int bn) {
   return st > 4 ? 4 : st;
 }
 
+// Three BF16 slices of an FP32 value: a = bf16(x), b = bf16(x - a),
+// c = bf16(x - a - b); the differences are exact in FP32, and a + b + c
+// carries the 24 bits of x.  FP64 inputs are first rounded to FP32 with
+// integer operations (no FP64 instructions on this path).
+__device__ __forceinline__ void split3f(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r);
+  c = __float2bfloat16_rn(r - __bfloat162float(b));
+}
 __device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(a);
-  b = __double2bfloat16(r);
-  r -= (double)__bfloat162float(b);
-  c = __double2bfloat16(r);
+  split3f(tc::d2f(x), a, b, c);
+}
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  split3f(x, a, b, c);
 }
 
 }  // namespace
@@ -57,7 +66,8 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16
 
 // 8 consecutive values -> 8 BF16 of each of the s slices, one 16-byte store
 // per slice (dst must be 16-byte aligned).
-__device__ __forceinline__ void store_slices8(const double (&v)[8], __nv_bfloat16* dst, long long sstr, int s) {
+template <class V>
+__device__ __forceinline__ void store_slices8(const V (&v)[8], __nv_bfloat16* dst, long long sstr, int s) {
   __align__(16) __nv_bfloat16 x0[8], x1[8], x2[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) split3(v[q], x0[q], x1[q], x2[q]);
@@ -157,9 +167,9 @@ __global__ void k_pair_slices(const double* __restrict__ phimu, long long ldp, i
   const int K = n_v * n_c;
   for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk < K; kk += gridDim.x * blockDim.x) {
     const int i = kk / n_c, j = kk - i * n_c;
-    const double v = phimu[a + ldp * i] * phimu[a + ldp * (long long)(n_v + j)] * sw[kk];
+    const float v = tc::d2f(phimu[a + ldp * i]) * tc::d2f(phimu[a + ldp * (long long)(n_v + j)]) * tc::d2f(sw[kk]);
     __nv_bfloat16 x0, x1, x2;
-    split3(v, x0, x1, x2);
+    split3f(v, x0, x1, x2);
     long long base = (long long)a * Kp + kk;
     dst[base] = x0;
     if (s > 1) dst[base + (long long)Rp * Kp] = x1;
@@ -328,9 +338,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __nv_bfloat16* dst = a.zs + (long long)m * a.zs_kp + n0 + c;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          double v[8];
+          float v[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = (double)v0[8 * h + q] * (double)v1[8 * h + q];
+          for (int q = 0; q < 8; ++q) v[q] = v0[8 * h + q] * v1[8 * h + q];
           store_slices8(v, dst + 8 * h, sstr, a.s);
         }
         continue;
@@ -339,19 +349,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c + i;
         if (n >= a.N) break;
-        double v = (NACC == 2) ? (double)v0[i] * (double)v1[i] : (double)v0[i];
+        const float vf = (NACC == 2) ? v0[i] * v1[i] : v0[i];
         if (EPI == EPI_HAD_SLICES) {
           __nv_bfloat16 x0, x1, x2;
-          split3(v, x0, x1, x2);
+          split3f(vf, x0, x1, x2);
           long long base = (long long)m * a.zs_kp + n;
           long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
           a.zs[base] = x0;
           if (a.s > 1) a.zs[base + sstr] = x1;
           if (a.s > 2) a.zs[base + 2 * sstr] = x2;
         } else if (a.partial) {
-          a.partial[(long long)blockIdx.z * a.M * a.N + m + (long long)a.M * n] = v;
+          a.partial[(long long)blockIdx.z * a.M * a.N + m + (long long)a.M * n] = tc::f2d(vf);
         } else {
-          double o = a.alpha * v;
+          // alpha = 1, beta = 0 (the common case) needs no FP64 arithmetic
+          double o = (a.alpha == 1.0) ? tc::f2d(vf) : a.alpha * tc::f2d(vf);
           if (a.beta != 0.0) o += a.beta * a.C[m + a.ldc * n];
           a.C[m + a.ldc * n] = o;
           if (a.lower_only && mt != nt) a.C[n + a.ldc * m] = o;

@@ -139,5 +139,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ---- FP64 <-> FP32 without the FP64 pipe ----------------------------------
+// GB300 runs FP64 arithmetic (conversions included) at 1/64 of the FP32
+// rate, so the slicing and epilogue code converts with integer operations on
+// the IEEE 754 bit patterns.  Round to nearest even; results below the FP32
+// normal range flush to zero and results above it become infinity (inputs
+// are finite and well inside the range: they are checked earlier).
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int ef = (int)((b >> 52) & 0x7FFull) - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
+  unsigned int bits = ((unsigned int)ef << 23) | (unsigned int)(m >> 29);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) bits += 1u;  // a carry moves into the exponent
+  return __uint_as_float(sign | bits);
+}
+// exact FP32 -> FP64 (zero and FP32 subnormals map to signed zero)
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned int b = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned int e = (b >> 23) & 0xFFu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 0xFFu) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull |
+                                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+  const unsigned long long ed = (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 }  // namespace tc
 }  // namespace isdf
