@@ -193,6 +193,14 @@ extern "C" int isdf_create(isdf_ctx** out, int n1, int n2, int n3, double L1, do
   c->d_wconv = c->d_tables + ntw + nh;
   e = cudaMalloc(&c->d_status, 64 * sizeof(unsigned));
   if (e != cudaSuccess) return bail(e, "cudaMalloc status");
+  {
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(e, "stream / event creation");
+  }
   c->d_bar = c->d_status + 8;
   c->d_ints = (int*)(c->d_status + 16);
   e = cudaMemset(c->d_status, 0, 64 * sizeof(unsigned));
@@ -204,11 +212,18 @@ extern "C" int isdf_create(isdf_ctx** out, int n1, int n2, int n3, double L1, do
 extern "C" int isdf_destroy(isdf_ctx* c) {
   if (!c) return ISDF_ERR_ARG;
   cudaStreamSynchronize(c->stream);
+  if (c->s2) {
+    cudaStreamSynchronize(c->s2);
+    cudaStreamDestroy(c->s2);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->d_fail) cudaFree(c->d_fail);
   DevBuf* bufs[] = {&c->phimu, &c->phimu_p, &c->A, &c->Lr, &c->Lc, &c->Bf, &c->chol_d, &c->chol_part,
                     &c->spec, &c->G, &c->D, &c->K, &c->R, &c->T, &c->W1, &c->Q, &c->partial,
                     &c->tmp1, &c->tmp2, &c->tmp3, &c->sw, &c->m_phis, &c->m_phimus, &c->m_zs, &c->m_linv,
                     &c->m_linvs, &c->m_work, &c->m_thetas_t, &c->m_s32, &c->m_ss, &c->m_pairs, &c->m_sa,
-                    &c->m_sb, &c->m_xs, &c->cb_work};
+                    &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw};
   for (DevBuf* b : bufs) release(*b);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
@@ -256,10 +271,22 @@ static int cholesky(isdf_ctx* c, const double* W, long long ldw, int n, int pivo
 // Blocked Cholesky (no pivoting) of W into Lout (ld n); *fail (device) = -1
 // on success, else the first column whose pivot fell to tol_rel * max diag.
 static int cholesky_blocked(isdf_ctx* c, const double* W, long long ldw, int n, double tol_rel, double* Lout,
-                            int* fail) {
-  CK(ensure(c->cb_work, 64 + 64 * 64 + (size_t)n * 64));
+                            int* fail, cudaStream_t st) {
   CK(launch_cholesky_blocked(W, ldw, n, tol_rel, Lout, n, c->cb_work.p + 64, c->cb_work.p, fail,
-                             c->cb_work.p + 64 + 64 * 64, c->stream));
+                             c->cb_work.p + 64 + 64 * 64, st));
+  return ISDF_OK;
+}
+
+// The main stream hands work to the second stream ...
+static int fork_s2(isdf_ctx* c) {
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+  return ISDF_OK;
+}
+// ... and everything queued on the main stream after this waits for it.
+static int join_s2(isdf_ctx* c) {
+  CK(cudaEventRecord(c->ev_join, c->s2));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   return ISDF_OK;
 }
 
@@ -301,16 +328,35 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   CK(ensure(c->Lc, (size_t)n_mu * n_mu));
   const double tol = (double)n_mu * 2.220446049250313e-16;
   int rc0 = ISDF_OK;
+  CK(ensure(c->cb_work, 64 + 64 * 64 + (size_t)n_mu * 64));
   {
-  PhaseScope ph(c, ISDF_PH_POINTS);
-  CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
-  CK(launch_facesplit_gram(c->phimu.p, n_mu, n_mu, c->phimu.p, n_mu, n_mu, n_v, n_e, c->A.p, n_mu,
-                           c->stream));
-  // Cholesky of C C^T in the given point order (blocked); if a pivot falls to
-  // the rank threshold, redo it with diagonal pivoting (rank-deficient C)
-  rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1);
-  if (rc0 != ISDF_OK) return rc0;
+    PhaseScope ph(c, ISDF_PH_POINTS);
+    CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
+    CK(launch_facesplit_gram(c->phimu.p, n_mu, n_mu, c->phimu.p, n_mu, n_mu, n_v, n_e, c->A.p, n_mu,
+                             c->stream));
   }
+  // Cholesky of C C^T in the given point order (blocked, on the second
+  // stream: it is a latency-bound FP64 chain); if a pivot falls to the rank
+  // threshold it is redone below with diagonal pivoting (rank-deficient C)
+  rc0 = fork_s2(c);
+  if (rc0 != ISDF_OK) return rc0;
+  {
+    PhaseScope ph(c, ISDF_PH_POINTS, c->s2);
+    rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1, c->s2);
+    if (rc0 != ISDF_OK) return rc0;
+  }
+  // meanwhile, speculatively, the face-split Gram M C^T with the points in
+  // the given order, which is the pivot order whenever the blocked
+  // factorisation succeeds
+  if (prec == ISDF_PREC_MIXED) {
+    CK(isdf::mixed_fit_gram(c, phi, c->phimu.p, n_v, n_c, n_mu));
+  } else {
+    PhaseScope ph(c, ISDF_PH_FIT_GRAM);
+    CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu.p, n_mu, n_mu, n_v, n_e, theta, c->n_r,
+                             c->stream));
+  }
+  rc0 = join_s2(c);
+  if (rc0 != ISDF_OK) return rc0;
   CK(cudaStreamSynchronize(c->stream));
   int rc;
   rc = check_status(c, "isdf_fit");
@@ -318,6 +364,7 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   int fail = 0, rank = 0;
   CK(cudaMemcpy(&fail, c->d_ints + 1, sizeof(int), cudaMemcpyDeviceToHost));
   c->perm.assign(n_mu, 0);
+  const bool gram_done = fail < 0;
   if (fail < 0) {
     rank = n_mu;
     for (int i = 0; i < n_mu; ++i) c->perm[i] = i;
@@ -353,11 +400,11 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     CK(ensure(c->phimu_p, (size_t)r * n_e));
     CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
     if (prec == ISDF_PREC_MIXED) {
-      CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
-      CK(isdf::mixed_fit(c, phi, theta, n_v, n_c, r));
+      if (!gram_done) CK(isdf::mixed_fit_gram(c, phi, c->phimu_p.p, n_v, n_c, r));
+      CK(isdf::mixed_fit_solve(c, theta, r));
     } else {
       // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
-      {
+      if (!gram_done) {
         PhaseScope ph(c, ISDF_PH_FIT_GRAM);
         CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
                                  c->stream));
@@ -433,6 +480,15 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
   CK(ensure(c->G, std::max<size_t>(rr, 1)));
   CK(ensure(c->D, std::max<size_t>(rr * n_omega, 1)));
   CK(ensure(c->K, std::max<size_t>(rr * n_omega, 1)));
+  CK(ensure(c->Rw, std::max<size_t>(rr * n_omega, 1)));
+  CK(ensure(c->cb_work, 64 + 64 * 64 + (size_t)std::max(r, 1) * 64));
+  if (c->cap_fail < (size_t)n_omega) {
+    if (c->d_fail) cudaFree(c->d_fail);
+    c->d_fail = nullptr;
+    c->cap_fail = 0;
+    CK(cudaMalloc(&c->d_fail, n_omega * sizeof(int)));
+    c->cap_fail = n_omega;
+  }
   if (r > 0) {
     // G = theta^T V theta = S^T S with S the weighted half spectrum (Parseval)
     const long long lds = 2 * c->n_half;
@@ -457,34 +513,51 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
         }
     }
     CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // D(w) for every frequency (main stream)
     if (c->prec == ISDF_PREC_MIXED) {
-      CK(isdf::mixed_polar(c, c->sw.p, n_omega));
+      CK(isdf::mixed_polar_D(c, c->sw.p, n_omega));
     } else {
-    {
-      PhaseScope ph(c, ISDF_PH_FFT);
-      CK(launch_fft_forward(c->fft, c->theta, c->n_r, r, c->spec.p, lds, c->d_wsyrk, c->smem_xy,
-                            c->smem_z, c->stream));
-    }
-    {
-      PhaseScope ph(c, ISDF_PH_SYRK_G);
-      CK(launch_gemm(c->spec.p, lds, true, c->spec.p, lds, true, r, r, (int)lds, 1.0, 0.0, c->G.p, r,
-                     true, sp, c->partial.p, false, c->stream));
-    }
-    // D(w) = L_r^-1 (-2 C_r Omega(iw)^-1 C_r^T) L_r^-T
-    for (int k = 0; k < n_omega; ++k) {
-      double* Dk = c->D.p + rr * k;
-      {
-        PhaseScope ph(c, ISDF_PH_POLAR_D);
-        CK(launch_polarizability(c->phimu_p.p, r, r, n_v, n_c, c->sw.p + npair * k, Dk, r, spd,
-                                 c->partial.p, c->stream));
+      for (int k = 0; k < n_omega; ++k) {
+        double* Dk = c->D.p + rr * k;
+        {
+          PhaseScope ph(c, ISDF_PH_POLAR_D);
+          CK(launch_polarizability(c->phimu_p.p, r, r, n_v, n_c, c->sw.p + npair * k, Dk, r, spd, c->partial.p,
+                                   c->stream));
+        }
+        PhaseScope ph(c, ISDF_PH_WHITEN_D);
+        CK(launch_trsm_right_lt(Dk, r, r, c->Bf.p, r, r, c->stream));
+        CK(launch_transpose(Dk, r, r, r, c->tmp1.p, r, c->stream));
+        CK(launch_trsm_right_lt(c->tmp1.p, r, r, c->Bf.p, r, r, c->stream));
+        CK(launch_symmetrize(c->tmp1.p, r, r, c->stream));
+        CK(cudaMemcpyAsync(Dk, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       }
-      PhaseScope ph(c, ISDF_PH_WHITEN_D);
-      CK(launch_trsm_right_lt(Dk, r, r, c->Bf.p, r, r, c->stream));
-      CK(launch_transpose(Dk, r, r, r, c->tmp1.p, r, c->stream));
-      CK(launch_trsm_right_lt(c->tmp1.p, r, r, c->Bf.p, r, r, c->stream));
-      CK(launch_symmetrize(c->tmp1.p, r, r, c->stream));
-      CK(cudaMemcpyAsync(Dk, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
+    // D(w) = R R^T on the second stream, beside the Coulomb work below
+    {
+      int rc0 = fork_s2(c);
+      if (rc0 != ISDF_OK) return rc0;
+      PhaseScope ph(c, ISDF_PH_SMW, c->s2);
+      for (int k = 0; k < n_omega; ++k) {
+        rc0 = cholesky_blocked(c, c->D.p + rr * k, r, r, 0.0, c->Rw.p + rr * k, c->d_fail + k, c->s2);
+        if (rc0 != ISDF_OK) return rc0;
+      }
+    }
+    // G = theta^T V theta (main stream)
+    if (c->prec == ISDF_PREC_MIXED) {
+      CK(isdf::mixed_polar_G(c));
+    } else {
+      {
+        PhaseScope ph(c, ISDF_PH_FFT);
+        CK(launch_fft_forward(c->fft, c->theta, c->n_r, r, c->spec.p, lds, c->d_wsyrk, c->smem_xy, c->smem_z,
+                              c->stream));
+      }
+      PhaseScope ph(c, ISDF_PH_SYRK_G);
+      CK(launch_gemm(c->spec.p, lds, true, c->spec.p, lds, true, r, r, (int)lds, 1.0, 0.0, c->G.p, r, true, sp,
+                     c->partial.p, false, c->stream));
+    }
+    {
+      int rc0 = join_s2(c);
+      if (rc0 != ISDF_OK) return rc0;
     }
   }
   if (G_out) {
@@ -525,9 +598,9 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
     CK(ensure(c->partial, (size_t)sp * rr));
     CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
     PhaseScope ph(c, ISDF_PH_SMW);
-    // D = R R^T
-    int rc = cholesky_blocked(c, c->D.p + rr * k, r, r, 0.0, c->R.p, c->d_ints + 2);
-    if (rc != ISDF_OK) return rc;
+    // D = R R^T: factored by build_polarizability on the second stream
+    int rc;
+    CK(cudaMemcpyAsync(c->R.p, c->Rw.p + rr * k, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     // T = I + R^T G R
     CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
     CK(launch_add_identity(c->T.p, r, r, 1.0, c->stream));
@@ -541,7 +614,7 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
       CK(launch_symmetrize(c->T.p, r, r, c->stream));
     }
     // T = U U^T; Q = R U^-T; K = -Q Q^T
-    rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, c->d_ints + 3);
+    rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, c->d_ints + 3, c->stream);
     if (rc != ISDF_OK) return rc;
     if (c->prec == ISDF_PREC_MIXED) {
       CK(isdf::mixed_smw_products_K(c, Kk));
@@ -564,7 +637,8 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
   if (rc != ISDF_OK) return rc;
   if (r > 0) {
     int fails[2] = {-1, -1};
-    CK(cudaMemcpy(fails, c->d_ints + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&fails[0], c->d_fail + k, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&fails[1], c->d_ints + 3, sizeof(int), cudaMemcpyDeviceToHost));
     if (fails[0] >= 0 || fails[1] >= 0)
       return fail(c, ISDF_ERR_NOT_SPD, "smw_inverse: capacitance factor not positive definite");
   }
@@ -613,8 +687,8 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
     int sp = sp0;  // nc <= nc0: the same split fits the partial buffer
     CK(launch_gemm(c->theta, nr, true, Xc, nr, true, r, nc, (int)nr, 1.0, 0.0, c->tmp1.p, r, false, sp,
                    c->partial.p, true, c->stream));
-    CK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 1, nullptr,
-                   true, c->stream));
+    CK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false,
+                   std::min(sp, 16), c->partial.p, true, c->stream));
     CK(launch_gemm(c->theta, nr, false, c->tmp2.p, r, true, (int)nr, nc, r, 1.0, 0.0, c->tmp3.p, nr,
                    false, 1, nullptr, true, c->stream));
     CK(launch_fft_convolve(c->fft, c->tmp3.p, nr, nc, c->spec.p, lds, c->d_wconv, Xc, nr, Yc, nr,

@@ -66,6 +66,13 @@ struct isdf_ctx {
 
   // mixed precision (ISDF_PREC_MIXED): BF16 slice matrices and FP64 helpers
   int prec = 0;
+  // second stream for the latency-bound FP64 factorisations, run beside the
+  // tensor-core / FFT work of the main stream; fork / join by events
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  DevBuf Rw;             // Cholesky factors of D(w), one r x r block per frequency
+  int* d_fail = nullptr; // their failure flags
+  size_t cap_fail = 0;
   DevBuf cb_work;  // blocked Cholesky: [0] max diagonal, [64..] 64 x 64 inverse block
   DevBuf m_phis, m_phimus, m_zs, m_linv, m_linvs, m_work, m_thetas_t, m_s32, m_ss, m_pairs, m_sa, m_sb, m_xs;
 
@@ -99,11 +106,13 @@ inline cudaEvent_t take_event(isdf_ctx* c) {
 struct PhaseTimer {
   isdf_ctx* c;
   int ph;
+  cudaStream_t st;
   cudaEvent_t e0 = nullptr;
-  PhaseTimer(isdf_ctx* ctx, int phase) : c(ctx), ph(phase) {
+  PhaseTimer(isdf_ctx* ctx, int phase, cudaStream_t stream = nullptr)
+      : c(ctx), ph(phase), st(stream ? stream : ctx->stream) {
     if (!c->prof_on) return;
     e0 = take_event(c);
-    if (e0) cudaEventRecord(e0, c->stream);
+    if (e0) cudaEventRecord(e0, st);
   }
   ~PhaseTimer() {
     if (!e0) return;
@@ -112,14 +121,16 @@ struct PhaseTimer {
       c->ev_pool.push_back(e0);
       return;
     }
-    cudaEventRecord(e1, c->stream);
+    cudaEventRecord(e1, st);
     c->prof_ev.push_back({ph, {e0, e1}});
   }
 };
 
 // mixed.cu
-cudaError_t mixed_fit(isdf_ctx* c, const double* phi, double* theta, int n_v, int n_c, int r);
-cudaError_t mixed_polar(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p, int n_v, int n_c, int r);
+cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r);
+cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_polar_G(isdf_ctx* c);
 cudaError_t mixed_smw_products_T(isdf_ctx* c);
 cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk);
 cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc);

@@ -133,10 +133,12 @@ cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, 
 // Eq. Hadamard), with A = B = Phi at the points it is C C^T.
 __global__ void __launch_bounds__(256) k_facesplit_gram(Operand<false> A, Operand<false> B, int n_v,
                                                         int n_e, double* __restrict__ C,
-                                                        long long ldc) {
+                                                        long long ldc, int sym) {
   using T = TileSq;
   __shared__ T::Smem s;
-  const int m0 = blockIdx.x * T::kBM, n0 = blockIdx.y * T::kBN;
+  int mt = blockIdx.x, nt = blockIdx.y;
+  if (sym) lower_tile(blockIdx.x, mt, nt);  // A == B: lower tiles, mirrored
+  const int m0 = mt * T::kBM, n0 = nt * T::kBN;
   double av[T::kTM][T::kTN], ac[T::kTM][T::kTN];
   zero_acc<T>(av);
   zero_acc<T>(ac);
@@ -149,7 +151,11 @@ __global__ void __launch_bounds__(256) k_facesplit_gram(Operand<false> A, Operan
 #pragma unroll
     for (int i = 0; i < T::kTM; ++i) {
       int m = tile_row<T>(m0, i);
-      if (m < A.rows) C[m + ldc * n] = av[i][j] * ac[i][j];
+      if (m < A.rows) {
+        const double v = av[i][j] * ac[i][j];
+        C[m + ldc * n] = v;
+        if (sym && mt != nt) C[n + ldc * m] = v;
+      }
     }
   }
 }
@@ -158,10 +164,12 @@ cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const d
                                   long long ldb, int N, int n_v, int n_e, double* C, long long ldc,
                                   cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((M + 63) / 64, (N + 63) / 64);
+  const bool sym = (A == B && lda == ldb && M == N);
+  const int tm = (M + 63) / 64;
+  dim3 grid = sym ? dim3(tm * (tm + 1) / 2, 1) : dim3(tm, (N + 63) / 64);
   note_launch();
   k_facesplit_gram<<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v,
-                                        n_e, C, ldc);
+                                        n_e, C, ldc, sym ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -190,7 +198,7 @@ __device__ __forceinline__ void store_tile(const double (&acc)[T::kTM][T::kTN], 
 template <class T, class OpA, class OpB>
 __global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int K, int klen,
                                                 double alpha, double beta, double* C, long long ldc,
-                                                double* partial, int lower_only) {
+                                                double* partial, int lower_only, int tri) {
   __shared__ typename T::Smem s;
   int mt, nt;
   if (lower_only) {
@@ -200,8 +208,12 @@ __global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int 
     nt = blockIdx.y;
   }
   const int m0 = mt * T::kBM, n0 = nt * T::kBN;
-  const int kbeg = blockIdx.z * klen;
-  const int kend = min(K, kbeg + klen);
+  int kbeg = blockIdx.z * klen;
+  int kend = min(K, kbeg + klen);
+  // triangular factors: op(B)(n, k) = 0 for k < n (TRI_B_LOWER_T) or
+  // op(A)(m, k) = 0 for k > m (TRI_A_LOWER): skip those k
+  if (tri & TRI_B_LOWER_T) kbeg = max(kbeg, n0);
+  if (tri & TRI_A_LOWER) kend = min(kend, m0 + T::kBM);
   double acc[T::kTM][T::kTN];
   zero_acc<T>(acc);
   gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
@@ -236,38 +248,40 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, 
 template <class T, class OpA, class OpB>
 __global__ void __launch_bounds__(T::NT) k_gemm_batched(OpA A, OpB B, long long sA, long long sB, int M, int N,
                                                         int K, double alpha, double beta, double* C, long long ldc,
-                                                        long long sC) {
+                                                        long long sC, int tri) {
   __shared__ typename T::Smem s;
   const int z = blockIdx.z;
   A.p += sA * z;
   B.p += sB * z;
   C += sC * z;
   const int m0 = blockIdx.x * T::kBM, n0 = blockIdx.y * T::kBN;
+  const int kbeg = (tri & TRI_B_LOWER_T) ? min(n0, K) : 0;
+  const int kend = (tri & TRI_A_LOWER) ? min(K, m0 + T::kBM) : K;
   double acc[T::kTM][T::kTN];
   zero_acc<T>(acc);
-  gemm_mainloop<T>(acc, s, A, B, m0, n0, 0, K);
+  gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
   store_tile<T>(acc, m0, n0, M, N, alpha, beta, C, ldc, false);
 }
 
 template <class T, bool KA, bool KB>
 static cudaError_t gemm_batched_dispatch(const double* A, long long lda, long long sA, const double* B, long long ldb,
                                          long long sB, int M, int N, int K, double alpha, double beta, double* C,
-                                         long long ldc, long long sC, int batch, cudaStream_t s) {
+                                         long long ldc, long long sC, int batch, int tri, cudaStream_t s) {
   dim3 grid((M + T::kBM - 1) / T::kBM, (N + T::kBN - 1) / T::kBN, batch);
   note_launch();
   k_gemm_batched<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(Operand<KA>{A, lda, M}, Operand<KB>{B, ldb, N},
-                                                                    sA, sB, M, N, K, alpha, beta, C, ldc, sC);
+                                                                    sA, sB, M, N, K, alpha, beta, C, ldc, sC, tri);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
                                 long long ldb, bool kb, long long sB, int M, int N, int K, double alpha, double beta,
-                                double* C, long long ldc, long long sC, int batch, cudaStream_t s) {
+                                double* C, long long ldc, long long sC, int batch, cudaStream_t s, int tri) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   const long long t64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * batch;
   const bool small = t64 < 2 * 152;
 #define ISDF_BGEMM_CASE(TT, a, b) \
-  if (ka == a && kb == b) return gemm_batched_dispatch<TT, a, b>(A, lda, sA, B, ldb, sB, M, N, K, alpha, beta, C, ldc, sC, batch, s);
+  if (ka == a && kb == b) return gemm_batched_dispatch<TT, a, b>(A, lda, sA, B, ldb, sB, M, N, K, alpha, beta, C, ldc, sC, batch, tri, s);
   if (small) {
     ISDF_BGEMM_CASE(TileSm, false, false)
     ISDF_BGEMM_CASE(TileSm, false, true)
@@ -295,7 +309,7 @@ cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N
 template <class T, bool KA, bool KB>
 static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B, long long ldb, int M,
                                  int N, int K, double alpha, double beta, double* C, long long ldc,
-                                 bool lower_only, int splits, double* partial, cudaStream_t s) {
+                                 bool lower_only, int splits, double* partial, int tri, cudaStream_t s) {
   Operand<KA> oa{A, lda, M};
   Operand<KB> ob{B, ldb, N};
   int tm = (M + T::kBM - 1) / T::kBM, tn = (N + T::kBN - 1) / T::kBN;
@@ -314,7 +328,7 @@ static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B
   note_launch();
   k_gemm<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
                                                             use_partial ? partial : nullptr,
-                                                            lower_only ? 1 : 0);
+                                                            lower_only ? 1 : 0, tri);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !use_partial) return e;
   dim3 rg((M + 127) / 128, N);
@@ -327,14 +341,14 @@ static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B
 cudaError_t launch_gemm(const double* A, long long lda, bool ka, const double* B, long long ldb,
                         bool kb, int M, int N, int K, double alpha, double beta, double* C,
                         long long ldc, bool lower_only, int splits, double* partial, bool narrow,
-                        cudaStream_t s) {
+                        cudaStream_t s, int tri) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (splits > 1 && !partial) return cudaErrorInvalidValue;
   if (lower_only && (M != N || narrow)) return cudaErrorInvalidValue;
 #define ISDF_GEMM_CASE(TT, a, b)                                                                 \
   if (ka == a && kb == b)                                                                        \
     return gemm_dispatch<TT, a, b>(A, lda, B, ldb, M, N, K, alpha, beta, C, ldc, lower_only,     \
-                                   splits, partial, s);
+                                   splits, partial, tri, s);
   // too few 64 x 64 tiles to fill the GPU twice: use 32 x 32 tiles (4x the blocks)
   const long long t64 = lower_only ? (long long)((M + 63) / 64) * ((M + 63) / 64 + 1) / 2
                                    : (long long)((M + 63) / 64) * ((N + 63) / 64);
@@ -544,7 +558,7 @@ namespace isdf {
 // for block sizes 64, 128, 256, ... (two GEMMs per merge, all merges of one
 // level independent).  work: (r/2 + 64)^2 doubles.
 cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li, long long ldi, double* work,
-                               cudaStream_t s) {
+                               double* partial, cudaStream_t s) {
   if (r <= 0) return cudaSuccess;
   cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, r * sizeof(double), r, s);
   if (e != cudaSuccess) return e;
@@ -557,23 +571,25 @@ cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li
     const int full = r / (2 * bs);
     if (full > 0) {
       const long long sL = 2ll * bs * (1 + ldl), sI = 2ll * bs * (1 + ldi), sW = (long long)bs * bs;
-      // X_z (bs x bs) = C_z A_z^-1
-      e = launch_gemm_batched(L + bs, ldl, false, sL, Li, ldi, true, sI, bs, bs, bs, 1.0, 0.0, work, bs, sW, full, s);
+      // X_z (bs x bs) = C_z A_z^-1 (A_z^-1 lower: k >= n)
+      e = launch_gemm_batched(L + bs, ldl, false, sL, Li, ldi, true, sI, bs, bs, bs, 1.0, 0.0, work, bs, sW, full, s,
+                              TRI_B_LOWER_T);
       if (e != cudaSuccess) return e;
-      // Li[B_z, A_z] = -B_z^-1 X_z
+      // Li[B_z, A_z] = -B_z^-1 X_z (B_z^-1 lower: k <= m)
       e = launch_gemm_batched(Li + bs + ldi * (long long)bs, ldi, false, sI, work, bs, true, sW, bs, bs, bs, -1.0,
-                              0.0, Li + bs, ldi, sI, full, s);
+                              0.0, Li + bs, ldi, sI, full, s, TRI_A_LOWER);
       if (e != cudaSuccess) return e;
     }
     // a ragged last merge (lower block shorter than bs)
     const int b = full * 2 * bs;
     if (b + bs < r) {
       const int sa = bs, sb = r - (b + bs);
+      const int sp = partial ? 4 : 1;
       e = launch_gemm(L + (b + bs) + ldl * (long long)b, ldl, false, Li + b + ldi * (long long)b, ldi, true, sb,
-                      sa, sa, 1.0, 0.0, work, sb, false, 1, nullptr, false, s);
+                      sa, sa, 1.0, 0.0, work, sb, false, sp, partial, false, s, TRI_B_LOWER_T);
       if (e != cudaSuccess) return e;
       e = launch_gemm(Li + (b + bs) + ldi * (long long)(b + bs), ldi, false, work, sb, true, sb, sa, sb, -1.0, 0.0,
-                      Li + (b + bs) + ldi * (long long)b, ldi, false, 1, nullptr, false, s);
+                      Li + (b + bs) + ldi * (long long)b, ldi, false, sp, partial, false, s, TRI_A_LOWER);
       if (e != cudaSuccess) return e;
     }
   }

@@ -25,10 +25,13 @@ cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const d
 // lower_only: M == N, only lower tiles are computed and mirrored (SYRK).
 // splits > 1 needs `partial` of splits * M * N doubles (deterministic reduce).
 // narrow: 128 x 16 tiles (N small) instead of 64 x 64.
+// tri: TRI_B_LOWER_T (op(B)(n, k) = 0 for k < n) and / or TRI_A_LOWER
+// (op(A)(m, k) = 0 for k > m): the zero k blocks are skipped.
+enum { TRI_B_LOWER_T = 1, TRI_A_LOWER = 2 };
 cudaError_t launch_gemm(const double* A, long long lda, bool ka, const double* B, long long ldb,
                         bool kb, int M, int N, int K, double alpha, double beta, double* C,
                         long long ldc, bool lower_only, int splits, double* partial, bool narrow,
-                        cudaStream_t s);
+                        cudaStream_t s, int tri = 0);
 // D (r x r, symmetric) = sum_{i<n_v, j<n_c} S(:, ij) S(:, ij)^T with
 // S(a, ij) = phimu(a, i) phimu(a, n_v + j) sw[i n_c + j]; phimu r x n_e.
 cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int n_v, int n_c,
@@ -48,10 +51,11 @@ cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaS
 // X_z = X + z * strideX (same layout conventions as launch_gemm)
 cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
                                 long long ldb, bool kb, long long sB, int M, int N, int K, double alpha, double beta,
-                                double* C, long long ldc, long long sC, int batch, cudaStream_t s);
-// Li = L^-1 for lower-triangular L (r x r), FP64; work >= (r/2 + 64)^2 doubles.
+                                double* C, long long ldc, long long sC, int batch, cudaStream_t s, int tri = 0);
+// Li = L^-1 for lower-triangular L (r x r), FP64; work >= (r/2 + 64)^2
+// doubles; partial (may be null) >= 4 (r/2 + 64)^2 doubles for split-K.
 cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li, long long ldi, double* work,
-                               cudaStream_t s);
+                               double* partial, cudaStream_t s);
 // L (n_full x n_full column-major) from the row-major pivoted factor Lr.
 cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
                                       double* L, long long ldl, int n_full, cudaStream_t s);

@@ -58,28 +58,35 @@ inline TcOperand op(const DevBuf& b, int rows_pad, int kp) { return TcOperand{b.
     if (_e != cudaSuccess) return _e;                   \
   } while (0)
 
-// theta (N_r x r, ld N_r) from the pivot-ordered point orbitals (c->phimu_p)
-// and the Cholesky factor c->Lc (r x r, ld r).
-cudaError_t mixed_fit(isdf_ctx* c, const double* phi, double* theta, int n_v, int n_c, int r) {
+// Slices of M C_r^T (the face-split Gram of the fit) into c->m_zs, from the
+// orbitals at the r points in pivot order (phimu_p, r x n_e, ld r).
+cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p, int n_v, int n_c, int r) {
   cudaStream_t st = c->stream;
   const long long nr = c->n_r;
   const int n_e = n_v + n_c;
   const int kvp = pad(n_v, 64), kp = kvp + pad(n_c, 64);
   const int nrp = pad(nr, 128), rp = pad(r, 128), rk = pad(r, 64);
-  {
-    PhaseTimer ph(c, ISDF_PH_FIT_GRAM);
-    MK(slices_cm(c->m_phis, phi, nr, (int)nr, n_e, nrp, kp, st, n_v, kvp));
-    MK(slices_cm(c->m_phimus, c->phimu_p.p, r, r, n_e, rp, kp, st, n_v, kvp));
-    const size_t nz = (size_t)NSL * nrp * rk;
-    MK(ensure_bf16(c->m_zs, nz));
-    MK(cudaMemsetAsync(c->m_zs.p, 0, nz * 2, st));
-    MK(tc_facesplit(op(c->m_phis, nrp, kp), op(c->m_phimus, rp, kp), (int)nr, r, kvp / 64, nullptr, 0,
-                    c->m_zs.bf(), nrp, rk, c->d_status, st));
-  }
+  PhaseTimer ph(c, ISDF_PH_FIT_GRAM);
+  MK(slices_cm(c->m_phis, phi, nr, (int)nr, n_e, nrp, kp, st, n_v, kvp));
+  MK(slices_cm(c->m_phimus, phimu_p, r, r, n_e, rp, kp, st, n_v, kvp));
+  const size_t nz = (size_t)NSL * nrp * rk;
+  MK(ensure_bf16(c->m_zs, nz));
+  MK(cudaMemsetAsync(c->m_zs.p, 0, nz * 2, st));
+  return tc_facesplit(op(c->m_phis, nrp, kp), op(c->m_phimus, rp, kp), (int)nr, r, kvp / 64, nullptr, 0,
+                      c->m_zs.bf(), nrp, rk, c->d_status, st);
+}
+
+// theta (N_r x r, ld N_r) = (M C_r^T) L^-T from c->m_zs and the Cholesky
+// factor c->Lc (r x r, ld r).
+cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r) {
+  cudaStream_t st = c->stream;
+  const long long nr = c->n_r;
+  const int nrp = pad(nr, 128), rp = pad(r, 128), rk = pad(r, 64);
   PhaseTimer ph(c, ISDF_PH_FIT_TRSM);
   MK(ensure(c->m_linv, (size_t)r * r));
-  MK(ensure(c->m_work, (size_t)(r / 2 + 64) * (r / 2 + 64)));
-  MK(launch_tri_inverse(c->Lc.p, r, r, c->m_linv.p, r, c->m_work.p, st));
+  const size_t wq = (size_t)(r / 2 + 64) * (r / 2 + 64);
+  MK(ensure(c->m_work, 5 * wq));
+  MK(launch_tri_inverse(c->Lc.p, r, r, c->m_linv.p, r, c->m_work.p, c->m_work.p + wq, st));
   MK(slices_cm(c->m_linvs, c->m_linv.p, r, r, r, rp, rk, st));
   MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, 1.0, 0.0, theta, nr, false, true,
                  nullptr, 1, c->num_sms, c->d_status, st));
@@ -89,15 +96,14 @@ cudaError_t mixed_fit(isdf_ctx* c, const double* phi, double* theta, int n_v, in
   return cudaSuccess;
 }
 
-// G (r x r) and D(w_k) for all frequencies, whitened, into c->G and c->D.
-cudaError_t mixed_polar(isdf_ctx* c, const double* sw, int n_omega) {
+// G = theta^T V theta (r x r) into c->G.
+cudaError_t mixed_polar_G(isdf_ctx* c) {
   cudaStream_t st = c->stream;
-  const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
+  const int r = c->rank;
   const size_t rr = (size_t)r * r;
-  const int rp = pad(r, 128), rk = pad(r, 64);
+  const int rp = pad(r, 128);
   const long long lds32 = 2 * c->n_half;
   const int kps = pad(lds32, 64);
-  const int npair = n_v * n_c, kpp = pad(npair, 64);
   const int max_split = 8;
   MK(ensure(c->partial, (size_t)max_split * rr));
   {
@@ -114,6 +120,18 @@ cudaError_t mixed_polar(isdf_ctx* c, const double* sw, int n_omega) {
     MK(tc_gemm_f64(op(c->m_ss, rp, kps), op(c->m_ss, rp, kps), r, r, 1.0, 0.0, c->G.p, r, true, false,
                    c->partial.p, max_split, c->num_sms, c->d_status, st));
   }
+  return cudaSuccess;
+}
+
+// D(w_k) for all frequencies, whitened, into c->D.
+cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
+  const size_t rr = (size_t)r * r;
+  const int rp = pad(r, 128), rk = pad(r, 64);
+  const int npair = n_v * n_c, kpp = pad(npair, 64);
+  const int max_split = 8;
+  MK(ensure(c->partial, (size_t)max_split * rr));
   MK(ensure(c->tmp1, rr));
   MK(ensure(c->tmp2, rr));
   const size_t np = (size_t)NSL * rp * kpp;
@@ -164,9 +182,10 @@ cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk) {
   const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
   const size_t rr = (size_t)r * r;
   const int max_split = 8;
-  MK(ensure(c->m_work, (size_t)(r / 2 + 64) * (r / 2 + 64)));
+  const size_t wq = (size_t)(r / 2 + 64) * (r / 2 + 64);
+  MK(ensure(c->m_work, 5 * wq));
   MK(ensure(c->partial, (size_t)max_split * rr));
-  MK(launch_tri_inverse(c->W1.p, r, r, c->Q.p, r, c->m_work.p, st));  // Q <- U^-1
+  MK(launch_tri_inverse(c->W1.p, r, r, c->Q.p, r, c->m_work.p, c->m_work.p + wq, st));  // Q <- U^-1
   MK(slices_cm(c->m_sa, c->R.p, r, r, r, rp, rk, st));
   MK(slices_cm(c->m_sb, c->Q.p, r, r, r, rp, rk, st));
   MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sb, rp, rk), r, r, 1.0, 0.0, c->Q.p, r, false, true, nullptr, 1,
@@ -193,7 +212,8 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
   MK(tc_gemm_f64(op(c->m_thetas_t, rp, kpg), op(c->m_xs, ncp, kpg), r, nc, 1.0, 0.0, c->tmp1.p, r, false, false,
                  c->partial.p, max_split, c->num_sms, c->d_status, st));
   // T2 = K T1 (FP64, small)
-  MK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 1, nullptr, true, st));
+  MK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 16, c->partial.p, true,
+                 st));
   // T3 = theta T2
   MK(slices_rm(c->m_xs, c->tmp2.p, r, nc, r, ncp, rk, st));
   MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_xs, ncp, rk), (int)nr, nc, 1.0, 0.0, c->tmp3.p, nr, false, false,
