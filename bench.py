@@ -45,13 +45,57 @@ N_RHS = 16
 # throughput microbenchmark on this machine measured 1.20 TFLOP/s at ~1.97 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
-# DRAM traffic per launch of the dominant kernels, from one ncu capture of
-# this workload (profiles/fp64_kernels_isdf48.md); None until captured or
-# once the kernel has changed since.
-NCU_DRAM_BYTES = {
-    # k_gemm<Tile<64,64,4,4>, K-contiguous x2> (G = S^T S): read 2.829616 GB + write 0.021971 GB
-    "coulomb_syrk": 2.851587e9,
-}
+
+def measured_peaks():
+    """HBM copy bandwidth and BF16 dense GEMM rate measured on this GPU type
+    (MEASURED_PEAKS.json beside this file), else the stated fallback."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "of measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of fallback"}
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the kernel a roofline cell names, from one ncu capture of this workload
+# (profiles/); absent until captured or once the kernel has changed since.
+NCU_DRAM_BYTES = {}
+
+# BF16 slice products per FP32-grade product on the tensor-core path
+# (three slices, pairs i + j < 3)
+SLICE_PRODUCTS = 6
+
+
+def kernel_roofline(fam, phase, ms, cnt, work, steps, peaks):
+    """Roofline of one (kernel family, phase) cell of the library's kernel
+    timing: work per launch / average launch time against the peak of the
+    unit that bounds the family."""
+    sec = ms / 1e3
+    cell = {"kernel": f"{fam}:{phase}", "launches_per_step": round(cnt / steps, 2),
+            "ms_per_launch": round(ms / cnt, 4), "ms_per_step": round(ms / steps, 4)}
+    if fam == "tc_gemm":
+        ach = work / sec / 1e12
+        cell.update({"bound": "tensor", "achieved": round(ach, 2), "peak": peaks["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": round(ach / peaks["bf16_tflops"], 4),
+                     "peak_source": f"bf16 dense burst {peaks['source']}",
+                     "useful_fp32_grade_tflops": round(ach / SLICE_PRODUCTS, 2),
+                     "work": "BF16 MMA flops of the 6 slice products"})
+    elif fam in ("fp64_gemm", "chol_diag"):
+        ach = work / sec / 1e12
+        cell.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                     "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe)",
+                     "work": "FP64 flops"})
+    else:
+        ach = work / sec / 1e9
+        cell.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                     "peak_source": f"HBM copy {peaks['source']}",
+                     "work": "algorithmic bytes (input read + output write)"})
+    cell["traffic"] = NCU_DRAM_BYTES.get(cell["kernel"])
+    return cell
 
 
 def algorithmic_flops(n_r, n_e, pairs, r, n_rhs, n_half2):
@@ -281,6 +325,7 @@ def run_native(args):
         sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
     pkg.isdf_set_profiling(ctx.ctx, True)
     pkg.isdf_read_profile(ctx.ctx)
+    pkg.isdf_read_kernel_profile(ctx.ctx)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -297,6 +342,7 @@ def run_native(args):
     launches = pkg.isdf_launch_count() - n0
     clocks = sampler.stop() if sampler else None
     prof = pkg.isdf_read_profile(ctx.ctx)
+    kprof = pkg.isdf_read_kernel_profile(ctx.ctx)
     pkg.isdf_set_profiling(ctx.ctx, False)
     rank_r = ctx.rank
     ms_total = max_over_ranks(e0.elapsed_time(e1), dev)
@@ -337,27 +383,16 @@ def run_native(args):
                "h2d_bytes_per_step": int(phi_h.numel() * 8 + x_h.numel() * 8 + s.mu_idx.nbytes + s.energies.nbytes + 8),
                "d2h_bytes_per_step": int(y_h.numel() * 8), "steps": k_e2e}
 
-    # ---- roofline of the dominant phase (FP64 pipe bound)
+    # ---- roofline of the dominant kernel, timed per launch on its own stream
     n_half2 = 2 * (s.n[0] // 2 + 1) * s.n[1] * s.n[2]
     fl = algorithmic_flops(s.n_r, s.n_e, s.n_v * s.n_c, rank_r, N_RHS, n_half2)
-    phases = {}
-    for name, (ms, cnt) in prof.items():
-        if cnt == 0:
-            continue
-        per = ms / cnt
-        achieved = fl[name] / (per / 1e3) / 1e12
-        phases[name] = {"ms": round(per, 3), "tflops": round(achieved, 4),
-                        "frac_fp64": round(achieved / FP64_PEAK_TFLOPS, 3)}
+    phases = {name: round(ms / args.steps, 3) for name, (ms, cnt) in prof.items() if cnt}
     flops_step = sum(fl.values())
-    dom = max(phases, key=lambda k: phases[k]["ms"]) if phases else None
-    roof = None
-    if dom:
-        ach = phases[dom]["tflops"]
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; no FP64 tensor path)",
-                "traffic": NCU_DRAM_BYTES.get(dom)}
-
+    peaks = measured_peaks()
+    cells = [kernel_roofline(f, p, ms, cnt, w, args.steps, peaks)
+             for (f, p), (ms, cnt, w) in kprof.items() if cnt and ms > 0]
+    cells.sort(key=lambda c: -c["ms_per_step"])
+    roof = cells[0] if cells else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws,
@@ -373,7 +408,7 @@ def run_native(args):
             "rel_err_vs_oracle": err,
             "fp64_path": fp64,
             "speedup_vs_fp64": (round(value / fp64["value"], 3) if fp64 else None),
-            "roofline": roof, "phases_ms": phases,
+            "roofline": roof, "kernels": cells[:8], "phases_ms": phases,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,
         }

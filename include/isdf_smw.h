@@ -135,6 +135,16 @@ ISDF_API int build_polarizability(isdf_ctx* ctx, const double* energies, const d
  * ISDF_ERR_NOT_SPD if D is not positive definite in floating point. */
 ISDF_API int smw_inverse(isdf_ctx* ctx, int omega_index, double* K_out);
 
+/* smw_inverse for every frequency of the last build_polarizability at once
+ * (the full-frequency form of Algorithm 3 step 3): on a MIXED context the
+ * products, the FP64 Cholesky factorisations and the triangular inverses
+ * of all frequencies run as batched launches (one launch per step for all
+ * of them); on an FP64 context the frequencies are queued one after the
+ * other.  One synchronisation at the end.
+ *   K_out    device, n_omega x n_mu x n_mu float64 out, or NULL.
+ * ISDF_ERR_NOT_SPD names the first frequency whose factor failed. */
+ISDF_API int smw_inverse_all(isdf_ctx* ctx, double* K_out);
+
 /* Y = eps^-1(i w) X = X + V theta K theta^T X (Eq. epsilon_with_SMW).
  *   X, Y     device, N_r x n_rhs float64 (ld = N_r); Y may equal X.
  *   n_rhs    >= 1.
@@ -165,6 +175,43 @@ ISDF_API int apply_eps_inv(isdf_ctx* ctx, int omega_index, const double* X, int 
  *   on the GPU (two streams, two threads, two contexts on the same device)
  *   race on the array: order them on one stream. */
 ISDF_API int apply_eps_inv_noalloc(isdf_ctx* ctx, int omega_index, const double* X, int n_rhs, double* Y);
+
+/* ---- Adjoint (gradients through the SMW inverse) -------------------------
+ * The differentiated quantity is the screened Coulomb operator in the ISDF
+ * basis, W_P = P^T eps^-1 V P = G_P + G_P K_P G_P (Eq. epsilon_with_SMW times
+ * V, projected on the interpolation vectors P of Eq. ISDF; G_P = P^T V P,
+ * K_P the capacitance in the points basis), as a function of the orbital
+ * energies and of the orbital samples at the interpolation points,
+ * phi_mu = Phi[mu, :], which enter through C = M[mu, :] and Omega
+ * (Eq. COmegaCstar).  The ISDF vectors (theta of the last fit) are held
+ * fixed: they are the checkpoint of the forward pass.  The paper states no
+ * derivative; these calls apply d(A^-1) = -A^-1 dA A^-1 to
+ * K = -D (I + G D)^-1, in FP64 (on a MIXED context G and K carry the mixed
+ * path's rounding). */
+
+/* Replace the orbital samples at the interpolation points used by the next
+ * build_polarizability (theta and the fit's factor stay).  phimu: device,
+ * n_mu x (n_v + n_c) float64, column-major with leading dimension ldp >=
+ * n_mu, rows in the order of the fit's mu_idx.  Invalidates the
+ * polarizability and every K.  Synchronises the context stream (checks for
+ * NaN / Inf: ISDF_ERR_NONFINITE). */
+ISDF_API int isdf_set_point_orbitals(isdf_ctx* ctx, const double* phimu, long long ldp);
+
+/* W_P for frequency omega[omega_index] in the points basis (rows and columns
+ * in the order of mu_idx; those of non-pivot points, if the rank r < n_mu,
+ * are zero).  W_out: device, n_mu x n_mu float64.  Requires smw_inverse for
+ * that frequency.  Asynchronous. */
+ISDF_API int isdf_screened_basis(isdf_ctx* ctx, int omega_index, double* W_out);
+
+/* Reverse mode: given W_bar = dL/dW_P (device, n_mu x n_mu float64, points
+ * order), writes dL/de (grad_energies, device, n_v + n_c float64) and
+ * dL/dphi_mu (grad_phimu, device, n_mu x (n_v + n_c) float64, ld n_mu; zero
+ * rows at non-pivot points).  Uses the state of the last build_polarizability
+ * and smw_inverse for omega_index (call between the forward and any other
+ * build_polarizability).  Workspace: 2 r n_v n_c + O(r^2) doubles.
+ * Synchronises the context stream. */
+ISDF_API int isdf_adjoint(isdf_ctx* ctx, int omega_index, const double* W_bar, double* grad_energies,
+                          double* grad_phimu);
 
 /* Split-precision DGEMM on the tensor cores, the building block of the
  * mixed-precision path (the paper has no counterpart; it is a GB300 means
@@ -207,13 +254,32 @@ enum {
 /* on != 0 starts recording (events are recorded around every phase of every
  * later call); on == 0 stops. */
 ISDF_API int isdf_set_profiling(isdf_ctx* ctx, int on);
-/* Synchronises the stream, then writes the summed milliseconds and the
+/* Synchronises the device, then writes the summed milliseconds and the
  * number of recorded intervals of every phase since the last read into
  * ms[ISDF_NUM_PHASES] and counts[ISDF_NUM_PHASES] (host; either may be
  * NULL) and clears the record. */
 ISDF_API int isdf_read_profile(isdf_ctx* ctx, double* ms, int* counts);
 /* Short name of a phase, or NULL. */
 ISDF_API const char* isdf_phase_name(int phase);
+/* Kernel timing by family (recorded with the phase profile, on each
+ * launch's own stream).  Families:                                         */
+enum {
+  ISDF_KF_TC_GEMM = 0,   /* tcgen05 split-precision GEMMs; work = BF16 MMA flops of the slice products */
+  ISDF_KF_FP64_GEMM = 1, /* FP64-pipe GEMMs (tiled, batched, face-split Gram); work = flops */
+  ISDF_KF_CHOL_DIAG = 2, /* 64 x 64 diagonal-block Cholesky + inverse; work = flops */
+  ISDF_KF_FFT = 3,       /* batched 3-D FFTs; work = bytes (input read + output write) */
+  ISDF_KF_SLICE = 4,     /* FP64 -> BF16 slicing; work = bytes */
+  ISDF_NUM_KERNEL_FAMILIES = 5
+};
+/* Synchronises the device, then writes per (family, phase) cell, index
+ * family * ISDF_NUM_PHASES + phase, the summed milliseconds, launch count
+ * and summed algorithmic work of the launches recorded since the last read
+ * (host arrays of ISDF_NUM_KERNEL_FAMILIES * ISDF_NUM_PHASES, any may be
+ * NULL) and clears the record.  Work counts the method's arithmetic on the
+ * launch's true sizes, not tile padding. */
+ISDF_API int isdf_read_kernel_profile(isdf_ctx* ctx, double* ms, int* counts, double* work);
+/* Short name of a kernel family, or NULL. */
+ISDF_API const char* isdf_kernel_family_name(int family);
 /* Number of kernel launches issued by this library in this process so far
  * (all contexts). */
 ISDF_API long long isdf_launch_count(void);

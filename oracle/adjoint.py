@@ -70,7 +70,7 @@ def screened_loss_grad(g: np.ndarray, phi_mu: np.ndarray, energies: np.ndarray, 
     kbar = g @ wbar @ g                                # dL/dK
     dbar = -e @ kbar @ e.T                             # dL/dD
     dsym = dbar + dbar.T
-    grad_d = np.einsum("ap,ab,bp->p", c, dbar, c)      # c_p^T dbar c_p
+    grad_d = np.sum(c * (dbar @ c), axis=0)            # c_p^T dbar c_p
     cbar = (dsym @ c) * d_p[None, :]                   # dL/dC
     ev = energies[:n_v]
     ec = energies[n_v:]

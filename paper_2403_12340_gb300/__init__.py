@@ -31,8 +31,11 @@ ISDF_PREC_FP64 = 0
 EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
             "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version",
             "isdf_set_profiling", "isdf_read_profile", "isdf_phase_name", "isdf_launch_count",
-            "apply_eps_inv_noalloc", "isdf_dgemm_split", "isdf_dgemm_split_error"]
+            "apply_eps_inv_noalloc", "isdf_dgemm_split", "isdf_dgemm_split_error",
+            "isdf_read_kernel_profile", "isdf_kernel_family_name", "isdf_set_point_orbitals",
+            "isdf_screened_basis", "isdf_adjoint", "smw_inverse_all"]
 NUM_PHASES = 9
+NUM_KERNEL_FAMILIES = 5
 
 
 class IsdfError(RuntimeError):
@@ -77,6 +80,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_read_profile.argtypes = [P, P, P]
     lib.isdf_phase_name.argtypes = [I]
     lib.isdf_phase_name.restype = ctypes.c_char_p
+    lib.smw_inverse_all.argtypes = [P, P]
+    lib.smw_inverse_all.restype = I
+    lib.isdf_set_point_orbitals.argtypes = [P, P, LL]
+    lib.isdf_screened_basis.argtypes = [P, I, P]
+    lib.isdf_adjoint.argtypes = [P, I, P, P, P]
+    for name in ["isdf_set_point_orbitals", "isdf_screened_basis", "isdf_adjoint"]:
+        getattr(lib, name).restype = I
+    lib.isdf_read_kernel_profile.argtypes = [P, P, P, P]
+    lib.isdf_read_kernel_profile.restype = I
+    lib.isdf_kernel_family_name.argtypes = [I]
+    lib.isdf_kernel_family_name.restype = ctypes.c_char_p
     lib.isdf_launch_count.argtypes = []
     lib.isdf_launch_count.restype = ctypes.c_longlong
     for name in ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
@@ -182,11 +196,31 @@ def smw_inverse(ctx, omega_index: int = 0, K_out=None) -> None:
     _check(load_library().smw_inverse(ctx, int(omega_index), pk), ctx)
 
 
+def smw_inverse_all(ctx, K_out=None) -> None:
+    pk = 0 if K_out is None else _dev_ptr(K_out.reshape(-1), name="K_out")
+    _check(load_library().smw_inverse_all(ctx, pk), ctx)
+
+
 def apply_eps_inv(ctx, omega_index: int, X, Y, n_r: int) -> None:
     n_rhs = X.shape[1] if X.dim() == 2 else 1
     px = _dev_ptr(X, n_r, None, "X")
     py = _dev_ptr(Y, n_r, n_rhs, "Y")
     _check(load_library().apply_eps_inv(ctx, int(omega_index), px, int(n_rhs), py), ctx)
+
+
+def isdf_set_point_orbitals(ctx, phimu, n_mu: int, n_e: int) -> None:
+    """Replace the orbital samples at the points (n_mu x n_e, column-major)."""
+    _check(load_library().isdf_set_point_orbitals(ctx, _dev_ptr(phimu, n_mu, n_e, "phimu"), int(n_mu)), ctx)
+
+
+def isdf_screened_basis(ctx, omega_index: int, W_out, n_mu: int) -> None:
+    _check(load_library().isdf_screened_basis(ctx, int(omega_index), _dev_ptr(W_out, n_mu, n_mu, "W_out")), ctx)
+
+
+def isdf_adjoint(ctx, omega_index: int, W_bar, grad_e, grad_phimu, n_mu: int, n_e: int) -> None:
+    _check(load_library().isdf_adjoint(ctx, int(omega_index), _dev_ptr(W_bar, n_mu, n_mu, "W_bar"),
+                                       _dev_ptr(grad_e, name="grad_energies"),
+                                       _dev_ptr(grad_phimu, n_mu, n_e, "grad_phimu")), ctx)
 
 
 def isdf_fit_factor(ctx, n_mu: int, L_out=None):
@@ -208,6 +242,26 @@ def isdf_read_profile(ctx):
     _check(load_library().isdf_read_profile(ctx, ms.ctypes.data, cnt.ctypes.data), ctx)
     lib = load_library()
     return {lib.isdf_phase_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(NUM_PHASES)}
+
+
+def isdf_read_kernel_profile(ctx):
+    """{(family, phase): (milliseconds, launches, work)} of the timed kernel
+    launches since the last read (syncs the device); work is flops for the
+    GEMM / Cholesky families and bytes for "fft" and "slice"."""
+    n = NUM_KERNEL_FAMILIES * NUM_PHASES
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.int32)
+    work = np.zeros(n, dtype=np.float64)
+    lib = load_library()
+    _check(lib.isdf_read_kernel_profile(ctx, ms.ctypes.data, cnt.ctypes.data, work.ctypes.data), ctx)
+    out = {}
+    for f in range(NUM_KERNEL_FAMILIES):
+        for p in range(NUM_PHASES):
+            i = f * NUM_PHASES + p
+            if cnt[i]:
+                out[(lib.isdf_kernel_family_name(f).decode(), lib.isdf_phase_name(p).decode())] = (
+                    float(ms[i]), int(cnt[i]), float(work[i]))
+    return out
 
 
 def isdf_dgemm_split(A, B, C, alpha=1.0, beta=0.0, nslices=3, stream=None) -> None:
@@ -289,11 +343,41 @@ class IsdfSmw:
         smw_inverse(self.ctx, omega_index, K)
         return K
 
+    def smw_all(self, n_omega, want_K=False):
+        """K for every frequency of the last polarizability (batched)."""
+        import torch
+
+        K = (torch.empty((n_omega, self.n_mu, self.n_mu), dtype=torch.float64, device=self.theta.device)
+             if want_K else None)
+        smw_inverse_all(self.ctx, K)
+        return K
+
     def apply(self, X, omega_index=0, Y=None):
         if Y is None:
             Y = fortran_empty(self.n_r, X.shape[1], X.device)
         apply_eps_inv(self.ctx, omega_index, X, Y, self.n_r)
         return Y
+
+    def set_point_orbitals(self, phimu):
+        """Orbital samples at the points (n_mu x n_e) for the next polarizability."""
+        t = phimu if phimu.stride() == (1, self.n_mu) else to_fortran(phimu, phimu.device)
+        isdf_set_point_orbitals(self.ctx, t, self.n_mu, t.shape[1])
+
+    def screened_basis(self, omega_index=0):
+        """W_P = P^T eps^-1 V P (n_mu x n_mu, points order) for one frequency."""
+        W = fortran_empty(self.n_mu, self.n_mu, self.theta.device)
+        isdf_screened_basis(self.ctx, omega_index, W, self.n_mu)
+        return W
+
+    def adjoint(self, W_bar, n_e, omega_index=0):
+        """(dL/de, dL/dphi_mu) for dL/dW_P = W_bar."""
+        import torch
+
+        wb = W_bar if (W_bar.dim() == 2 and W_bar.stride() == (1, self.n_mu)) else to_fortran(W_bar, W_bar.device)
+        ge = torch.empty(n_e, dtype=torch.float64, device=self.theta.device)
+        gp = fortran_empty(self.n_mu, n_e, self.theta.device)
+        isdf_adjoint(self.ctx, omega_index, wb, ge, gp, self.n_mu, n_e)
+        return ge, gp
 
     def factor(self, want_L=False):
         import torch
@@ -302,3 +386,37 @@ class IsdfSmw:
         piv = isdf_fit_factor(self.ctx, self.n_mu, L)
         # the library writes L column-major; the transposed view is L itself
         return piv, (L.t() if L is not None else None)
+
+
+def _autograd_function():
+    import torch
+
+    class ScreenedCoulombBasis(torch.autograd.Function):
+        """W_P(e, phi_mu) = P^T eps^-1(i w) V P with the ISDF vectors of a
+        fitted IsdfSmw held fixed (the checkpoint).  forward runs the CUDA
+        polarizability, SMW and projection; backward runs the CUDA adjoint.
+        Between a forward and its backward the solver must not be used for
+        another polarizability."""
+
+        @staticmethod
+        def forward(fctx, solver, energies, phi_mu, omega):
+            solver.set_point_orbitals(phi_mu.detach())
+            solver.polarizability(energies.detach().cpu().numpy(), [float(omega)])
+            solver.smw(0)
+            W = solver.screened_basis(0)
+            fctx.solver = solver
+            fctx.n_e = phi_mu.shape[1]
+            fctx.e_device = energies.device
+            return W
+
+        @staticmethod
+        def backward(fctx, gW):
+            ge, gp = fctx.solver.adjoint(gW, fctx.n_e, 0)
+            return None, ge.to(fctx.e_device), gp, None
+
+    return ScreenedCoulombBasis
+
+
+def screened_coulomb_basis(solver, energies, phi_mu, omega=0.0):
+    """Differentiable W_P = P^T eps^-1 V P (torch.autograd) on a fitted solver."""
+    return _autograd_function().apply(solver, energies, phi_mu, omega)

@@ -219,11 +219,14 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->d_fail) cudaFree(c->d_fail);
+  if (c->b_fail) cudaFree(c->b_fail);
   DevBuf* bufs[] = {&c->phimu, &c->phimu_p, &c->A, &c->Lr, &c->Lc, &c->Bf, &c->chol_d, &c->chol_part,
                     &c->spec, &c->G, &c->D, &c->K, &c->R, &c->T, &c->W1, &c->Q, &c->partial,
                     &c->tmp1, &c->tmp2, &c->tmp3, &c->sw, &c->m_phis, &c->m_phimus, &c->m_zs, &c->m_linv,
                     &c->m_linvs, &c->m_work, &c->m_thetas_t, &c->m_s32, &c->m_ss, &c->m_pairs, &c->m_sa,
-                    &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw};
+                    &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
+                    &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
+                    &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd};
   for (DevBuf* b : bufs) release(*b);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
@@ -502,6 +505,7 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
     CK(ensure(c->partial, (size_t)std::max(sp, spd) * rr));
     CK(ensure(c->sw, npair * n_omega));
     CK(ensure(c->tmp1, rr));
+    if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)(64 * 64 + 1 + (size_t)r * 64) * n_omega));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
     std::vector<double> sw(npair * n_omega);
     for (int k = 0; k < n_omega; ++k) {
@@ -515,7 +519,11 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
     CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // D(w) for every frequency (main stream)
     if (c->prec == ISDF_PREC_MIXED) {
-      CK(isdf::mixed_polar_D(c, c->sw.p, n_omega));
+      if (n_omega > 1) {
+        CK(isdf::mixed_polar_D_batched(c, c->sw.p, n_omega));
+      } else {
+        CK(isdf::mixed_polar_D(c, c->sw.p, n_omega));
+      }
     } else {
       for (int k = 0; k < n_omega; ++k) {
         double* Dk = c->D.p + rr * k;
@@ -537,8 +545,14 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
       int rc0 = fork_s2(c);
       if (rc0 != ISDF_OK) return rc0;
       PhaseScope ph(c, ISDF_PH_SMW, c->s2);
-      for (int k = 0; k < n_omega; ++k) {
-        rc0 = cholesky_blocked(c, c->D.p + rr * k, r, r, 0.0, c->Rw.p + rr * k, c->d_fail + k, c->s2);
+      if (n_omega > 1) {  // all frequencies in one factorisation sequence
+        double* dinv = c->b_cbd.p;
+        double* dmax = dinv + (size_t)64 * 64 * n_omega;
+        double* pan = dmax + n_omega;
+        CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr, dinv,
+                                           dmax, c->d_fail, pan, c->s2));
+      } else {
+        rc0 = cholesky_blocked(c, c->D.p, r, r, 0.0, c->Rw.p, c->d_fail, c->s2);
         if (rc0 != ISDF_OK) return rc0;
       }
     }
@@ -572,8 +586,85 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
   }
   c->n_omega = n_omega;
   c->omega.assign(omega, omega + n_omega);
+  c->energies.assign(energies, energies + n_e);
   c->k_ready.assign(n_omega, 0);
   c->polar_ready = true;
+  return ISDF_OK;
+}
+
+// Queue the SMW capacitance of frequency k (no synchronisation); the
+// failure flag of the factorisation of I + R^T G R goes to failT.
+static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
+  const int r = c->rank;
+  const size_t rr = (size_t)r * r;
+  double* Kk = c->K.p + rr * k;
+  long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
+  int sp = split_for(tiles, std::max(r, 1), c->num_sms);
+  PhaseScope ph(c, ISDF_PH_SMW);
+  // D = R R^T: factored by build_polarizability on the second stream
+  CK(cudaMemcpyAsync(c->R.p, c->Rw.p + rr * k, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  // T = I + R^T G R
+  CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
+  CK(launch_add_identity(c->T.p, r, r, 1.0, c->stream));
+  if (c->prec == ISDF_PREC_MIXED) {
+    CK(isdf::mixed_smw_products_T(c));
+  } else {
+    CK(launch_gemm(c->G.p, r, false, c->R.p, r, true, r, r, r, 1.0, 0.0, c->W1.p, r, false, 1, nullptr, false,
+                   c->stream));
+    CK(launch_gemm(c->R.p, r, true, c->W1.p, r, true, r, r, r, 1.0, 1.0, c->T.p, r, false, 1, nullptr, false,
+                   c->stream));
+    CK(launch_symmetrize(c->T.p, r, r, c->stream));
+  }
+  // T = U U^T; Q = R U^-T; K = -Q Q^T
+  int rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, failT, c->stream);
+  if (rc != ISDF_OK) return rc;
+  if (c->prec == ISDF_PREC_MIXED) {
+    CK(isdf::mixed_smw_products_K(c, Kk));
+  } else {
+    CK(launch_trsm_prep(c->W1.p, r, r, c->Bf.p + 0, r, c->stream));
+    CK(cudaMemcpyAsync(c->Q.p, c->R.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_trsm_right_lt(c->Q.p, r, r, c->Bf.p, r, r, c->stream));
+    CK(launch_gemm(c->Q.p, r, false, c->Q.p, r, false, r, r, r, -1.0, 0.0, Kk, r, true, sp, c->partial.p, false,
+                   c->stream));
+    // restore the fit's TRSM table (Bf held L_r^-1 blocks for D(w) of later calls)
+    CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+  }
+  return ISDF_OK;
+}
+
+// Size the single-frequency SMW workspace (synchronising first if a buffer grows).
+static int smw_workspace(isdf_ctx* c) {
+  const int r = c->rank;
+  const size_t rr = (size_t)r * r;
+  long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
+  int sp = split_for(tiles, std::max(r, 1), c->num_sms);
+  if (c->R.cap < rr || c->T.cap < rr || c->W1.cap < rr || c->Q.cap < rr || c->partial.cap < sp * rr)
+    CK(cudaStreamSynchronize(c->stream));  // a resize frees memory that earlier work may read
+  CK(ensure(c->R, rr));
+  CK(ensure(c->T, rr));
+  CK(ensure(c->W1, rr));
+  CK(ensure(c->Q, rr));
+  CK(ensure(c->partial, (size_t)sp * rr));
+  return ISDF_OK;
+}
+
+// Synchronise, then check the device status and the failure flags of the
+// factorisations of D(w_k) (d_fail) and of I + R^T G R (failT) for k in
+// [k0, k0 + nk).
+static int smw_finish(isdf_ctx* c, int k0, int nk, const int* failT, const char* who) {
+  CK(cudaStreamSynchronize(c->stream));
+  int rc = check_status(c, who);
+  if (rc != ISDF_OK) return rc;
+  if (c->rank > 0) {
+    std::vector<int> fd(nk), ft(nk);
+    CK(cudaMemcpy(fd.data(), c->d_fail + k0, nk * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ft.data(), failT, nk * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nk; ++i)
+      if (fd[i] >= 0 || ft[i] >= 0)
+        return fail(c, ISDF_ERR_NOT_SPD, std::string(who) + ": capacitance factor not positive definite at omega_index " +
+                                             std::to_string(k0 + i));
+  }
+  for (int i = 0; i < nk; ++i) c->k_ready[k0 + i] = 1;
   return ISDF_OK;
 }
 
@@ -584,66 +675,58 @@ extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
   if (k < 0 || k >= c->n_omega) return fail(c, ISDF_ERR_ARG, "smw_inverse: omega_index out of range");
   const int r = c->rank, m = c->n_mu;
   const size_t rr = (size_t)r * r;
-  double* Kk = c->K.p + rr * k;
   c->k_ready[k] = 0;
-  long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
-  int sp = split_for(tiles, std::max(r, 1), c->num_sms);
   if (r > 0) {
-    if (c->R.cap < rr || c->T.cap < rr || c->W1.cap < rr || c->Q.cap < rr || c->partial.cap < sp * rr)
-      CK(cudaStreamSynchronize(c->stream));  // a resize frees memory that earlier work may read
-    CK(ensure(c->R, rr));
-    CK(ensure(c->T, rr));
-    CK(ensure(c->W1, rr));
-    CK(ensure(c->Q, rr));
-    CK(ensure(c->partial, (size_t)sp * rr));
-    CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
-    PhaseScope ph(c, ISDF_PH_SMW);
-    // D = R R^T: factored by build_polarizability on the second stream
-    int rc;
-    CK(cudaMemcpyAsync(c->R.p, c->Rw.p + rr * k, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    // T = I + R^T G R
-    CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
-    CK(launch_add_identity(c->T.p, r, r, 1.0, c->stream));
-    if (c->prec == ISDF_PREC_MIXED) {
-      CK(isdf::mixed_smw_products_T(c));
-    } else {
-      CK(launch_gemm(c->G.p, r, false, c->R.p, r, true, r, r, r, 1.0, 0.0, c->W1.p, r, false, 1, nullptr,
-                     false, c->stream));
-      CK(launch_gemm(c->R.p, r, true, c->W1.p, r, true, r, r, r, 1.0, 1.0, c->T.p, r, false, 1, nullptr,
-                     false, c->stream));
-      CK(launch_symmetrize(c->T.p, r, r, c->stream));
-    }
-    // T = U U^T; Q = R U^-T; K = -Q Q^T
-    rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, c->d_ints + 3, c->stream);
+    int rc = smw_workspace(c);
     if (rc != ISDF_OK) return rc;
-    if (c->prec == ISDF_PREC_MIXED) {
-      CK(isdf::mixed_smw_products_K(c, Kk));
+    CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+    rc = smw_enqueue(c, k, c->d_ints + 3);
+    if (rc != ISDF_OK) return rc;
+  }
+  if (K_out) {
+    int rc = copy_padded(c, K_out, c->K.p + rr * k, r, m);
+    if (rc != ISDF_OK) return rc;
+  }
+  return smw_finish(c, k, 1, c->d_ints + 3, "smw_inverse");
+}
+
+extern "C" int smw_inverse_all(isdf_ctx* c, double* K_out) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  if (!c->polar_ready) return fail(c, ISDF_ERR_STATE, "smw_inverse_all: call build_polarizability first");
+  const int r = c->rank, m = c->n_mu, nw = c->n_omega;
+  const size_t rr = (size_t)r * r;
+  std::fill(c->k_ready.begin(), c->k_ready.end(), 0);
+  if (c->cap_bfail < (size_t)nw) {
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->b_fail) cudaFree(c->b_fail);
+    c->b_fail = nullptr;
+    c->cap_bfail = 0;
+    CK(cudaMalloc(&c->b_fail, nw * sizeof(int)));
+    c->cap_bfail = nw;
+  }
+  if (r > 0) {
+    CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(c->b_fail, 0xff, nw * sizeof(int), c->stream));
+    if (c->prec == ISDF_PREC_MIXED && nw > 1) {
+      PhaseScope ph(c, ISDF_PH_SMW);
+      CK(isdf::mixed_smw_batched(c, nw, c->b_fail));
     } else {
-    CK(launch_trsm_prep(c->W1.p, r, r, c->Bf.p + 0, r, c->stream));
-    CK(cudaMemcpyAsync(c->Q.p, c->R.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    CK(launch_trsm_right_lt(c->Q.p, r, r, c->Bf.p, r, r, c->stream));
-    CK(launch_gemm(c->Q.p, r, false, c->Q.p, r, false, r, r, r, -1.0, 0.0, Kk, r, true, sp, c->partial.p,
-                   false, c->stream));
-    // restore the fit's TRSM table (Bf held L_r^-1 blocks for D(w) of later calls)
-    CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+      int rc = smw_workspace(c);
+      if (rc != ISDF_OK) return rc;
+      for (int k = 0; k < nw; ++k) {
+        rc = smw_enqueue(c, k, c->b_fail + k);
+        if (rc != ISDF_OK) return rc;
+      }
     }
   }
   if (K_out) {
-    int rc = copy_padded(c, K_out, Kk, r, m);
-    if (rc != ISDF_OK) return rc;
+    for (int k = 0; k < nw; ++k) {
+      int rc = copy_padded(c, K_out + (size_t)m * m * k, c->K.p + rr * k, r, m);
+      if (rc != ISDF_OK) return rc;
+    }
   }
-  CK(cudaStreamSynchronize(c->stream));
-  int rc = check_status(c, "smw_inverse");
-  if (rc != ISDF_OK) return rc;
-  if (r > 0) {
-    int fails[2] = {-1, -1};
-    CK(cudaMemcpy(&fails[0], c->d_fail + k, sizeof(int), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&fails[1], c->d_ints + 3, sizeof(int), cudaMemcpyDeviceToHost));
-    if (fails[0] >= 0 || fails[1] >= 0)
-      return fail(c, ISDF_ERR_NOT_SPD, "smw_inverse: capacitance factor not positive definite");
-  }
-  c->k_ready[k] = 1;
-  return ISDF_OK;
+  return smw_finish(c, 0, nw, c->b_fail, "smw_inverse_all");
 }
 
 extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, double* Y) {
@@ -712,9 +795,64 @@ extern "C" int isdf_set_profiling(isdf_ctx* c, int on) {
   return ISDF_OK;
 }
 
+thread_local isdf_ctx* isdf::tl_prof_ctx = nullptr;
+thread_local int isdf::tl_prof_phase = -1;
+
+isdf::KernelTimer::KernelTimer(int f, cudaStream_t s, double w) : fam(f), st(s), work(w) {
+  isdf_ctx* c = tl_prof_ctx;
+  if (!c || !c->prof_on) return;
+  e0 = take_event(c);
+  if (e0) cudaEventRecord(e0, st);
+}
+
+isdf::KernelTimer::~KernelTimer() {
+  isdf_ctx* c = tl_prof_ctx;
+  if (!e0 || !c) return;
+  cudaEvent_t e1 = take_event(c);
+  if (!e1) {
+    c->ev_pool.push_back(e0);
+    return;
+  }
+  cudaEventRecord(e1, st);
+  c->kprof.push_back({fam, tl_prof_phase, e0, e1, work});
+}
+
+static_assert(KF_COUNT == ISDF_NUM_KERNEL_FAMILIES, "kernel families of the header and the launchers differ");
+static const char* kFamilyNames[KF_COUNT] = {"tc_gemm", "fp64_gemm", "chol_diag", "fft", "slice"};
+
+extern "C" const char* isdf_kernel_family_name(int fam) {
+  return (fam >= 0 && fam < KF_COUNT) ? kFamilyNames[fam] : nullptr;
+}
+
+extern "C" int isdf_read_kernel_profile(isdf_ctx* c, double* ms, int* counts, double* work) {
+  if (!c) return ISDF_ERR_ARG;
+  CK(cudaDeviceSynchronize());
+  const int n = ISDF_NUM_KERNEL_FAMILIES * ISDF_NUM_PHASES;
+  std::vector<double> acc(n, 0.0), wk(n, 0.0);
+  std::vector<int> cnt(n, 0);
+  for (auto& r : c->kprof) {
+    float t = 0.f;
+    if (r.ph >= 0 && r.ph < ISDF_NUM_PHASES && cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) {
+      const int i = r.fam * ISDF_NUM_PHASES + r.ph;
+      acc[i] += t;
+      wk[i] += r.work;
+      cnt[i] += 1;
+    }
+    c->ev_pool.push_back(r.e0);
+    c->ev_pool.push_back(r.e1);
+  }
+  c->kprof.clear();
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (counts) counts[i] = cnt[i];
+    if (work) work[i] = wk[i];
+  }
+  return ISDF_OK;
+}
+
 extern "C" int isdf_read_profile(isdf_ctx* c, double* ms, int* counts) {
   if (!c) return ISDF_ERR_ARG;
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaDeviceSynchronize());
   double acc[ISDF_NUM_PHASES] = {0};
   int cnt[ISDF_NUM_PHASES] = {0};
   for (auto& pe : c->prof_ev) {

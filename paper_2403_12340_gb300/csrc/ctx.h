@@ -80,11 +80,28 @@ struct isdf_ctx {
   bool prof_on = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
   std::vector<cudaEvent_t> ev_pool;
+  struct KRec {
+    int fam, ph;
+    cudaEvent_t e0, e1;
+    double work;
+  };
+  std::vector<KRec> kprof;
+
+  // all frequencies at once (mixed.cu, api.cu): per-frequency r x r stacks,
+  // their slice stacks, scratch of the batched factorisations, failure flags
+  DevBuf bW1, bT, bU, bQ, b_s1, b_s2, b_s3, b_work, b_cb, b_dtmp, b_cbd;
+  int* b_fail = nullptr;
+  size_t cap_bfail = 0;
+
+  // adjoint (adjoint.cu): L_r^-1, r x r products, the pair matrix at the
+  // points and its gradient, device copy of the energies
+  DevBuf a_linv, a_m1, a_m2, a_m3, a_m4, a_cp, a_y, a_gd, a_e;
 
   // polarizability / SMW state
   bool polar_ready = false;
   int n_omega = 0;
   std::vector<double> omega;
+  std::vector<double> energies;  // of the last build_polarizability
   std::vector<char> k_ready;
 };
 
@@ -101,20 +118,35 @@ inline cudaEvent_t take_event(isdf_ctx* c) {
   return e;
 }
 
+// Context and phase that KernelTimer records into on this thread (null
+// outside a profiled phase).
+extern thread_local isdf_ctx* tl_prof_ctx;
+extern thread_local int tl_prof_phase;
+
 // Records a start event now and an end event when it goes out of scope
-// (only while profiling is on).
+// (only while profiling is on); launches inside the scope are timed too.
 struct PhaseTimer {
   isdf_ctx* c;
   int ph;
   cudaStream_t st;
   cudaEvent_t e0 = nullptr;
+  isdf_ctx* prev_ctx = nullptr;
+  int prev_ph = -1;
   PhaseTimer(isdf_ctx* ctx, int phase, cudaStream_t stream = nullptr)
       : c(ctx), ph(phase), st(stream ? stream : ctx->stream) {
     if (!c->prof_on) return;
+    prev_ctx = tl_prof_ctx;
+    prev_ph = tl_prof_phase;
+    tl_prof_ctx = c;
+    tl_prof_phase = ph;
     e0 = take_event(c);
     if (e0) cudaEventRecord(e0, st);
   }
   ~PhaseTimer() {
+    if (c->prof_on || e0) {
+      tl_prof_ctx = prev_ctx;
+      tl_prof_phase = prev_ph;
+    }
     if (!e0) return;
     cudaEvent_t e1 = take_event(c);
     if (!e1) {
@@ -134,5 +166,10 @@ cudaError_t mixed_polar_G(isdf_ctx* c);
 cudaError_t mixed_smw_products_T(isdf_ctx* c);
 cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk);
 cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc);
+// All frequencies at once: D(w_k) for k < n_omega (chunked to a memory
+// budget), and K(w_k) from the factors R(w_k) in c->Rw (T factors and
+// their failure flags in c->bU / fail_T).
+cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_smw_batched(isdf_ctx* c, int n_omega, int* fail_T);
 
 }  // namespace isdf

@@ -16,8 +16,12 @@ namespace isdf {
 
 constexpr int CB = 64;
 
-__global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, double* out, int* fail) {
+__global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, double* out, int* fail,
+                           long long sW = 0) {
   __shared__ double red[256];
+  W += sW * blockIdx.x;
+  out += blockIdx.x;
+  fail += blockIdx.x;
   double m = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, W[i + ldw * (long long)i]);
   red[threadIdx.x] = m;
@@ -47,8 +51,13 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
 constexpr int TRI = CB * (CB - 1) / 2;  // entries of a strictly lower 63-row triangle
 
 __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int j0, int bs, double* dinv,
-                                                  const double* dmax, double tol_rel, int* fail) {
+                                                  const double* dmax, double tol_rel, int* fail, long long sA = 0) {
   __shared__ double Ls[CB][CB + 1];
+  // problem blockIdx.x of a batch: its matrix, inverse block, max and flag
+  A += sA * blockIdx.x;
+  dinv += (long long)CB * CB * blockIdx.x;
+  dmax += blockIdx.x;
+  fail += blockIdx.x;
   __shared__ double Xs[CB][CB + 1];
   __shared__ double rdiag[CB];
   __shared__ unsigned char ta[TRI], tb[TRI];
@@ -139,11 +148,20 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
   }
 }
 
-// Zero the strict upper triangle.
-__global__ void k_zero_upper(double* A, long long lda, int n) {
+// Zero the strict upper triangle (matrix blockIdx.z at A + z sA).
+__global__ void k_zero_upper(double* A, long long lda, int n, long long sA = 0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
+  A += sA * blockIdx.z;
   if (i < k && k < n) A[i + lda * (long long)k] = 0.0;
+}
+
+// dst(i, j) = src(i, j) for i < rows, j < cols; problem blockIdx.z at
+// dst + z sD, src + z sS
+__global__ void k_copy_block(const double* __restrict__ src, long long lds, long long sS, double* __restrict__ dst,
+                             long long ldd, long long sD, int rows, int cols) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < rows && j < cols) dst[sD * blockIdx.z + i + ldd * j] = src[sS * blockIdx.z + i + lds * j];
 }
 
 cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
@@ -160,9 +178,13 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
-    note_launch();
-    k_chol_diag<<<1, 256, 0, s>>>(L, ldl, j0, bs, dinv, dmax, tol_rel, fail);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+      // factor bs^3 / 3 flops and triangular inverse bs^3 / 3 flops
+      KernelTimer kt(KF_CHOL_DIAG, s, 2.0 * bs * bs * bs / 3.0);
+      note_launch();
+      k_chol_diag<<<1, 256, 0, s>>>(L, ldl, j0, bs, dinv, dmax, tol_rel, fail);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
     // panel: L[j0+bs:, J] = A[j0+bs:, J] Dinv^T, computed into `pan` (rem x bs,
@@ -182,6 +204,51 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
   dim3 g((n + 127) / 128, n);
   note_launch();
   k_zero_upper<<<g, 128, 0, s>>>(L, ldl, n);
+  return cudaGetLastError();
+}
+
+// The same factorisation for `batch` matrices of equal size n (W_z = W + z
+// sW, L_z = L + z sL): one launch per step covers every matrix.  dinv:
+// batch 64 x 64 blocks, dmax / fail: batch entries, pan: batch n x 64.
+cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
+                                            double tol_rel, double* L, long long ldl, long long sL, double* dinv,
+                                            double* dmax, int* fail, double* pan, cudaStream_t s) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (L != W || ldl != ldw || sL != sW) {
+    note_launch();
+    k_copy_block<<<dim3((n + 127) / 128, n, batch), 128, 0, s>>>(W, ldw, sW, L, ldl, sL, n, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  note_launch();
+  k_diag_max<<<batch, 256, 0, s>>>(L, ldl, n, dmax, fail, sL);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long sP = (long long)n * CB;
+  for (int j0 = 0; j0 < n; j0 += CB) {
+    const int bs = min(CB, n - j0);
+    {
+      KernelTimer kt(KF_CHOL_DIAG, s, 2.0 * bs * bs * bs / 3.0 * batch);
+      note_launch();
+      k_chol_diag<<<batch, 256, 0, s>>>(L, ldl, j0, bs, dinv, dmax, tol_rel, fail, sL);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int rem = n - j0 - bs;
+    if (rem <= 0) break;
+    double* Pj = L + (j0 + bs) + ldl * (long long)j0;
+    GemmBatch pb{batch, 1, sL, (long long)CB * CB, sP, 0, 0, 0};
+    e = launch_gemm_batched2(Pj, ldl, false, dinv, CB, false, rem, bs, bs, 1.0, 0.0, pan, n, pb, false, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_copy_block<<<dim3((rem + 127) / 128, bs, batch), 128, 0, s>>>(pan, n, sP, Pj, ldl, sL, rem, bs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    GemmBatch tb{batch, 1, sP, sP, sL, 0, 0, 0};
+    e = launch_gemm_batched2(pan, n, false, pan, n, false, rem, rem, bs, -1.0, 1.0,
+                             L + (j0 + bs) + ldl * (long long)(j0 + bs), ldl, tb, true, s);
+    if (e != cudaSuccess) return e;
+  }
+  note_launch();
+  k_zero_upper<<<dim3((n + 127) / 128, n, batch), 128, 0, s>>>(L, ldl, n, sL);
   return cudaGetLastError();
 }
 

@@ -73,9 +73,10 @@ cudaError_t launch_transpose(const double* src, long long lds, int M, int N, dou
   return cudaGetLastError();
 }
 
-__global__ void k_symmetrize(double* A, long long lda, int n) {
+__global__ void k_symmetrize(double* A, long long lda, int n, long long sA = 0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
+  A += sA * blockIdx.z;
   if (i < n && j < i) {
     double v = 0.5 * (A[i + lda * j] + A[j + lda * i]);
     A[i + lda * j] = v;
@@ -83,23 +84,26 @@ __global__ void k_symmetrize(double* A, long long lda, int n) {
   }
 }
 
-cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s) {
-  if (n <= 1) return cudaSuccess;
-  dim3 grid((n + 127) / 128, n);
+cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, int batch, long long sA) {
+  if (n <= 1 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  dim3 grid((n + 127) / 128, n, batch);
   note_launch();
-  k_symmetrize<<<grid, 128, 0, s>>>(A, lda, n);
+  k_symmetrize<<<grid, 128, 0, s>>>(A, lda, n, sA);
   return cudaGetLastError();
 }
 
-__global__ void k_add_identity(double* A, long long lda, int n, double v) {
+__global__ void k_add_identity(double* A, long long lda, int n, double v, long long sA = 0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  A += sA * blockIdx.y;
   if (i < n) A[i + lda * i] += v;
 }
 
-cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
+cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s, int batch, long long sA) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
   note_launch();
-  k_add_identity<<<(n + 127) / 128, 128, 0, s>>>(A, lda, n, v);
+  k_add_identity<<<dim3((n + 127) / 128, batch), 128, 0, s>>>(A, lda, n, v, sA);
   return cudaGetLastError();
 }
 
@@ -167,6 +171,7 @@ cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const d
   const bool sym = (A == B && lda == ldb && M == N);
   const int tm = (M + 63) / 64;
   dim3 grid = sym ? dim3(tm * (tm + 1) / 2, 1) : dim3(tm, (N + 63) / 64);
+  KernelTimer kt(KF_FP64_GEMM, s, 2.0 * n_e * (sym ? 0.5 * M * (M + 1.0) : (double)M * N));
   note_launch();
   k_facesplit_gram<<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v,
                                         n_e, C, ldc, sym ? 1 : 0);
@@ -227,12 +232,16 @@ __global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int 
 
 // C = alpha * sum_z partial[z] + beta * C; for lower_only the upper tiles are
 // read mirrored from the lower ones.
+// Batched over blockIdx.z: partials of problem z start at z * splits * M * N,
+// its C at C + z * sC.
 __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, int M, int N,
                                 double alpha, double beta, double* C, long long ldc, int lower_only,
-                                int tile) {
+                                int tile, long long sC = 0) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   int n = blockIdx.y;
   if (m >= M || n >= N) return;
+  partial += (long long)blockIdx.z * splits * M * N;
+  C += sC * blockIdx.z;
   int pm = m, pn = n;
   if (lower_only && (m / tile) < (n / tile)) {
     pm = n;
@@ -246,42 +255,72 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, 
 }
 
 template <class T, class OpA, class OpB>
-__global__ void __launch_bounds__(T::NT) k_gemm_batched(OpA A, OpB B, long long sA, long long sB, int M, int N,
-                                                        int K, double alpha, double beta, double* C, long long ldc,
-                                                        long long sC, int tri) {
+__global__ void __launch_bounds__(T::NT) k_gemm_batched(OpA A, OpB B, GemmBatch bt, int M, int N, int K, double alpha,
+                                                        double beta, double* C, long long ldc, int tri, int lower) {
   __shared__ typename T::Smem s;
   const int z = blockIdx.z;
-  A.p += sA * z;
-  B.p += sB * z;
-  C += sC * z;
-  const int m0 = blockIdx.x * T::kBM, n0 = blockIdx.y * T::kBN;
+  const int z1 = z % bt.b1, z2 = z / bt.b1;
+  A.p += bt.sA1 * z1 + bt.sA2 * z2;
+  B.p += bt.sB1 * z1 + bt.sB2 * z2;
+  C += bt.sC1 * z1 + bt.sC2 * z2;
+  int mt, nt;
+  if (lower) {
+    lower_tile(blockIdx.x, mt, nt);
+  } else {
+    mt = blockIdx.x;
+    nt = blockIdx.y;
+  }
+  const int m0 = mt * T::kBM, n0 = nt * T::kBN;
   const int kbeg = (tri & TRI_B_LOWER_T) ? min(n0, K) : 0;
   const int kend = (tri & TRI_A_LOWER) ? min(K, m0 + T::kBM) : K;
   double acc[T::kTM][T::kTN];
   zero_acc<T>(acc);
   gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
-  store_tile<T>(acc, m0, n0, M, N, alpha, beta, C, ldc, false);
+  store_tile<T>(acc, m0, n0, M, N, alpha, beta, C, ldc, lower && mt != nt);
+}
+
+// Multiply-adds of C(m, n) += sum_k A(m, k) B(n, k) over the (m, n, k) the
+// method needs: lower triangle only for a SYRK, k >= n / k <= m under the
+// triangular flags.
+static double gemm_terms(int M, int N, int K, bool lower_only, int tri) {
+  double t = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const long long nmax = lower_only ? m : N - 1;
+    const long long kmax = (tri & TRI_A_LOWER) ? (m + 1 < K ? m + 1 : K) : K;
+    if (tri & TRI_B_LOWER_T) {
+      const long long c = nmax + 1 < kmax ? nmax + 1 : kmax;
+      t += (double)(c * kmax - c * (c - 1) / 2);
+    } else {
+      t += (double)(nmax + 1) * (double)kmax;
+    }
+  }
+  return t;
 }
 
 template <class T, bool KA, bool KB>
-static cudaError_t gemm_batched_dispatch(const double* A, long long lda, long long sA, const double* B, long long ldb,
-                                         long long sB, int M, int N, int K, double alpha, double beta, double* C,
-                                         long long ldc, long long sC, int batch, int tri, cudaStream_t s) {
-  dim3 grid((M + T::kBM - 1) / T::kBM, (N + T::kBN - 1) / T::kBN, batch);
+static cudaError_t gemm_batched_dispatch(const double* A, long long lda, const double* B, long long ldb, int M, int N,
+                                         int K, double alpha, double beta, double* C, long long ldc,
+                                         const GemmBatch& bt, bool lower, int tri, cudaStream_t s) {
+  const int tm = (M + T::kBM - 1) / T::kBM;
+  const int nb = bt.b1 * bt.b2;
+  dim3 grid = lower ? dim3(tm * (tm + 1) / 2, 1, nb) : dim3(tm, (N + T::kBN - 1) / T::kBN, nb);
+  KernelTimer kt(KF_FP64_GEMM, s, 2.0 * nb * gemm_terms(M, N, K, lower, tri));
   note_launch();
   k_gemm_batched<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(Operand<KA>{A, lda, M}, Operand<KB>{B, ldb, N},
-                                                                    sA, sB, M, N, K, alpha, beta, C, ldc, sC, tri);
+                                                                    bt, M, N, K, alpha, beta, C, ldc, tri, lower);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
-                                long long ldb, bool kb, long long sB, int M, int N, int K, double alpha, double beta,
-                                double* C, long long ldc, long long sC, int batch, cudaStream_t s, int tri) {
-  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  const long long t64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * batch;
+cudaError_t launch_gemm_batched2(const double* A, long long lda, bool ka, const double* B, long long ldb, bool kb,
+                                 int M, int N, int K, double alpha, double beta, double* C, long long ldc,
+                                 const GemmBatch& bt, bool lower, cudaStream_t s, int tri) {
+  const long long nb = (long long)bt.b1 * bt.b2;
+  if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+  if (nb > 65535 || (lower && M != N)) return cudaErrorInvalidValue;
+  const long long t64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * nb / (lower ? 2 : 1);
   const bool small = t64 < 2 * 152;
 #define ISDF_BGEMM_CASE(TT, a, b) \
-  if (ka == a && kb == b) return gemm_batched_dispatch<TT, a, b>(A, lda, sA, B, ldb, sB, M, N, K, alpha, beta, C, ldc, sC, batch, tri, s);
+  if (ka == a && kb == b) return gemm_batched_dispatch<TT, a, b>(A, lda, B, ldb, M, N, K, alpha, beta, C, ldc, bt, lower, tri, s);
   if (small) {
     ISDF_BGEMM_CASE(TileSm, false, false)
     ISDF_BGEMM_CASE(TileSm, false, true)
@@ -297,12 +336,21 @@ cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long lo
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
+                                long long ldb, bool kb, long long sB, int M, int N, int K, double alpha, double beta,
+                                double* C, long long ldc, long long sC, int batch, cudaStream_t s, int tri) {
+  GemmBatch bt{batch, 1, sA, sB, sC, 0, 0, 0};
+  return launch_gemm_batched2(A, lda, ka, B, ldb, kb, M, N, K, alpha, beta, C, ldc, bt, false, s, tri);
+}
+
 cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
-                                 double* C, long long ldc, bool lower_only, int tile, cudaStream_t s) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 rg((M + 127) / 128, N);
+                                 double* C, long long ldc, bool lower_only, int tile, cudaStream_t s, int batch,
+                                 long long sC) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  dim3 rg((M + 127) / 128, N, batch);
   note_launch();
-  k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, M, N, alpha, beta, C, ldc, lower_only ? 1 : 0, tile);
+  k_splitk_reduce<<<rg, 128, 0, s>>>(partial, splits, M, N, alpha, beta, C, ldc, lower_only ? 1 : 0, tile, sC);
   return cudaGetLastError();
 }
 
@@ -325,11 +373,15 @@ static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B
   } else {
     grid = dim3(tm, tn, splits);
   }
-  note_launch();
-  k_gemm<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
-                                                            use_partial ? partial : nullptr,
-                                                            lower_only ? 1 : 0, tri);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  {
+    KernelTimer kt(KF_FP64_GEMM, s, 2.0 * gemm_terms(M, N, K, lower_only, tri));
+    note_launch();
+    k_gemm<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
+                                                              use_partial ? partial : nullptr,
+                                                              lower_only ? 1 : 0, tri);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || !use_partial) return e;
   dim3 rg((M + 127) / 128, N);
   note_launch();
@@ -424,9 +476,13 @@ cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int
   splits = (K + klen - 1) / klen;
   int tm = (r + 63) / 64;
   dim3 grid(tm * (tm + 1) / 2, 1, splits);
-  note_launch();
-  k_polarizability<<<grid, 256, 0, s>>>(S, K, klen, D, ldd, splits > 1 ? partial : nullptr);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  {
+    KernelTimer kt(KF_FP64_GEMM, s, (double)r * (r + 1) * K);
+    note_launch();
+    k_polarizability<<<grid, 256, 0, s>>>(S, K, klen, D, ldd, splits > 1 ? partial : nullptr);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || splits == 1) return e;
   dim3 rg((r + 127) / 128, r);
   note_launch();
@@ -437,13 +493,21 @@ cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int
 // ------------------------------------------------------------ triangular solve
 constexpr int TRSM_NB = 64;
 
+// Zero an r x r block per problem (problem blockIdx.z at A + z sA).
+__global__ void k_copy_zero(double* A, long long lda, long long sA, int r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < r) A[sA * blockIdx.z + i + lda * (long long)j] = 0.0;
+}
+
 // Inverse of each 64 x 64 diagonal block of the lower-triangular L, written
 // into the diagonal blocks of Bf (lower part; the strict upper part is 0).
 // Thread c solves L_JJ x = e_c by forward substitution.
 __global__ void k_diag_inverse(const double* __restrict__ L, long long ldl, int r, double* __restrict__ Bf,
-                               long long ldb) {
+                               long long ldb, long long sL = 0, long long sB = 0) {
   __shared__ double Ls[TRSM_NB][TRSM_NB + 1];
   __shared__ double Xs[TRSM_NB][TRSM_NB + 1];
+  L += sL * blockIdx.y;  // matrix blockIdx.y of a batch
+  Bf += sB * blockIdx.y;
   const int j0 = blockIdx.x * TRSM_NB;
   const int bs = min(TRSM_NB, r - j0);
   const int c = threadIdx.x;
@@ -540,6 +604,7 @@ cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* 
   if (M <= 0 || r <= 0) return cudaSuccess;
   for (int j0 = 0; j0 < r; j0 += TRSM_NB) {
     int bs = min(TRSM_NB, r - j0);
+    KernelTimer kt(KF_FP64_GEMM, s, (double)M * bs * (2.0 * j0 + bs));
     note_launch();
     k_trsm_step<<<(M + 63) / 64, 256, 0, s>>>(X, ldx, M, Bf, ldb, j0, bs);
     cudaError_t e = cudaGetLastError();
@@ -590,6 +655,50 @@ cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li
       if (e != cudaSuccess) return e;
       e = launch_gemm(Li + (b + bs) + ldi * (long long)(b + bs), ldi, false, work, sb, true, sb, sa, sb, -1.0, 0.0,
                       Li + (b + bs) + ldi * (long long)b, ldi, false, sp, partial, false, s, TRI_A_LOWER);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Li_z = L_z^-1 for batch lower-triangular matrices L + z sL -> Li + z sI;
+// work: batch * (r/2 + 64)^2 doubles.
+cudaError_t launch_tri_inverse_batched(const double* L, long long ldl, long long sL, int r, int batch, double* Li,
+                                       long long ldi, long long sI, double* work, cudaStream_t s) {
+  if (r <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  const long long wq = (long long)(r / 2 + 64) * (r / 2 + 64);
+  note_launch();
+  k_copy_zero<<<dim3((r + 127) / 128, r, batch), 128, 0, s>>>(Li, ldi, sI, r);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nb = (r + TRSM_NB - 1) / TRSM_NB;
+  note_launch();
+  k_diag_inverse<<<dim3(nb, batch), TRSM_NB, 0, s>>>(L, ldl, r, Li, ldi, sL, sI);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int bs = TRSM_NB; bs < r; bs *= 2) {
+    const int full = r / (2 * bs);
+    if (full > 0) {
+      const long long sL1 = 2ll * bs * (1 + ldl), sI1 = 2ll * bs * (1 + ldi), sW1 = (long long)bs * bs;
+      GemmBatch b1{full, batch, sL1, sI1, sW1, sL, sI, wq};
+      e = launch_gemm_batched2(L + bs, ldl, false, Li, ldi, true, bs, bs, bs, 1.0, 0.0, work, bs, b1, false, s,
+                               TRI_B_LOWER_T);
+      if (e != cudaSuccess) return e;
+      GemmBatch b2{full, batch, sI1, sW1, sI1, sI, wq, sI};
+      e = launch_gemm_batched2(Li + bs + ldi * (long long)bs, ldi, false, work, bs, true, bs, bs, bs, -1.0, 0.0,
+                               Li + bs, ldi, b2, false, s, TRI_A_LOWER);
+      if (e != cudaSuccess) return e;
+    }
+    const int b = full * 2 * bs;
+    if (b + bs < r) {
+      const int sa = bs, sb = r - (b + bs);
+      GemmBatch b1{batch, 1, sL, sI, wq, 0, 0, 0};
+      e = launch_gemm_batched2(L + (b + bs) + ldl * (long long)b, ldl, false, Li + b + ldi * (long long)b, ldi, true,
+                               sb, sa, sa, 1.0, 0.0, work, sb, b1, false, s, TRI_B_LOWER_T);
+      if (e != cudaSuccess) return e;
+      GemmBatch b2{batch, 1, sI, wq, sI, 0, 0, 0};
+      e = launch_gemm_batched2(Li + (b + bs) + ldi * (long long)(b + bs), ldi, false, work, sb, true, sb, sa, sb,
+                               -1.0, 0.0, Li + (b + bs) + ldi * (long long)b, ldi, b2, false, s, TRI_A_LOWER);
       if (e != cudaSuccess) return e;
     }
   }

@@ -158,8 +158,8 @@ __device__ __forceinline__ void bfly(C* v, const C* tw, int n) {
 // One Stockham pass of radix R over `nlines` lines of length n (element e of
 // line l at buf[l * sl + e * se]); Ns = product of the radices done so far.
 template <int R, int DIR, class C>
-__device__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int n, int Ns, int nlines, int se,
-                              int sl, const C* tw) {
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int n, int Ns,
+                                              int nlines, int se, int sl, const C* tw) {
   const int nR = n / R;
   const int tstep = n / (Ns * R);
   for (int idx = threadIdx.x; idx < nlines * nR; idx += blockDim.x) {
@@ -202,6 +202,25 @@ __device__ C* fft_lines(C* src, C* dst, const FftAxis& ax, const C* tw, int nlin
     Ns *= R;
   }
   return src;
+}
+
+// ---- compile-time transform length ---------------------------------------
+// With the length known at compile time every index division in the passes
+// becomes a multiplication by a constant and the pass loop unrolls.
+__host__ __device__ constexpr int first_radix(int n) {
+  return n % 4 == 0 ? 4 : n % 2 == 0 ? 2 : n % 3 == 0 ? 3 : n % 5 == 0 ? 5 : n % 7 == 0 ? 7 : n % 11 == 0 ? 11 : 13;
+}
+
+template <int N, int NS, int REM, int DIR, class C>
+__device__ __forceinline__ C* fft_lines_ct(C* src, C* dst, const C* tw, int nlines, int se, int sl) {
+  if constexpr (REM == 1) {
+    return src;
+  } else {
+    constexpr int R = first_radix(REM);
+    stockham_pass<R, DIR>(src, dst, N, NS, nlines, se, sl, tw);
+    __syncthreads();
+    return fft_lines_ct<N, NS * R, REM / R, DIR>(dst, src, tw, nlines, se, sl);
+  }
 }
 
 struct XYShape {
@@ -384,6 +403,101 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z(FftGrid g, typename Real<
   }
 }
 
+// FP32 forward transform for a cubic N^3 grid with N known at compile time:
+// the same steps as k_fft_xy_fwd<float2> and k_fft_z<2, float2>.
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd_ct(FftGrid g, const double* __restrict__ X, long long ldx,
+                                                               float* __restrict__ S, long long lds) {
+  using C = float2;
+  constexpr int H = N / 2 + 1, NP = (N + 1) / 2, BUF = (NP * N > H * N) ? NP * N : H * N;
+  __shared__ C twx[N];
+  __shared__ C b0[BUF], b1[BUF];
+  const int z = blockIdx.x, col = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) twx[t] = from_tw<C>(((const double2*)g.ax[0].tw)[t]);
+  const double* plane = X + ldx * (long long)col + (long long)z * N * N;
+  for (int idx = threadIdx.x; idx < NP * N; idx += blockDim.x) {
+    const int t = idx / N, x = idx - t * N;
+    const double re = plane[x + N * (2 * t)];
+    const double im = (2 * t + 1 < N) ? plane[x + N * (2 * t + 1)] : 0.0;
+    b0[idx] = mk<C>(to_real<float>(re), to_real<float>(im));
+  }
+  __syncthreads();
+  C* res = fft_lines_ct<N, 1, N, -1>(b0, b1, twx, NP, 1, N);
+  C* P = (res == b0) ? b1 : b0;
+  for (int idx = threadIdx.x; idx < NP * H; idx += blockDim.x) {
+    const int t = idx / H, k = idx - t * H;
+    const C zk = res[t * N + k];
+    const C zm = res[t * N + (k == 0 ? 0 : N - k)];
+    P[(2 * t) * H + k] = mk<C>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    if (2 * t + 1 < N) P[(2 * t + 1) * H + k] = mk<C>(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  }
+  __syncthreads();
+  C* other = (P == b0) ? b1 : b0;
+  C* Q = fft_lines_ct<N, 1, N, -1>(P, other, twx, H, H, 1);
+  C* out = (C*)(S + lds * (long long)col) + (long long)z * N * H;
+  for (int idx = threadIdx.x; idx < N * H; idx += blockDim.x) out[idx] = Q[idx];
+}
+
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_slices_ct(FftGrid g, const float* S, long long lds,
+                                                                 const double* __restrict__ wt, __nv_bfloat16* out,
+                                                                 int rows_pad, int kp, int nsl) {
+  using C = float2;
+  constexpr int H = N / 2 + 1, PLANE = N * H;
+  __shared__ C twz[N];
+  __shared__ C b0[N * FFT_ZCHUNK], b1[N * FFT_ZCHUNK];
+  const int q0 = blockIdx.x * FFT_ZCHUNK, col = blockIdx.y;
+  const int nq = min(FFT_ZCHUNK, PLANE - q0);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) twz[t] = from_tw<C>(((const double2*)g.ax[2].tw)[t]);
+  const C* base = (const C*)(S + lds * (long long)col);
+  for (int idx = threadIdx.x; idx < N * FFT_ZCHUNK; idx += blockDim.x) {
+    const int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
+    b0[idx] = c < nq ? base[(long long)z * PLANE + q0 + c] : mk<C>(0.f, 0.f);
+  }
+  __syncthreads();
+  C* R = fft_lines_ct<N, 1, N, -1>(b0, b1, twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
+  const long long sstr = (long long)rows_pad * kp;
+  for (int idx = threadIdx.x; idx < N * FFT_ZCHUNK; idx += blockDim.x) {
+    const int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
+    if (c >= nq) continue;
+    const long long q = (long long)z * PLANE + q0 + c;
+    const float w = to_real<float>(wt[q]);
+    const float v[2] = {R[idx].x * w, R[idx].y * w};
+    __nv_bfloat162 x0, x1, x2;
+    __nv_bfloat16* p0 = reinterpret_cast<__nv_bfloat16*>(&x0);
+    __nv_bfloat16* p1 = reinterpret_cast<__nv_bfloat16*>(&x1);
+    __nv_bfloat16* p2 = reinterpret_cast<__nv_bfloat16*>(&x2);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      p0[h] = __float2bfloat16_rn(v[h]);
+      const float r1 = v[h] - __bfloat162float(p0[h]);
+      p1[h] = __float2bfloat16_rn(r1);
+      p2[h] = __float2bfloat16_rn(r1 - __bfloat162float(p1[h]));
+    }
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + (long long)col * kp + 2 * q);
+    o[0] = x0;
+    if (nsl > 1) o[sstr / 2] = x1;
+    if (nsl > 2) o[sstr] = x2;
+  }
+}
+
+template <int N>
+static cudaError_t fft_slices_ct(const FftGrid& g, const double* X, long long ldx, int ncols, float* S32, long long lds32,
+                                 const double* wt, __nv_bfloat16* out, int rows_pad, int kp, int nsl, cudaStream_t s) {
+  // read theta (8 B per grid point), write nsl BF16 slices of the half spectrum
+  KernelTimer kt(KF_FFT, s, (double)ncols * ((double)N * N * N * 8.0 + (double)N * N * (N / 2 + 1) * 4.0 * nsl));
+  dim3 gxy(N, ncols);
+  note_launch();
+  k_fft_xy_fwd_ct<N><<<gxy, FFT_THREADS, 0, s>>>(g, X, ldx, S32, lds32);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr int PLANE = N * (N / 2 + 1);
+  dim3 gz((PLANE + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+  note_launch();
+  k_fft_z_slices_ct<N><<<gz, FFT_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
+  return cudaGetLastError();
+}
+
 size_t fft_smem_xy(const FftGrid& g) {
   int n1 = g.ax[0].n, n2 = g.ax[1].n, h = g.h;
   int npair = (n2 + 1) / 2;
@@ -417,6 +531,8 @@ cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx,
                                long long lds, const double* wt, size_t smem_xy, size_t smem_z,
                                cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
+  const double nr = (double)g.ax[0].n * g.ax[1].n * g.ax[2].n, nh = (double)g.h * g.ax[1].n * g.ax[2].n;
+  KernelTimer kt(KF_FFT, s, ncols * (nr * 8.0 + nh * 16.0));  // read X, write the half spectrum
   dim3 gxy(g.ax[2].n, ncols);
   note_launch();
   k_fft_xy_fwd<double2><<<gxy, FFT_THREADS, smem_xy, s>>>(g, X, ldx, S, lds);
@@ -434,6 +550,8 @@ cudaError_t launch_fft_convolve(const FftGrid& g, const double* In, long long ld
                                 double* Y, long long ldy, size_t smem_xy, size_t smem_z,
                                 cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
+  const double nr = (double)g.ax[0].n * g.ax[1].n * g.ax[2].n;
+  KernelTimer kt(KF_FFT, s, ncols * nr * 8.0 * (Add ? 3.0 : 2.0));  // read In (and Add), write Y
   dim3 gxy(g.ax[2].n, ncols);
   note_launch();
   k_fft_xy_fwd<double2><<<gxy, FFT_THREADS, smem_xy, s>>>(g, In, ldin, S, lds);
@@ -458,6 +576,22 @@ cudaError_t launch_fft_forward_slices(const FftGrid& g, const double* X, long lo
                                       long long lds32, const double* wt, __nv_bfloat16* out, int rows_pad, int kp,
                                       int nsl, size_t smem_xy, size_t smem_z, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
+  const int n = g.ax[0].n;
+  // bf16x2 stores of (re, im) need kp and rows_pad * kp even: kp is a multiple of 64
+  if (n == g.ax[1].n && n == g.ax[2].n && (kp % 2) == 0) {
+    switch (n) {
+      case 16: return fft_slices_ct<16>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      case 24: return fft_slices_ct<24>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      case 32: return fft_slices_ct<32>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      case 48: return fft_slices_ct<48>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      case 60: return fft_slices_ct<60>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      case 64: return fft_slices_ct<64>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      case 72: return fft_slices_ct<72>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      default: break;
+    }
+  }
+  const double nr = (double)g.ax[0].n * g.ax[1].n * g.ax[2].n, nh = (double)g.h * g.ax[1].n * g.ax[2].n;
+  KernelTimer kt(KF_FFT, s, ncols * (nr * 8.0 + nh * 4.0 * nsl));
   dim3 gxy(g.ax[2].n, ncols);
   note_launch();
   k_fft_xy_fwd<float2><<<gxy, FFT_THREADS, smem_xy / 2, s>>>(g, X, ldx, S32, lds32);

@@ -83,8 +83,11 @@ __device__ __forceinline__ void store_slices8(const V (&v)[8], __nv_bfloat16* ds
 // along the rows where the destination is 16-byte aligned (Kp % 8 == 0),
 // element stores elsewhere.
 __global__ void __launch_bounds__(256) k_slice_cm(const double* __restrict__ src, long long lds, int R, int C, int kv,
-                                                  int kvp, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+                                                  int kvp, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s,
+                                                  long long sstride, long long dstride) {
   __shared__ double t[64][65];
+  src += sstride * blockIdx.z;
+  dst += dstride * blockIdx.z;
   const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     int rr = idx & 63, cc = idx >> 6;
@@ -124,7 +127,10 @@ __global__ void __launch_bounds__(256) k_slice_cm(const double* __restrict__ src
 // Row-major FP64 source (element (row, k) at src[k + lds row]) -> slices;
 // eight k per thread, 16-byte slice stores.
 __global__ void k_slice_rm(const double* __restrict__ src, long long lds, int R, int K,
-                           __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+                           __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s, long long sstride,
+                           long long dstride) {
+  src += sstride * blockIdx.z;
+  dst += dstride * blockIdx.z;
   const int row = blockIdx.y;
   const long long sstr = (long long)Rp * Kp;
   const double* in = src + lds * (long long)row;
@@ -137,24 +143,27 @@ __global__ void k_slice_rm(const double* __restrict__ src, long long lds, int R,
 }
 
 cudaError_t launch_slice_colmajor(const double* src, long long lds, int R, int C, int kv, int kvp,
-                                  __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st) {
-  if (R <= 0 || C <= 0) return cudaSuccess;
-  if (Kp % 8) return cudaErrorInvalidValue;
-  dim3 grid((R + 63) / 64, (C + 63) / 64);
+                                  __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch,
+                                  long long sstride, long long dstride) {
+  if (R <= 0 || C <= 0 || batch <= 0) return cudaSuccess;
+  if (Kp % 8 || batch > 65535 || (dstride % 8)) return cudaErrorInvalidValue;
+  dim3 grid((R + 63) / 64, (C + 63) / 64, batch);
+  KernelTimer kt(KF_SLICE, st, (double)R * C * (8.0 + 2.0 * s) * batch);
   note_launch();
-  k_slice_cm<<<grid, 256, 0, st>>>(src, lds, R, C, kv, kvp, dst, Rp, Kp, s);
+  k_slice_cm<<<grid, 256, 0, st>>>(src, lds, R, C, kv, kvp, dst, Rp, Kp, s, sstride, dstride);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K, __nv_bfloat16* dst, int Rp,
-                                  int Kp, int s, cudaStream_t st) {
-  if (R <= 0 || K <= 0) return cudaSuccess;
-  if (Kp % 8 || Kp < (K + 7) / 8 * 8) return cudaErrorInvalidValue;
+                                  int Kp, int s, cudaStream_t st, int batch, long long sstride, long long dstride) {
+  if (R <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (Kp % 8 || Kp < (K + 7) / 8 * 8 || R > 65535 || batch > 65535 || (dstride % 8)) return cudaErrorInvalidValue;
   int bx = (K + 2047) / 2048;
   if (bx > 64) bx = 64;
-  dim3 grid(bx, R);
+  dim3 grid(bx, R, batch);
+  KernelTimer kt(KF_SLICE, st, (double)R * K * (8.0 + 2.0 * s) * batch);
   note_launch();
-  k_slice_rm<<<grid, 256, 0, st>>>(src, lds, R, K, dst, Rp, Kp, s);
+  k_slice_rm<<<grid, 256, 0, st>>>(src, lds, R, K, dst, Rp, Kp, s, sstride, dstride);
   return cudaGetLastError();
 }
 
@@ -162,8 +171,11 @@ cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K
 // S(a, i n_c + j) = phimu(a, i) phimu(a, n_v + j) sw[i n_c + j], a < r
 // (the columns of C, Eq. MatrixExpressionISDF, scaled by sqrt(-2 Omega^-1)).
 __global__ void k_pair_slices(const double* __restrict__ phimu, long long ldp, int r, int n_v, int n_c,
-                              const double* __restrict__ sw, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s) {
+                              const double* __restrict__ sw, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s,
+                              long long dstride) {
   const int a = blockIdx.y;
+  sw += (long long)n_v * n_c * blockIdx.z;
+  dst += dstride * blockIdx.z;
   const int K = n_v * n_c;
   for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk < K; kk += gridDim.x * blockDim.x) {
     const int i = kk / n_c, j = kk - i * n_c;
@@ -178,14 +190,18 @@ __global__ void k_pair_slices(const double* __restrict__ phimu, long long ldp, i
 }
 
 cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
-                               __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st) {
-  if (r <= 0) return cudaSuccess;
+                               __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch,
+                               long long dstride) {
+  if (r <= 0 || batch <= 0) return cudaSuccess;
+  if (r > 65535 || batch > 65535) return cudaErrorInvalidValue;
   int K = n_v * n_c;
   int bx = (K + 255) / 256;
   if (bx > 128) bx = 128;
-  dim3 grid(bx, r);
+  dim3 grid(bx, r, batch);
+  KernelTimer kt(KF_SLICE, st,
+                 ((double)r * (n_v + n_c) * 8.0 + (double)K * 8.0 + (double)r * K * 2.0 * s) * batch);
   note_launch();
-  k_pair_slices<<<grid, 256, 0, st>>>(phimu, ldp, r, n_v, n_c, sw, dst, Rp, Kp, s);
+  k_pair_slices<<<grid, 256, 0, st>>>(phimu, ldp, r, n_v, n_c, sw, dst, Rp, Kp, s, dstride);
   return cudaGetLastError();
 }
 
@@ -201,6 +217,9 @@ struct TcArgs {
   int lower_only;              // M == N; only tiles with n-tile <= m-tile
   int tri_b;                   // B(n, k) == 0 for k > n: skip chunks beyond the tile's last n
   int tiles_n;                 // number of n tiles (grid.x when !lower_only)
+  int splits;                  // K splits per problem: blockIdx.z = problem * splits + split
+  int a_brows, b_brows;        // rows between the slice stacks of consecutive problems (0: shared)
+  long long c_bstride;         // elements between the C of consecutive problems
   double alpha, beta;
   double* C;
   long long ldc;
@@ -235,7 +254,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mt = blockIdx.y;
   }
   const int m0 = mt * TC_BM, n0 = nt * BN;
-  int kb = blockIdx.z * a.k_per_split;
+  const int bidx = blockIdx.z / a.splits;
+  const int a_row0 = bidx * a.a_brows, b_row0 = bidx * a.b_brows;
+  int kb = (blockIdx.z - bidx * a.splits) * a.k_per_split;
   int ke = min(a.k_iters, kb + a.k_per_split);
   if (a.tri_b) ke = min(ke, (n0 + BN + TC_BK - 1) / TC_BK);
   const int nk = ke > kb ? ke - kb : 0;
@@ -272,8 +293,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint8_t* sb = sa + a.s * TC_BM * TC_BK * 2;
       const int kx = (kb + it) * TC_BK;
       for (int l = 0; l < a.s; ++l) {
-        tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, l * a.a_rows_pad + m0);
-        tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, l * a.b_rows_pad + n0);
+        tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, a_row0 + l * a.a_rows_pad + m0);
+        tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, b_row0 + l * a.b_rows_pad + n0);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -362,10 +383,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           a.partial[(long long)blockIdx.z * a.M * a.N + m + (long long)a.M * n] = tc::f2d(vf);
         } else {
           // alpha = 1, beta = 0 (the common case) needs no FP64 arithmetic
+          double* Cb = a.C + a.c_bstride * bidx;
           double o = (a.alpha == 1.0) ? tc::f2d(vf) : a.alpha * tc::f2d(vf);
-          if (a.beta != 0.0) o += a.beta * a.C[m + a.ldc * n];
-          a.C[m + a.ldc * n] = o;
-          if (a.lower_only && mt != nt) a.C[n + a.ldc * m] = o;
+          if (a.beta != 0.0) o += a.beta * Cb[m + a.ldc * n];
+          Cb[m + a.ldc * n] = o;
+          if (a.lower_only && mt != nt) Cb[n + a.ldc * m] = o;
         }
       }
     }
@@ -406,11 +428,14 @@ static cudaError_t make_map(CUtensorMap* m, const __nv_bfloat16* base, int kp, l
 }
 
 template <int BN, int NACC, int EPI>
-static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, int splits, cudaStream_t st) {
+static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, int splits, int batch,
+                             double mma_flops, cudaStream_t st) {
   CUtensorMap ma, mb;
-  cudaError_t e = make_map(&ma, A.p, A.kp, (long long)A.rows_pad * a.s, TC_BM);
+  const long long arows = (long long)A.rows_pad * a.s + (long long)a.a_brows * (batch - 1);
+  const long long brows = (long long)B.rows_pad * a.s + (long long)a.b_brows * (batch - 1);
+  cudaError_t e = make_map(&ma, A.p, A.kp, arows, TC_BM);
   if (e != cudaSuccess) return e;
-  e = make_map(&mb, B.p, B.kp, (long long)B.rows_pad * a.s, BN);
+  e = make_map(&mb, B.p, B.kp, brows, BN);
   if (e != cudaSuccess) return e;
   const int smem = tc_stages(a.s, BN) * tc_stage_bytes(a.s, BN) + 1024 + 256;
   static bool configured = false;
@@ -423,7 +448,10 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
   if (smem > TC_SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
   const int tm = (a.M + TC_BM - 1) / TC_BM, tn = (a.N + BN - 1) / BN;
   a.tiles_n = tn;
-  dim3 grid = a.lower_only ? dim3(tm * (tm + 1) / 2, 1, splits) : dim3(tn, tm, splits);
+  a.splits = splits;
+  if ((long long)splits * batch > 65535) return cudaErrorInvalidValue;
+  dim3 grid = a.lower_only ? dim3(tm * (tm + 1) / 2, 1, splits * batch) : dim3(tn, tm, splits * batch);
+  KernelTimer kt(KF_TC_GEMM, st, mma_flops);
   note_launch();
   k_tc_gemm<BN, NACC, EPI><<<grid, TC_THREADS, smem, st>>>(ma, mb, a);
   return cudaGetLastError();
@@ -438,10 +466,10 @@ static void split_k(int k_iters, int tiles, int num_sms, int max_split, int& spl
   splits = (k_iters + per - 1) / per;
 }
 
-cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta, double* C,
-                        long long ldc, bool lower_only, bool tri_b, double* partial, int max_split, int num_sms,
-                        unsigned* status, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
+cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
+                                double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
+                                int num_sms, unsigned* status, cudaStream_t st, const TcBatch& bt) {
+  if (M <= 0 || N <= 0 || bt.count <= 0) return cudaSuccess;
   if (A.s != B.s || A.kp != B.kp || A.kp % TC_BK) return cudaErrorInvalidValue;
   if (lower_only && M != N) return cudaErrorInvalidValue;
   TcArgs a{};
@@ -458,18 +486,37 @@ cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, do
   a.C = C;
   a.ldc = ldc;
   a.status = status;
+  a.a_brows = bt.a_rows;
+  a.b_brows = bt.b_rows;
+  a.c_bstride = bt.c_stride;
   const int tm = (M + TC_BM - 1) / TC_BM, tn = (N + 127) / 128;
-  const int tiles = lower_only ? tm * (tm + 1) / 2 : tm * tn;
+  const int tiles = (lower_only ? tm * (tm + 1) / 2 : tm * tn) * bt.count;
   int splits = 1, per = a.k_iters;
   if (partial && !tri_b) split_k(a.k_iters, tiles, num_sms, max_split, splits, per);
   a.k_per_split = per;
+  // BF16 MMA flops of the s (s + 1) / 2 slice products over the outputs the
+  // method needs (lower triangle of a SYRK; k <= n under tri_b)
+  const double prods = 0.5 * a.s * (a.s + 1);
+  const double kk = (double)A.kp;
+  const double outk = lower_only ? 0.5 * M * (M + 1.0) * kk
+                      : tri_b    ? (double)M * 0.5 * N * (N + 1.0)
+                                 : (double)M * N * kk;
+  const double mma = 2.0 * prods * outk * bt.count;
   if (splits > 1) {
     a.partial = partial;
-    cudaError_t e = tc_launch<128, 1, EPI_F64>(A, B, a, splits, st);
+    cudaError_t e = tc_launch<128, 1, EPI_F64>(A, B, a, splits, bt.count, mma, st);
     if (e != cudaSuccess) return e;
-    return launch_splitk_reduce(partial, splits, M, N, alpha, beta, C, ldc, lower_only, TC_BM, st);
+    return launch_splitk_reduce(partial, splits, M, N, alpha, beta, C, ldc, lower_only, TC_BM, st, bt.count,
+                                bt.c_stride);
   }
-  return tc_launch<128, 1, EPI_F64>(A, B, a, 1, st);
+  return tc_launch<128, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st);
+}
+
+cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta, double* C,
+                        long long ldc, bool lower_only, bool tri_b, double* partial, int max_split, int num_sms,
+                        unsigned* status, cudaStream_t st) {
+  return tc_gemm_f64_batched(A, B, M, N, alpha, beta, C, ldc, lower_only, tri_b, partial, max_split, num_sms, status,
+                             st, TcBatch{1, 0, 0, 0});
 }
 
 cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, int kv_iters, double* C,
@@ -493,8 +540,10 @@ cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, i
   a.zs_rows_pad = zs_rows_pad;
   a.zs_kp = zs_kp;
   a.status = status;
-  if (zs) return tc_launch<128, 2, EPI_HAD_SLICES>(A, B, a, 1, st);
-  return tc_launch<128, 2, EPI_HAD_F64>(A, B, a, 1, st);
+  a.splits = 1;
+  const double mma = 2.0 * 0.5 * a.s * (a.s + 1) * (double)M * N * (double)A.kp;
+  if (zs) return tc_launch<128, 2, EPI_HAD_SLICES>(A, B, a, 1, 1, mma, st);
+  return tc_launch<128, 2, EPI_HAD_F64>(A, B, a, 1, 1, mma, st);
 }
 
 }  // namespace isdf

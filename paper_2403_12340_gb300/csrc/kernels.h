@@ -11,6 +11,24 @@ namespace isdf {
 void note_launch();
 long long launch_count();
 
+// Per-launch timing by kernel family.  While an API call on a context with
+// profiling on is inside one of its phases, a KernelTimer records CUDA
+// events around the launch on the launch's own stream, tagged with the
+// family, the phase and the launch's algorithmic work (flops for the GEMM
+// and Cholesky families, bytes for the FFT and slicing families; for
+// KF_TC_GEMM the BF16 MMA flops of the slice products).
+enum { KF_TC_GEMM = 0, KF_FP64_GEMM = 1, KF_CHOL_DIAG = 2, KF_FFT = 3, KF_SLICE = 4, KF_COUNT = 5 };
+struct KernelTimer {
+  KernelTimer(int fam, cudaStream_t s, double work);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+  int fam;
+  cudaStream_t st;
+  double work;
+  cudaEvent_t e0 = nullptr;
+};
+
 // ---- k_dense.cu -----------------------------------------------------------
 cudaError_t launch_check_finite(const double* p, long long n, unsigned* status, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* src, long long lds, const int* idx, int nrows, int ncols,
@@ -45,8 +63,20 @@ cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* 
                                  int r, cudaStream_t s);
 cudaError_t launch_transpose(const double* src, long long lds, int M, int N, double* dst,
                              long long ldd, cudaStream_t s);
-cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s);
-cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s);
+// batch > 1: matrices A + z sA
+cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, int batch = 1, long long sA = 0);
+cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s, int batch = 1,
+                                long long sA = 0);
+// Two-level batch of GEMMs: problem (z1, z2), z1 < b1, z2 < b2, has
+// X_z = X + z1 * sX1 + z2 * sX2 (X = A, B, C); b1 * b2 <= 65535.
+struct GemmBatch {
+  int b1, b2;
+  long long sA1, sB1, sC1, sA2, sB2, sC2;
+};
+// lower: M == N, only the lower tiles are computed and mirrored (SYRK).
+cudaError_t launch_gemm_batched2(const double* A, long long lda, bool ka, const double* B, long long ldb, bool kb,
+                                 int M, int N, int K, double alpha, double beta, double* C, long long ldc,
+                                 const GemmBatch& bt, bool lower, cudaStream_t s, int tri = 0);
 // batch independent GEMMs C_z = alpha op(A_z) op(B_z)^T + beta C_z, z < batch,
 // X_z = X + z * strideX (same layout conventions as launch_gemm)
 cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long long sA, const double* B,
@@ -56,14 +86,21 @@ cudaError_t launch_gemm_batched(const double* A, long long lda, bool ka, long lo
 // doubles; partial (may be null) >= 4 (r/2 + 64)^2 doubles for split-K.
 cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li, long long ldi, double* work,
                                double* partial, cudaStream_t s);
+// Li_z = L_z^-1 for batch lower-triangular r x r matrices L + z sL ->
+// Li + z sI (same merges, one launch per merge for the whole batch);
+// work: batch (r/2 + 64)^2 doubles.
+cudaError_t launch_tri_inverse_batched(const double* L, long long ldl, long long sL, int r, int batch, double* Li,
+                                       long long ldi, long long sI, double* work, cudaStream_t s);
 // L (n_full x n_full column-major) from the row-major pivoted factor Lr.
 cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, const int* rank,
                                       double* L, long long ldl, int n_full, cudaStream_t s);
 
 // C = alpha * sum_z partial[z] + beta * C (partials column-major M x N);
 // lower_only: tiles above the diagonal (tile size `tile`) are read mirrored.
+// batch > 1: problem z reads partial + z * splits * M * N and writes C + z * sC.
 cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
-                                 double* C, long long ldc, bool lower_only, int tile, cudaStream_t s);
+                                 double* C, long long ldc, bool lower_only, int tile, cudaStream_t s, int batch = 1,
+                                 long long sC = 0);
 
 // ---- k_chol_blocked.cu ----------------------------------------------------
 // Blocked Cholesky without pivoting of the symmetric n x n W (column-major,
@@ -73,6 +110,11 @@ cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N
 cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
                                     double* dinv, double* dmax, int* fail, double* pan, cudaStream_t s);
 // pan: n x 64 doubles of scratch (the solved panel).
+// The same for `batch` equal-size matrices W + z sW -> L + z sL; dinv: batch
+// 64 x 64 blocks, dmax and fail: batch entries, pan: batch n x 64.
+cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
+                                            double tol_rel, double* L, long long ldl, long long sL, double* dinv,
+                                            double* dmax, int* fail, double* pan, cudaStream_t s);
 
 // ---- k_chol.cu ------------------------------------------------------------
 struct CholWork {
@@ -140,15 +182,21 @@ struct TcOperand {
 };
 // slices of a column-major FP64 matrix (R x C, element (r, c) at src[r + lds c]);
 // columns c >= kv are shifted to c - kv + kvp (kv = kvp = 0: no shift)
+// batch > 1: matrix z at src + z * sstride, its slices at dst + z * dstride
+// (elements; dstride % 8 == 0), for all three slicing launchers.
 cudaError_t launch_slice_colmajor(const double* src, long long lds, int R, int C, int kv, int kvp,
-                                  __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st);
+                                  __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch = 1,
+                                  long long sstride = 0, long long dstride = 0);
 // slices of a row-major FP64 matrix (R x K, element (r, k) at src[k + lds r])
 cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K, __nv_bfloat16* dst, int Rp,
-                                  int Kp, int s, cudaStream_t st);
+                                  int Kp, int s, cudaStream_t st, int batch = 1, long long sstride = 0,
+                                  long long dstride = 0);
 // Slices of the pair operand at the points, S(a, i n_c + j) =
-// phimu(a, i) phimu(a, n_v + j) sw[i n_c + j] (r rows, K = n_v n_c).
+// phimu(a, i) phimu(a, n_v + j) sw[i n_c + j] (r rows, K = n_v n_c); for
+// batch > 1, problem z uses sw + z n_v n_c.
 cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
-                               __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st);
+                               __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch = 1,
+                               long long dstride = 0);
 // C (M x N, column-major FP64) = alpha sum_{i+j<s} A_i B_j^T + beta C.  With
 // `partial` (max_split * M * N doubles) long K is split over blocks and
 // reduced in FP64.  lower_only: SYRK-style (M == N, mirrored).  tri_b: B is
@@ -156,6 +204,18 @@ cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_
 cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
                         double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
                         int num_sms, unsigned* status, cudaStream_t st);
+// A batch of `count` problems of the same shape: problem b reads its A slice
+// stack starting at row b * a_rows of A.p (a_rows = 0: one A for all), its B
+// at row b * b_rows, and writes C + b * c_stride (split-K partials: b *
+// splits * M * N).
+struct TcBatch {
+  int count;
+  int a_rows, b_rows;
+  long long c_stride;
+};
+cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
+                                double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
+                                int num_sms, unsigned* status, cudaStream_t st, const TcBatch& bt);
 // Face-split Gram (A_v B_v^T) .* (A_c B_c^T): chunks [0, kv_iters) feed the
 // first accumulator, the rest the second.  Output FP64 column-major (C) or,
 // with zs non-null, BF16 slices (row-major M x N, zs_rows_pad x zs_kp).

@@ -50,6 +50,29 @@ inline cudaError_t slices_rm(DevBuf& buf, const double* src, long long lds, int 
 
 inline TcOperand op(const DevBuf& b, int rows_pad, int kp) { return TcOperand{b.bf(), rows_pad, kp, NSL}; }
 
+// Slices of `count` matrices src + z sstride; problem z's slice stack starts
+// at row z NSL rows_pad of buf.  buf must already hold count stacks.
+inline cudaError_t slices_cm_b(DevBuf& buf, const double* src, long long lds, long long sstride, int R, int C,
+                               int rows_pad, int kp, int count, cudaStream_t st) {
+  const size_t per = (size_t)NSL * rows_pad * kp;
+  if (buf.cap * 4 < per * count) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(buf.p, 0, per * count * 2, st);
+  if (e != cudaSuccess) return e;
+  return launch_slice_colmajor(src, lds, R, C, 0, 0, buf.bf(), rows_pad, kp, NSL, st, count, sstride, (long long)per);
+}
+
+inline cudaError_t slices_rm_b(DevBuf& buf, const double* src, long long lds, long long sstride, int R, int K,
+                               int rows_pad, int kp, int count, cudaStream_t st) {
+  const size_t per = (size_t)NSL * rows_pad * kp;
+  if (buf.cap * 4 < per * count) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(buf.p, 0, per * count * 2, st);
+  if (e != cudaSuccess) return e;
+  return launch_slice_rowmajor(src, lds, R, K, buf.bf(), rows_pad, kp, NSL, st, count, sstride, (long long)per);
+}
+
+// byte budget of the pair-operand slices of one batch of frequencies
+constexpr size_t kPairSliceBudget = size_t(4) << 30;
+
 }  // namespace
 
 #define MK(expr)                                        \
@@ -157,6 +180,94 @@ cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega) {
     MK(launch_symmetrize(Dk, r, r, st));
   }
   return cudaSuccess;
+}
+
+// D(w_k) for all frequencies: the same products as mixed_polar_D, each one
+// launch for a chunk of frequencies whose pair slices fit the budget.
+cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
+  const size_t rr = (size_t)r * r;
+  const int rp = pad(r, 128), rk = pad(r, 64);
+  const int npair = n_v * n_c, kpp = pad(npair, 64);
+  const size_t per_pair = (size_t)NSL * rp * kpp, per_sq = (size_t)NSL * rp * rk;
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_omega, kPairSliceBudget / (per_pair * 2)));
+  // all workspace first: a resize frees memory that queued kernels may use
+  MK(cudaStreamSynchronize(st));
+  MK(ensure_bf16(c->m_pairs, per_pair * chunk));
+  MK(ensure_bf16(c->b_s1, per_sq * chunk));
+  MK(ensure(c->b_dtmp, 2 * rr * chunk));
+  double* Dpp = c->b_dtmp.p;
+  double* X = c->b_dtmp.p + rr * chunk;
+  for (int k0 = 0; k0 < n_omega; k0 += chunk) {
+    const int nb = std::min(chunk, n_omega - k0);
+    {
+      PhaseTimer ph(c, ISDF_PH_POLAR_D);
+      MK(cudaMemsetAsync(c->m_pairs.p, 0, per_pair * nb * 2, st));
+      MK(launch_pair_slices(c->phimu_p.p, r, r, n_v, n_c, sw + (size_t)npair * k0, c->m_pairs.bf(), rp, kpp, NSL, st,
+                            nb, (long long)per_pair));
+      const int pr = NSL * rp;
+      MK(tc_gemm_f64_batched(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, Dpp, r, true, false,
+                             nullptr, 1, c->num_sms, c->d_status, st, TcBatch{nb, pr, pr, (long long)rr}));
+    }
+    PhaseTimer ph(c, ISDF_PH_WHITEN_D);
+    const int sr = NSL * rp;
+    MK(slices_cm_b(c->b_s1, Dpp, r, rr, r, r, rp, rk, nb, st));
+    MK(tc_gemm_f64_batched(op(c->m_linvs, rp, rk), op(c->b_s1, rp, rk), r, r, 1.0, 0.0, X, r, false, false, nullptr,
+                           1, c->num_sms, c->d_status, st, TcBatch{nb, 0, sr, (long long)rr}));
+    MK(slices_cm_b(c->b_s1, X, r, rr, r, r, rp, rk, nb, st));
+    MK(tc_gemm_f64_batched(op(c->b_s1, rp, rk), op(c->m_linvs, rp, rk), r, r, 1.0, 0.0, c->D.p + rr * k0, r, false,
+                           true, nullptr, 1, c->num_sms, c->d_status, st, TcBatch{nb, sr, 0, (long long)rr}));
+    MK(launch_symmetrize(c->D.p + rr * k0, r, r, st, nb, (long long)rr));
+  }
+  return cudaSuccess;
+}
+
+// K(w_k) for all frequencies from R(w_k) = c->Rw + k rr: the products of
+// mixed_smw_products_T / _K and the FP64 factorisations, one launch per
+// step for every frequency.
+cudaError_t mixed_smw_batched(isdf_ctx* c, int nw, int* fail_T) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const size_t rr = (size_t)r * r, per_sq = (size_t)NSL * rp * rk;
+  const size_t wq = (size_t)(r / 2 + 64) * (r / 2 + 64);
+  const long long srr = (long long)rr;
+  const int sr = NSL * rp;
+  MK(cudaStreamSynchronize(st));
+  MK(ensure(c->bW1, rr * nw));
+  MK(ensure(c->bT, rr * nw));
+  MK(ensure(c->bU, rr * nw));
+  MK(ensure(c->bQ, rr * nw));
+  MK(ensure_bf16(c->b_s1, per_sq * nw));
+  MK(ensure_bf16(c->b_s2, per_sq * nw));
+  MK(ensure_bf16(c->b_s3, per_sq));
+  MK(ensure(c->b_work, std::max(wq, (size_t)r * 64) * nw));
+  MK(ensure(c->b_cb, (size_t)(64 * 64 + 1) * nw));
+  const double* R = c->Rw.p;
+  // T = I + R^T (G R)
+  MK(slices_cm(c->b_s3, c->G.p, r, r, r, rp, rk, st));
+  MK(slices_rm_b(c->b_s1, R, r, srr, r, r, rp, rk, nw, st));
+  MK(tc_gemm_f64_batched(op(c->b_s3, rp, rk), op(c->b_s1, rp, rk), r, r, 1.0, 0.0, c->bW1.p, r, false, false, nullptr,
+                         1, c->num_sms, c->d_status, st, TcBatch{nw, 0, sr, srr}));
+  MK(slices_rm_b(c->b_s2, c->bW1.p, r, srr, r, r, rp, rk, nw, st));
+  MK(cudaMemsetAsync(c->bT.p, 0, rr * nw * sizeof(double), st));
+  MK(launch_add_identity(c->bT.p, r, r, 1.0, st, nw, srr));
+  MK(tc_gemm_f64_batched(op(c->b_s1, rp, rk), op(c->b_s2, rp, rk), r, r, 1.0, 1.0, c->bT.p, r, false, false, nullptr,
+                         1, c->num_sms, c->d_status, st, TcBatch{nw, sr, sr, srr}));
+  MK(launch_symmetrize(c->bT.p, r, r, st, nw, srr));
+  // T = U U^T (FP64), U^-1, Q = R U^-T, K = -Q Q^T
+  double* dinv = c->b_cb.p;
+  double* dmax = c->b_cb.p + (size_t)64 * 64 * nw;
+  MK(launch_cholesky_blocked_batched(c->bT.p, r, srr, r, nw, 0.0, c->bU.p, r, srr, dinv, dmax, fail_T, c->b_work.p,
+                                     st));
+  MK(launch_tri_inverse_batched(c->bU.p, r, srr, r, nw, c->bQ.p, r, srr, c->b_work.p, st));
+  MK(slices_cm_b(c->b_s1, R, r, srr, r, r, rp, rk, nw, st));
+  MK(slices_cm_b(c->b_s2, c->bQ.p, r, srr, r, r, rp, rk, nw, st));
+  MK(tc_gemm_f64_batched(op(c->b_s1, rp, rk), op(c->b_s2, rp, rk), r, r, 1.0, 0.0, c->bW1.p, r, false, true, nullptr,
+                         1, c->num_sms, c->d_status, st, TcBatch{nw, sr, sr, srr}));
+  MK(slices_cm_b(c->b_s1, c->bW1.p, r, srr, r, r, rp, rk, nw, st));
+  return tc_gemm_f64_batched(op(c->b_s1, rp, rk), op(c->b_s1, rp, rk), r, r, -1.0, 0.0, c->K.p, r, true, false,
+                             nullptr, 1, c->num_sms, c->d_status, st, TcBatch{nw, sr, sr, srr});
 }
 
 // K = -Q Q^T for frequency k into Kk (r x r).  Needs the unpivoted FP64

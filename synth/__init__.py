@@ -225,6 +225,12 @@ BATCH_SYSTEMS = [(24, 8), (27, 18), (30, 28), (32, 38), (32, 49), (36, 59), (40,
                  (45, 89), (45, 99), (48, 109), (50, 119), (54, 130), (54, 140), (60, 150), (60, 160)]
 
 
+def batch_system(i: int) -> System:
+    """System i of the batched full-frequency set (seed index 100 + i)."""
+    n, n_v = BATCH_SYSTEMS[i]
+    return make_system(n, n_v, 7 * n_v, 12 * n_v, 100 + i, name=f"batch{i}")
+
+
 def workload(name: str) -> System:
     cfg = WORKLOADS[name]
     return make_system(cfg["n"], cfg["n_v"], cfg["n_c"], cfg["n_mu"], cfg["seed_index"], name=name)
