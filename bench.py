@@ -418,6 +418,177 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------ full-frequency batch arm
+
+BATCH_OMEGAS = 32
+
+
+def _gen_batch_system(i):
+    import synth
+
+    return synth.batch_system(i)
+
+
+def batch_systems():
+    """The 16-system full-frequency set, generated in spawned host processes."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import synth
+
+    n = len(synth.BATCH_SYSTEMS)
+    workers = max(1, min(8, cpu_cores() // 4))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_batch_system, range(n)))
+
+
+def oracle_batch_sample(s, omegas):
+    """The FP64 oracle on one system at every frequency: fit and G once, then
+    B(w) and K(w) per frequency (the units the batch counts)."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    theta, _ = O.isdf_fit(s.phi, s.n_v, s.mu_idx)
+    g = O.coulomb_in_basis(theta, s.n, s.cell)
+    pm = s.phi[s.mu_idx]
+    for w in omegas:
+        O.capacitance(g, O.polarizability(pm, s.energies, s.n_v, float(w)))
+    return time.perf_counter() - t0
+
+
+def run_batch(args):
+    """Config 4: every system of the set at 32 imaginary frequencies per step,
+    K(w) of every (system, frequency) pair; throughput and per-system latency."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2403_12340_gb300 as pkg
+    import synth
+
+    ws, rank, local = dist_env()
+    systems = batch_systems()  # before CUDA starts (spawned processes)
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    omegas, _ = synth.gauss_legendre_frequencies(BATCH_OMEGAS)
+    for s in systems:
+        s.phi_dev = pkg.to_fortran(s.phi, dev)
+    n_sys = len(systems)
+    batch = pkg.IsdfBatch(systems, prec=PREC[args.prec], n_workers=args.batch_workers)
+    for _ in range(max(1, args.warmup)):
+        batch.run(omegas)  # the first run sizes every workspace
+
+    # parity sample: the smallest system, first and last frequency, 4 probes
+    err = None
+    if rank == 0:
+        import oracle as O
+
+        s0 = systems[0]
+        ctx0, _ = batch.context(0)
+        x = synth.probe_block(s0.n_r, 4)
+        X = pkg.to_fortran(x, dev)
+        Y = pkg.fortran_empty(s0.n_r, 4, dev)
+        errs = []
+        for k in (0, BATCH_OMEGAS - 1):
+            pkg.apply_eps_inv(ctx0, k, X, Y, s0.n_r)
+            ref = O.isdf_smw_solve(s0.phi, s0.energies, s0.n_v, s0.mu_idx, s0.n, s0.cell, x, omega=float(omegas[k]))
+            errs.append(float(np.linalg.norm(Y.cpu().numpy() - ref.y) / np.linalg.norm(ref.y)))
+        err = max(errs)
+
+    ctxs = [batch.context(i)[0] for i in range(n_sys)]
+    sampler = None
+    if rank == 0:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    n0 = pkg.isdf_launch_count()
+    lats, svcs, tot_ms = [], [], 0.0
+    for _ in range(args.steps):
+        lat, svc, tot = batch.run(omegas)
+        lats.append(lat)
+        svcs.append(svc)
+        tot_ms += tot
+    torch.cuda.synchronize(dev)
+    launches = pkg.isdf_launch_count() - n0
+    clocks = sampler.stop() if sampler else None
+    ms_max = max_over_ranks(tot_ms, dev)
+    # kernel timing: one more run with a single worker, so that no other
+    # system's kernels share the GPU with the launch being timed
+    for c in ctxs:
+        pkg.isdf_set_profiling(c, True)
+        pkg.isdf_read_profile(c)
+        pkg.isdf_read_kernel_profile(c)
+    _, _, prof_ms = batch.run(omegas, n_workers=1)
+    kprof = {}
+    for c in ctxs:
+        for key, (ms, cnt, w) in pkg.isdf_read_kernel_profile(c).items():
+            a = kprof.get(key, (0.0, 0, 0.0))
+            kprof[key] = (a[0] + ms, a[1] + cnt, a[2] + w)
+        pkg.isdf_set_profiling(c, False)
+    solves = ws * n_sys * BATCH_OMEGAS * args.steps
+    value = solves / (ms_max / 1e3)
+    lat_all = np.concatenate(lats)
+    svc_all = np.concatenate(svcs)
+
+    flops_run = 0.0
+    for s in systems:
+        n_half2 = 2 * (s.n[0] // 2 + 1) * s.n[1] * s.n[2]
+        fl = algorithmic_flops(s.n_r, s.n_e, s.n_v * s.n_c, s.n_mu, 0, n_half2)
+        flops_run += (fl["points_chol"] + fl["fit_gram"] + fl["fit_trsm"] + fl["coulomb_fft"] + fl["coulomb_syrk"]
+                      + BATCH_OMEGAS * (fl["polar_d"] + fl["whiten_d"] + fl["smw"]))
+    peaks = measured_peaks()
+    cells = [kernel_roofline(f, ph, ms, cnt, w, 1, peaks) for (f, ph), (ms, cnt, w) in kprof.items() if cnt and ms > 0]
+    cells.sort(key=lambda c: -c["ms_per_step"])
+    for c in cells:
+        c["timed_in"] = f"a one-worker run after the timed runs ({prof_ms:.0f} ms for the whole batch)"
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t = oracle_batch_sample(systems[0], omegas)
+        cpu = {"value": round(BATCH_OMEGAS / t, 3), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": (f"system 0 of the set ({systems[0].n[0]}^3, N_v={systems[0].n_v}, N_mu={systems[0].n_mu}) "
+                          f"at all {BATCH_OMEGAS} frequencies: fit and G once, B(w) and K(w) per frequency, "
+                          f"{t:.1f} s, numpy/scipy FP64")}
+    if rank == 0:
+        sizes = ", ".join(f"{s.n[0]}^3/{s.n_v}" for s in systems)
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else "bf16x3 (f32 accumulate) + f64", "data": "synthetic",
+            "config": {"workload": (f"batch16: 16 systems (grid^3/N_v: {sizes}), N_c = 7 N_v, N_mu = 12 N_v, "
+                                    f"{BATCH_OMEGAS} Gauss-Legendre imaginary frequencies each; a solve is "
+                                    "K(w) of one (system, frequency)"),
+                       "precision": args.prec, "precision_detail": PREC_DETAIL[args.prec],
+                       "host_workers": args.batch_workers, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (phi 0.05-2.2 GB per system)",
+                       "timing": "host wall clock around each run; a run returns after every system's GPU work"},
+            "tflops": round(flops_run * args.steps * ws / (ms_max / 1e3) / 1e12, 3),
+            "flops_per_step": flops_run,
+            "latency_ms": {"p50": round(float(np.percentile(lat_all, 50)), 2),
+                           "p99": round(float(np.percentile(lat_all, 99)), 2),
+                           "kind": "per system, from the start of the run to its last K(w)"},
+            "service_ms": {"p50": round(float(np.percentile(svc_all, 50)), 2),
+                           "p99": round(float(np.percentile(svc_all, 99)), 2),
+                           "kind": "per system, from the start of its fit to its last K(w)"},
+            "rel_err_vs_oracle": err,
+            "roofline": cells[0] if cells else None, "kernels": cells[:8],
+            "cpu_baseline": cpu, "e2e": None,
+            "e2e_note": "not measured for the batch: the default bench line carries the end-to-end number",
+            "gpu_launches": int(launches), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 # ---------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -462,11 +633,16 @@ def main(argv=None):
                     help="mixed: split-BF16 tensor-core contractions (the headline); fp64: FP64 pipe only")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path next to the mixed one")
+    ap.add_argument("--workload", choices=["isdf48", "batch16"], default="isdf48",
+                    help="isdf48: one 48^3 system (the default line); batch16: 16 systems x 32 frequencies")
+    ap.add_argument("--batch-workers", type=int, default=4, help="host threads of the batch runner")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch16":
+        run_batch(args)
     else:
         run_native(args)
 

@@ -213,6 +213,53 @@ ISDF_API int isdf_screened_basis(isdf_ctx* ctx, int omega_index, double* W_out);
 ISDF_API int isdf_adjoint(isdf_ctx* ctx, int omega_index, const double* W_bar, double* grad_energies,
                           double* grad_phimu);
 
+/* ---- Batched full-frequency runner ----------------------------------------
+ * Many systems of different sizes, every frequency of each (the
+ * full-frequency form of Algorithm 3 steps 1-3 over a set of systems).
+ * The paper has no counterpart: it treats one system at a time.  Each
+ * system keeps its own context, CUDA stream and theta for the life of the
+ * batch (repeated runs allocate nothing new once the first run has sized the
+ * workspaces); a run hands the systems, largest estimated cost first, to a
+ * pool of host threads that drive isdf_fit, build_polarizability and
+ * smw_inverse_all of one system at a time, so that systems overlap on the
+ * GPU. */
+typedef struct isdf_batch isdf_batch;
+typedef struct {
+  int n1, n2, n3;           /* grid */
+  double L1, L2, L3;        /* cell lengths (Bohr) */
+  const double* phi;        /* device, N_r x (n_v + n_c), ld N_r; kept alive by the caller */
+  int n_v, n_c;
+  const int64_t* mu_idx;    /* host, n_mu grid indices (copied at create) */
+  int n_mu;
+  const double* energies;   /* host, n_v + n_c (Hartree; copied at create) */
+} isdf_system;
+
+/* Create a batch on the current device: one context, non-blocking stream and
+ * theta buffer (N_r x n_mu float64) per system.  prec: ISDF_PREC_FP64 or
+ * ISDF_PREC_MIXED for every system.  n_workers: host threads of a run
+ * (1..64).  On error *batch is NULL and isdf_batch_last_error(NULL) says
+ * why. */
+ISDF_API int isdf_batch_create(isdf_batch** batch, const isdf_system* systems, int n_systems, int prec,
+                               int n_workers);
+ISDF_API int isdf_batch_destroy(isdf_batch* batch);
+
+/* Fit, polarizability and SMW capacitance of every system at the n_omega
+ * frequencies omega (host, Hartree, >= 0) on n_workers host threads (0: the
+ * number given at create; 1 runs the systems one after the other, which
+ * isolates each kernel for timing).  latency_ms (host, n_systems, or
+ * NULL): time from the start of the run to the moment that system's K(w)
+ * were all complete on the GPU; service_ms (host, n_systems, or NULL): time
+ * from the start of that system's fit to the same moment; total_ms (host, or
+ * NULL): the whole run.  Returns the first error of any system (and stops
+ * handing out systems). */
+ISDF_API int isdf_batch_run(isdf_batch* batch, const double* omega, int n_omega, int n_workers,
+                            double* latency_ms, double* service_ms, double* total_ms);
+
+/* The context of one system (for apply_eps_inv, smw K copies, profiling)
+ * and its rank after the last run. */
+ISDF_API int isdf_batch_context(isdf_batch* batch, int system, isdf_ctx** ctx, int* rank);
+ISDF_API const char* isdf_batch_last_error(isdf_batch* batch);
+
 /* Split-precision DGEMM on the tensor cores, the building block of the
  * mixed-precision path (the paper has no counterpart; it is a GB300 means
  * of running FP64 contractions at tensor-core rates).

@@ -33,7 +33,8 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "isdf_set_profiling", "isdf_read_profile", "isdf_phase_name", "isdf_launch_count",
             "apply_eps_inv_noalloc", "isdf_dgemm_split", "isdf_dgemm_split_error",
             "isdf_read_kernel_profile", "isdf_kernel_family_name", "isdf_set_point_orbitals",
-            "isdf_screened_basis", "isdf_adjoint", "smw_inverse_all"]
+            "isdf_screened_basis", "isdf_adjoint", "smw_inverse_all", "isdf_batch_create",
+            "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 5
 
@@ -80,6 +81,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_read_profile.argtypes = [P, P, P]
     lib.isdf_phase_name.argtypes = [I]
     lib.isdf_phase_name.restype = ctypes.c_char_p
+    lib.isdf_batch_create.argtypes = [P, P, I, I, I]
+    lib.isdf_batch_destroy.argtypes = [P]
+    lib.isdf_batch_run.argtypes = [P, P, I, I, P, P, P]
+    lib.isdf_batch_context.argtypes = [P, I, P, P]
+    for name in ["isdf_batch_create", "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context"]:
+        getattr(lib, name).restype = I
+    lib.isdf_batch_last_error.argtypes = [P]
+    lib.isdf_batch_last_error.restype = ctypes.c_char_p
     lib.smw_inverse_all.argtypes = [P, P]
     lib.smw_inverse_all.restype = I
     lib.isdf_set_point_orbitals.argtypes = [P, P, LL]
@@ -420,3 +429,71 @@ def _autograd_function():
 def screened_coulomb_basis(solver, energies, phi_mu, omega=0.0):
     """Differentiable W_P = P^T eps^-1 V P (torch.autograd) on a fitted solver."""
     return _autograd_function().apply(solver, energies, phi_mu, omega)
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+                ("L1", ctypes.c_double), ("L2", ctypes.c_double), ("L3", ctypes.c_double),
+                ("phi", ctypes.c_void_p), ("n_v", ctypes.c_int), ("n_c", ctypes.c_int),
+                ("mu_idx", ctypes.c_void_p), ("n_mu", ctypes.c_int), ("energies", ctypes.c_void_p)]
+
+
+class IsdfBatch:
+    """Many systems, all frequencies (isdf_batch_* of the C ABI).  systems:
+    objects with n, cell, n_v, n_c, mu_idx, energies and a column-major
+    float64 CUDA tensor `phi_dev` (N_r x N_e), kept alive here."""
+
+    def __init__(self, systems, prec=ISDF_PREC_FP64, n_workers=4):
+        lib = load_library()
+        self._keep = []
+        arr = (_System * len(systems))()
+        for i, s in enumerate(systems):
+            mu = np.ascontiguousarray(np.asarray(s.mu_idx, dtype=np.int64))
+            e = np.ascontiguousarray(np.asarray(s.energies, dtype=np.float64))
+            n_r = int(np.prod(s.n))
+            pp = _dev_ptr(s.phi_dev, n_r, s.n_v + s.n_c, "phi_dev")
+            self._keep += [mu, e, s.phi_dev]
+            arr[i] = _System(s.n[0], s.n[1], s.n[2], s.cell[0], s.cell[1], s.cell[2], pp, s.n_v, s.n_c,
+                             mu.ctypes.data, mu.shape[0], e.ctypes.data)
+        h = ctypes.c_void_p()
+        rc = lib.isdf_batch_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(systems), int(prec),
+                                   int(n_workers))
+        if rc != ISDF_OK:
+            raise IsdfError(rc, (lib.isdf_batch_last_error(None) or b"").decode())
+        self.h = h
+        self.n = len(systems)
+
+    def run(self, omega, n_workers=0):
+        """(latency_ms, service_ms, total_ms) of one run over all systems
+        (n_workers 0: the number given at creation)."""
+        lib = load_library()
+        w = np.ascontiguousarray(np.atleast_1d(np.asarray(omega, dtype=np.float64)))
+        lat = np.zeros(self.n)
+        svc = np.zeros(self.n)
+        tot = ctypes.c_double(0.0)
+        rc = lib.isdf_batch_run(self.h, w.ctypes.data, int(w.shape[0]), int(n_workers), lat.ctypes.data,
+                                svc.ctypes.data, ctypes.byref(tot))
+        if rc != ISDF_OK:
+            raise IsdfError(rc, (lib.isdf_batch_last_error(self.h) or b"").decode())
+        return lat, svc, tot.value
+
+    def context(self, i):
+        """(context handle, rank) of system i."""
+        c = ctypes.c_void_p()
+        r = ctypes.c_int(0)
+        lib = load_library()
+        rc = lib.isdf_batch_context(self.h, int(i), ctypes.byref(c), ctypes.byref(r))
+        if rc != ISDF_OK:
+            raise IsdfError(rc, (lib.isdf_batch_last_error(self.h) or b"").decode())
+        return c, r.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            load_library().isdf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

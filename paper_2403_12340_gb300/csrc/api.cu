@@ -275,8 +275,7 @@ static int cholesky(isdf_ctx* c, const double* W, long long ldw, int n, int pivo
 // on success, else the first column whose pivot fell to tol_rel * max diag.
 static int cholesky_blocked(isdf_ctx* c, const double* W, long long ldw, int n, double tol_rel, double* Lout,
                             int* fail, cudaStream_t st) {
-  CK(launch_cholesky_blocked(W, ldw, n, tol_rel, Lout, n, c->cb_work.p + 64, c->cb_work.p, fail,
-                             c->cb_work.p + 64 + 64 * 64, st));
+  CK(launch_cholesky_blocked(W, ldw, n, tol_rel, Lout, n, c->cb_work.p, fail, st));
   return ISDF_OK;
 }
 
@@ -331,7 +330,7 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   CK(ensure(c->Lc, (size_t)n_mu * n_mu));
   const double tol = (double)n_mu * 2.220446049250313e-16;
   int rc0 = ISDF_OK;
-  CK(ensure(c->cb_work, 64 + 64 * 64 + (size_t)n_mu * 64));
+  CK(ensure(c->cb_work, 1));
   {
     PhaseScope ph(c, ISDF_PH_POINTS);
     CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
@@ -484,7 +483,7 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
   CK(ensure(c->D, std::max<size_t>(rr * n_omega, 1)));
   CK(ensure(c->K, std::max<size_t>(rr * n_omega, 1)));
   CK(ensure(c->Rw, std::max<size_t>(rr * n_omega, 1)));
-  CK(ensure(c->cb_work, 64 + 64 * 64 + (size_t)std::max(r, 1) * 64));
+  CK(ensure(c->cb_work, 1));
   if (c->cap_fail < (size_t)n_omega) {
     if (c->d_fail) cudaFree(c->d_fail);
     c->d_fail = nullptr;
@@ -505,7 +504,7 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
     CK(ensure(c->partial, (size_t)std::max(sp, spd) * rr));
     CK(ensure(c->sw, npair * n_omega));
     CK(ensure(c->tmp1, rr));
-    if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)(64 * 64 + 1 + (size_t)r * 64) * n_omega));
+    if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)n_omega));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
     std::vector<double> sw(npair * n_omega);
     for (int k = 0; k < n_omega; ++k) {
@@ -546,11 +545,8 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
       if (rc0 != ISDF_OK) return rc0;
       PhaseScope ph(c, ISDF_PH_SMW, c->s2);
       if (n_omega > 1) {  // all frequencies in one factorisation sequence
-        double* dinv = c->b_cbd.p;
-        double* dmax = dinv + (size_t)64 * 64 * n_omega;
-        double* pan = dmax + n_omega;
-        CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr, dinv,
-                                           dmax, c->d_fail, pan, c->s2));
+        CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr,
+                                           c->b_cbd.p, c->d_fail, c->s2));
       } else {
         rc0 = cholesky_blocked(c, c->D.p, r, r, 0.0, c->Rw.p, c->d_fail, c->s2);
         if (rc0 != ISDF_OK) return rc0;

@@ -1,0 +1,205 @@
+// Batched full-frequency runner (declared in include/isdf_smw.h): many
+// systems of different sizes, every frequency of each, on one GPU.
+//
+// Each system owns a context, a non-blocking CUDA stream and its theta
+// buffer for the life of the batch, so repeated runs allocate nothing.  A
+// run hands the systems, largest estimated cost first, to a pool of host
+// worker threads; a worker runs one system's fit, all-frequency
+// polarizability and all-frequency SMW (smw_inverse_all) on the system's
+// stream, then takes the next.  Systems on different workers overlap on the
+// GPU; the largest start first, so the small ones fill the tail.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/isdf_smw.h"
+
+struct isdf_batch {
+  int device = 0;
+  int prec = 0;
+  int n_workers = 1;
+  struct Sys {
+    isdf_system d;
+    std::vector<int64_t> mu;
+    std::vector<double> energies;
+    isdf_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    double* theta = nullptr;
+    int rank = 0;
+    double cost = 0.0;
+  };
+  std::vector<Sys> sys;
+  std::vector<int> order;  // largest estimated cost first
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_err;
+
+void free_batch(isdf_batch* b) {
+  for (auto& s : b->sys) {
+    if (s.ctx) isdf_destroy(s.ctx);
+    if (s.theta) cudaFree(s.theta);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  delete b;
+}
+
+// flops of one system's fit, polarizability and SMW at n_omega frequencies,
+// for the largest-first order
+double cost_estimate(const isdf_system& d, int n_omega) {
+  const double nr = (double)d.n1 * d.n2 * d.n3, m = d.n_mu, ne = d.n_v + d.n_c, np = (double)d.n_v * d.n_c;
+  return nr * m * (2.0 * ne + m) + nr * m * m + n_omega * (m * m * np + 9.0 * m * m * m);
+}
+
+}  // namespace
+
+extern "C" int isdf_batch_create(isdf_batch** out, const isdf_system* systems, int n_systems, int prec,
+                                 int n_workers) {
+  g_batch_create_err.clear();
+  if (!out || !systems) {
+    g_batch_create_err = "isdf_batch_create: null pointer argument";
+    return ISDF_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n_systems < 1 || n_workers < 1 || n_workers > 64) {
+    g_batch_create_err = "isdf_batch_create: need n_systems >= 1 and 1 <= n_workers <= 64";
+    return ISDF_ERR_SHAPE;
+  }
+  if (prec != ISDF_PREC_FP64 && prec != ISDF_PREC_MIXED) {
+    g_batch_create_err = "isdf_batch_create: prec must be ISDF_PREC_FP64 or ISDF_PREC_MIXED";
+    return ISDF_ERR_ARG;
+  }
+  isdf_batch* b = new isdf_batch();
+  b->prec = prec;
+  b->n_workers = n_workers;
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    delete b;
+    g_batch_create_err = "isdf_batch_create: no current CUDA device";
+    return ISDF_ERR_CUDA;
+  }
+  b->sys.resize(n_systems);
+  for (int i = 0; i < n_systems; ++i) {
+    const isdf_system& d = systems[i];
+    auto& s = b->sys[i];
+    if (!d.phi || !d.mu_idx || !d.energies || d.n_mu < 1 || d.n_v < 1 || d.n_c < 1) {
+      free_batch(b);
+      g_batch_create_err = "isdf_batch_create: system " + std::to_string(i) + " has a null pointer or empty size";
+      return ISDF_ERR_ARG;
+    }
+    s.d = d;
+    s.mu.assign(d.mu_idx, d.mu_idx + d.n_mu);
+    s.energies.assign(d.energies, d.energies + d.n_v + d.n_c);
+    s.d.mu_idx = s.mu.data();
+    s.d.energies = s.energies.data();
+    cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    const long long nr = (long long)d.n1 * d.n2 * d.n3;
+    if (e == cudaSuccess) e = cudaMalloc(&s.theta, (size_t)nr * d.n_mu * sizeof(double));
+    if (e != cudaSuccess) {
+      free_batch(b);
+      g_batch_create_err = std::string("isdf_batch_create: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? ISDF_ERR_NOMEM : ISDF_ERR_CUDA;
+    }
+    int rc = isdf_create(&s.ctx, d.n1, d.n2, d.n3, d.L1, d.L2, d.L3, s.stream);
+    if (rc != ISDF_OK) {
+      g_batch_create_err = std::string("isdf_batch_create: system ") + std::to_string(i) + ": " +
+                           isdf_last_error(nullptr);
+      free_batch(b);
+      return rc;
+    }
+  }
+  b->order.resize(n_systems);
+  for (int i = 0; i < n_systems; ++i) b->order[i] = i;
+  *out = b;
+  return ISDF_OK;
+}
+
+extern "C" int isdf_batch_destroy(isdf_batch* b) {
+  if (!b) return ISDF_ERR_ARG;
+  for (auto& s : b->sys)
+    if (s.stream) cudaStreamSynchronize(s.stream);
+  free_batch(b);
+  return ISDF_OK;
+}
+
+extern "C" int isdf_batch_run(isdf_batch* b, const double* omega, int n_omega, int n_workers, double* latency_ms,
+                              double* service_ms, double* total_ms) {
+  if (!b) return ISDF_ERR_ARG;
+  b->err.clear();
+  if (!omega || n_omega < 1) {
+    b->err = "isdf_batch_run: need n_omega >= 1 frequencies";
+    return ISDF_ERR_ARG;
+  }
+  if (n_workers < 0 || n_workers > 64) {
+    b->err = "isdf_batch_run: n_workers must be in [0, 64]";
+    return ISDF_ERR_ARG;
+  }
+  const int n = (int)b->sys.size();
+  for (auto& s : b->sys) s.cost = cost_estimate(s.d, n_omega);
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int x, int y) { return b->sys[x].cost > b->sys[y].cost; });
+  std::vector<double> lat(n, 0.0), svc(n, 0.0);
+  std::atomic<int> next{0};
+  std::atomic<int> first_rc{ISDF_OK};
+  std::mutex err_mu;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms_since = [](std::chrono::steady_clock::time_point a) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+  };
+  auto worker = [&]() {
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+      first_rc.store(ISDF_ERR_CUDA);
+      return;
+    }
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n || first_rc.load() != ISDF_OK) return;
+      auto& s = b->sys[b->order[i]];
+      const auto ts = std::chrono::steady_clock::now();
+      int rc = isdf_fit(s.ctx, s.d.phi, s.d.n_v, s.d.n_c, s.d.mu_idx, s.d.n_mu, b->prec, s.theta, &s.rank);
+      if (rc == ISDF_OK) rc = build_polarizability(s.ctx, s.d.energies, omega, n_omega, nullptr, nullptr);
+      if (rc == ISDF_OK) rc = smw_inverse_all(s.ctx, nullptr);
+      if (rc != ISDF_OK) {
+        int expect = ISDF_OK;
+        if (first_rc.compare_exchange_strong(expect, rc)) {
+          std::lock_guard<std::mutex> g(err_mu);
+          b->err = "isdf_batch_run: system " + std::to_string(b->order[i]) + ": " + isdf_last_error(s.ctx);
+        }
+        return;
+      }
+      svc[b->order[i]] = ms_since(ts);
+      lat[b->order[i]] = ms_since(t0);
+    }
+  };
+  std::vector<std::thread> pool;
+  const int nw = std::min(n_workers > 0 ? n_workers : b->n_workers, n);
+  for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  if (total_ms) *total_ms = ms_since(t0);
+  if (latency_ms)
+    for (int i = 0; i < n; ++i) latency_ms[i] = lat[i];
+  if (service_ms)
+    for (int i = 0; i < n; ++i) service_ms[i] = svc[i];
+  return first_rc.load();
+}
+
+extern "C" int isdf_batch_context(isdf_batch* b, int system, isdf_ctx** ctx, int* rank) {
+  if (!b || !ctx) return ISDF_ERR_ARG;
+  if (system < 0 || system >= (int)b->sys.size()) {
+    b->err = "isdf_batch_context: system index out of range";
+    return ISDF_ERR_ARG;
+  }
+  *ctx = b->sys[system].ctx;
+  if (rank) *rank = b->sys[system].rank;
+  return ISDF_OK;
+}
+
+extern "C" const char* isdf_batch_last_error(isdf_batch* b) {
+  return b ? b->err.c_str() : g_batch_create_err.c_str();
+}

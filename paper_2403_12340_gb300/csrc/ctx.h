@@ -73,7 +73,7 @@ struct isdf_ctx {
   DevBuf Rw;             // Cholesky factors of D(w), one r x r block per frequency
   int* d_fail = nullptr; // their failure flags
   size_t cap_fail = 0;
-  DevBuf cb_work;  // blocked Cholesky: [0] max diagonal, [64..] 64 x 64 inverse block
+  DevBuf cb_work;  // blocked Cholesky: the max diagonal
   DevBuf m_phis, m_phimus, m_zs, m_linv, m_linvs, m_work, m_thetas_t, m_s32, m_ss, m_pairs, m_sa, m_sb, m_xs;
 
   // phase profiling

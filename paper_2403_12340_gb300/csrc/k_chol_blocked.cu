@@ -1,9 +1,9 @@
 // Blocked right-looking Cholesky (no pivoting), FP64.
 //
 // For J = 0, 1, ...: the 64 x 64 diagonal block is factored in shared memory
-// by one thread block, which also inverts its factor; the panel below is
-// solved as one GEMM with that inverse; the trailing matrix gets a SYRK
-// update.  All the O(n^3) work is in the two GEMMs, which use every SM.
+// by one thread block; the panel below is solved in place by forward
+// substitution, one warp per row over every SM; the trailing matrix gets a
+// lower SYRK update, which carries nearly all of the O(n^3) work.
 //
 // A pivot at or below tol_rel * max(diag) stops the factorisation: the
 // first failing column goes to *fail and every later kernel of the sequence
@@ -36,38 +36,32 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
   }
 }
 
-// Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place and
-// write its inverse into dinv (bs x bs, ld CB).  One thread block on one
-// SM, whose FP64 pipe (2 DFMA / clock) is the limit, so the kernel issues as
-// few FP64 warp instructions as it can:
-//  * the rank-1 update of step j touches only the m (m + 1) / 2 entries of
-//    the remaining lower triangle, packed densely over the threads through a
-//    table of (row, column) offsets, so no lane idles under a mask;
-//  * one reciprocal square root per pivot (thread 0), columns scaled by it;
-//  * the inverse by 16 x 16 blocks: the four diagonal blocks in parallel by
-//    forward substitution, then the off-diagonal blocks as products
-//    X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ in order of I - J, which keeps
-//    the dependent FMA chains 16 long instead of up to 2000.
+// Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place; the
+// strict upper part of the block is zeroed.  One thread block on one SM,
+// whose FP64 pipe (2 DFMA / clock) is the limit, so the kernel issues as few
+// FP64 warp instructions and barriers as it can: right-looking outer
+// products on the unscaled columns, A(i, k) -= A(i, j) A(k, j) / d_j with
+// d_j the current pivot, over the m (m + 1) / 2 entries of the remaining
+// lower triangle packed densely over the threads through a table of
+// (row, column) offsets, one barrier per column; each warp forms 1 / d_j
+// itself (no serial step on one thread).  Column j is scaled by d_j^-1/2 and
+// the diagonal set to d_j^1/2 at the end.
 constexpr int TRI = CB * (CB - 1) / 2;  // entries of a strictly lower 63-row triangle
 
-__global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int j0, int bs, double* dinv,
-                                                  const double* dmax, double tol_rel, int* fail, long long sA = 0) {
+__global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int j0, int bs, const double* dmax,
+                                                  double tol_rel, int* fail, long long sA = 0) {
   __shared__ double Ls[CB][CB + 1];
-  // problem blockIdx.x of a batch: its matrix, inverse block, max and flag
+  __shared__ double sq[CB], rsq[CB];
+  __shared__ unsigned char ta[TRI], tb[TRI];
+  // problem blockIdx.x of a batch: its matrix, max and flag
   A += sA * blockIdx.x;
-  dinv += (long long)CB * CB * blockIdx.x;
   dmax += blockIdx.x;
   fail += blockIdx.x;
-  __shared__ double Xs[CB][CB + 1];
-  __shared__ double rdiag[CB];
-  __shared__ unsigned char ta[TRI], tb[TRI];
-  __shared__ int s_bad;
   if (*(volatile int*)fail >= 0) return;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31;
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
     int i = idx & (CB - 1), k = idx >> 6;
     Ls[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
-    Xs[i][k] = 0.0;
   }
   // (a, b) with b <= a for the packed index a (a + 1) / 2 + b
   for (int a = t; a < CB - 1; a += blockDim.x) {
@@ -77,74 +71,79 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
       tb[base + b] = (unsigned char)b;
     }
   }
-  if (t == 0) s_bad = -1;
   const double thresh = tol_rel * (*dmax);
   __syncthreads();
+  int bad = -1;
   for (int j = 0; j < bs; ++j) {
-    if (t == 0) {
-      const double d = Ls[j][j];
-      if (!(d > thresh)) {  // also catches NaN
-        s_bad = j;
-      } else {
-        const double ri = rsqrt(d);
-        Ls[j][j] = d * ri;
-        rdiag[j] = ri;
-      }
+    const double d = Ls[j][j];  // the same value in every thread: the branch below is uniform
+    if (!(d > thresh)) {        // also catches NaN
+      bad = j;
+      break;
     }
-    __syncthreads();
-    if (s_bad >= 0) break;
-    const double r = rdiag[j];
-    for (int i = j + 1 + t; i < bs; i += blockDim.x) Ls[i][j] *= r;
-    __syncthreads();
-    // Ls[i][k] -= Ls[i][j] Ls[k][j] for j < k <= i < bs, packed
+    double rd = 0.0;
+    if (lane == 0) rd = 1.0 / d;
+    rd = __shfl_sync(0xffffffffu, rd, 0);
     const int m = bs - j - 1;
     const int cnt = m * (m + 1) / 2;
     for (int idx = t; idx < cnt; idx += blockDim.x) {
       const int i = j + 1 + ta[idx], k = j + 1 + tb[idx];
-      Ls[i][k] = fma(-Ls[i][j], Ls[k][j], Ls[i][k]);
+      Ls[i][k] = fma(-Ls[i][j] * rd, Ls[k][j], Ls[i][k]);
     }
     __syncthreads();
   }
-  if (s_bad >= 0) {
-    if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
+  if (bad >= 0) {
+    if (t == 0) atomicCAS(fail, -1, j0 + bad);
     return;
   }
-  // inverse, step 1: the four diagonal 16 x 16 blocks (thread = block * 16 + column)
-  if (t < CB) {
-    const int o = (t >> 4) * 16, c = o + (t & 15);
-    if (c < bs) {
-      Xs[c][c] = rdiag[c];
-      for (int i = c + 1; i < o + 16 && i < bs; ++i) {
-        double acc = 0.0;
-        for (int k = c; k < i; ++k) acc = fma(Ls[i][k], Xs[k][c], acc);
-        Xs[i][c] = -acc * rdiag[i];
-      }
-    }
+  if (t < bs) {
+    const double r = sqrt(Ls[t][t]);
+    sq[t] = r;
+    rsq[t] = 1.0 / r;
   }
   __syncthreads();
-  // step 2: off-diagonal blocks by distance; thread (row u, col v) of a 16 x 16 block
-  const int u = t & 15, v = t >> 4;
-  for (int dist = 1; dist < 4; ++dist) {
-    for (int J = 0; J + dist < 4; ++J) {
-      const int I = J + dist;
-      // W = sum_{K=J}^{I-1} L_IK X_KJ  (16 x 16), then X_IJ = -X_II W
-      double w = 0.0;
-      for (int K = J; K < I; ++K)
-        for (int q = 0; q < 16; ++q) w = fma(Ls[I * 16 + u][K * 16 + q], Xs[K * 16 + q][J * 16 + v], w);
-      __syncthreads();
-      Ls[J * 16 + u][I * 16 + v] = w;  // scratch in the (unused) strict upper part
-      __syncthreads();
-      double x = 0.0;
-      for (int q = 0; q <= u; ++q) x = fma(Xs[I * 16 + u][I * 16 + q], Ls[J * 16 + q][I * 16 + v], x);
-      __syncthreads();
-      Xs[I * 16 + u][J * 16 + v] = -x;
-      __syncthreads();
-    }
-  }
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
-    int i = idx % bs, k = idx / bs;
-    A[(j0 + i) + lda * (long long)(j0 + k)] = (k <= i) ? Ls[i][k] : 0.0;
-    dinv[i + CB * k] = (k <= i) ? Xs[i][k] : 0.0;
+    const int i = idx % bs, k = idx / bs;
+    A[(j0 + i) + lda * (long long)(j0 + k)] = (k < i) ? Ls[i][k] * rsq[k] : (k == i ? sq[k] : 0.0);
+  }
+}
+
+// The panel below a factored diagonal block, A21 <- A21 L_jj^-T, in place:
+// one warp per row, lane l holding columns l and l + 32 of the row; forward
+// substitution by columns, each solved value broadcast by a shuffle.  Rows
+// are independent, so every SM takes part however short the panel is.
+__global__ void __launch_bounds__(256) k_panel_trsm(double* A, long long lda, int j0, int bs, int rem,
+                                                   const int* fail, long long sA = 0) {
+  __shared__ double Lt[CB][CB + 1];  // Lt[c][k] = L_jj(c, k), zero outside the lower triangle
+  __shared__ double inv[CB];
+  A += sA * blockIdx.y;  // problem blockIdx.y of a batch
+  if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < CB * CB; idx += blockDim.x) {
+    const int i = idx & (CB - 1), k = idx >> 6;
+    Lt[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
+  }
+  __syncthreads();
+  if (t < bs) inv[t] = 1.0 / Lt[t][t];
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+  for (int row = blockIdx.x * 8 + warp; row < rem; row += gridDim.x * 8) {
+    double* a = A + (j0 + bs + row) + lda * (long long)j0;
+    double x0 = lane < bs ? a[lda * lane] : 0.0;
+    double x1 = lane + 32 < bs ? a[lda * (lane + 32)] : 0.0;
+    for (int k = 0; k < bs; ++k) {
+      double xk;
+      if (k < 32) {
+        if (lane == k) x0 *= inv[k];
+        xk = __shfl_sync(0xffffffffu, x0, k);
+      } else {
+        if (lane == k - 32) x1 *= inv[k];
+        xk = __shfl_sync(0xffffffffu, x1, k - 32);
+      }
+      if (lane > k) x0 = fma(-xk, Lt[lane][k], x0);
+      if (lane + 32 > k) x1 = fma(-xk, Lt[lane + 32][k], x1);
+    }
+    if (lane < bs) a[lda * lane] = x0;
+    if (lane + 32 < bs) a[lda * (lane + 32)] = x1;
   }
 }
 
@@ -164,8 +163,13 @@ __global__ void k_copy_block(const double* __restrict__ src, long long lds, long
   if (i < rows && j < cols) dst[sD * blockIdx.z + i + ldd * j] = src[sS * blockIdx.z + i + lds * j];
 }
 
+static unsigned panel_blocks(int rem) {
+  const int b = (rem + 7) / 8;
+  return (unsigned)(b < 4 * 152 ? b : 4 * 152);
+}
+
 cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
-                                    double* dinv, double* dmax, int* fail, double* pan, cudaStream_t s) {
+                                    double* dmax, int* fail, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
   if (L != W) {
@@ -179,25 +183,22 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
     {
-      // factor bs^3 / 3 flops and triangular inverse bs^3 / 3 flops
-      KernelTimer kt(KF_CHOL_DIAG, s, 2.0 * bs * bs * bs / 3.0);
+      KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0);  // bs^3 / 3 flops
       note_launch();
-      k_chol_diag<<<1, 256, 0, s>>>(L, ldl, j0, bs, dinv, dmax, tol_rel, fail);
+      k_chol_diag<<<1, 256, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
-    // panel: L[j0+bs:, J] = A[j0+bs:, J] Dinv^T, computed into `pan` (rem x bs,
-    // ld n) and copied back: a tile narrower than the panel must not
-    // overwrite columns that another block still reads
-    double* Pj = L + (j0 + bs) + ldl * (long long)j0;
-    e = launch_gemm(Pj, ldl, false, dinv, CB, false, rem, bs, bs, 1.0, 0.0, pan, n, false, 1, nullptr, false, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpy2DAsync(Pj, ldl * sizeof(double), pan, n * sizeof(double), rem * sizeof(double), bs,
-                          cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
+    {
+      KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs);  // triangular solve, rem bs^2 flops
+      note_launch();
+      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles, mirrored)
-    e = launch_gemm(pan, n, false, pan, n, false, rem, rem, bs, -1.0, 1.0, L + (j0 + bs) + ldl * (long long)(j0 + bs),
+    double* Pj = L + (j0 + bs) + ldl * (long long)j0;
+    e = launch_gemm(Pj, ldl, false, Pj, ldl, false, rem, rem, bs, -1.0, 1.0, L + (j0 + bs) + ldl * (long long)(j0 + bs),
                     ldl, true, 1, nullptr, false, s);
     if (e != cudaSuccess) return e;
   }
@@ -208,11 +209,11 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
 }
 
 // The same factorisation for `batch` matrices of equal size n (W_z = W + z
-// sW, L_z = L + z sL): one launch per step covers every matrix.  dinv:
-// batch 64 x 64 blocks, dmax / fail: batch entries, pan: batch n x 64.
+// sW, L_z = L + z sL): one launch per step covers every matrix.  dmax and
+// fail: batch entries.
 cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
-                                            double tol_rel, double* L, long long ldl, long long sL, double* dinv,
-                                            double* dmax, int* fail, double* pan, cudaStream_t s) {
+                                            double tol_rel, double* L, long long ldl, long long sL, double* dmax,
+                                            int* fail, cudaStream_t s) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -224,26 +225,25 @@ cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long
   note_launch();
   k_diag_max<<<batch, 256, 0, s>>>(L, ldl, n, dmax, fail, sL);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long sP = (long long)n * CB;
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
     {
-      KernelTimer kt(KF_CHOL_DIAG, s, 2.0 * bs * bs * bs / 3.0 * batch);
+      KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0 * batch);
       note_launch();
-      k_chol_diag<<<batch, 256, 0, s>>>(L, ldl, j0, bs, dinv, dmax, tol_rel, fail, sL);
+      k_chol_diag<<<batch, 256, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
+    {
+      KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs * batch);
+      note_launch();
+      k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     double* Pj = L + (j0 + bs) + ldl * (long long)j0;
-    GemmBatch pb{batch, 1, sL, (long long)CB * CB, sP, 0, 0, 0};
-    e = launch_gemm_batched2(Pj, ldl, false, dinv, CB, false, rem, bs, bs, 1.0, 0.0, pan, n, pb, false, s);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    k_copy_block<<<dim3((rem + 127) / 128, bs, batch), 128, 0, s>>>(pan, n, sP, Pj, ldl, sL, rem, bs);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    GemmBatch tb{batch, 1, sP, sP, sL, 0, 0, 0};
-    e = launch_gemm_batched2(pan, n, false, pan, n, false, rem, rem, bs, -1.0, 1.0,
+    GemmBatch tb{batch, 1, sL, sL, sL, 0, 0, 0};
+    e = launch_gemm_batched2(Pj, ldl, false, Pj, ldl, false, rem, rem, bs, -1.0, 1.0,
                              L + (j0 + bs) + ldl * (long long)(j0 + bs), ldl, tb, true, s);
     if (e != cudaSuccess) return e;
   }

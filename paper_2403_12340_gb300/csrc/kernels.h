@@ -106,15 +106,14 @@ cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N
 // Blocked Cholesky without pivoting of the symmetric n x n W (column-major,
 // lower part read) into L (may equal W).  *fail = -1 on success, else the
 // first column whose pivot is <= tol_rel * max(diag W) (later steps are
-// skipped).  dinv: 64 x 64 doubles of scratch; dmax: one double.
+// skipped); dmax: one double of scratch.
 cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
-                                    double* dinv, double* dmax, int* fail, double* pan, cudaStream_t s);
-// pan: n x 64 doubles of scratch (the solved panel).
-// The same for `batch` equal-size matrices W + z sW -> L + z sL; dinv: batch
-// 64 x 64 blocks, dmax and fail: batch entries, pan: batch n x 64.
+                                    double* dmax, int* fail, cudaStream_t s);
+// The same for `batch` equal-size matrices W + z sW -> L + z sL; dmax and
+// fail: batch entries.
 cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
-                                            double tol_rel, double* L, long long ldl, long long sL, double* dinv,
-                                            double* dmax, int* fail, double* pan, cudaStream_t s);
+                                            double tol_rel, double* L, long long ldl, long long sL, double* dmax,
+                                            int* fail, cudaStream_t s);
 
 // ---- k_chol.cu ------------------------------------------------------------
 struct CholWork {

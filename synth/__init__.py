@@ -216,7 +216,7 @@ def gauss_legendre_frequencies(count: int = 32, omega0: float = 1.0) -> Tuple[np
 WORKLOADS = {
     "isdf16": dict(n=16, n_v=4, n_c=28, n_mu=128, seed_index=0),
     "isdf48": dict(n=48, n_v=64, n_c=448, n_mu=1536, seed_index=1),
-    "isdf72": dict(n=72, n_v=256, n_c=1792, n_mu=6144, seed_index=2),
+    "isdf72": dict(n=72, n_v=256, n_c=1792, n_mu=6144, seed_index=2, points="random"),
 }
 
 # Batched full-frequency set: 16 systems (grid n, N_v), N_c = 7 N_v,
@@ -225,12 +225,38 @@ BATCH_SYSTEMS = [(24, 8), (27, 18), (30, 28), (32, 38), (32, 49), (36, 59), (40,
                  (45, 89), (45, 99), (48, 109), (50, 119), (54, 130), (54, 140), (60, 150), (60, 160)]
 
 
+def random_points(n_r: int, n_mu: int, seed: int) -> np.ndarray:
+    """n_mu distinct grid points drawn uniformly (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.asarray(rng.choice(n_r, size=n_mu, replace=False), dtype=np.int64)
+
+
 def batch_system(i: int) -> System:
-    """System i of the batched full-frequency set (seed index 100 + i)."""
+    """System i of the batched full-frequency set (seed index c = 100 + i):
+    orbitals seed 1000 + c, energies 2000 + c, and N_mu uniformly random
+    distinct points (seed 3000 + c) instead of QRCP, whose host cost (minutes
+    for the largest systems) would dominate the generation."""
     n, n_v = BATCH_SYSTEMS[i]
-    return make_system(n, n_v, 7 * n_v, 12 * n_v, 100 + i, name=f"batch{i}")
+    c = 100 + i
+    nn = (n, n, n)
+    n_c = 7 * n_v
+    phi = make_orbitals(nn, n_v + n_c, 1000 + c)
+    energies = make_energies(n_v, n_c, 2000 + c)
+    mu = random_points(n * n * n, 12 * n_v, 3000 + c)
+    cell = tuple(v * GRID_SPACING_BOHR for v in nn)
+    return System(n=nn, cell=cell, n_v=n_v, n_c=n_c, phi=phi, energies=energies, mu_idx=mu, name=f"batch{i}")
 
 
 def workload(name: str) -> System:
+    """A named workload; points by QRCP, or (isdf72, whose QRCP would take
+    hours of host time) N_mu uniformly random distinct points, seed 3000 + c."""
     cfg = WORKLOADS[name]
-    return make_system(cfg["n"], cfg["n_v"], cfg["n_c"], cfg["n_mu"], cfg["seed_index"], name=name)
+    if cfg.get("points") != "random":
+        return make_system(cfg["n"], cfg["n_v"], cfg["n_c"], cfg["n_mu"], cfg["seed_index"], name=name)
+    c = cfg["seed_index"]
+    nn = (cfg["n"],) * 3
+    phi = make_orbitals(nn, cfg["n_v"] + cfg["n_c"], 1000 + c)
+    energies = make_energies(cfg["n_v"], cfg["n_c"], 2000 + c)
+    mu = random_points(int(np.prod(nn)), cfg["n_mu"], 3000 + c)
+    cell = tuple(v * GRID_SPACING_BOHR for v in nn)
+    return System(n=nn, cell=cell, n_v=cfg["n_v"], n_c=cfg["n_c"], phi=phi, energies=energies, mu_idx=mu, name=name)

@@ -90,3 +90,33 @@ def test_smw_inverse_all_state_errors():
         with pytest.raises(pkg.IsdfError) as ei:
             sol.smw_all(1)
         assert ei.value.code == -9
+
+
+def test_batch_runner_many_systems():
+    """isdf_batch_*: three systems of different sizes, four frequencies, two
+    host workers; every system's eps^-1 X at every frequency against the
+    oracle, and a second run of the same batch gives the same K."""
+    import torch
+    import paper_2403_12340_gb300 as pkg
+
+    systems = [small_system(16, 4, 12, n_mu=40, seed_index=85), small_system((12, 15, 10), 3, 9, n_mu=24, seed_index=86),
+               small_system(18, 5, 20, n_mu=96, seed_index=87)]
+    omegas, _ = synth.gauss_legendre_frequencies(4)
+    for s in systems:
+        s.phi_dev = pkg.to_fortran(s.phi)
+    for prec in (0, 1):
+        batch = pkg.IsdfBatch(systems, prec=prec, n_workers=2)
+        lat, svc, tot = batch.run(omegas)
+        assert np.all(lat > 0) and np.all(svc > 0) and np.all(svc <= lat + 1e-6) and tot >= lat.max()
+        for i, s in enumerate(systems):
+            ctx, rank = batch.context(i)
+            x = synth.probe_block(s.n_r, 3)
+            X = pkg.to_fortran(x)
+            Y = pkg.fortran_empty(s.n_r, 3, X.device)
+            for k, w in enumerate(omegas):
+                pkg.apply_eps_inv(ctx, k, X, Y, s.n_r)
+                ref = O.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x, omega=float(w))
+                assert rel_fro(Y.cpu().numpy(), ref.y) < TOL[prec], (prec, i, k)
+        batch.run(omegas)
+        torch.cuda.synchronize()
+        batch.close()
