@@ -83,7 +83,16 @@ enum {
  * in FP32; the Cholesky factorisations, triangular inverses and the FFT of
  * the probe block stay in FP64.  Results agree with FP64 to about 1e-6
  * relative on well-conditioned systems. */
-enum { ISDF_PREC_FP64 = 0, ISDF_PREC_MIXED = 1 };
+enum { ISDF_PREC_FP64 = 0, ISDF_PREC_MIXED = 1, ISDF_PREC_MIXED_PAIRS = 2 };
+/* MIXED whitens D as L_r^-1 (C_r Omega^-1 C_r^T) L_r^-T, which multiplies
+ * the FP32-grade error of the pair products by cond(C C^T); when the fit's
+ * factor shows mean(lambda) mean(1/lambda) > 4 for the eigenvalues of
+ * C C^T (from ||L_r||_F and ||L_r^-1||_F; this is 1 for a perfectly
+ * conditioned C C^T and grows with its condition number) it instead forms
+ * S = L_r^-1 C_r diag(sqrt(-2 Omega^-1)) in pair space and D = S S^T, which
+ * multiplies that error by cond(L_r) only, at the cost of one more
+ * N_mu x N_pairs x N_mu tensor-core GEMM.  MIXED_PAIRS takes the pair-space
+ * route always. */
 
 /* Create a context for one periodic grid n1 x n2 x n3 with cell lengths
  * L1, L2, L3 (Bohr).  cuda_stream is a cudaStream_t (NULL = legacy default
@@ -126,6 +135,27 @@ ISDF_API int isdf_fit(isdf_ctx* ctx, const double* phi, int n_v, int n_c, const 
  * Requires a successful isdf_fit. */
 ISDF_API int build_polarizability(isdf_ctx* ctx, const double* energies, const double* omega, int n_omega,
                          double* D_out, double* G_out);
+
+/* build_polarizability for the static case (w = 0) with D computed by the
+ * contour integral of Algorithm 2 instead of the sum over pairs:
+ * B = C Omega^-1 C^T = (1/pi) Im of the integral of J(z) over the upper
+ * half of a contour around the unoccupied energies,
+ * J(z) = (Psi_v diag(1/(z - e_v)) Psi_v^T) .* (Psi_c diag(1/(z - e_c)) Psi_c^T),
+ * with the conformal map of Algorithm 2 and the midpoint rule with n_nodes
+ * nodes; the quadrature error falls like exp(-pi^2 n_nodes / (2 log(Q/q) + 6))
+ * (Eq. rel_err_Cauchy; q the gap, Q the width from the highest occupied
+ * energy to the top of the unoccupied band).  Costs 2 N_mu^2 (n_v + n_c)
+ * FP64 flops per node instead of N_mu^2 n_v n_c.  energies, D_out, G_out
+ * as for build_polarizability; the context then holds one frequency
+ * (omega_index 0, w = 0).  ISDF_ERR_ARG unless 1 <= n_nodes <= 1024. */
+ISDF_API int build_polarizability_contour(isdf_ctx* ctx, const double* energies, int n_nodes, double* D_out,
+                                          double* G_out);
+
+/* Nodes that the bound of Eq. rel_err_Cauchy asks for a relative
+ * quadrature error tol (0 < tol < 1), from the energies (host, n_v + n_c);
+ * negative ISDF_ERR_* on bad arguments or no gap.  The bound's constant is
+ * not known, and in practice fewer nodes reach tol. */
+ISDF_API int isdf_contour_nodes(const double* energies, int n_v, int n_c, double tol);
 
 /* SMW capacitance for frequency omega[omega_index] (K of Section "Cubic
  * scaling algorithm", Algorithm 3 step 3), in the singular-B-safe form

@@ -27,6 +27,8 @@ ERRORS = {
     -9: "ISDF_ERR_STATE", -10: "ISDF_ERR_NOMEM",
 }
 ISDF_PREC_FP64 = 0
+ISDF_PREC_MIXED = 1
+ISDF_PREC_MIXED_PAIRS = 2
 
 EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
             "apply_eps_inv", "isdf_fit_factor", "isdf_last_error", "isdf_version",
@@ -34,7 +36,8 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "apply_eps_inv_noalloc", "isdf_dgemm_split", "isdf_dgemm_split_error",
             "isdf_read_kernel_profile", "isdf_kernel_family_name", "isdf_set_point_orbitals",
             "isdf_screened_basis", "isdf_adjoint", "smw_inverse_all", "isdf_batch_create",
-            "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error"]
+            "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error",
+            "build_polarizability_contour", "isdf_contour_nodes"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 5
 
@@ -89,6 +92,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = I
     lib.isdf_batch_last_error.argtypes = [P]
     lib.isdf_batch_last_error.restype = ctypes.c_char_p
+    lib.build_polarizability_contour.argtypes = [P, P, I, P, P]
+    lib.build_polarizability_contour.restype = I
+    lib.isdf_contour_nodes.argtypes = [P, I, I, D]
+    lib.isdf_contour_nodes.restype = I
     lib.smw_inverse_all.argtypes = [P, P]
     lib.smw_inverse_all.restype = I
     lib.isdf_set_point_orbitals.argtypes = [P, P, LL]
@@ -198,6 +205,21 @@ def build_polarizability(ctx, energies, omega, D_out=None, G_out=None) -> None:
     pg = 0 if G_out is None else _dev_ptr(G_out.reshape(-1), name="G_out")
     _check(load_library().build_polarizability(ctx, e.ctypes.data, w.ctypes.data, int(w.shape[0]), pd, pg),
            ctx)
+
+
+def build_polarizability_contour(ctx, energies, n_nodes: int, D_out=None, G_out=None) -> None:
+    e = np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
+    pd = 0 if D_out is None else _dev_ptr(D_out.reshape(-1), name="D_out")
+    pg = 0 if G_out is None else _dev_ptr(G_out.reshape(-1), name="G_out")
+    _check(load_library().build_polarizability_contour(ctx, e.ctypes.data, int(n_nodes), pd, pg), ctx)
+
+
+def isdf_contour_nodes(energies, n_v: int, n_c: int, tol: float) -> int:
+    e = np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
+    n = load_library().isdf_contour_nodes(e.ctypes.data, int(n_v), int(n_c), float(tol))
+    if n < 0:
+        raise IsdfError(n, "isdf_contour_nodes: bad arguments or no gap")
+    return n
 
 
 def smw_inverse(ctx, omega_index: int = 0, K_out=None) -> None:
@@ -343,6 +365,16 @@ class IsdfSmw:
         D = torch.empty((w.shape[0], self.n_mu, self.n_mu), dtype=torch.float64, device=dev) if want_D else None
         G = torch.empty((self.n_mu, self.n_mu), dtype=torch.float64, device=dev) if want_G else None
         build_polarizability(self.ctx, energies, w, D, G)
+        return D, G
+
+    def polarizability_contour(self, energies, n_nodes, want_D=False, want_G=False):
+        """Static D by the contour integral of Algorithm 2 (one frequency, w = 0)."""
+        import torch
+
+        dev = self.theta.device
+        D = torch.empty((1, self.n_mu, self.n_mu), dtype=torch.float64, device=dev) if want_D else None
+        G = torch.empty((self.n_mu, self.n_mu), dtype=torch.float64, device=dev) if want_G else None
+        build_polarizability_contour(self.ctx, energies, n_nodes, D, G)
         return D, G
 
     def smw(self, omega_index=0, want_K=False):

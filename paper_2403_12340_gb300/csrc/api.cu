@@ -24,6 +24,10 @@ using isdf::release;
 
 static thread_local std::string g_create_err;
 
+// Above this value of mean(lambda) mean(1 / lambda) of C C^T (cond(C C^T) of
+// about 14 or more) the mixed path whitens D in pair space.
+static constexpr double kPairWhitenMean = 4.0;
+
 using PhaseScope = isdf::PhaseTimer;
 
 static int fail(isdf_ctx* c, int code, const std::string& msg) {
@@ -226,7 +230,8 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->m_linvs, &c->m_work, &c->m_thetas_t, &c->m_s32, &c->m_ss, &c->m_pairs, &c->m_sa,
                     &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
-                    &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd};
+                    &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
+                    &c->m_pairs_t, &c->swf, &c->kappa_work};
   for (DevBuf* b : bufs) release(*b);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
@@ -299,6 +304,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   c->fitted = false;
   c->polar_ready = false;
   if (!phi || !theta || !mu_idx) return fail(c, ISDF_ERR_ARG, "isdf_fit: null pointer argument");
+  const int mode = prec;
+  if (prec == ISDF_PREC_MIXED_PAIRS) prec = ISDF_PREC_MIXED;
   if (prec != ISDF_PREC_FP64 && prec != ISDF_PREC_MIXED)
     return fail(c, ISDF_ERR_ARG, "isdf_fit: unknown precision mode");
   if (n_v < 1 || n_c < 1) return fail(c, ISDF_ERR_SHAPE, "isdf_fit: n_v and n_c must be >= 1");
@@ -404,6 +411,10 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     if (prec == ISDF_PREC_MIXED) {
       if (!gram_done) CK(isdf::mixed_fit_gram(c, phi, c->phimu_p.p, n_v, n_c, r));
       CK(isdf::mixed_fit_solve(c, theta, r));
+      // ||L||_F^2 = tr(C C^T) and ||L^-1||_F^2 = tr((C C^T)^-1), read by build_polarizability
+      CK(ensure(c->kappa_work, 2 + 256));
+      CK(launch_sumsq(c->Lc.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p, c->stream));
+      CK(launch_sumsq(c->m_linv.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p + 1, c->stream));
     } else {
       // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
       if (!gram_done) {
@@ -421,6 +432,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   c->phi = phi;
   c->theta = theta;
   c->prec = prec;
+  c->pair_mode = mode;
+  c->pair_whiten = mode == ISDF_PREC_MIXED_PAIRS;
   c->n_v = n_v;
   c->n_c = n_c;
   c->n_mu = n_mu;
@@ -459,8 +472,10 @@ static int split_for(long long tiles, long long K, int num_sms) {
   return (int)std::max(1ll, std::min(want, std::min(maxs, 64ll)));
 }
 
-extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const double* omega, int n_omega,
-                                    double* D_out, double* G_out) {
+// D(w) for every frequency and G; with n_nodes > 0 the static D by the
+// contour integral of Algorithm 2 instead of the pair sum.
+static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, int n_omega, double* D_out,
+                      double* G_out, int n_nodes) {
   if (!c) return ISDF_ERR_ARG;
   c->err.clear();
   if (!c->fitted) return fail(c, ISDF_ERR_STATE, "build_polarizability: call isdf_fit first");
@@ -479,6 +494,14 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
   c->polar_ready = false;
   const size_t rr = (size_t)r * r;
   CK(cudaStreamSynchronize(c->stream));
+  if (c->prec == ISDF_PREC_MIXED && c->pair_mode == ISDF_PREC_MIXED && r > 0) {
+    // mean(lambda) mean(1 / lambda) of C C^T: 1 when perfectly conditioned, at
+    // most (1 + cond)^2 / (4 cond) (Kantorovich), so a large value flags a
+    // large cond(C C^T)
+    double fro[2] = {0.0, 0.0};
+    CK(cudaMemcpy(fro, c->kappa_work.p, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    c->pair_whiten = (fro[0] / r) * (fro[1] / r) > kPairWhitenMean;
+  }
   CK(ensure(c->G, std::max<size_t>(rr, 1)));
   CK(ensure(c->D, std::max<size_t>(rr * n_omega, 1)));
   CK(ensure(c->K, std::max<size_t>(rr * n_omega, 1)));
@@ -505,6 +528,8 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
     CK(ensure(c->sw, npair * n_omega));
     CK(ensure(c->tmp1, rr));
     if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)n_omega));
+    if (n_nodes > 0) CK(ensure(c->ctab, (size_t)2 * n_nodes * (n_e + 1)));
+    if (c->pair_whiten) CK(ensure(c->swf, (npair * n_omega + 1) / 2));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
     std::vector<double> sw(npair * n_omega);
     for (int k = 0; k < n_omega; ++k) {
@@ -517,7 +542,35 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
     }
     CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // D(w) for every frequency (main stream)
-    if (c->prec == ISDF_PREC_MIXED) {
+    if (n_nodes > 0) {
+      // static D by the contour integral: resolvent weights of every node
+      std::vector<double> wt, wn;
+      CK(contour_tables(energies, n_v, n_c, n_nodes, wt, wn));
+      CK(cudaMemcpyAsync(c->ctab.p, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->ctab.p + wt.size(), wn.data(), wn.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream));
+      double* Dpp = c->prec == ISDF_PREC_MIXED ? c->tmp1.p : c->D.p;
+      {
+        PhaseScope ph(c, ISDF_PH_POLAR_D);
+        CK(launch_contour_polarizability(c->phimu_p.p, r, r, n_v, n_c, c->ctab.p, c->ctab.p + wt.size(), n_nodes, Dpp,
+                                         r, c->partial.p, c->partial.cap, c->num_sms, c->stream));
+      }
+      if (c->prec == ISDF_PREC_MIXED) {
+        CK(isdf::mixed_whiten_D(c, Dpp, c->D.p));
+      } else {
+        PhaseScope ph(c, ISDF_PH_WHITEN_D);
+        CK(launch_trsm_right_lt(c->D.p, r, r, c->Bf.p, r, r, c->stream));
+        CK(launch_transpose(c->D.p, r, r, r, c->tmp1.p, r, c->stream));
+        CK(launch_trsm_right_lt(c->tmp1.p, r, r, c->Bf.p, r, r, c->stream));
+        CK(launch_symmetrize(c->tmp1.p, r, r, c->stream));
+        CK(cudaMemcpyAsync(c->D.p, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      }
+    } else if (c->prec == ISDF_PREC_MIXED && c->pair_whiten) {
+      std::vector<float> swf(sw.begin(), sw.end());
+      CK(cudaMemcpyAsync(c->swf.p, swf.data(), swf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
+      CK(isdf::mixed_polar_D_pairspace(c, reinterpret_cast<const float*>(c->swf.p), n_omega));
+    } else if (c->prec == ISDF_PREC_MIXED) {
       if (n_omega > 1) {
         CK(isdf::mixed_polar_D_batched(c, c->sw.p, n_omega));
       } else {
@@ -586,6 +639,31 @@ extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const d
   c->k_ready.assign(n_omega, 0);
   c->polar_ready = true;
   return ISDF_OK;
+}
+
+extern "C" int build_polarizability(isdf_ctx* c, const double* energies, const double* omega, int n_omega,
+                                    double* D_out, double* G_out) {
+  return polar_impl(c, energies, omega, n_omega, D_out, G_out, 0);
+}
+
+extern "C" int build_polarizability_contour(isdf_ctx* c, const double* energies, int n_nodes, double* D_out,
+                                            double* G_out) {
+  if (!c) return ISDF_ERR_ARG;
+  if (n_nodes < 1 || n_nodes > 1024) return fail(c, ISDF_ERR_ARG, "build_polarizability_contour: n_nodes in [1, 1024]");
+  const double w0 = 0.0;
+  return polar_impl(c, energies, &w0, 1, D_out, G_out, n_nodes);
+}
+
+extern "C" int isdf_contour_nodes(const double* energies, int n_v, int n_c, double tol) {
+  if (!energies || n_v < 1 || n_c < 1 || !(tol > 0.0) || !(tol < 1.0)) return ISDF_ERR_ARG;
+  double e_n = energies[0], e_lo = energies[n_v], e_hi = energies[n_v];
+  for (int i = 0; i < n_v; ++i) e_n = std::max(e_n, energies[i]);
+  for (int i = n_v; i < n_v + n_c; ++i) {
+    e_lo = std::min(e_lo, energies[i]);
+    e_hi = std::max(e_hi, energies[i]);
+  }
+  if (!(e_lo > e_n)) return ISDF_ERR_ORDER;
+  return std::max(1, contour_nodes_recommended(e_lo - e_n, e_hi - e_n, tol));
 }
 
 // Queue the SMW capacitance of frequency k (no synchronisation); the

@@ -90,6 +90,11 @@ struct isdf_ctx {
   // all frequencies at once (mixed.cu, api.cu): per-frequency r x r stacks,
   // their slice stacks, scratch of the batched factorisations, failure flags
   DevBuf bW1, bT, bU, bQ, b_s1, b_s2, b_s3, b_work, b_cb, b_dtmp, b_cbd;
+  DevBuf ctab;  // contour-integral polarizability: resolvent weights and node weights
+  DevBuf m_pairs_t, swf;  // pair-space whitening: transposed pair slices, FP32 pair weights
+  bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
+  int pair_mode = 0;         // the precision argument of the last fit
+  DevBuf kappa_work;         // [0] ||L||_F^2, [1] ||L^-1||_F^2, [2..] reduction scratch
   int* b_fail = nullptr;
   size_t cap_bfail = 0;
 
@@ -162,6 +167,8 @@ struct PhaseTimer {
 cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p, int n_v, int n_c, int r);
 cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r);
 cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_whiten_D(isdf_ctx* c, const double* Dpp, double* Dk);
+cudaError_t mixed_polar_D_pairspace(isdf_ctx* c, const float* swf, int n_omega);
 cudaError_t mixed_polar_G(isdf_ctx* c);
 cudaError_t mixed_smw_products_T(isdf_ctx* c);
 cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk);

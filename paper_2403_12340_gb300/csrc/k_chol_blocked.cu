@@ -38,19 +38,34 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
 
 // Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place; the
 // strict upper part of the block is zeroed.  One thread block on one SM,
-// whose FP64 pipe (2 DFMA / clock) is the limit, so the kernel issues as few
-// FP64 warp instructions and barriers as it can: right-looking outer
-// products on the unscaled columns, A(i, k) -= A(i, j) A(k, j) / d_j with
-// d_j the current pivot, over the m (m + 1) / 2 entries of the remaining
-// lower triangle packed densely over the threads through a table of
-// (row, column) offsets, one barrier per column; each warp forms 1 / d_j
-// itself (no serial step on one thread).  Column j is scaled by d_j^-1/2 and
-// the diagonal set to d_j^1/2 at the end.
+// whose FP64 pipe (2 DFMA / clock) is the limit.  An FP64 warp instruction
+// costs that pipe the same whether one lane or 32 are active, so the kernel
+// keeps single-lane FP64 work off the per-column path: right-looking outer
+// products on the unscaled columns, A(i, k) -= s_i A(k, j) with s_i =
+// A(i, j) / d_j formed once per row, over the m (m + 1) / 2 entries of the
+// remaining lower triangle packed densely over the threads through a table
+// of (row, column) offsets; 1 / d_{j+1} is formed by the thread that
+// finishes d_{j+1} (an FP32 reciprocal refined by two Newton steps,
+// r <- r (2 - d r), each doubling the correct bits).  Column j is scaled by
+// d_j^-1/2 and the diagonal set to d_j^1/2 at the end.
 constexpr int TRI = CB * (CB - 1) / 2;  // entries of a strictly lower 63-row triangle
 
-__global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int j0, int bs, const double* dmax,
-                                                  double tol_rel, int* fail, long long sA = 0) {
+__device__ __forceinline__ double recip_newton(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;  // outside the FP32 range of the first estimate
+  double r = (double)(1.0f / (float)d);
+  r = r * fma(-d, r, 2.0);
+  return r * fma(-d, r, 2.0);
+}
+
+constexpr int DIAG_THREADS = 512;  // 16 warps: enough to hide FP64 and shared-memory latency per column
+
+__global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long lda, int j0, int bs,
+                                                           const double* dmax, double tol_rel, int* fail,
+                                                           long long sA = 0) {
   __shared__ double Ls[CB][CB + 1];
+  __shared__ double sc[CB];        // s_i of the current column
+  __shared__ double rdiag[CB + 1]; // 1 / d_j
   __shared__ double sq[CB], rsq[CB];
   __shared__ unsigned char ta[TRI], tb[TRI];
   // problem blockIdx.x of a batch: its matrix, max and flag
@@ -58,20 +73,22 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
   dmax += blockIdx.x;
   fail += blockIdx.x;
   if (*(volatile int*)fail >= 0) return;
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
     int i = idx & (CB - 1), k = idx >> 6;
     Ls[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
   }
   // (a, b) with b <= a for the packed index a (a + 1) / 2 + b
-  for (int a = t; a < CB - 1; a += blockDim.x) {
-    const int base = a * (a + 1) / 2;
-    for (int b = 0; b <= a; ++b) {
-      ta[base + b] = (unsigned char)a;
-      tb[base + b] = (unsigned char)b;
-    }
+  for (int idx = t; idx < TRI; idx += blockDim.x) {
+    int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+    while (a * (a + 1) / 2 > idx) --a;
+    ta[idx] = (unsigned char)a;
+    tb[idx] = (unsigned char)(idx - a * (a + 1) / 2);
   }
   const double thresh = tol_rel * (*dmax);
+  __syncthreads();
+  if (t == 0) rdiag[0] = recip_newton(Ls[0][0]);
   __syncthreads();
   int bad = -1;
   for (int j = 0; j < bs; ++j) {
@@ -80,14 +97,17 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
       bad = j;
       break;
     }
-    double rd = 0.0;
-    if (lane == 0) rd = 1.0 / d;
-    rd = __shfl_sync(0xffffffffu, rd, 0);
     const int m = bs - j - 1;
+    const double rd = rdiag[j];
+    for (int i = t; i < m; i += blockDim.x) sc[i] = Ls[j + 1 + i][j] * rd;
+    __syncthreads();
     const int cnt = m * (m + 1) / 2;
     for (int idx = t; idx < cnt; idx += blockDim.x) {
-      const int i = j + 1 + ta[idx], k = j + 1 + tb[idx];
-      Ls[i][k] = fma(-Ls[i][j] * rd, Ls[k][j], Ls[i][k]);
+      const int a = ta[idx], b = tb[idx];
+      const int i = j + 1 + a, k = j + 1 + b;
+      const double v = fma(-sc[a], Ls[k][j], Ls[i][k]);
+      Ls[i][k] = v;
+      if (idx == 0 && m > 0) rdiag[j + 1] = recip_newton(v);  // thread 0 finishes d_{j+1} first
     }
     __syncthreads();
   }
@@ -98,7 +118,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, long long lda, int
   if (t < bs) {
     const double r = sqrt(Ls[t][t]);
     sq[t] = r;
-    rsq[t] = 1.0 / r;
+    rsq[t] = recip_newton(r);
   }
   __syncthreads();
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
@@ -185,7 +205,7 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
     {
       KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0);  // bs^3 / 3 flops
       note_launch();
-      k_chol_diag<<<1, 256, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail);
+      k_chol_diag<<<1, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int rem = n - j0 - bs;
@@ -230,7 +250,7 @@ cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long
     {
       KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0 * batch);
       note_launch();
-      k_chol_diag<<<batch, 256, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
+      k_chol_diag<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int rem = n - j0 - bs;

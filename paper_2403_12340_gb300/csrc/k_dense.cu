@@ -493,6 +493,45 @@ cudaError_t launch_polarizability(const double* phimu, long long ldp, int r, int
 // ------------------------------------------------------------ triangular solve
 constexpr int TRSM_NB = 64;
 
+// sum of squares of n doubles: per-block partials, then one block sums them
+// in a fixed order (deterministic)
+__global__ void k_sumsq_partial(const double* __restrict__ a, long long n, double* __restrict__ part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc = fma(a[i], a[i], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_fixed(const double* __restrict__ part, int n, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t launch_sumsq(const double* a, long long n, double* scratch, double* out, cudaStream_t s) {
+  note_launch();
+  k_sumsq_partial<<<256, 256, 0, s>>>(a, n, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  note_launch();
+  k_sum_fixed<<<1, 256, 0, s>>>(scratch, 256, out);
+  return cudaGetLastError();
+}
+
 // Zero an r x r block per problem (problem blockIdx.z at A + z sA).
 __global__ void k_copy_zero(double* A, long long lda, long long sA, int r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;

@@ -580,13 +580,12 @@ cudaError_t launch_fft_forward_slices(const FftGrid& g, const double* X, long lo
   // bf16x2 stores of (re, im) need kp and rows_pad * kp even: kp is a multiple of 64
   if (n == g.ax[1].n && n == g.ax[2].n && (kp % 2) == 0) {
     switch (n) {
-      case 16: return fft_slices_ct<16>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
-      case 24: return fft_slices_ct<24>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
-      case 32: return fft_slices_ct<32>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
-      case 48: return fft_slices_ct<48>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
-      case 60: return fft_slices_ct<60>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
-      case 64: return fft_slices_ct<64>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
-      case 72: return fft_slices_ct<72>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+#define ISDF_FFT_CT(N) \
+  case N: return fft_slices_ct<N>(g, X, ldx, ncols, S32, lds32, wt, out, rows_pad, kp, nsl, s);
+      ISDF_FFT_CT(16) ISDF_FFT_CT(24) ISDF_FFT_CT(27) ISDF_FFT_CT(30) ISDF_FFT_CT(32) ISDF_FFT_CT(36)
+      ISDF_FFT_CT(40) ISDF_FFT_CT(45) ISDF_FFT_CT(48) ISDF_FFT_CT(50) ISDF_FFT_CT(54) ISDF_FFT_CT(60)
+      ISDF_FFT_CT(64) ISDF_FFT_CT(72)
+#undef ISDF_FFT_CT
       default: break;
     }
   }

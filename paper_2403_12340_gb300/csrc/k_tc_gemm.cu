@@ -20,6 +20,8 @@
 // NACC = 2 runs two accumulators over two K ranges (the occupied and the
 // unoccupied part of the orbital index) and multiplies them in the epilogue:
 // the face-split Gram (Phi_v Phi_v,mu^T) .* (Phi_c Phi_c,mu^T) of the ISDF fit.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -189,6 +191,38 @@ __global__ void k_pair_slices(const double* __restrict__ phimu, long long ldp, i
   }
 }
 
+// Slices of the unscaled pair operand, transposed: rows are the pairs
+// p = i n_c + j, the K index the r points, value phimu(a, i) phimu(a, n_v + j);
+// eight points per thread, 16-byte slice stores.
+__global__ void k_pair_slices_t(const double* __restrict__ phimu, long long ldp, int r, int n_v, int n_c,
+                                __nv_bfloat16* __restrict__ dst, int Pp, int Kp, int s) {
+  const long long p = blockIdx.y * (long long)gridDim.x + blockIdx.x;
+  if (p >= (long long)n_v * n_c) return;
+  const int i = (int)(p / n_c), j = (int)(p - (long long)i * n_c);
+  const double* pv = phimu + ldp * (long long)i;
+  const double* pc = phimu + ldp * (long long)(n_v + j);
+  const long long sstr = (long long)Pp * Kp;
+  for (int a8 = threadIdx.x * 8; a8 < r; a8 += blockDim.x * 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (a8 + q < r) ? tc::d2f(pv[a8 + q]) * tc::d2f(pc[a8 + q]) : 0.f;
+    store_slices8(v, dst + p * Kp + a8, sstr, s);
+  }
+}
+
+cudaError_t launch_pair_slices_t(const double* phimu, long long ldp, int r, int n_v, int n_c, __nv_bfloat16* dst,
+                                 int Pp, int Kp, int s, cudaStream_t st) {
+  const long long np = (long long)n_v * n_c;
+  if (r <= 0 || np <= 0) return cudaSuccess;
+  if (Kp % 8 || Kp < r) return cudaErrorInvalidValue;
+  const unsigned gx = (unsigned)std::min<long long>(np, 65535);
+  dim3 grid(gx, (unsigned)((np + gx - 1) / gx));
+  KernelTimer kt(KF_SLICE, st, (double)r * (n_v + n_c) * 8.0 + (double)np * r * 2.0 * s);
+  note_launch();
+  k_pair_slices_t<<<grid, 128, 0, st>>>(phimu, ldp, r, n_v, n_c, dst, Pp, Kp, s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
                                __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch,
                                long long dstride) {
@@ -216,21 +250,55 @@ struct TcArgs {
   int kv_iters;                // NACC == 2: chunks of the first accumulator
   int lower_only;              // M == N; only tiles with n-tile <= m-tile
   int tri_b;                   // B(n, k) == 0 for k > n: skip chunks beyond the tile's last n
-  int tiles_n;                 // number of n tiles (grid.x when !lower_only)
-  int splits;                  // K splits per problem: blockIdx.z = problem * splits + split
+  int tiles_m, tiles_n;        // tiles along M and N
+  int count;                   // problems of the batch
+  int splits;                  // K splits per problem (units: problem, split, tile)
   int a_brows, b_brows;        // rows between the slice stacks of consecutive problems (0: shared)
   long long c_bstride;         // elements between the C of consecutive problems
   double alpha, beta;
   double* C;
   long long ldc;
   double* partial;             // raw FP64 partial tiles [z][M N] (column-major M x N)
-  __nv_bfloat16* zs;           // EPI_HAD_SLICES output slices (row-major)
+  __nv_bfloat16* zs;           // EPI_HAD_SLICES / EPI_SCALE_SLICES output slices (row-major)
   int zs_rows_pad, zs_kp;
+  long long zs_bstride;        // elements between the output slices of consecutive problems
+  const float* colscale;       // EPI_SCALE_SLICES: column n of problem b scaled by colscale[b cs_bstride + n]
+  long long cs_bstride;
   unsigned* status;
 };
 
-enum { EPI_F64 = 0, EPI_HAD_F64 = 1, EPI_HAD_SLICES = 2 };
+enum { EPI_F64 = 0, EPI_HAD_F64 = 1, EPI_HAD_SLICES = 2, EPI_SCALE_SLICES = 3 };
 
+// One work unit: a 128 x BN output tile of one problem over one K range.
+struct TcUnit {
+  int mt, nt, m0, n0, bidx, split, kb, ke;
+};
+
+__device__ __forceinline__ TcUnit tc_unit(const TcArgs& a, long long u, int tiles, int bn) {
+  TcUnit w;
+  const long long per_b = (long long)a.splits * tiles;
+  w.bidx = (int)(u / per_b);
+  const long long rem = u - (long long)w.bidx * per_b;
+  w.split = (int)(rem / tiles);
+  const int tile = (int)(rem - (long long)w.split * tiles);
+  if (a.lower_only) {
+    lower_tile(tile, w.mt, w.nt);
+  } else {
+    w.mt = tile / a.tiles_n;  // n fastest: consecutive units share the A tile (L2 reuse)
+    w.nt = tile - w.mt * a.tiles_n;
+  }
+  w.m0 = w.mt * TC_BM;
+  w.n0 = w.nt * bn;
+  w.kb = w.split * a.k_per_split;
+  w.ke = min(a.k_iters, w.kb + a.k_per_split);
+  if (a.tri_b) w.ke = min(w.ke, (w.n0 + bn + TC_BK - 1) / TC_BK);
+  if (w.ke < w.kb) w.ke = w.kb;
+  return w;
+}
+
+// Persistent: block b computes units b, b + gridDim.x, ...; the stage ring
+// runs on across units, and the accumulator alternates between two TMEM
+// buffers so that the epilogue of one unit overlaps the MMAs of the next.
 template <int BN, int NACC, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb, TcArgs a) {
@@ -241,25 +309,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int stage_bytes = tc_stage_bytes(a.s, BN);
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + 4;
-  uint64_t* done = empty + 4;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* tfull = empty + 4;   // accumulator buffer b holds a finished unit (MMA -> epilogue)
+  uint64_t* tempty = tfull + 2;  // accumulator buffer b has been read (epilogue -> MMA), 4 warps
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   __shared__ int s_abort;
+  constexpr uint32_t ACC_COLS = NACC * BN;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int mt, nt;
-  if (a.lower_only) {
-    lower_tile(blockIdx.x, mt, nt);
-  } else {
-    nt = blockIdx.x;  // n fastest: consecutive blocks share the A tile (L2 reuse)
-    mt = blockIdx.y;
-  }
-  const int m0 = mt * TC_BM, n0 = nt * BN;
-  const int bidx = blockIdx.z / a.splits;
-  const int a_row0 = bidx * a.a_brows, b_row0 = bidx * a.b_brows;
-  int kb = (blockIdx.z - bidx * a.splits) * a.k_per_split;
-  int ke = min(a.k_iters, kb + a.k_per_split);
-  if (a.tri_b) ke = min(ke, (n0 + BN + TC_BK - 1) / TC_BK);
-  const int nk = ke > kb ? ke - kb : 0;
+  const int tiles = a.lower_only ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
+  const long long units = (long long)a.count * a.splits * tiles;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -267,10 +325,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
     }
-    tc::mbar_init(done, 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&tfull[i], 1);
+      tc::mbar_init(&tempty[i], 4);
+    }
     tc::fence_mbar_init();
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, NACC * BN);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 2 * ACC_COLS);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -281,120 +342,155 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc::prefetch_tmap(&tma);
     tc::prefetch_tmap(&tmb);
     const uint32_t bytes = (uint32_t)stage_bytes;
-    for (int it = 0; it < nk; ++it) {
-      const int st = it % S;
-      const uint32_t ph = (uint32_t)(it / S) & 1u;
-      if (!tc::mbar_wait(&empty[st], ph ^ 1u, a.status)) {
-        s_abort = 1;
-        break;
-      }
-      tc::mbar_expect_tx(&full[st], bytes);
-      uint8_t* sa = smem + st * stage_bytes;
-      uint8_t* sb = sa + a.s * TC_BM * TC_BK * 2;
-      const int kx = (kb + it) * TC_BK;
-      for (int l = 0; l < a.s; ++l) {
-        tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, a_row0 + l * a.a_rows_pad + m0);
-        tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, b_row0 + l * a.b_rows_pad + n0);
+    uint32_t g = 0;  // stage-ring position, continuous across units
+    for (long long u = blockIdx.x; u < units && !s_abort; u += gridDim.x) {
+      const TcUnit w = tc_unit(a, u, tiles, BN);
+      const int a_row0 = w.bidx * a.a_brows + w.m0, b_row0 = w.bidx * a.b_brows + w.n0;
+      for (int kc = w.kb; kc < w.ke; ++kc, ++g) {
+        const int st = (int)(g % (uint32_t)S);
+        const uint32_t ph = (g / (uint32_t)S) & 1u;
+        if (!tc::mbar_wait(&empty[st], ph ^ 1u, a.status)) {
+          s_abort = 1;
+          break;
+        }
+        tc::mbar_expect_tx(&full[st], bytes);
+        uint8_t* sa = smem + st * stage_bytes;
+        uint8_t* sb = sa + a.s * TC_BM * TC_BK * 2;
+        const int kx = kc * TC_BK;
+        for (int l = 0; l < a.s; ++l) {
+          tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, a_row0 + l * a.a_rows_pad);
+          tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, b_row0 + l * a.b_rows_pad);
+        }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_BM, BN);
-    bool first[2] = {true, true};
-    for (int it = 0; it < nk; ++it) {
-      const int st = it % S;
-      const uint32_t ph = (uint32_t)(it / S) & 1u;
-      if (!tc::mbar_wait(&full[st], ph, a.status)) {
+    uint32_t g = 0;
+    int li = 0;  // units done by this block
+    for (long long u = blockIdx.x; u < units && !s_abort; u += gridDim.x, ++li) {
+      const TcUnit w = tc_unit(a, u, tiles, BN);
+      const int buf = li & 1;
+      // the epilogue has read this buffer's previous unit (two units ago)
+      if (!tc::mbar_wait(&tempty[buf], ((uint32_t)(li >> 1) & 1u) ^ 1u, a.status)) {
         s_abort = 1;
         break;
       }
       tc::fence_after_sync();
-      const int acc = (NACC == 2 && (kb + it) >= a.kv_iters) ? 1 : 0;
-      const uint32_t d = tmem + (uint32_t)(acc * BN);
-      const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
-      const uint32_t sb = sa + (uint32_t)(a.s * TC_BM * TC_BK * 2);
+      const uint32_t dbase = tmem + (uint32_t)buf * ACC_COLS;
+      bool first[2] = {true, true};
+      bool ok = true;
+      for (int kc = w.kb; kc < w.ke; ++kc, ++g) {
+        const int st = (int)(g % (uint32_t)S);
+        const uint32_t ph = (g / (uint32_t)S) & 1u;
+        if (!tc::mbar_wait(&full[st], ph, a.status)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int acc = (NACC == 2 && kc >= a.kv_iters) ? 1 : 0;
+        const uint32_t d = dbase + (uint32_t)(acc * BN);
+        const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
+        const uint32_t sb = sa + (uint32_t)(a.s * TC_BM * TC_BK * 2);
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        for (int i = 0; i < a.s; ++i) {
-          for (int j = 0; i + j < a.s; ++j) {
-            const uint64_t ad = tc::desc_kmajor_sw128(sa + (uint32_t)(i * TC_BM * TC_BK * 2 + kk * 32));
-            const uint64_t bd = tc::desc_kmajor_sw128(sb + (uint32_t)(j * BN * TC_BK * 2 + kk * 32));
-            tc::mma_bf16(d, ad, bd, idesc, first[acc] ? 0u : 1u);
-            first[acc] = false;
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          for (int i = 0; i < a.s; ++i) {
+            for (int j = 0; i + j < a.s; ++j) {
+              const uint64_t ad = tc::desc_kmajor_sw128(sa + (uint32_t)(i * TC_BM * TC_BK * 2 + kk * 32));
+              const uint64_t bd = tc::desc_kmajor_sw128(sb + (uint32_t)(j * BN * TC_BK * 2 + kk * 32));
+              tc::mma_bf16(d, ad, bd, idesc, first[acc] ? 0u : 1u);
+              first[acc] = false;
+            }
           }
         }
+        tc::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
       }
-      tc::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
-    }
-    if (nk > 0) {
-      tc::mma_commit(done);
-    } else {
-      tc::mbar_arrive(done);
+      if (!ok) {
+        s_abort = 1;
+        break;
+      }
+      if (w.ke > w.kb) {
+        tc::mma_commit(&tfull[buf]);
+      } else {
+        tc::mbar_arrive(&tfull[buf]);
+      }
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: thread <-> tile row (TMEM lane)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
-    const int m = m0 + row;
-    const bool ok = tc::mbar_wait(done, 0u, a.status);
-    tc::fence_after_sync();
-    const bool have = ok && nk > 0;
-    const bool have1 = NACC == 2 && have && ke > a.kv_iters;
-    const bool have0 = have && (NACC == 1 || kb < a.kv_iters);
-    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    for (int c = 0; c < BN; c += 16) {
-      float v0[16], v1[16];
-      if (have0) tc::tmem_ld16(lane_addr + (uint32_t)c, v0);
-      else
-        for (int i = 0; i < 16; ++i) v0[i] = 0.f;
-      if (NACC == 2) {
-        if (have1) tc::tmem_ld16(lane_addr + (uint32_t)(BN + c), v1);
+    int li = 0;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x, ++li) {
+      const TcUnit w = tc_unit(a, u, tiles, BN);
+      const int buf = li & 1;
+      const bool ok = tc::mbar_wait(&tfull[buf], (uint32_t)(li >> 1) & 1u, a.status);
+      tc::fence_after_sync();
+      if (!ok || s_abort) break;
+      const int m = w.m0 + row;
+      const bool have = w.ke > w.kb;
+      const bool have1 = NACC == 2 && have && w.ke > a.kv_iters;
+      const bool have0 = have && (NACC == 1 || w.kb < a.kv_iters);
+      const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * ACC_COLS;
+      double* Cb = a.C + a.c_bstride * w.bidx;
+      for (int c = 0; c < BN; c += 16) {
+        float v0[16], v1[16];
+        if (have0) tc::tmem_ld16(lane_addr + (uint32_t)c, v0);
         else
-          for (int i = 0; i < 16; ++i) v1[i] = 0.f;
-      }
-      if (m >= a.M) continue;
-      if (EPI == EPI_HAD_SLICES && n0 + c + 16 <= a.N) {
-        // whole 16-column chunk: two 16-byte stores per slice
-        const long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
-        __nv_bfloat16* dst = a.zs + (long long)m * a.zs_kp + n0 + c;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float v[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = v0[8 * h + q] * v1[8 * h + q];
-          store_slices8(v, dst + 8 * h, sstr, a.s);
+          for (int i = 0; i < 16; ++i) v0[i] = 0.f;
+        if (NACC == 2) {
+          if (have1) tc::tmem_ld16(lane_addr + (uint32_t)(BN + c), v1);
+          else
+            for (int i = 0; i < 16; ++i) v1[i] = 0.f;
         }
-        continue;
-      }
+        if (m >= a.M) continue;
+        const float* cs = (EPI == EPI_SCALE_SLICES) ? a.colscale + a.cs_bstride * w.bidx : nullptr;
+        if ((EPI == EPI_HAD_SLICES || EPI == EPI_SCALE_SLICES) && w.n0 + c + 16 <= a.N) {
+          // whole 16-column chunk: two 16-byte stores per slice
+          const long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
+          __nv_bfloat16* dst = a.zs + a.zs_bstride * w.bidx + (long long)m * a.zs_kp + w.n0 + c;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int n = n0 + c + i;
-        if (n >= a.N) break;
-        const float vf = (NACC == 2) ? v0[i] * v1[i] : v0[i];
-        if (EPI == EPI_HAD_SLICES) {
-          __nv_bfloat16 x0, x1, x2;
-          split3f(vf, x0, x1, x2);
-          long long base = (long long)m * a.zs_kp + n;
-          long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
-          a.zs[base] = x0;
-          if (a.s > 1) a.zs[base + sstr] = x1;
-          if (a.s > 2) a.zs[base + 2 * sstr] = x2;
-        } else if (a.partial) {
-          a.partial[(long long)blockIdx.z * a.M * a.N + m + (long long)a.M * n] = tc::f2d(vf);
-        } else {
-          // alpha = 1, beta = 0 (the common case) needs no FP64 arithmetic
-          double* Cb = a.C + a.c_bstride * bidx;
-          double o = (a.alpha == 1.0) ? tc::f2d(vf) : a.alpha * tc::f2d(vf);
-          if (a.beta != 0.0) o += a.beta * Cb[m + a.ldc * n];
-          Cb[m + a.ldc * n] = o;
-          if (a.lower_only && mt != nt) Cb[n + a.ldc * m] = o;
+          for (int h = 0; h < 2; ++h) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              v[e] = (EPI == EPI_SCALE_SLICES) ? v0[8 * h + e] * cs[w.n0 + c + 8 * h + e] : v0[8 * h + e] * v1[8 * h + e];
+            store_slices8(v, dst + 8 * h, sstr, a.s);
+          }
+          continue;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = w.n0 + c + i;
+          if (n >= a.N) break;
+          const float vf = (EPI == EPI_SCALE_SLICES) ? v0[i] * cs[n] : ((NACC == 2) ? v0[i] * v1[i] : v0[i]);
+          if (EPI == EPI_HAD_SLICES || EPI == EPI_SCALE_SLICES) {
+            __nv_bfloat16 x0, x1, x2;
+            split3f(vf, x0, x1, x2);
+            long long base = a.zs_bstride * w.bidx + (long long)m * a.zs_kp + n;
+            long long sstr = (long long)a.zs_rows_pad * a.zs_kp;
+            a.zs[base] = x0;
+            if (a.s > 1) a.zs[base + sstr] = x1;
+            if (a.s > 2) a.zs[base + 2 * sstr] = x2;
+          } else if (a.partial) {
+            a.partial[((long long)w.bidx * a.splits + w.split) * a.M * a.N + m + (long long)a.M * n] = tc::f2d(vf);
+          } else {
+            // alpha = 1, beta = 0 (the common case) needs no FP64 arithmetic
+            double o = (a.alpha == 1.0) ? tc::f2d(vf) : a.alpha * tc::f2d(vf);
+            if (a.beta != 0.0) o += a.beta * Cb[m + a.ldc * n];
+            Cb[m + a.ldc * n] = o;
+            if (a.lower_only && w.mt != w.nt) Cb[n + a.ldc * m] = o;
+          }
         }
       }
+      // this warp has read its lanes of the buffer: hand it back to the MMA warp
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[buf]);
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, NACC * BN);
+  if (warp == 1) tc::tmem_dealloc(tmem, 2 * ACC_COLS);
 }
 
 // ------------------------------------------------------------ host side
@@ -447,10 +543,20 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
   }
   if (smem > TC_SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
   const int tm = (a.M + TC_BM - 1) / TC_BM, tn = (a.N + BN - 1) / BN;
+  a.tiles_m = tm;
   a.tiles_n = tn;
   a.splits = splits;
-  if ((long long)splits * batch > 65535) return cudaErrorInvalidValue;
-  dim3 grid = a.lower_only ? dim3(tm * (tm + 1) / 2, 1, splits * batch) : dim3(tn, tm, splits * batch);
+  a.count = batch;
+  const long long tiles = a.lower_only ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
+  const long long units = tiles * splits * batch;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  // one block per SM (the stage ring takes most of the shared memory), each looping over units
+  dim3 grid((unsigned)std::min<long long>(units, sms));
   KernelTimer kt(KF_TC_GEMM, st, mma_flops);
   note_launch();
   k_tc_gemm<BN, NACC, EPI><<<grid, TC_THREADS, smem, st>>>(ma, mb, a);
@@ -459,6 +565,8 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
 
 static void split_k(int k_iters, int tiles, int num_sms, int max_split, int& splits, int& per) {
   int want = (2 * num_sms + tiles - 1) / tiles;
+  const int accuracy = (k_iters + kTcMaxChunksPerSplit - 1) / kTcMaxChunksPerSplit;
+  if (want < accuracy) want = accuracy;
   if (want > max_split) want = max_split;
   if (want > k_iters) want = k_iters;
   if (want < 1) want = 1;
@@ -517,6 +625,33 @@ cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, do
                         unsigned* status, cudaStream_t st) {
   return tc_gemm_f64_batched(A, B, M, N, alpha, beta, C, ldc, lower_only, tri_b, partial, max_split, num_sms, status,
                              st, TcBatch{1, 0, 0, 0});
+}
+
+cudaError_t tc_scaled_slices(const TcOperand& A, const TcOperand& B, int M, int N, const float* colscale,
+                             long long cs_bstride, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, long long zs_bstride,
+                             unsigned* status, cudaStream_t st, const TcBatch& bt) {
+  if (M <= 0 || N <= 0 || bt.count <= 0) return cudaSuccess;
+  if (A.s != B.s || A.kp != B.kp || A.kp % TC_BK || (zs_kp % 8) || (zs_bstride % 8)) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.a_rows_pad = A.rows_pad;
+  a.b_rows_pad = B.rows_pad;
+  a.s = A.s;
+  a.k_iters = A.kp / TC_BK;
+  a.k_per_split = a.k_iters;
+  a.alpha = 1.0;
+  a.status = status;
+  a.a_brows = bt.a_rows;
+  a.b_brows = bt.b_rows;
+  a.zs = zs;
+  a.zs_rows_pad = zs_rows_pad;
+  a.zs_kp = zs_kp;
+  a.zs_bstride = zs_bstride;
+  a.colscale = colscale;
+  a.cs_bstride = cs_bstride;
+  const double mma = 2.0 * 0.5 * a.s * (a.s + 1) * (double)M * N * (double)A.kp * bt.count;
+  return tc_launch<128, 1, EPI_SCALE_SLICES>(A, B, a, 1, bt.count, mma, st);
 }
 
 cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, int kv_iters, double* C,

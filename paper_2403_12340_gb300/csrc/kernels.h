@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace isdf {
 
 // Count of kernel launches issued by this library (all contexts, all threads).
@@ -63,6 +65,8 @@ cudaError_t launch_trsm_right_lt(double* X, long long ldx, int M, const double* 
                                  int r, cudaStream_t s);
 cudaError_t launch_transpose(const double* src, long long lds, int M, int N, double* dst,
                              long long ldd, cudaStream_t s);
+// *out = sum of a[i]^2, i < n (deterministic; scratch: 256 doubles)
+cudaError_t launch_sumsq(const double* a, long long n, double* scratch, double* out, cudaStream_t s);
 // batch > 1: matrices A + z sA
 cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, int batch = 1, long long sA = 0);
 cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s, int batch = 1,
@@ -101,6 +105,22 @@ cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, 
 cudaError_t launch_splitk_reduce(const double* partial, int splits, int M, int N, double alpha, double beta,
                                  double* C, long long ldc, bool lower_only, int tile, cudaStream_t s, int batch = 1,
                                  long long sC = 0);
+
+// ---- k_contour.cu: contour-integral polarizability (Algorithm 2) ----------
+// Nodes from the bound of Eq. rel_err_Cauchy for a target error tol.
+int contour_nodes_recommended(double gap, double width, double tol);
+// Host tables of the n_nodes midpoint nodes z_j on the upper half contour:
+// wtab (2 n_nodes (n_v + n_c) doubles) = 1 / (z_j - e_i) as (re, im), wnode
+// (2 n_nodes) = the weights h z'(t_j).  cudaErrorInvalidValue without a gap.
+cudaError_t contour_tables(const double* energies, int n_v, int n_c, int n_nodes, std::vector<double>& wtab,
+                           std::vector<double>& wnode);
+// D (r x r, symmetric) = -2 C_r Omega^-1 C_r^T by the contour integral over
+// the orbitals at the r points (phimu, r x (n_v + n_c), ld ldp); nodes may
+// be split across blocks (partial: split r^2 doubles, at most partial_cap).
+cudaError_t launch_contour_polarizability(const double* phimu, long long ldp, int r, int n_v, int n_c,
+                                          const double* d_wtab, const double* d_wnode, int n_nodes, double* D,
+                                          long long ldd, double* partial, size_t partial_cap, int num_sms,
+                                          cudaStream_t s);
 
 // ---- k_chol_blocked.cu ----------------------------------------------------
 // Blocked Cholesky without pivoting of the symmetric n x n W (column-major,
@@ -196,13 +216,24 @@ cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K
 cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
                                __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch = 1,
                                long long dstride = 0);
+// Unscaled pair operand transposed: slices with rows p = i n_c + j (Pp rows
+// per slice), K = the r points (Kp >= r, multiple of 8).
+cudaError_t launch_pair_slices_t(const double* phimu, long long ldp, int r, int n_v, int n_c, __nv_bfloat16* dst,
+                                 int Pp, int Kp, int s, cudaStream_t st);
 // C (M x N, column-major FP64) = alpha sum_{i+j<s} A_i B_j^T + beta C.  With
 // `partial` (max_split * M * N doubles) long K is split over blocks and
-// reduced in FP64.  lower_only: SYRK-style (M == N, mirrored).  tri_b: B is
+// reduced in FP64; pass max_split >= tc_min_splits(kp) to keep every
+// accumulator within kTcMaxChunksPerSplit chunks.  lower_only: SYRK-style (M == N, mirrored).  tri_b: B is
 // lower triangular as B(n, k), chunks past the tile's last n are skipped.
 cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
                         double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
                         int num_sms, unsigned* status, cudaStream_t st);
+// A tensor-memory accumulator sums at most this many 64-wide K chunks
+// (8192 terms): FP32 accumulation error grows with the number of terms
+// (the long SYRKs add hundreds of thousands of same-sign products), so a
+// longer K is split across blocks whose partial tiles are summed in FP64.
+constexpr int kTcMaxChunksPerSplit = 128;
+inline int tc_min_splits(long long kp) { return (int)((kp / 64 + kTcMaxChunksPerSplit - 1) / kTcMaxChunksPerSplit); }
 // A batch of `count` problems of the same shape: problem b reads its A slice
 // stack starting at row b * a_rows of A.p (a_rows = 0: one A for all), its B
 // at row b * b_rows, and writes C + b * c_stride (split-K partials: b *
@@ -218,6 +249,12 @@ cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, i
 // Face-split Gram (A_v B_v^T) .* (A_c B_c^T): chunks [0, kv_iters) feed the
 // first accumulator, the rest the second.  Output FP64 column-major (C) or,
 // with zs non-null, BF16 slices (row-major M x N, zs_rows_pad x zs_kp).
+// X = A B^T with column n of problem b scaled by colscale[b cs_bstride + n],
+// written as BF16 slices (row-major M x N, slice stride zs_rows_pad rows of
+// zs_kp; problem b at zs + b zs_bstride) instead of FP64.
+cudaError_t tc_scaled_slices(const TcOperand& A, const TcOperand& B, int M, int N, const float* colscale,
+                             long long cs_bstride, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, long long zs_bstride,
+                             unsigned* status, cudaStream_t st, const TcBatch& bt);
 cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, int kv_iters, double* C,
                          long long ldc, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, unsigned* status,
                          cudaStream_t st);

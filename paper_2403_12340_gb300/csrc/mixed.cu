@@ -127,7 +127,7 @@ cudaError_t mixed_polar_G(isdf_ctx* c) {
   const int rp = pad(r, 128);
   const long long lds32 = 2 * c->n_half;
   const int kps = pad(lds32, 64);
-  const int max_split = 8;
+  const int max_split = std::max(8, tc_min_splits(kps));
   MK(ensure(c->partial, (size_t)max_split * rr));
   {
     PhaseTimer ph(c, ISDF_PH_FFT);
@@ -153,8 +153,11 @@ cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega) {
   const size_t rr = (size_t)r * r;
   const int rp = pad(r, 128), rk = pad(r, 64);
   const int npair = n_v * n_c, kpp = pad(npair, 64);
-  const int max_split = 8;
-  MK(ensure(c->partial, (size_t)max_split * rr));
+  const int max_split = std::max(8, tc_min_splits(kpp));
+  // also the split of the SYRK of G that follows on this stream: size the
+  // partials once, before anything runs on the second stream
+  const int max_split_g = std::max(8, tc_min_splits(pad(2 * c->n_half, 64)));
+  MK(ensure(c->partial, (size_t)std::max(max_split, max_split_g) * rr));
   MK(ensure(c->tmp1, rr));
   MK(ensure(c->tmp2, rr));
   const size_t np = (size_t)NSL * rp * kpp;
@@ -169,17 +172,27 @@ cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega) {
       MK(tc_gemm_f64(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, c->tmp1.p, r, true, false,
                      c->partial.p, max_split, c->num_sms, c->d_status, st));
     }
-    PhaseTimer ph(c, ISDF_PH_WHITEN_D);
-    // X = L^-1 D_pp, then D = X L^-T
-    MK(slices_cm(c->m_sa, c->tmp1.p, r, r, r, rp, rk, st));
-    MK(tc_gemm_f64(op(c->m_linvs, rp, rk), op(c->m_sa, rp, rk), r, r, 1.0, 0.0, c->tmp2.p, r, false, false,
-                   nullptr, 1, c->num_sms, c->d_status, st));
-    MK(slices_cm(c->m_sa, c->tmp2.p, r, r, r, rp, rk, st));
-    MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_linvs, rp, rk), r, r, 1.0, 0.0, Dk, r, false, true, nullptr, 1,
-                   c->num_sms, c->d_status, st));
-    MK(launch_symmetrize(Dk, r, r, st));
+    MK(mixed_whiten_D(c, c->tmp1.p, Dk));
   }
   return cudaSuccess;
+}
+
+// D = L^-1 D_pp L^-T (symmetrised) on the tensor cores; D_pp may be c->tmp1.
+cudaError_t mixed_whiten_D(isdf_ctx* c, const double* Dpp, double* Dk) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank;
+  const size_t rr = (size_t)r * r;
+  const int rp = pad(r, 128), rk = pad(r, 64);
+  MK(ensure(c->tmp2, rr));
+  PhaseTimer ph(c, ISDF_PH_WHITEN_D);
+  // X = L^-1 D_pp, then D = X L^-T
+  MK(slices_cm(c->m_sa, Dpp, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_linvs, rp, rk), op(c->m_sa, rp, rk), r, r, 1.0, 0.0, c->tmp2.p, r, false, false, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  MK(slices_cm(c->m_sa, c->tmp2.p, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_linvs, rp, rk), r, r, 1.0, 0.0, Dk, r, false, true, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  return launch_symmetrize(Dk, r, r, st);
 }
 
 // D(w_k) for all frequencies: the same products as mixed_polar_D, each one
@@ -192,8 +205,11 @@ cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
   const int npair = n_v * n_c, kpp = pad(npair, 64);
   const size_t per_pair = (size_t)NSL * rp * kpp, per_sq = (size_t)NSL * rp * rk;
   const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_omega, kPairSliceBudget / (per_pair * 2)));
+  const int ms = tc_min_splits(kpp);  // accumulation-length split of the long pair SYRK
+  const int max_split_g = std::max(8, tc_min_splits(pad(2 * c->n_half, 64)));
   // all workspace first: a resize frees memory that queued kernels may use
   MK(cudaStreamSynchronize(st));
+  MK(ensure(c->partial, std::max((size_t)ms * chunk, (size_t)max_split_g) * rr));
   MK(ensure_bf16(c->m_pairs, per_pair * chunk));
   MK(ensure_bf16(c->b_s1, per_sq * chunk));
   MK(ensure(c->b_dtmp, 2 * rr * chunk));
@@ -208,7 +224,8 @@ cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
                             nb, (long long)per_pair));
       const int pr = NSL * rp;
       MK(tc_gemm_f64_batched(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, Dpp, r, true, false,
-                             nullptr, 1, c->num_sms, c->d_status, st, TcBatch{nb, pr, pr, (long long)rr}));
+                             ms > 1 ? c->partial.p : nullptr, ms, c->num_sms, c->d_status, st,
+                             TcBatch{nb, pr, pr, (long long)rr}));
     }
     PhaseTimer ph(c, ISDF_PH_WHITEN_D);
     const int sr = NSL * rp;
@@ -219,6 +236,49 @@ cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
     MK(tc_gemm_f64_batched(op(c->b_s1, rp, rk), op(c->m_linvs, rp, rk), r, r, 1.0, 0.0, c->D.p + rr * k0, r, false,
                            true, nullptr, 1, c->num_sms, c->d_status, st, TcBatch{nb, sr, 0, (long long)rr}));
     MK(launch_symmetrize(c->D.p + rr * k0, r, r, st, nb, (long long)rr));
+  }
+  return cudaSuccess;
+}
+
+// D(w_k) for all frequencies by whitening in pair space: S~ = L^-1 C_r
+// diag(sqrt(-2 Omega^-1)) comes out of one GEMM as BF16 slices (the
+// transposed pair operand is the B side, the weights scale its columns in
+// the epilogue), then D = S~ S~^T.  The FP32-grade error of the pair
+// operand reaches D multiplied by cond(L) instead of cond(L)^2 as in
+// L^-1 (C_r diag C_r^T) L^-T, at the cost of the r x pairs x r GEMM.
+cudaError_t mixed_polar_D_pairspace(isdf_ctx* c, const float* swf, int n_omega) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
+  const size_t rr = (size_t)r * r;
+  const int rp = pad(r, 128), rk = pad(r, 64);
+  const int npair = n_v * n_c, kpp = pad(npair, 64), Pp = pad(npair, 128);
+  const size_t per_pair = (size_t)NSL * rp * kpp, n_t = (size_t)NSL * Pp * rk;
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_omega, kPairSliceBudget / (per_pair * 2)));
+  const int ms = tc_min_splits(kpp);
+  const int max_split_g = std::max(8, tc_min_splits(pad(2 * c->n_half, 64)));
+  MK(cudaStreamSynchronize(st));
+  MK(ensure(c->partial, std::max((size_t)std::max(ms, 8) * chunk, (size_t)max_split_g) * rr));
+  MK(ensure_bf16(c->m_pairs, per_pair * chunk));
+  MK(ensure_bf16(c->m_pairs_t, n_t));
+  {
+    PhaseTimer ph(c, ISDF_PH_POLAR_D);
+    MK(cudaMemsetAsync(c->m_pairs_t.p, 0, n_t * 2, st));
+    MK(launch_pair_slices_t(c->phimu_p.p, r, r, n_v, n_c, c->m_pairs_t.bf(), Pp, rk, NSL, st));
+  }
+  for (int k0 = 0; k0 < n_omega; k0 += chunk) {
+    const int nb = std::min(chunk, n_omega - k0);
+    {
+      PhaseTimer ph(c, ISDF_PH_WHITEN_D);
+      MK(cudaMemsetAsync(c->m_pairs.p, 0, per_pair * nb * 2, st));
+      MK(tc_scaled_slices(op(c->m_linvs, rp, rk), op(c->m_pairs_t, Pp, rk), r, npair, swf + (size_t)npair * k0,
+                          npair, c->m_pairs.bf(), rp, kpp, (long long)per_pair, c->d_status, st, TcBatch{nb, 0, 0, 0}));
+    }
+    PhaseTimer ph(c, ISDF_PH_POLAR_D);
+    const int pr = NSL * rp;
+    const int msb = std::max(ms, nb == 1 ? 8 : 1);
+    MK(tc_gemm_f64_batched(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, c->D.p + rr * k0, r,
+                           true, false, c->partial.p, msb, c->num_sms, c->d_status, st,
+                           TcBatch{nb, pr, pr, (long long)rr}));
   }
   return cudaSuccess;
 }
@@ -310,7 +370,7 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
   const long long nr = c->n_r;
   const int nrp = pad(nr, 128), kpg = pad(nr, 64);
   const int ncp = pad(nc, 128);
-  const int max_split = 64;
+  const int max_split = std::max(64, tc_min_splits(kpg));
   MK(ensure(c->partial, (size_t)max_split * r * nc));
   MK(ensure(c->tmp1, (size_t)r * nc));
   MK(ensure(c->tmp2, (size_t)r * nc));

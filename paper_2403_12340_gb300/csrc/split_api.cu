@@ -1,5 +1,6 @@
 // isdf_dgemm_split: the split-precision tensor-core GEMM of the mixed path
 // as a stand-alone C-ABI call (declared in include/isdf_smw.h).
+#include <algorithm>
 #include <string>
 
 #include "../../include/isdf_smw.h"
@@ -32,7 +33,7 @@ extern "C" int isdf_dgemm_split(int M, int N, int K, double alpha, const double*
   const int s = nslices;
   const int Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128;
   const int Kp = (K > 0 ? (K + 63) / 64 : 1) * 64;
-  const int max_split = 64;
+  const int max_split = std::max(64, tc_min_splits(Kp));
   const size_t na = (size_t)s * Mp * Kp, nb = (size_t)s * Np * Kp;
   const size_t npart = (size_t)max_split * M * N;
   __nv_bfloat16 *sa = nullptr, *sb = nullptr;

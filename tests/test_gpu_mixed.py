@@ -70,3 +70,28 @@ def test_mixed_intermediates_close_to_fp64():
     # D is whitened with L^-1 on both sides: its error grows with kappa(L)^2
     assert rel_fro(b["D"][0], a["D"][0]) < 1e-5
     assert rel_fro(b["K"][0], a["K"][0]) < 1e-5
+
+
+@pytest.mark.parametrize("grid,nv,nc,nmu", CASES[:4] + CASES[5:])
+def test_mixed_pair_space_whitening_matches_oracle(grid, nv, nc, nmu):
+    """ISDF_PREC_MIXED_PAIRS: D whitened in pair space (S = L^-1 C_r diag,
+    D = S S^T) on the same systems, two frequencies (the frequency batch)."""
+    s = small_system(grid, nv, nc, nmu, seed_index=hash((grid, nv, nc)) % 97)
+    x = synth.probe_block(s.n_r, 5)
+    omegas = (0.0, 0.37)
+    g = run_gpu(s, x, omegas, prec=2)
+    for k, w in enumerate(omegas):
+        ref = O.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x, omega=w)
+        assert rel_fro(g["y"][k], ref.y) < TOL_MIXED, k
+
+
+def test_mixed_ill_conditioned_points():
+    """Uniformly random points give cond(C C^T) in the hundreds: the mixed
+    path then whitens in pair space by itself and stays within 1e-6."""
+    s = small_system((20, 20, 20), 8, 40, 160, seed_index=33)
+    s.mu_idx = synth.random_points(s.n_r, 160, 77)
+    x = synth.probe_block(s.n_r, 5)
+    g = run_gpu(s, x, prec=MIXED)
+    ref = O.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x)
+    assert g["rank"] == ref.rank
+    assert rel_fro(g["y"][0], ref.y) < TOL_MIXED
