@@ -243,6 +243,29 @@ ISDF_API int isdf_screened_basis(isdf_ctx* ctx, int omega_index, double* W_out);
 ISDF_API int isdf_adjoint(isdf_ctx* ctx, int omega_index, const double* W_bar, double* grad_energies,
                           double* grad_phimu);
 
+/* ---- Static COHSEX self-energies (Algorithm 3 steps 4-7) -------------------
+ * Band self-energies of the static COHSEX approximation (Section "GW
+ * approximation": Sigma_SEX_X, Sigma_X, Sigma_COH of every band n) from
+ * three ISDF fits on one grid, each in its own context:
+ *   ctx_vc  the dielectric fit: isdf_fit on the orbitals (n_v occupied), then
+ *           build_polarizability with omega[0] = 0 and smw_inverse(0);
+ *   ctx_vn  isdf_fit on [Phi_v | Phi] (N_r x (n_v + n_e), n_v "occupied"),
+ *           with its own interpolation points: the occupied x all pairs;
+ *   ctx_nn  isdf_fit on [Phi | Phi] (n_e "occupied"): the all x all pairs.
+ * W_vn = (P_vn^T V P_vc) K (P_vc^T V P_vn), V_vn = P_vn^T V P_vn and
+ * W_nn = (P_nn^T V P_vc) K (P_vc^T V P_nn), then by the Hadamard identity
+ * (Eq. Hadamard) Sigma_SEX_X(n) = -psi_n^T (W_vn .* Psi_v Psi_v^T) psi_n and
+ * Sigma_X(n) = -psi_n^T (V_vn .* Psi_v Psi_v^T) psi_n at the vn points,
+ * Sigma_COH(n) = 1/2 psi_n^T (W_nn .* Psi Psi^T) psi_n at the nn points.
+ * The quasiparticle energies of Algorithm 3 step 8 are
+ * e_n + Sigma_SEX_X(n) + Sigma_X(n) + Sigma_COH(n) - (V_xc)_n.
+ *   sigma  device, 3 n_e float64 out: [0, n_e) SEX_X, [n_e, 2 n_e) X,
+ *          [2 n_e, 3 n_e) COH.
+ * FP64 throughout, on ctx_vc's stream (the three contexts' streams are
+ * synchronised first); synchronises at the end.  ISDF_ERR_STATE / _SHAPE
+ * for missing steps or mismatched fits. */
+ISDF_API int isdf_cohsex(isdf_ctx* ctx_vc, isdf_ctx* ctx_vn, isdf_ctx* ctx_nn, double* sigma);
+
 /* ---- Batched full-frequency runner ----------------------------------------
  * Many systems of different sizes, every frequency of each (the
  * full-frequency form of Algorithm 3 steps 1-3 over a set of systems).

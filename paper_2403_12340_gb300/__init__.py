@@ -37,7 +37,7 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "isdf_read_kernel_profile", "isdf_kernel_family_name", "isdf_set_point_orbitals",
             "isdf_screened_basis", "isdf_adjoint", "smw_inverse_all", "isdf_batch_create",
             "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error",
-            "build_polarizability_contour", "isdf_contour_nodes"]
+            "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 5
 
@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.build_polarizability_contour.restype = I
     lib.isdf_contour_nodes.argtypes = [P, I, I, D]
     lib.isdf_contour_nodes.restype = I
+    lib.isdf_cohsex.argtypes = [P, P, P, P]
+    lib.isdf_cohsex.restype = I
     lib.smw_inverse_all.argtypes = [P, P]
     lib.smw_inverse_all.restype = I
     lib.isdf_set_point_orbitals.argtypes = [P, P, LL]
@@ -220,6 +222,15 @@ def isdf_contour_nodes(energies, n_v: int, n_c: int, tol: float) -> int:
     if n < 0:
         raise IsdfError(n, "isdf_contour_nodes: bad arguments or no gap")
     return n
+
+
+def isdf_cohsex(ctx_vc, ctx_vn, ctx_nn, n_e: int, device="cuda"):
+    """(SEX_X, X, COH) band self-energies (n_e each, device tensors)."""
+    import torch
+
+    sig = torch.empty(3 * n_e, dtype=torch.float64, device=device)
+    _check(load_library().isdf_cohsex(ctx_vc, ctx_vn, ctx_nn, _dev_ptr(sig, name="sigma")), ctx_vc)
+    return sig[:n_e], sig[n_e:2 * n_e], sig[2 * n_e:]
 
 
 def smw_inverse(ctx, omega_index: int = 0, K_out=None) -> None:

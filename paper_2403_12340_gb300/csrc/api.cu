@@ -233,6 +233,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
                     &c->m_pairs_t, &c->swf, &c->kappa_work};
   for (DevBuf* b : bufs) release(*b);
+  for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);

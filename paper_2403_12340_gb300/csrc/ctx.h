@@ -91,6 +91,7 @@ struct isdf_ctx {
   // their slice stacks, scratch of the batched factorisations, failure flags
   DevBuf bW1, bT, bU, bQ, b_s1, b_s2, b_s3, b_work, b_cb, b_dtmp, b_cbd;
   DevBuf ctab;  // contour-integral polarizability: resolvent weights and node weights
+  DevBuf cx[12];  // COHSEX (cohsex.cu): spectra, cross products, scratch
   DevBuf m_pairs_t, swf;  // pair-space whitening: transposed pair slices, FP32 pair weights
   bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
   int pair_mode = 0;         // the precision argument of the last fit

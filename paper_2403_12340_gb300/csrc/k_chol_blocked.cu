@@ -37,93 +37,116 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
 }
 
 // Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place; the
-// strict upper part of the block is zeroed.  One thread block on one SM,
-// whose FP64 pipe (2 DFMA / clock) is the limit.  An FP64 warp instruction
-// costs that pipe the same whether one lane or 32 are active, so the kernel
-// keeps single-lane FP64 work off the per-column path: right-looking outer
-// products on the unscaled columns, A(i, k) -= s_i A(k, j) with s_i =
-// A(i, j) / d_j formed once per row, over the m (m + 1) / 2 entries of the
-// remaining lower triangle packed densely over the threads through a table
-// of (row, column) offsets; 1 / d_{j+1} is formed by the thread that
-// finishes d_{j+1} (an FP32 reciprocal refined by two Newton steps,
-// r <- r (2 - d r), each doubling the correct bits).  Column j is scaled by
-// d_j^-1/2 and the diagonal set to d_j^1/2 at the end.
-constexpr int TRI = CB * (CB - 1) / 2;  // entries of a strictly lower 63-row triangle
+// strict upper part of the block is zeroed.  One thread block on one SM.
+// The block is factored 8 columns at a time, so that the 64 dependent
+// column steps cost 3 block barriers per 8 columns instead of one or two
+// per column (barriers dominated the column-by-column version):
+//   A: warp 0 factors the 8 x 8 diagonal sub-block warp-synchronously (lane i
+//      holds row i; the reciprocal square root of each pivot from an FP32
+//      estimate refined by two Newton steps y <- y (3 - d y^2) / 2);
+//   B: the rows below solve against it (one thread per row and column of
+//      the panel, forward substitution over the 8 columns);
+//   C: every thread applies the rank-8 update to its share of the remaining
+//      lower triangle.
+// An FP64 warp instruction costs the FP64 pipe the same with one lane or
+// 32, so no step runs FP64 on a single lane of many warps.
+constexpr int SUB = 8;
 
-__device__ __forceinline__ double recip_newton(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;  // outside the FP32 range of the first estimate
-  double r = (double)(1.0f / (float)d);
-  r = r * fma(-d, r, 2.0);
-  return r * fma(-d, r, 2.0);
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);  // outside the FP32 range of the first estimate
+  double y = (double)rsqrtf((float)d);
+  y = y * fma(-0.5 * d * y, y, 1.5);
+  return y * fma(-0.5 * d * y, y, 1.5);
 }
 
-constexpr int DIAG_THREADS = 512;  // 16 warps: enough to hide FP64 and shared-memory latency per column
+constexpr int DIAG_THREADS = 512;
 
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long lda, int j0, int bs,
                                                            const double* dmax, double tol_rel, int* fail,
                                                            long long sA = 0) {
   __shared__ double Ls[CB][CB + 1];
-  __shared__ double sc[CB];        // s_i of the current column
-  __shared__ double rdiag[CB + 1]; // 1 / d_j
-  __shared__ double sq[CB], rsq[CB];
-  __shared__ unsigned char ta[TRI], tb[TRI];
+  __shared__ double ysub[SUB];  // 1 / L(c, c) of the current sub-block
+  __shared__ int s_bad;
   // problem blockIdx.x of a batch: its matrix, max and flag
   A += sA * blockIdx.x;
   dmax += blockIdx.x;
   fail += blockIdx.x;
   if (*(volatile int*)fail >= 0) return;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
     int i = idx & (CB - 1), k = idx >> 6;
     Ls[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
   }
-  // (a, b) with b <= a for the packed index a (a + 1) / 2 + b
-  for (int idx = t; idx < TRI; idx += blockDim.x) {
-    int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-    while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-    while (a * (a + 1) / 2 > idx) --a;
-    ta[idx] = (unsigned char)a;
-    tb[idx] = (unsigned char)(idx - a * (a + 1) / 2);
-  }
+  if (t == 0) s_bad = -1;
   const double thresh = tol_rel * (*dmax);
   __syncthreads();
-  if (t == 0) rdiag[0] = recip_newton(Ls[0][0]);
-  __syncthreads();
-  int bad = -1;
-  for (int j = 0; j < bs; ++j) {
-    const double d = Ls[j][j];  // the same value in every thread: the branch below is uniform
-    if (!(d > thresh)) {        // also catches NaN
-      bad = j;
-      break;
+  for (int jb = 0; jb < bs; jb += SUB) {
+    const int w = min(SUB, bs - jb);
+    // A: the w x w diagonal sub-block, warp 0, lane i <-> row jb + i
+    if (warp == 0) {
+      for (int c = 0; c < w; ++c) {
+        __syncwarp();
+        const double d = Ls[jb + c][jb + c];
+        if (!(d > thresh)) {  // the same value in every lane; also catches NaN
+          if (lane == 0) s_bad = jb + c;
+          break;
+        }
+        const double y = rsqrt_newton(d);
+        __syncwarp();
+        if (lane == c) {
+          Ls[jb + c][jb + c] = d * y;
+          ysub[c] = y;
+        }
+        if (lane > c && lane < w) Ls[jb + lane][jb + c] *= y;
+        __syncwarp();
+        if (lane > c && lane < w) {
+          const double lic = Ls[jb + lane][jb + c];
+          for (int k = c + 1; k <= lane; ++k) Ls[jb + lane][jb + k] = fma(-lic, Ls[jb + k][jb + c], Ls[jb + lane][jb + k]);
+        }
+      }
     }
-    const int m = bs - j - 1;
-    const double rd = rdiag[j];
-    for (int i = t; i < m; i += blockDim.x) sc[i] = Ls[j + 1 + i][j] * rd;
     __syncthreads();
+    if (s_bad >= 0) break;
+    const int r0 = jb + w, m = bs - r0;  // rows below the sub-block
+    // B: panel rows r0.. against the sub-block: x (L_sub)^T = a, row by row
+    for (int i = t; i < m; i += blockDim.x) {
+      double x[SUB];
+#pragma unroll
+      for (int c = 0; c < SUB; ++c) {
+        if (c < w) {
+          double sacc = Ls[r0 + i][jb + c];
+#pragma unroll
+          for (int k = 0; k < SUB; ++k)
+            if (k < c) sacc = fma(-x[k], Ls[jb + c][jb + k], sacc);
+          x[c] = sacc * ysub[c];
+          Ls[r0 + i][jb + c] = x[c];
+        }
+      }
+    }
+    __syncthreads();
+    // C: rank-w update of the lower triangle of rows / columns r0..bs
     const int cnt = m * (m + 1) / 2;
     for (int idx = t; idx < cnt; idx += blockDim.x) {
-      const int a = ta[idx], b = tb[idx];
-      const int i = j + 1 + a, k = j + 1 + b;
-      const double v = fma(-sc[a], Ls[k][j], Ls[i][k]);
+      int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+      while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+      while (a * (a + 1) / 2 > idx) --a;
+      const int b = idx - a * (a + 1) / 2;
+      const int i = r0 + a, k = r0 + b;
+      double v = Ls[i][k];
+#pragma unroll
+      for (int c = 0; c < SUB; ++c)
+        if (c < w) v = fma(-Ls[i][jb + c], Ls[k][jb + c], v);
       Ls[i][k] = v;
-      if (idx == 0 && m > 0) rdiag[j + 1] = recip_newton(v);  // thread 0 finishes d_{j+1} first
     }
     __syncthreads();
   }
-  if (bad >= 0) {
-    if (t == 0) atomicCAS(fail, -1, j0 + bad);
+  if (s_bad >= 0) {
+    if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
     return;
   }
-  if (t < bs) {
-    const double r = sqrt(Ls[t][t]);
-    sq[t] = r;
-    rsq[t] = recip_newton(r);
-  }
-  __syncthreads();
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
     const int i = idx % bs, k = idx / bs;
-    A[(j0 + i) + lda * (long long)(j0 + k)] = (k < i) ? Ls[i][k] * rsq[k] : (k == i ? sq[k] : 0.0);
+    A[(j0 + i) + lda * (long long)(j0 + k)] = (k <= i) ? Ls[i][k] : 0.0;
   }
 }
 
