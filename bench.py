@@ -313,9 +313,14 @@ def run_native(args):
         fp64 = {"value": round(job_throughput(ws, k64, ms64), 4), "unit": "solves/s",
                 "ms_per_step": round(ms64 / k64, 3), "steps": k64, "rel_err_vs_oracle": err64}
 
+    # tile autotuner: the first warm-up step times the GEMM tile candidates
+    if args.autotune == "on":
+        pkg.isdf_set_autotune(1)
     for _ in range(args.warmup):
         step(phi, X, Y)
     torch.cuda.synchronize(dev)
+    pkg.isdf_set_autotune(0)
+    tuned = pkg.isdf_autotune_table()
     err = rel_err()
 
     # ---- device-timed region: inputs resident in HBM
@@ -402,7 +407,8 @@ def run_native(args):
             "data": "synthetic",
             "config": workload_config(s, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                           "rank": rank_r, "precision": args.prec,
-                                          "precision_detail": PREC_DETAIL[args.prec]}),
+                                          "precision_detail": PREC_DETAIL[args.prec],
+                                          "autotune": autotune_summary(args, tuned)}),
             "tflops": round(flops_step * value / 1e12, 4),
             "flops_per_step": flops_step,
             "rel_err_vs_oracle": err,
@@ -416,6 +422,17 @@ def run_native(args):
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def autotune_summary(args, table):
+    """How many GEMM shapes the tile autotuner timed and how many it moved
+    off the built-in heuristic (tile width or split count)."""
+    if args.autotune != "on":
+        return "off"
+    moved = [t for t in table if t["ms_best"] < t["ms_heuristic"]]
+    saved = sum(t["ms_heuristic"] - t["ms_best"] for t in moved)
+    return {"shapes": len(table), "changed": len(moved), "ms_saved_per_call_sum": round(saved, 3),
+            "tiles_64": sum(1 for t in table if t["bn"] == 64)}
 
 
 # ------------------------------------------------ full-frequency batch arm
@@ -477,8 +494,22 @@ def run_batch(args):
         s.phi_dev = pkg.to_fortran(s.phi, dev)
     n_sys = len(systems)
     batch = pkg.IsdfBatch(systems, prec=PREC[args.prec], n_workers=args.batch_workers)
+    if args.autotune == "on":
+        pkg.isdf_set_autotune(1)
+    batch.run(omegas, n_workers=1)  # sizes every workspace; tunes the GEMM tiles one system at a time
+    pkg.isdf_set_autotune(0)
+    tuned = pkg.isdf_autotune_table()
+    n0 = pkg.isdf_launch_count()
+    batch.run(omegas)
+    launches_per_run = pkg.isdf_launch_count() - n0
+    graph = args.batch_mode == "graph"
+    if graph:
+        batch.capture(omegas)  # one eager run, then the graph of every system's device work
     for _ in range(max(1, args.warmup)):
-        batch.run(omegas)  # the first run sizes every workspace
+        if graph:
+            batch.replay()
+        else:
+            batch.run(omegas)
 
     # parity sample: the smallest system, first and last frequency, 4 probes
     err = None
@@ -510,12 +541,17 @@ def run_batch(args):
     n0 = pkg.isdf_launch_count()
     lats, svcs, tot_ms = [], [], 0.0
     for _ in range(args.steps):
-        lat, svc, tot = batch.run(omegas)
+        if graph:
+            lat, tot = batch.replay()
+            svc = lat
+        else:
+            lat, svc, tot = batch.run(omegas)
         lats.append(lat)
         svcs.append(svc)
         tot_ms += tot
     torch.cuda.synchronize(dev)
-    launches = pkg.isdf_launch_count() - n0
+    # a replay issues the kernels recorded in its graph: those of one eager run
+    launches = launches_per_run * args.steps if graph else pkg.isdf_launch_count() - n0
     clocks = sampler.stop() if sampler else None
     ms_max = max_over_ranks(tot_ms, dev)
     # kernel timing: one more run with a single worker, so that no other
@@ -567,16 +603,22 @@ def run_batch(args):
                                     "K(w) of one (system, frequency)"),
                        "precision": args.prec, "precision_detail": PREC_DETAIL[args.prec],
                        "host_workers": args.batch_workers, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "mode": ("one CUDA graph of every system's fit, polarizability and SMW at all frequencies, "
+                                "one launch per step" if graph else "host worker threads, eager calls"),
+                       "autotune": autotune_summary(args, tuned),
                        "l2": "inputs larger than L2 (phi 0.05-2.2 GB per system)",
                        "timing": "host wall clock around each run; a run returns after every system's GPU work"},
             "tflops": round(flops_run * args.steps * ws / (ms_max / 1e3) / 1e12, 3),
             "flops_per_step": flops_run,
             "latency_ms": {"p50": round(float(np.percentile(lat_all, 50)), 2),
                            "p99": round(float(np.percentile(lat_all, 99)), 2),
-                           "kind": "per system, from the start of the run to its last K(w)"},
+                           "kind": ("per system, from the start of the run to its last K(w)" if not graph else
+                                    "per system, from the start of the graph to the end of its branch "
+                                    "(events recorded inside the graph)")},
             "service_ms": {"p50": round(float(np.percentile(svc_all, 50)), 2),
                            "p99": round(float(np.percentile(svc_all, 99)), 2),
-                           "kind": "per system, from the start of its fit to its last K(w)"},
+                           "kind": ("per system, from the start of its fit to its last K(w)" if not graph else
+                                    "the graph starts every system at once: equal to the latency")},
             "rel_err_vs_oracle": err,
             "roofline": cells[0] if cells else None, "kernels": cells[:8],
             "cpu_baseline": cpu, "e2e": None,
@@ -636,6 +678,10 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["isdf48", "batch16"], default="isdf48",
                     help="isdf48: one 48^3 system (the default line); batch16: 16 systems x 32 frequencies")
     ap.add_argument("--batch-workers", type=int, default=4, help="host threads of the batch runner")
+    ap.add_argument("--batch-mode", choices=["graph", "threads"], default="graph",
+                    help="batch16: replay one captured CUDA graph per step, or drive eager calls from host threads")
+    ap.add_argument("--autotune", choices=["on", "off"], default="on",
+                    help="time the tensor-core GEMM tile candidates during the warm-up")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

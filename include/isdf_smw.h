@@ -308,6 +308,50 @@ ISDF_API int isdf_batch_destroy(isdf_batch* batch);
 ISDF_API int isdf_batch_run(isdf_batch* batch, const double* omega, int n_omega, int n_workers,
                             double* latency_ms, double* service_ms, double* total_ms);
 
+/* CUDA-graph form of isdf_batch_run.  isdf_batch_capture first runs the
+ * batch eagerly at the frequencies omega (host, n_omega), which sizes every
+ * workspace and fixes each system's rank, then captures the device work of
+ * all systems (fit, polarizability at every frequency, SMW) into one graph:
+ * the systems are parallel branches off one origin stream, each system's
+ * two streams forked and joined inside its branch.  Every fit must have been
+ * unpivoted at full rank (else ISDF_ERR_STATE: a pivoted fit decides on the
+ * host).  isdf_batch_replay launches that graph once (one cudaGraphLaunch,
+ * no host work between the systems), synchronises, then checks each
+ * system's device status and factorisation flags exactly as the eager calls
+ * do (ISDF_ERR_NOT_SPD, ISDF_ERR_NONFINITE, ...).  The replay reads the
+ * orbitals from the same device buffers at the time of the replay, so new
+ * orbital values of the same shape need no recapture; the energies and
+ * frequencies are those of the capture.  latency_ms (host, n_systems, or
+ * NULL): time from the start of the graph to the end of each system's
+ * branch, from events recorded inside the graph; total_ms (host or NULL):
+ * host wall time of the launch and the synchronisation.  A new capture
+ * replaces the old graph; isdf_batch_destroy frees it. */
+ISDF_API int isdf_batch_capture(isdf_batch* batch, const double* omega, int n_omega);
+ISDF_API int isdf_batch_replay(isdf_batch* batch, double* latency_ms, double* total_ms);
+
+/* Tile autotuner of the tensor-core GEMMs of the mixed path (process-wide,
+ * all contexts and threads).  isdf_set_autotune(1) turns it on (returns the
+ * previous setting): the first call of each GEMM shape then times the
+ * candidate tile widths (128 or 64 output columns per tile) and split-K
+ * counts (the built-in heuristic's, twice and half of it, never below the
+ * FP32 accumulation-length minimum) on the call's own operands, keeps the
+ * fastest, and every later call of that shape uses it; calls recorded into a
+ * CUDA graph use the table and never time.  Products that accumulate into
+ * their output (beta != 0) keep the heuristic.  Tuning synchronises the
+ * calling stream; a tuned choice changes results only by the FP32
+ * accumulation order (split count), within the mixed path's error bound.
+ * isdf_autotune_entry(i, key, choice, ms): entry i < isdf_autotune_size()
+ * as key[8] = {M, N, K padded, slices, lower-only, triangular B, batch
+ * count, split cap}, choice[2] = {tile width, splits}, ms[2] = {best,
+ * heuristic} (ms per call when tuned); returns -1 if i is out of range.
+ * isdf_autotune_clear() empties the table.  isdf_set_autotune(2) times
+ * nothing and records the 64-wide tile wherever it is allowed (heuristic
+ * splits), so that a workload exercises every tile path (tests). */
+ISDF_API int isdf_set_autotune(int on);
+ISDF_API int isdf_autotune_size(void);
+ISDF_API int isdf_autotune_entry(int i, int* key, int* choice, double* ms);
+ISDF_API void isdf_autotune_clear(void);
+
 /* The context of one system (for apply_eps_inv, smw K copies, profiling)
  * and its rank after the last run. */
 ISDF_API int isdf_batch_context(isdf_batch* batch, int system, isdf_ctx** ctx, int* rank);

@@ -37,7 +37,9 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "isdf_read_kernel_profile", "isdf_kernel_family_name", "isdf_set_point_orbitals",
             "isdf_screened_basis", "isdf_adjoint", "smw_inverse_all", "isdf_batch_create",
             "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error",
-            "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex"]
+            "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex", "isdf_batch_capture",
+            "isdf_batch_replay", "isdf_set_autotune", "isdf_autotune_size", "isdf_autotune_entry",
+            "isdf_autotune_clear"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 5
 
@@ -88,7 +90,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_batch_destroy.argtypes = [P]
     lib.isdf_batch_run.argtypes = [P, P, I, I, P, P, P]
     lib.isdf_batch_context.argtypes = [P, I, P, P]
-    for name in ["isdf_batch_create", "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context"]:
+    lib.isdf_set_autotune.argtypes = [I]
+    lib.isdf_autotune_size.argtypes = []
+    lib.isdf_autotune_entry.argtypes = [I, P, P, P]
+    lib.isdf_autotune_clear.argtypes = []
+    lib.isdf_autotune_clear.restype = None
+    lib.isdf_batch_capture.argtypes = [P, P, I]
+    lib.isdf_batch_replay.argtypes = [P, P, P]
+    for name in ["isdf_batch_create", "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context",
+                 "isdf_batch_capture", "isdf_batch_replay"]:
         getattr(lib, name).restype = I
     lib.isdf_batch_last_error.argtypes = [P]
     lib.isdf_batch_last_error.restype = ctypes.c_char_p
@@ -214,6 +224,33 @@ def build_polarizability_contour(ctx, energies, n_nodes: int, D_out=None, G_out=
     pd = 0 if D_out is None else _dev_ptr(D_out.reshape(-1), name="D_out")
     pg = 0 if G_out is None else _dev_ptr(G_out.reshape(-1), name="G_out")
     _check(load_library().build_polarizability_contour(ctx, e.ctypes.data, int(n_nodes), pd, pg), ctx)
+
+
+def isdf_set_autotune(on) -> int:
+    """Turn the tensor-core GEMM tile autotuner on (1) or off (0), or record
+    the narrowest tiles without timing (2); returns the previous setting."""
+    return int(load_library().isdf_set_autotune(2 if on == 2 else (1 if on else 0)))
+
+
+def isdf_autotune_table():
+    """The autotuner's table: a list of dicts (shape key, chosen tile width
+    and splits, best and heuristic ms per call)."""
+    lib = load_library()
+    out = []
+    key = (ctypes.c_int * 8)()
+    ch = (ctypes.c_int * 2)()
+    ms = (ctypes.c_double * 2)()
+    for i in range(lib.isdf_autotune_size()):
+        if lib.isdf_autotune_entry(i, key, ch, ms) != 0:
+            break
+        out.append({"M": key[0], "N": key[1], "Kp": key[2], "slices": key[3], "lower": key[4], "tri_b": key[5],
+                    "count": key[6], "max_split": key[7], "bn": ch[0], "splits": ch[1], "ms_best": ms[0],
+                    "ms_heuristic": ms[1]})
+    return out
+
+
+def isdf_autotune_clear() -> None:
+    load_library().isdf_autotune_clear()
 
 
 def isdf_contour_nodes(energies, n_v: int, n_c: int, tol: float) -> int:
@@ -519,6 +556,26 @@ class IsdfBatch:
         if rc != ISDF_OK:
             raise IsdfError(rc, (lib.isdf_batch_last_error(self.h) or b"").decode())
         return lat, svc, tot.value
+
+    def capture(self, omega):
+        """Eager run at omega, then one CUDA graph of every system's device
+        work (isdf_batch_capture)."""
+        lib = load_library()
+        w = np.ascontiguousarray(np.atleast_1d(np.asarray(omega, dtype=np.float64)))
+        self._graph_omega = w
+        rc = lib.isdf_batch_capture(self.h, w.ctypes.data, int(w.shape[0]))
+        if rc != ISDF_OK:
+            raise IsdfError(rc, (lib.isdf_batch_last_error(self.h) or b"").decode())
+
+    def replay(self):
+        """(latency_ms per system, total_ms) of one launch of the captured graph."""
+        lib = load_library()
+        lat = np.zeros(self.n)
+        tot = ctypes.c_double(0.0)
+        rc = lib.isdf_batch_replay(self.h, lat.ctypes.data, ctypes.byref(tot))
+        if rc != ISDF_OK:
+            raise IsdfError(rc, (lib.isdf_batch_last_error(self.h) or b"").decode())
+        return lat, tot.value
 
     def context(self, i):
         """(context handle, rank) of system i."""

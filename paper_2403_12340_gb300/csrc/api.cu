@@ -46,8 +46,17 @@ static int cuda_fail(isdf_ctx* c, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);   \
   } while (0)
 
+// host synchronisation, skipped while a graph is captured
+#define SYNC(st)                                             \
+  do {                                                       \
+    if (!isdf::tl_capture) CK(cudaStreamSynchronize(st));    \
+  } while (0)
+
+thread_local bool isdf::tl_capture = false;
+
 cudaError_t isdf::ensure(DevBuf& b, size_t n) {
   if (n <= b.cap) return cudaSuccess;
+  if (tl_capture) return cudaErrorStreamCaptureUnsupported;  // sized by the eager run before the capture
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;
@@ -250,6 +259,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
 
 static cudaError_t ensure_ints(int*& p, size_t& cap, size_t n) {
   if (n <= cap) return cudaSuccess;
+  if (isdf::tl_capture) return cudaErrorStreamCaptureUnsupported;
   if (p) cudaFree(p);
   p = nullptr;
   cap = 0;
@@ -325,11 +335,18 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     if (sorted[i] == sorted[i - 1]) return fail(c, ISDF_ERR_INDEX, "isdf_fit: repeated interpolation index");
   const int n_e = n_v + n_c;
   std::vector<int> idx32(mu_idx, mu_idx + n_mu);
-  CK(cudaStreamSynchronize(c->stream));  // earlier work may still read workspace that is resized below
+  if (isdf::tl_capture) {
+    // a graph replays the eager fit before it: same points, same precision,
+    // unpivoted at full rank (the point indices are already on the device)
+    if (!c->fit_full || c->fit_idx != idx32 || c->fit_mode != mode || c->n_v != n_v || c->n_c != n_c)
+      return fail(c, ISDF_ERR_STATE, "isdf_fit: a captured fit needs an eager full-rank fit of the same points first");
+  }
+  SYNC(c->stream);  // earlier work may still read workspace that is resized below
   CK(ensure_ints(c->d_idx, c->cap_idx, (size_t)3 * n_mu));
   c->d_perm = c->d_idx + n_mu;
   c->d_perm2 = c->d_idx + 2 * n_mu;
-  CK(cudaMemcpyAsync(c->d_idx, idx32.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  if (!isdf::tl_capture)
+    CK(cudaMemcpyAsync(c->d_idx, idx32.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
   CK(launch_check_finite(phi, c->n_r * n_e, c->d_status, c->stream));
   // orbitals at the points, C C^T (face-split Gram of the point block), its pivoted Cholesky
@@ -367,18 +384,21 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   }
   rc0 = join_s2(c);
   if (rc0 != ISDF_OK) return rc0;
-  CK(cudaStreamSynchronize(c->stream));
   int rc;
-  rc = check_status(c, "isdf_fit");
-  if (rc != ISDF_OK) return rc;
-  int fail = 0, rank = 0;
-  CK(cudaMemcpy(&fail, c->d_ints + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  int fail = -1, rank = 0;
+  if (!isdf::tl_capture) {  // captured: the flags are read after the replay (graph_check)
+    CK(cudaStreamSynchronize(c->stream));
+    rc = check_status(c, "isdf_fit");
+    if (rc != ISDF_OK) return rc;
+    CK(cudaMemcpy(&fail, c->d_ints + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  }
   c->perm.assign(n_mu, 0);
   const bool gram_done = fail < 0;
   if (fail < 0) {
     rank = n_mu;
     for (int i = 0; i < n_mu; ++i) c->perm[i] = i;
-    CK(cudaMemcpyAsync(c->d_perm, c->perm.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if (!isdf::tl_capture)  // captured: the identity order of the eager fit is on the device
+      CK(cudaMemcpyAsync(c->d_perm, c->perm.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   } else {
     {
       PhaseScope ph(c, ISDF_PH_POINTS);
@@ -439,7 +459,12 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   c->n_c = n_c;
   c->n_mu = n_mu;
   c->rank = r;
-  c->fitted = true;
+  c->fitted = true;  // captured: graph_check clears it if the replay's factorisation failed
+  if (!isdf::tl_capture) {
+    c->fit_idx = idx32;
+    c->fit_mode = mode;
+    c->fit_full = gram_done;
+  }
   if (rank_out) *rank_out = r;
   return ISDF_OK;
 }
@@ -494,8 +519,18 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
       return fail(c, ISDF_ERR_ARG, "build_polarizability: frequencies must be finite and >= 0");
   c->polar_ready = false;
   const size_t rr = (size_t)r * r;
-  CK(cudaStreamSynchronize(c->stream));
-  if (c->prec == ISDF_PREC_MIXED && c->pair_mode == ISDF_PREC_MIXED && r > 0) {
+  const bool cap = isdf::tl_capture;
+  if (cap) {
+    // a graph replays the eager call before it: the pair weights and the
+    // contour tables it uploaded stay on the device, so they must not change
+    if (c->n_omega != n_omega || c->omega != std::vector<double>(omega, omega + n_omega) ||
+        c->energies != std::vector<double>(energies, energies + n_e) || c->polar_nodes != n_nodes)
+      return fail(c, ISDF_ERR_STATE,
+                  "build_polarizability: a captured call needs an eager call with the same energies and frequencies first");
+    c->pair_whiten = c->polar_whiten;
+  }
+  SYNC(c->stream);
+  if (!cap && c->prec == ISDF_PREC_MIXED && c->pair_mode == ISDF_PREC_MIXED && r > 0) {
     // mean(lambda) mean(1 / lambda) of C C^T: 1 when perfectly conditioned, at
     // most (1 + cond)^2 / (4 cond) (Kantorovich), so a large value flags a
     // large cond(C C^T)
@@ -523,7 +558,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     int sp = split_for(tiles, lds, c->num_sms);
     int spd = split_for(tiles, (long long)npair, c->num_sms);
     // size all workspace before the first launch (a resize frees memory)
-    CK(cudaStreamSynchronize(c->stream));
+    SYNC(c->stream);
     CK(ensure(c->spec, (size_t)lds * r));
     CK(ensure(c->partial, (size_t)std::max(sp, spd) * rr));
     CK(ensure(c->sw, npair * n_omega));
@@ -532,8 +567,8 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     if (n_nodes > 0) CK(ensure(c->ctab, (size_t)2 * n_nodes * (n_e + 1)));
     if (c->pair_whiten) CK(ensure(c->swf, (npair * n_omega + 1) / 2));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
-    std::vector<double> sw(npair * n_omega);
-    for (int k = 0; k < n_omega; ++k) {
+    std::vector<double> sw(cap ? 0 : npair * n_omega);
+    for (int k = 0; k < (cap ? 0 : n_omega); ++k) {
       const double w2 = omega[k] * omega[k];
       for (int i = 0; i < n_v; ++i)
         for (int j = 0; j < n_c; ++j) {
@@ -541,15 +576,17 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
           sw[npair * k + (size_t)i * n_c + j] = std::sqrt(-2.0 * d / (d * d + w2));
         }
     }
-    CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (!cap) CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // D(w) for every frequency (main stream)
     if (n_nodes > 0) {
       // static D by the contour integral: resolvent weights of every node
       std::vector<double> wt, wn;
       CK(contour_tables(energies, n_v, n_c, n_nodes, wt, wn));
-      CK(cudaMemcpyAsync(c->ctab.p, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-      CK(cudaMemcpyAsync(c->ctab.p + wt.size(), wn.data(), wn.size() * sizeof(double), cudaMemcpyHostToDevice,
-                         c->stream));
+      if (!cap) {
+        CK(cudaMemcpyAsync(c->ctab.p, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ctab.p + wt.size(), wn.data(), wn.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream));
+      }
       double* Dpp = c->prec == ISDF_PREC_MIXED ? c->tmp1.p : c->D.p;
       {
         PhaseScope ph(c, ISDF_PH_POLAR_D);
@@ -567,9 +604,11 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
         CK(cudaMemcpyAsync(c->D.p, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       }
     } else if (c->prec == ISDF_PREC_MIXED && c->pair_whiten) {
-      std::vector<float> swf(sw.begin(), sw.end());
-      CK(cudaMemcpyAsync(c->swf.p, swf.data(), swf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-      CK(cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
+      if (!cap) {
+        std::vector<float> swf(sw.begin(), sw.end());
+        CK(cudaMemcpyAsync(c->swf.p, swf.data(), swf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
+      }
       CK(isdf::mixed_polar_D_pairspace(c, reinterpret_cast<const float*>(c->swf.p), n_omega));
     } else if (c->prec == ISDF_PREC_MIXED) {
       if (n_omega > 1) {
@@ -639,6 +678,8 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
   c->energies.assign(energies, energies + n_e);
   c->k_ready.assign(n_omega, 0);
   c->polar_ready = true;
+  c->polar_whiten = c->pair_whiten;
+  c->polar_nodes = n_nodes;
   return ISDF_OK;
 }
 
@@ -714,7 +755,7 @@ static int smw_workspace(isdf_ctx* c) {
   long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
   int sp = split_for(tiles, std::max(r, 1), c->num_sms);
   if (c->R.cap < rr || c->T.cap < rr || c->W1.cap < rr || c->Q.cap < rr || c->partial.cap < sp * rr)
-    CK(cudaStreamSynchronize(c->stream));  // a resize frees memory that earlier work may read
+    SYNC(c->stream);  // a resize frees memory that earlier work may read
   CK(ensure(c->R, rr));
   CK(ensure(c->T, rr));
   CK(ensure(c->W1, rr));
@@ -727,6 +768,7 @@ static int smw_workspace(isdf_ctx* c) {
 // factorisations of D(w_k) (d_fail) and of I + R^T G R (failT) for k in
 // [k0, k0 + nk).
 static int smw_finish(isdf_ctx* c, int k0, int nk, const int* failT, const char* who) {
+  if (isdf::tl_capture) return ISDF_OK;  // read by graph_check after the replay
   CK(cudaStreamSynchronize(c->stream));
   int rc = check_status(c, who);
   if (rc != ISDF_OK) return rc;
@@ -741,6 +783,28 @@ static int smw_finish(isdf_ctx* c, int k0, int nk, const int* failT, const char*
   }
   for (int i = 0; i < nk; ++i) c->k_ready[k0 + i] = 1;
   return ISDF_OK;
+}
+
+int isdf::graph_check(isdf_ctx* c, const char* who) {
+  c->err.clear();
+  int rc = check_status(c, who);
+  int fit_fail = -1;
+  if (rc == ISDF_OK) {
+    CK(cudaMemcpy(&fit_fail, c->d_ints + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fit_fail >= 0) {
+      c->fitted = false;
+      c->polar_ready = false;
+      return fail(c, ISDF_ERR_NOT_SPD, std::string(who) + ": the replayed fit needs pivoting (C C^T lost rank); "
+                                                          "run it eagerly");
+    }
+  }
+  if (rc != ISDF_OK) {
+    c->polar_ready = false;
+    return rc;
+  }
+  // the frequency factorisations: smw_finish's check, now on the host side
+  std::fill(c->k_ready.begin(), c->k_ready.end(), 0);
+  return smw_finish(c, 0, c->n_omega, c->b_fail, who);
 }
 
 extern "C" int smw_inverse(isdf_ctx* c, int k, double* K_out) {
@@ -773,6 +837,7 @@ extern "C" int smw_inverse_all(isdf_ctx* c, double* K_out) {
   const size_t rr = (size_t)r * r;
   std::fill(c->k_ready.begin(), c->k_ready.end(), 0);
   if (c->cap_bfail < (size_t)nw) {
+    if (isdf::tl_capture) return fail(c, ISDF_ERR_STATE, "smw_inverse_all: a captured call needs an eager call first");
     CK(cudaStreamSynchronize(c->stream));
     if (c->b_fail) cudaFree(c->b_fail);
     c->b_fail = nullptr;
@@ -781,7 +846,8 @@ extern "C" int smw_inverse_all(isdf_ctx* c, double* K_out) {
     c->cap_bfail = nw;
   }
   if (r > 0) {
-    CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+    // captured: the status word keeps the fit's flags for graph_check
+    if (!isdf::tl_capture) CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->b_fail, 0xff, nw * sizeof(int), c->stream));
     if (c->prec == ISDF_PREC_MIXED && nw > 1) {
       PhaseScope ph(c, ISDF_PH_SMW);

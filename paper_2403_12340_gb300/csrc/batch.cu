@@ -1,6 +1,11 @@
 // Batched full-frequency runner (declared in include/isdf_smw.h): many
 // systems of different sizes, every frequency of each, on one GPU.
 //
+// Two forms.  isdf_batch_run drives the entry points eagerly from host
+// threads; isdf_batch_capture records the same device work of every system
+// into one CUDA graph (after an eager run that sizes the workspace and fixes
+// the ranks) and isdf_batch_replay launches it as a single graph.
+//
 // Each system owns a context, a non-blocking CUDA stream and its theta
 // buffer for the life of the batch, so repeated runs allocate nothing.  A
 // run hands the systems, largest estimated cost first, to a pool of host
@@ -18,6 +23,7 @@
 #include <vector>
 
 #include "../../include/isdf_smw.h"
+#include "ctx.h"
 
 struct isdf_batch {
   int device = 0;
@@ -36,13 +42,33 @@ struct isdf_batch {
   std::vector<Sys> sys;
   std::vector<int> order;  // largest estimated cost first
   std::string err;
+  // captured graph of every system's fit, polarizability and SMW
+  cudaStream_t origin = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_link = nullptr;
+  std::vector<cudaEvent_t> ev_end;  // one per system, recorded at the end of its branch
+  std::vector<double> g_omega;
 };
 
 namespace {
 
 thread_local std::string g_batch_create_err;
 
+void free_graph(isdf_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
 void free_batch(isdf_batch* b) {
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  free_graph(b);
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
+  if (b->ev_link) cudaEventDestroy(b->ev_link);
+  for (cudaEvent_t e : b->ev_end) cudaEventDestroy(e);
+  if (b->origin) cudaStreamDestroy(b->origin);
   for (auto& s : b->sys) {
     if (s.ctx) isdf_destroy(s.ctx);
     if (s.theta) cudaFree(s.theta);
@@ -202,4 +228,148 @@ extern "C" int isdf_batch_context(isdf_batch* b, int system, isdf_ctx** ctx, int
 
 extern "C" const char* isdf_batch_last_error(isdf_batch* b) {
   return b ? b->err.c_str() : g_batch_create_err.c_str();
+}
+
+namespace {
+
+// Capture every system's device work into b->graph; the caller ends the
+// capture on error (cudaStreamEndCapture) through end_capture below.
+int capture_systems(isdf_batch* b, const double* omega, int n_omega) {
+  auto cuda_err = [&](cudaError_t e, const char* what) {
+    b->err = std::string("isdf_batch_capture: ") + what + ": " + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  };
+  cudaError_t e = cudaEventRecordWithFlags(b->ev_start, b->origin, cudaEventRecordExternal);
+  if (e != cudaSuccess) return cuda_err(e, "start event");
+  if ((e = cudaEventRecord(b->ev_link, b->origin)) != cudaSuccess) return cuda_err(e, "fork event");
+  for (auto& s : b->sys)
+    if ((e = cudaStreamWaitEvent(s.stream, b->ev_link, 0)) != cudaSuccess) return cuda_err(e, "fork");
+  for (int j = 0; j < (int)b->order.size(); ++j) {
+    const int i = b->order[j];
+    auto& s = b->sys[i];
+    int rank = 0;
+    int rc = isdf_fit(s.ctx, s.d.phi, s.d.n_v, s.d.n_c, s.d.mu_idx, s.d.n_mu, b->prec, s.theta, &rank);
+    if (rc == ISDF_OK) rc = build_polarizability(s.ctx, s.d.energies, omega, n_omega, nullptr, nullptr);
+    if (rc == ISDF_OK) rc = smw_inverse_all(s.ctx, nullptr);
+    if (rc != ISDF_OK) {
+      b->err = "isdf_batch_capture: system " + std::to_string(i) + ": " + isdf_last_error(s.ctx);
+      return rc;
+    }
+    if ((e = cudaEventRecordWithFlags(b->ev_end[i], s.stream, cudaEventRecordExternal)) != cudaSuccess)
+      return cuda_err(e, "end event");
+    if ((e = cudaEventRecord(b->ev_link, s.stream)) != cudaSuccess) return cuda_err(e, "join event");
+    if ((e = cudaStreamWaitEvent(b->origin, b->ev_link, 0)) != cudaSuccess) return cuda_err(e, "join");
+  }
+  return ISDF_OK;
+}
+
+}  // namespace
+
+extern "C" int isdf_batch_capture(isdf_batch* b, const double* omega, int n_omega) {
+  if (!b) return ISDF_ERR_ARG;
+  b->err.clear();
+  if (b->origin) {
+    cudaError_t e = cudaStreamSynchronize(b->origin);
+    if (e != cudaSuccess) {
+      b->err = std::string("isdf_batch_capture: ") + cudaGetErrorString(e);
+      return ISDF_ERR_CUDA;
+    }
+  }
+  free_graph(b);
+  b->g_omega.clear();
+  // the eager run: workspace sizes, ranks, uploaded weights
+  int rc = isdf_batch_run(b, omega, n_omega, 0, nullptr, nullptr, nullptr);
+  if (rc != ISDF_OK) return rc;
+  for (int i = 0; i < (int)b->sys.size(); ++i)
+    if (!b->sys[i].ctx->fit_full) {
+      b->err = "isdf_batch_capture: system " + std::to_string(i) +
+               " needed a pivoted (rank-deficient) fit, which a captured graph cannot replay";
+      return ISDF_ERR_STATE;
+    }
+  if (cudaSetDevice(b->device) != cudaSuccess) {
+    b->err = "isdf_batch_capture: cudaSetDevice failed";
+    return ISDF_ERR_CUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->origin) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !b->ev_start) e = cudaEventCreate(&b->ev_start);
+  if (e == cudaSuccess && !b->ev_link) e = cudaEventCreateWithFlags(&b->ev_link, cudaEventDisableTiming);
+  while (e == cudaSuccess && b->ev_end.size() < b->sys.size()) {
+    cudaEvent_t x = nullptr;
+    e = cudaEventCreate(&x);
+    if (e == cudaSuccess) b->ev_end.push_back(x);
+  }
+  if (e != cudaSuccess) {
+    b->err = std::string("isdf_batch_capture: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  for (auto& s : b->sys) cudaStreamSynchronize(s.stream);
+  // the capture itself: entry points in capture mode on this thread only
+  e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    b->err = std::string("isdf_batch_capture: begin capture: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  isdf::tl_capture = true;
+  rc = capture_systems(b, omega, n_omega);
+  isdf::tl_capture = false;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->origin, &g);
+  if (rc == ISDF_OK && e != cudaSuccess) {
+    b->err = std::string("isdf_batch_capture: end capture: ") + cudaGetErrorString(e);
+    rc = ISDF_ERR_CUDA;
+  }
+  if (rc != ISDF_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // clear the runtime's last-error slot after a failed capture
+    return rc;
+  }
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e == cudaSuccess) e = cudaGraphUpload(b->exec, b->origin);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
+  if (e != cudaSuccess) {
+    free_graph(b);
+    b->err = std::string("isdf_batch_capture: instantiate: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  b->g_omega.assign(omega, omega + n_omega);
+  return ISDF_OK;
+}
+
+extern "C" int isdf_batch_replay(isdf_batch* b, double* latency_ms, double* total_ms) {
+  if (!b) return ISDF_ERR_ARG;
+  b->err.clear();
+  if (!b->exec) {
+    b->err = "isdf_batch_replay: no captured graph (call isdf_batch_capture first)";
+    return ISDF_ERR_STATE;
+  }
+  if (cudaSetDevice(b->device) != cudaSuccess) {
+    b->err = "isdf_batch_replay: cudaSetDevice failed";
+    return ISDF_ERR_CUDA;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaGraphLaunch(b->exec, b->origin);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
+  const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (e != cudaSuccess) {
+    b->err = std::string("isdf_batch_replay: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  if (total_ms) *total_ms = wall;
+  const int n = (int)b->sys.size();
+  for (int i = 0; i < n; ++i) {
+    if (latency_ms) {
+      float ms = -1.0f;
+      if (cudaEventElapsedTime(&ms, b->ev_start, b->ev_end[i]) != cudaSuccess) ms = -1.0f;
+      latency_ms[i] = ms;
+    }
+    const int rc = isdf::graph_check(b->sys[i].ctx, "isdf_batch_replay");
+    if (rc != ISDF_OK) {
+      b->err = "isdf_batch_replay: system " + std::to_string(i) + ": " + isdf_last_error(b->sys[i].ctx);
+      return rc;
+    }
+  }
+  cudaGetLastError();
+  return ISDF_OK;
 }

@@ -13,6 +13,24 @@ enum : unsigned {
   ST_BADINDEX = 8u,    // an index failed a device-side bounds check
 };
 
+// 1 / d: an FP32 estimate from the leading bits of d (integer operations and
+// one FP32 reciprocal), then two Newton steps y <- y + y (1 - d y) in FP64
+// (4 FP64 instructions on the chain, no conversion on the FP64 pipe).
+__device__ __forceinline__ double recip_newton(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int ef = (int)((b >> 52) & 0x7FFull) - 1023 + 127;
+  if (ef <= 1 || ef >= 253) return 1.0 / d;  // outside the FP32 range of the estimate
+  const float df = __uint_as_float((unsigned)((b >> 63) << 31) | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+  const unsigned yb = __float_as_uint(__frcp_rn(df));  // a normal float: 2 <= its biased exponent <= 252
+  double y = __longlong_as_double((long long)(((unsigned long long)(yb >> 31) << 63) |
+                                              ((unsigned long long)(((yb >> 23) & 0xFFu) - 127 + 1023) << 52) |
+                                              ((unsigned long long)(yb & 0x7FFFFFu) << 29)));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

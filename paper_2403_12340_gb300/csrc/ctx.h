@@ -109,6 +109,13 @@ struct isdf_ctx {
   std::vector<double> omega;
   std::vector<double> energies;  // of the last build_polarizability
   std::vector<char> k_ready;
+
+  // what a graph capture replays (recorded by the eager calls)
+  std::vector<int> fit_idx;  // points of the last fit
+  int fit_mode = -1;         // its precision argument
+  bool fit_full = false;     // factored unpivoted at full rank
+  bool polar_whiten = false; // pair-space whitening chosen by the last build_polarizability
+  int polar_nodes = 0;       // its contour node count (0: pair sum)
 };
 
 namespace isdf {
@@ -138,9 +145,11 @@ struct PhaseTimer {
   cudaEvent_t e0 = nullptr;
   isdf_ctx* prev_ctx = nullptr;
   int prev_ph = -1;
+  bool active = false;
   PhaseTimer(isdf_ctx* ctx, int phase, cudaStream_t stream = nullptr)
       : c(ctx), ph(phase), st(stream ? stream : ctx->stream) {
-    if (!c->prof_on) return;
+    if (!c->prof_on || tl_capture) return;  // a captured graph carries no timing events
+    active = true;
     prev_ctx = tl_prof_ctx;
     prev_ph = tl_prof_phase;
     tl_prof_ctx = c;
@@ -149,7 +158,7 @@ struct PhaseTimer {
     if (e0) cudaEventRecord(e0, st);
   }
   ~PhaseTimer() {
-    if (c->prof_on || e0) {
+    if (active) {
       tl_prof_ctx = prev_ctx;
       tl_prof_phase = prev_ph;
     }
@@ -179,5 +188,11 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
 // their failure flags in c->bU / fail_T).
 cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega);
 cudaError_t mixed_smw_batched(isdf_ctx* c, int n_omega, int* fail_T);
+
+// api.cu: after a captured graph of isdf_fit, build_polarizability and
+// smw_inverse_all has run (stream synchronised), read the device status and
+// failure flags that the eager calls read themselves, and set the host state
+// those calls would have set.
+int graph_check(isdf_ctx* c, const char* who);
 
 }  // namespace isdf

@@ -38,20 +38,22 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
 
 // Factor A[j0:j0+bs, j0:j0+bs] (lower part, already updated) in place; the
 // strict upper part of the block is zeroed.  One thread block on one SM.
-// The block is factored 8 columns at a time, so that the 64 dependent
-// column steps cost 3 block barriers per 8 columns instead of one or two
-// per column (barriers dominated the column-by-column version):
-//   A: warp 0 factors the 8 x 8 diagonal sub-block warp-synchronously (lane i
-//      holds row i; the reciprocal square root of each pivot from an FP32
-//      estimate refined by two Newton steps y <- y (3 - d y^2) / 2);
-//   B: the rows below solve against it (one thread per row and column of
-//      the panel, forward substitution over the 8 columns);
-//   C: every thread applies the rank-8 update to its share of the remaining
-//      lower triangle.
-// An FP64 warp instruction costs the FP64 pipe the same with one lane or
-// 32, so no step runs FP64 on a single lane of many warps.
-constexpr int SUB = 8;
-
+//
+// On GB300 a warp's FP64 instruction holds its SM sub-partition for about
+// 64 cycles however many of its lanes are active, and one warp's independent
+// FP64 instructions do not overlap; the four sub-partitions together finish
+// about one warp instruction per 19 cycles.  So the 64 dependent pivots are
+// one warp's chain, run alone on its sub-partition, while the three other
+// warps (one per remaining sub-partition) apply the updates one column
+// behind.  The chain carries no square root (LDL^T form):
+//   iteration j, warp 0:   a_j <- a_j - l_{j-1} a_{j,j-1}   (last update of column j)
+//                          r_j = 1 / d_j, d_j = a_jj        (FP32 estimate, two
+//                                                           Newton steps r (2 - d r))
+//                          l_j = a_j r_j                   (below the diagonal)
+//   iteration j, warps 1-3: a_k <- a_k - l_{j-1} a_{k,j-1}  for the columns k > j
+//   one block barrier per iteration.
+// l_j is double buffered, so the chain writes l_j while the others read
+// l_{j-1}.  At the end L = A D^-1/2 below the diagonal and D^1/2 on it.
 __device__ __forceinline__ double rsqrt_newton(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);  // outside the FP32 range of the first estimate
   double y = (double)rsqrtf((float)d);
@@ -59,13 +61,15 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y * fma(-0.5 * d * y, y, 1.5);
 }
 
-constexpr int DIAG_THREADS = 512;
+constexpr int DIAG_THREADS = 128;
 
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long lda, int j0, int bs,
                                                            const double* dmax, double tol_rel, int* fail,
                                                            long long sA = 0) {
-  __shared__ double Ls[CB][CB + 1];
-  __shared__ double ysub[SUB];  // 1 / L(c, c) of the current sub-block
+  __shared__ double Ls[CB][CB + 1];  // Ls[i][k]: the block (lower part), unscaled LDL^T columns
+  __shared__ double lc[2][CB];       // l_j and l_{j-1}
+  __shared__ double piv[CB];         // d_j
+  __shared__ double q[CB];           // d_j^-1/2
   __shared__ int s_bad;
   // problem blockIdx.x of a batch: its matrix, max and flag
   A += sA * blockIdx.x;
@@ -80,73 +84,47 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
   if (t == 0) s_bad = -1;
   const double thresh = tol_rel * (*dmax);
   __syncthreads();
-  for (int jb = 0; jb < bs; jb += SUB) {
-    const int w = min(SUB, bs - jb);
-    // A: the w x w diagonal sub-block, warp 0, lane i <-> row jb + i
+  for (int j = 0; j < bs; ++j) {
+    const double* lp = lc[(j + 1) & 1];  // l_{j-1}
     if (warp == 0) {
-      for (int c = 0; c < w; ++c) {
+      if (j > 0) {
+        const double ajj1 = Ls[j][j - 1];
+        for (int i = j + lane; i < bs; i += 32) Ls[i][j] = fma(-lp[i], ajj1, Ls[i][j]);
         __syncwarp();
-        const double d = Ls[jb + c][jb + c];
-        if (!(d > thresh)) {  // the same value in every lane; also catches NaN
-          if (lane == 0) s_bad = jb + c;
-          break;
-        }
-        const double y = rsqrt_newton(d);
-        __syncwarp();
-        if (lane == c) {
-          Ls[jb + c][jb + c] = d * y;
-          ysub[c] = y;
-        }
-        if (lane > c && lane < w) Ls[jb + lane][jb + c] *= y;
-        __syncwarp();
-        if (lane > c && lane < w) {
-          const double lic = Ls[jb + lane][jb + c];
-          for (int k = c + 1; k <= lane; ++k) Ls[jb + lane][jb + k] = fma(-lic, Ls[jb + k][jb + c], Ls[jb + lane][jb + k]);
-        }
+      }
+      const double d = Ls[j][j];
+      if (!(d > thresh)) {  // the same value in every lane; also catches NaN
+        if (lane == 0) s_bad = j;
+      } else {
+        const double r = recip_newton(d);
+        if (lane == 0) piv[j] = d;
+        double* lj = lc[j & 1];
+        for (int i = j + 1 + lane; i < bs; i += 32) lj[i] = Ls[i][j] * r;
+      }
+    } else if (j > 0) {
+      const int m = bs - j - 1;  // columns and rows j+1 .. bs-1
+      const int cnt = m * (m + 1) / 2;
+      for (int idx = t - 32; idx < cnt; idx += DIAG_THREADS - 32) {
+        int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+        while (a * (a + 1) / 2 > idx) --a;
+        const int i = j + 1 + a, k = j + 1 + idx - a * (a + 1) / 2;
+        Ls[i][k] = fma(-lp[i], Ls[k][j - 1], Ls[i][k]);
       }
     }
     __syncthreads();
     if (s_bad >= 0) break;
-    const int r0 = jb + w, m = bs - r0;  // rows below the sub-block
-    // B: panel rows r0.. against the sub-block: x (L_sub)^T = a, row by row
-    for (int i = t; i < m; i += blockDim.x) {
-      double x[SUB];
-#pragma unroll
-      for (int c = 0; c < SUB; ++c) {
-        if (c < w) {
-          double sacc = Ls[r0 + i][jb + c];
-#pragma unroll
-          for (int k = 0; k < SUB; ++k)
-            if (k < c) sacc = fma(-x[k], Ls[jb + c][jb + k], sacc);
-          x[c] = sacc * ysub[c];
-          Ls[r0 + i][jb + c] = x[c];
-        }
-      }
-    }
-    __syncthreads();
-    // C: rank-w update of the lower triangle of rows / columns r0..bs
-    const int cnt = m * (m + 1) / 2;
-    for (int idx = t; idx < cnt; idx += blockDim.x) {
-      int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-      while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-      while (a * (a + 1) / 2 > idx) --a;
-      const int b = idx - a * (a + 1) / 2;
-      const int i = r0 + a, k = r0 + b;
-      double v = Ls[i][k];
-#pragma unroll
-      for (int c = 0; c < SUB; ++c)
-        if (c < w) v = fma(-Ls[i][jb + c], Ls[k][jb + c], v);
-      Ls[i][k] = v;
-    }
-    __syncthreads();
   }
   if (s_bad >= 0) {
     if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
     return;
   }
+  if (t < bs) q[t] = rsqrt_newton(piv[t]);
+  __syncthreads();
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
     const int i = idx % bs, k = idx / bs;
-    A[(j0 + i) + lda * (long long)(j0 + k)] = (k <= i) ? Ls[i][k] : 0.0;
+    const double v = (k < i) ? Ls[i][k] * q[k] : (k == i ? piv[i] * q[i] : 0.0);
+    A[(j0 + i) + lda * (long long)(j0 + k)] = v;
   }
 }
 
@@ -206,6 +184,96 @@ __global__ void k_copy_block(const double* __restrict__ src, long long lds, long
   if (i < rows && j < cols) dst[sD * blockIdx.z + i + ldd * j] = src[sS * blockIdx.z + i + lds * j];
 }
 
+// The trailing update of one step, A22 <- A22 - P P^T over the lower tiles
+// of A22, P = L[j0 + bs :, j0 : j0 + bs] the solved panel (K = bs <= 64):
+// one TS x TS output tile per block, (TS / 4)^2 threads with a 4 x 4
+// register tile each, strided by TS / 4 so that the shared-memory reads of a
+// warp hit consecutive words; the panel rows of the tile go through shared
+// memory in K chunks of 32.  Every thread issues only FP64 FMAs in the inner
+// loop, 16 per pair of 4-element reads.  The strict upper triangle of a
+// diagonal tile is left alone (only the lower triangle is ever read).
+// Problem blockIdx.y of a batch at L + y sL.
+template <int TS>
+__global__ void __launch_bounds__((TS / 4) * (TS / 4)) k_trail_update(double* L, long long ldl, int j0, int bs,
+                                                                     int rem, const int* fail, long long sL) {
+  constexpr int Q = TS / 4, NT = Q * Q, KC = 32;
+  __shared__ double As[KC][TS], Bs[KC][TS];
+  L += sL * blockIdx.y;
+  if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
+  const int tile = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+  while (ti * (ti + 1) / 2 > tile) --ti;
+  const int tj = tile - ti * (ti + 1) / 2;
+  const int i0 = ti * TS, k0 = tj * TS;  // tile origin inside the trailing block
+  const int t = threadIdx.x, tx = t % Q, ty = t / Q;
+  const long long r0 = j0 + bs;
+  const double* P = L + r0 + ldl * (long long)j0;  // P(i, c) at P[i + ldl c]
+  double acc[4][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n) acc[m][n] = 0.0;
+  for (int c0 = 0; c0 < bs; c0 += KC) {
+    const int kc = min(KC, bs - c0);
+    for (int idx = t; idx < KC * TS; idx += NT) {
+      const int i = idx % TS, c = idx / TS;
+      const bool in_k = c < kc;
+      As[c][i] = (in_k && i0 + i < rem) ? P[(i0 + i) + ldl * (long long)(c0 + c)] : 0.0;
+      Bs[c][i] = (in_k && k0 + i < rem) ? P[(k0 + i) + ldl * (long long)(c0 + c)] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < KC; ++c) {
+      double a[4], b[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        a[m] = As[c][tx + Q * m];
+        b[m] = Bs[c][ty + Q * m];
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc[m][n] = fma(a[m], b[n], acc[m][n]);
+    }
+    __syncthreads();
+  }
+  double* C = L + r0 + ldl * r0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int i = i0 + tx + Q * m, k = k0 + ty + Q * n;
+      if (i < rem && k < rem && (ti != tj || i >= k)) C[i + ldl * (long long)k] -= acc[m][n];
+    }
+}
+
+// Tile width of a trailing update: 64 while there are at least three waves
+// of 64-wide tiles, else 32 (four times the tiles, so that the late, small
+// updates still spread over the SMs).
+static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int rem, int batch, const int* fail,
+                                long long sL, cudaStream_t s) {
+  auto tiles = [](int m, int ts) {
+    const long long T = (m + ts - 1) / ts;
+    return T * (T + 1) / 2;
+  };
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  KernelTimer kt(KF_FP64_GEMM, s, (double)rem * (rem + 1) * bs * batch);  // lower triangle, 2 flops per term
+  note_launch();
+  if (tiles(rem, 64) * batch >= 3LL * sms) {
+    k_trail_update<64><<<dim3((unsigned)tiles(rem, 64), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
+  } else {
+    k_trail_update<32><<<dim3((unsigned)tiles(rem, 32), batch), 64, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
+  }
+  return cudaGetLastError();
+}
+
 static unsigned panel_blocks(int rem) {
   const int b = (rem + 7) / 8;
   return (unsigned)(b < 4 * 152 ? b : 4 * 152);
@@ -239,10 +307,8 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
       k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles, mirrored)
-    double* Pj = L + (j0 + bs) + ldl * (long long)j0;
-    e = launch_gemm(Pj, ldl, false, Pj, ldl, false, rem, rem, bs, -1.0, 1.0, L + (j0 + bs) + ldl * (long long)(j0 + bs),
-                    ldl, true, 1, nullptr, false, s);
+    // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles)
+    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s);
     if (e != cudaSuccess) return e;
   }
   dim3 g((n + 127) / 128, n);
@@ -284,10 +350,7 @@ cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long
       k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    double* Pj = L + (j0 + bs) + ldl * (long long)j0;
-    GemmBatch tb{batch, 1, sL, sL, sL, 0, 0, 0};
-    e = launch_gemm_batched2(Pj, ldl, false, Pj, ldl, false, rem, rem, bs, -1.0, 1.0,
-                             L + (j0 + bs) + ldl * (long long)(j0 + bs), ldl, tb, true, s);
+    e = trail_update(L, ldl, j0, bs, rem, batch, fail, sL, s);
     if (e != cudaSuccess) return e;
   }
   note_launch();

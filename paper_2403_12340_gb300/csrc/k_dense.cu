@@ -540,31 +540,46 @@ __global__ void k_copy_zero(double* A, long long lda, long long sA, int r) {
 
 // Inverse of each 64 x 64 diagonal block of the lower-triangular L, written
 // into the diagonal blocks of Bf (lower part; the strict upper part is 0).
-// Thread c solves L_JJ x = e_c by forward substitution.
-__global__ void k_diag_inverse(const double* __restrict__ L, long long ldl, int r, double* __restrict__ Bf,
-                               long long ldb, long long sL = 0, long long sB = 0) {
+// Forward substitution L X = I row by row, with the sums kept as running
+// updates: row k of X is (e_k - acc_k) / L_kk, then every later row i adds
+// L_ik X_k to its acc_i.  Row k costs one FP64 instruction on the chain and
+// its update is spread over all threads (an FP64 instruction holds a warp's
+// sub-partition for ~64 cycles whatever its active lanes, so one thread per
+// column running its own substitution, as before, was ~7 times slower).
+constexpr int DINV_THREADS = 256;
+__global__ void __launch_bounds__(DINV_THREADS) k_diag_inverse(const double* __restrict__ L, long long ldl, int r,
+                                                              double* __restrict__ Bf, long long ldb, long long sL = 0,
+                                                              long long sB = 0) {
   __shared__ double Ls[TRSM_NB][TRSM_NB + 1];
-  __shared__ double Xs[TRSM_NB][TRSM_NB + 1];
+  __shared__ double Xs[TRSM_NB][TRSM_NB + 1];  // acc, then X, row by row
+  __shared__ double rinv[TRSM_NB];
   L += sL * blockIdx.y;  // matrix blockIdx.y of a batch
   Bf += sB * blockIdx.y;
   const int j0 = blockIdx.x * TRSM_NB;
   const int bs = min(TRSM_NB, r - j0);
-  const int c = threadIdx.x;
-  for (int i = 0; i < bs; ++i)
-    if (c < bs) Ls[i][c] = L[(j0 + i) + ldl * (j0 + c)];
-  __syncthreads();
-  if (c < bs) {
-    for (int i = 0; i < c; ++i) Xs[i][c] = 0.0;
-    Xs[c][c] = 1.0 / Ls[c][c];
-    for (int i = c + 1; i < bs; ++i) {
-      double acc = 0.0;
-      for (int k = c; k < i; ++k) acc = fma(Ls[i][k], Xs[k][c], acc);
-      Xs[i][c] = -acc / Ls[i][i];
-    }
+  const int t = threadIdx.x;
+  for (int idx = t; idx < TRSM_NB * TRSM_NB; idx += DINV_THREADS) {
+    const int i = idx % TRSM_NB, c = idx / TRSM_NB;
+    Ls[i][c] = (i < bs && c <= i) ? L[(j0 + i) + ldl * (long long)(j0 + c)] : 0.0;
+    Xs[i][c] = 0.0;
   }
   __syncthreads();
-  for (int i = 0; i < bs; ++i)
-    if (c < bs) Bf[(j0 + i) + ldb * (j0 + c)] = Xs[i][c];
+  if (t < bs) rinv[t] = recip_newton(Ls[t][t]);
+  __syncthreads();
+  for (int k = 0; k < bs; ++k) {
+    if (t <= k) Xs[k][t] = fma(-Xs[k][t], rinv[k], t == k ? rinv[k] : 0.0);
+    __syncthreads();
+    const int cols = k + 1, cnt = (bs - 1 - k) * cols;
+    for (int idx = t; idx < cnt; idx += DINV_THREADS) {
+      const int i = k + 1 + idx / cols, c = idx - (idx / cols) * cols;
+      Xs[i][c] = fma(Ls[i][k], Xs[k][c], Xs[i][c]);
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < bs * bs; idx += DINV_THREADS) {
+    const int i = idx % bs, c = idx / bs;
+    Bf[(j0 + i) + ldb * (long long)(j0 + c)] = (c <= i) ? Xs[i][c] : 0.0;
+  }
 }
 
 // Bf[J, I] = -L_JJ^-1 L_JI for I < J (64 x 64 blocks), the diagonal
@@ -601,7 +616,7 @@ cudaError_t launch_trsm_prep(const double* L, long long ldl, int r, double* Bf, 
   if (r <= 0) return cudaSuccess;
   int nb = (r + TRSM_NB - 1) / TRSM_NB;
   note_launch();
-  k_diag_inverse<<<nb, TRSM_NB, 0, s>>>(L, ldl, r, Bf, ldb);
+  k_diag_inverse<<<nb, DINV_THREADS, 0, s>>>(L, ldl, r, Bf, ldb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nb == 1) return e;
   dim3 grid(nb - 1, nb - 1);
@@ -668,7 +683,7 @@ cudaError_t launch_tri_inverse(const double* L, long long ldl, int r, double* Li
   if (e != cudaSuccess) return e;
   int nb = (r + TRSM_NB - 1) / TRSM_NB;
   note_launch();
-  k_diag_inverse<<<nb, TRSM_NB, 0, s>>>(L, ldl, r, Li, ldi);
+  k_diag_inverse<<<nb, DINV_THREADS, 0, s>>>(L, ldl, r, Li, ldi);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int bs = TRSM_NB; bs < r; bs *= 2) {
     // merges of this level with a full-size lower block, batched
@@ -713,7 +728,7 @@ cudaError_t launch_tri_inverse_batched(const double* L, long long ldl, long long
   if (e != cudaSuccess) return e;
   const int nb = (r + TRSM_NB - 1) / TRSM_NB;
   note_launch();
-  k_diag_inverse<<<dim3(nb, batch), TRSM_NB, 0, s>>>(L, ldl, r, Li, ldi, sL, sI);
+  k_diag_inverse<<<dim3(nb, batch), DINV_THREADS, 0, s>>>(L, ldl, r, Li, ldi, sL, sI);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int bs = TRSM_NB; bs < r; bs *= 2) {
     const int full = r / (2 * bs);

@@ -17,6 +17,8 @@
 // host in float64.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -512,19 +514,36 @@ size_t fft_smem_z(const FftGrid& g) {
 
 // The FP32 kernels use half of these byte counts.
 
+// The limit is an attribute of the kernel (per device), shared by every
+// context: it only ever grows, so that a context on a smaller grid created
+// later does not lower it below what an existing context launches with.
 cudaError_t fft_configure(size_t smem_xy, size_t smem_z) {
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_fft_xy_fwd<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+  static std::mutex mu;
+  static size_t cur_xy[64] = {}, cur_z[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fft_xy_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fft_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fft_z<0, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fft_z<2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fft_z<1, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem_xy > cur_xy[dev]) {
+    e = cudaFuncSetAttribute(k_fft_xy_fwd<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fft_xy_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fft_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_xy);
+    if (e != cudaSuccess) return e;
+    cur_xy[dev] = smem_xy;
+  }
+  if (smem_z > cur_z[dev]) {
+    e = cudaFuncSetAttribute(k_fft_z<0, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fft_z<2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fft_z<1, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z);
+    if (e != cudaSuccess) return e;
+    cur_z[dev] = smem_z;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_fft_forward(const FftGrid& g, const double* X, long long ldx, int ncols, double* S,

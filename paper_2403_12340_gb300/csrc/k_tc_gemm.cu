@@ -21,10 +21,15 @@
 // unoccupied part of the orbital index) and multiplies them in the epilogue:
 // the face-split Gram (Phi_v Phi_v,mu^T) .* (Phi_c Phi_c,mu^T) of the ISDF fit.
 #include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include "../../include/isdf_smw.h"
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -574,6 +579,63 @@ static void split_k(int k_iters, int tiles, int num_sms, int max_split, int& spl
   splits = (k_iters + per - 1) / per;
 }
 
+// ------------------------------------------------------------ tile autotuner
+//
+// The split-K count and the tile width of an EPI_F64 GEMM come from a
+// heuristic (two units per SM, the accumulation-length minimum, 128-wide
+// tiles).  With the autotuner on, the first call of each shape instead times
+// the candidates -- the heuristic split, twice and half of it (within the
+// accumulation minimum and the caller's partial buffer), each with 128- and
+// 64-wide tiles (a 64-wide tile leaves room for three pipeline stages
+// instead of two; lower-only SYRKs keep square tiles) -- on the call's own
+// operands and output, and keeps the fastest for every later call of that
+// shape, including calls recorded into a CUDA graph.  Calls that accumulate
+// into C (beta != 0) keep the heuristic, because a timed candidate would
+// change C.
+struct TuneKey {
+  int M, N, kp, s, lower, tri, count, max_split;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(M, N, kp, s, lower, tri, count, max_split) <
+           std::tie(o.M, o.N, o.kp, o.s, o.lower, o.tri, o.count, o.max_split);
+  }
+};
+struct TuneVal {
+  int bn, splits;
+  float ms_best, ms_heuristic;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+std::atomic<int> g_autotune{0};
+
+struct TcPlan {
+  int bn, splits, per;
+};
+
+static cudaError_t tc_run_plan(const TcOperand& A, const TcOperand& B, TcArgs a, const TcPlan& p, int M, int N,
+                               double alpha, double beta, double* C, long long ldc, bool lower_only, double* partial,
+                               double mma, cudaStream_t st, const TcBatch& bt) {
+  a.k_per_split = p.per;
+  if (p.splits > 1) {
+    a.partial = partial;
+    cudaError_t e = p.bn == 64 ? tc_launch<64, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st)
+                               : tc_launch<128, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st);
+    if (e != cudaSuccess) return e;
+    return launch_splitk_reduce(partial, p.splits, M, N, alpha, beta, C, ldc, lower_only, TC_BM, st, bt.count,
+                                bt.c_stride);
+  }
+  a.partial = nullptr;
+  return p.bn == 64 ? tc_launch<64, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st)
+                    : tc_launch<128, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st);
+}
+
+static TcPlan plan_for(int k_iters, int splits_wanted, int bn) {
+  TcPlan p;
+  p.bn = bn;
+  p.per = (k_iters + splits_wanted - 1) / splits_wanted;
+  p.splits = (k_iters + p.per - 1) / p.per;
+  return p;
+}
+
 cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
                                 double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
                                 int num_sms, unsigned* status, cudaStream_t st, const TcBatch& bt) {
@@ -599,9 +661,10 @@ cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, i
   a.c_bstride = bt.c_stride;
   const int tm = (M + TC_BM - 1) / TC_BM, tn = (N + 127) / 128;
   const int tiles = (lower_only ? tm * (tm + 1) / 2 : tm * tn) * bt.count;
+  const bool can_split = partial && !tri_b;
   int splits = 1, per = a.k_iters;
-  if (partial && !tri_b) split_k(a.k_iters, tiles, num_sms, max_split, splits, per);
-  a.k_per_split = per;
+  if (can_split) split_k(a.k_iters, tiles, num_sms, max_split, splits, per);
+  TcPlan plan{128, splits, per};
   // BF16 MMA flops of the s (s + 1) / 2 slice products over the outputs the
   // method needs (lower triangle of a SYRK; k <= n under tri_b)
   const double prods = 0.5 * a.s * (a.s + 1);
@@ -610,14 +673,70 @@ cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, i
                       : tri_b    ? (double)M * 0.5 * N * (N + 1.0)
                                  : (double)M * N * kk;
   const double mma = 2.0 * prods * outk * bt.count;
-  if (splits > 1) {
-    a.partial = partial;
-    cudaError_t e = tc_launch<128, 1, EPI_F64>(A, B, a, splits, bt.count, mma, st);
-    if (e != cudaSuccess) return e;
-    return launch_splitk_reduce(partial, splits, M, N, alpha, beta, C, ldc, lower_only, TC_BM, st, bt.count,
-                                bt.c_stride);
+  const TuneKey key{M, N, A.kp, a.s, a.lower_only, a.tri_b, bt.count, can_split ? max_split : 1};
+  bool tuned = false;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      plan = plan_for(a.k_iters, it->second.splits, it->second.bn);
+      tuned = true;
+    }
   }
-  return tc_launch<128, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st);
+  if (!tuned && g_autotune.load() == 2 && !tl_capture) {
+    // the narrowest tile wherever it is allowed, heuristic splits, no timing:
+    // runs every tile path of a workload (tests)
+    plan = plan_for(a.k_iters, splits, lower_only ? 128 : 64);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = TuneVal{plan.bn, plan.splits, 0.0f, 0.0f};
+  } else if (!tuned && g_autotune.load() == 1 && !tl_capture && beta == 0.0) {
+    // candidates: (tile width, splits), the heuristic first
+    const int acc =
+        can_split ? std::min(max_split, (a.k_iters + kTcMaxChunksPerSplit - 1) / kTcMaxChunksPerSplit) : 1;
+    std::vector<TcPlan> cand;
+    auto add = [&](int sp, int bn) {
+      if (sp < acc || sp < 1 || sp > a.k_iters || (sp > 1 && !can_split) || (can_split && sp > max_split)) return;
+      if (bn == 64 && lower_only) return;
+      const TcPlan p = plan_for(a.k_iters, sp, bn);
+      for (const TcPlan& q : cand)
+        if (q.bn == p.bn && q.splits == p.splits) return;
+      cand.push_back(p);
+    };
+    for (int bn : {128, 64}) {
+      add(splits, bn);
+      add(splits * 2, bn);
+      add(splits / 2, bn);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f, heur = 0.0f;
+    TcPlan best_plan = plan;
+    for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+      e = tc_run_plan(A, B, a, cand[i], M, N, alpha, beta, C, ldc, lower_only, partial, mma, st, bt);  // warm
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+        e = tc_run_plan(A, B, a, cand[i], M, N, alpha, beta, C, ldc, lower_only, partial, mma, st, bt);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) break;
+      ms *= 0.5f;
+      if (i == 0) heur = ms;
+      if (ms < best) {
+        best = ms;
+        best_plan = cand[i];
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    plan = best_plan;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = TuneVal{plan.bn, plan.splits, best, heur};
+  }
+  return tc_run_plan(A, B, a, plan, M, N, alpha, beta, C, ldc, lower_only, partial, mma, st, bt);
 }
 
 cudaError_t tc_gemm_f64(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta, double* C,
@@ -682,3 +801,37 @@ cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, i
 }
 
 }  // namespace isdf
+
+// ---- tile autotuner: C ABI (declared in include/isdf_smw.h)
+extern "C" int isdf_set_autotune(int on) { return isdf::g_autotune.exchange(on == 2 ? 2 : (on ? 1 : 0)); }
+
+extern "C" int isdf_autotune_size(void) {
+  std::lock_guard<std::mutex> g(isdf::g_tune_mu);
+  return (int)isdf::g_tune.size();
+}
+
+extern "C" int isdf_autotune_entry(int i, int* key, int* choice, double* ms) {
+  std::lock_guard<std::mutex> g(isdf::g_tune_mu);
+  if (i < 0 || i >= (int)isdf::g_tune.size()) return -1;
+  auto it = isdf::g_tune.begin();
+  std::advance(it, i);
+  const isdf::TuneKey& k = it->first;
+  const int kv[8] = {k.M, k.N, k.kp, k.s, k.lower, k.tri, k.count, k.max_split};
+  if (key)
+    for (int j = 0; j < 8; ++j) key[j] = kv[j];
+  if (choice) {
+    choice[0] = it->second.bn;
+    choice[1] = it->second.splits;
+  }
+  if (ms) {
+    ms[0] = it->second.ms_best;
+    ms[1] = it->second.ms_heuristic;
+  }
+  return 0;
+}
+
+extern "C" void isdf_autotune_clear(void) {
+  std::lock_guard<std::mutex> g(isdf::g_tune_mu);
+  isdf::g_tune.clear();
+}
+

@@ -13,6 +13,13 @@ namespace isdf {
 void note_launch();
 long long launch_count();
 
+// True on a thread that is capturing a CUDA graph of the entry points
+// (batch.cu): the entry points then skip their host synchronisations and
+// host reads, take the shapes, rank and uploaded tables of the eager run
+// before the capture, ensure() refuses to allocate and the tile autotuner
+// only looks up its table.
+extern thread_local bool tl_capture;
+
 // Per-launch timing by kernel family.  While an API call on a context with
 // profiling on is inside one of its phases, a KernelTimer records CUDA
 // events around the launch on the launch's own stream, tagged with the

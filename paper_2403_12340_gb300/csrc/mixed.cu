@@ -208,7 +208,7 @@ cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
   const int ms = tc_min_splits(kpp);  // accumulation-length split of the long pair SYRK
   const int max_split_g = std::max(8, tc_min_splits(pad(2 * c->n_half, 64)));
   // all workspace first: a resize frees memory that queued kernels may use
-  MK(cudaStreamSynchronize(st));
+  if (!tl_capture) MK(cudaStreamSynchronize(st));
   MK(ensure(c->partial, std::max((size_t)ms * chunk, (size_t)max_split_g) * rr));
   MK(ensure_bf16(c->m_pairs, per_pair * chunk));
   MK(ensure_bf16(c->b_s1, per_sq * chunk));
@@ -256,7 +256,7 @@ cudaError_t mixed_polar_D_pairspace(isdf_ctx* c, const float* swf, int n_omega) 
   const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_omega, kPairSliceBudget / (per_pair * 2)));
   const int ms = tc_min_splits(kpp);
   const int max_split_g = std::max(8, tc_min_splits(pad(2 * c->n_half, 64)));
-  MK(cudaStreamSynchronize(st));
+  if (!tl_capture) MK(cudaStreamSynchronize(st));
   MK(ensure(c->partial, std::max((size_t)std::max(ms, 8) * chunk, (size_t)max_split_g) * rr));
   MK(ensure_bf16(c->m_pairs, per_pair * chunk));
   MK(ensure_bf16(c->m_pairs_t, n_t));
@@ -293,7 +293,7 @@ cudaError_t mixed_smw_batched(isdf_ctx* c, int nw, int* fail_T) {
   const size_t wq = (size_t)(r / 2 + 64) * (r / 2 + 64);
   const long long srr = (long long)rr;
   const int sr = NSL * rp;
-  MK(cudaStreamSynchronize(st));
+  if (!tl_capture) MK(cudaStreamSynchronize(st));
   MK(ensure(c->bW1, rr * nw));
   MK(ensure(c->bT, rr * nw));
   MK(ensure(c->bU, rr * nw));

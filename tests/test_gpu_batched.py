@@ -120,3 +120,66 @@ def test_batch_runner_many_systems():
         batch.run(omegas)
         torch.cuda.synchronize()
         batch.close()
+
+
+def test_batch_graph_replay():
+    """isdf_batch_capture / isdf_batch_replay: one CUDA graph of three
+    systems' fits, all-frequency polarizabilities and SMW; the replay matches
+    the oracle, and after the orbitals in the device buffers are replaced by
+    other orbitals of the same shape a second replay matches the oracle for
+    those (the graph recomputes from the buffers)."""
+    import torch
+    import paper_2403_12340_gb300 as pkg
+
+    shapes = [(16, 4, 12, 32, 88), ((12, 15, 10), 3, 9, 18, 89), (18, 5, 20, 64, 90)]
+    systems = [small_system(n, v, c, n_mu=m, seed_index=sd) for n, v, c, m, sd in shapes]
+    omegas, _ = synth.gauss_legendre_frequencies(3)
+    for s in systems:
+        s.phi_dev = pkg.to_fortran(s.phi)
+    for prec in (0, 1):
+        for s in systems:  # the first orbitals again (the previous precision's replay replaced them)
+            s.phi_dev.copy_(pkg.to_fortran(s.phi))
+        batch = pkg.IsdfBatch(systems, prec=prec, n_workers=2)
+        batch.capture(omegas)
+        for rep in range(2):
+            phis = []
+            for i, s in enumerate(systems):
+                if rep == 0:
+                    phis.append(s.phi)
+                else:  # other orbitals, same shape, same points and energies
+                    n, v, c, m, sd = shapes[i]
+                    phi2 = small_system(n, v, c, n_mu=m, seed_index=sd + 50).phi
+                    s.phi_dev.copy_(pkg.to_fortran(phi2))
+                    phis.append(phi2)
+            torch.cuda.synchronize()
+            lat, tot = batch.replay()
+            assert np.all(lat > 0) and tot > 0
+            for i, s in enumerate(systems):
+                ctx, rank = batch.context(i)
+                x = synth.probe_block(s.n_r, 3)
+                X = pkg.to_fortran(x)
+                Y = pkg.fortran_empty(s.n_r, 3, X.device)
+                for k, w in enumerate(omegas):
+                    pkg.apply_eps_inv(ctx, k, X, Y, s.n_r)
+                    ref = O.isdf_smw_solve(phis[i], s.energies, s.n_v, s.mu_idx, s.n, s.cell, x, omega=float(w))
+                    assert rel_fro(Y.cpu().numpy(), ref.y) < TOL[prec], (prec, rep, i, k)
+        batch.close()
+
+
+def test_batch_graph_needs_full_rank():
+    """A system whose fit needs pivoting (N_mu above the pair count) cannot
+    be captured: ISDF_ERR_STATE, and the eager run still works."""
+    import paper_2403_12340_gb300 as pkg
+
+    systems = [small_system(16, 4, 12, n_mu=32, seed_index=91), small_system(12, 2, 4, n_mu=12, seed_index=92)]
+    for s in systems:
+        s.phi_dev = pkg.to_fortran(s.phi)
+    batch = pkg.IsdfBatch(systems, prec=0, n_workers=1)
+    with pytest.raises(pkg.IsdfError) as ei:
+        batch.capture([0.0])
+    assert ei.value.code == -9
+    with pytest.raises(pkg.IsdfError) as ei:
+        batch.replay()
+    assert ei.value.code == -9
+    batch.run([0.0])
+    batch.close()
