@@ -43,14 +43,16 @@ __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, d
 // 64 cycles however many of its lanes are active, and one warp's independent
 // FP64 instructions do not overlap; the four sub-partitions together finish
 // about one warp instruction per 19 cycles.  So the 64 dependent pivots are
-// one warp's chain, run alone on its sub-partition, while the three other
-// warps (one per remaining sub-partition) apply the updates one column
-// behind.  The chain carries no square root (LDL^T form):
+// one warp's chain, run alone on its sub-partition, while twelve warps on
+// the other three sub-partitions apply the updates one column behind, each
+// thread to a fixed set of lower-triangle elements (no index arithmetic in
+// the loop; enough warps to hide the shared-memory latency).  The chain
+// carries no square root (LDL^T form):
 //   iteration j, warp 0:   a_j <- a_j - l_{j-1} a_{j,j-1}   (last update of column j)
 //                          r_j = 1 / d_j, d_j = a_jj        (FP32 estimate, two
 //                                                           Newton steps r (2 - d r))
 //                          l_j = a_j r_j                   (below the diagonal)
-//   iteration j, warps 1-3: a_k <- a_k - l_{j-1} a_{k,j-1}  for the columns k > j
+//   iteration j, the others: a_k <- a_k - l_{j-1} a_{k,j-1}  for the columns k > j
 //   one block barrier per iteration.
 // l_j is double buffered, so the chain writes l_j while the others read
 // l_{j-1}.  At the end L = A D^-1/2 below the diagonal and D^1/2 on it.
@@ -61,7 +63,9 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y * fma(-0.5 * d * y, y, 1.5);
 }
 
-constexpr int DIAG_THREADS = 128;
+constexpr int DIAG_THREADS = 512;
+constexpr int DIAG_BULK = DIAG_THREADS / 4 * 3;                       // threads of the warps off sub-partition 0
+constexpr int DIAG_EPT = (CB * (CB + 1) / 2 + DIAG_BULK - 1) / DIAG_BULK;  // lower-triangle elements per thread
 
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long lda, int j0, int bs,
                                                            const double* dmax, double tol_rel, int* fail,
@@ -80,6 +84,23 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
     int i = idx & (CB - 1), k = idx >> 6;
     Ls[i][k] = (i < bs && k <= i) ? A[(j0 + i) + lda * (long long)(j0 + k)] : 0.0;
+  }
+  // the warps on sub-partitions 1-3 own fixed lower-triangle elements (row * 64 + column)
+  const bool bulk = (warp & 3) != 0;
+  int own[DIAG_EPT];
+  {
+    const int b = (warp - 1 - (warp >> 2)) * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < DIAG_EPT; ++q) {
+      const int e = b + DIAG_BULK * q;
+      own[q] = -1;
+      if (bulk && e < CB * (CB + 1) / 2) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        while (a * (a + 1) / 2 > e) --a;
+        own[q] = a * CB + (e - a * (a + 1) / 2);
+      }
+    }
   }
   if (t == 0) s_bad = -1;
   const double thresh = tol_rel * (*dmax);
@@ -101,15 +122,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
         double* lj = lc[j & 1];
         for (int i = j + 1 + lane; i < bs; i += 32) lj[i] = Ls[i][j] * r;
       }
-    } else if (j > 0) {
-      const int m = bs - j - 1;  // columns and rows j+1 .. bs-1
-      const int cnt = m * (m + 1) / 2;
-      for (int idx = t - 32; idx < cnt; idx += DIAG_THREADS - 32) {
-        int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-        while (a * (a + 1) / 2 > idx) --a;
-        const int i = j + 1 + a, k = j + 1 + idx - a * (a + 1) / 2;
-        Ls[i][k] = fma(-lp[i], Ls[k][j - 1], Ls[i][k]);
+    } else if (bulk && j > 0) {
+      // column j-1 applied to the owned elements of the columns k > j
+#pragma unroll
+      for (int q = 0; q < DIAG_EPT; ++q) {
+        const int o = own[q];
+        const int i = o >> 6, k = o & (CB - 1);
+        if (o >= 0 && k > j && i < bs) Ls[i][k] = fma(-lp[i], Ls[k][j - 1], Ls[i][k]);
       }
     }
     __syncthreads();
@@ -193,10 +212,10 @@ __global__ void k_copy_block(const double* __restrict__ src, long long lds, long
 // loop, 16 per pair of 4-element reads.  The strict upper triangle of a
 // diagonal tile is left alone (only the lower triangle is ever read).
 // Problem blockIdx.y of a batch at L + y sL.
-template <int TS>
-__global__ void __launch_bounds__((TS / 4) * (TS / 4)) k_trail_update(double* L, long long ldl, int j0, int bs,
-                                                                     int rem, const int* fail, long long sL) {
-  constexpr int Q = TS / 4, NT = Q * Q, KC = 32;
+template <int TS, int TM>
+__global__ void __launch_bounds__((TS / TM) * (TS / TM)) k_trail_update(double* L, long long ldl, int j0, int bs,
+                                                                       int rem, const int* fail, long long sL) {
+  constexpr int Q = TS / TM, NT = Q * Q, KC = 32;
   __shared__ double As[KC][TS], Bs[KC][TS];
   L += sL * blockIdx.y;
   if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
@@ -209,11 +228,11 @@ __global__ void __launch_bounds__((TS / 4) * (TS / 4)) k_trail_update(double* L,
   const int t = threadIdx.x, tx = t % Q, ty = t / Q;
   const long long r0 = j0 + bs;
   const double* P = L + r0 + ldl * (long long)j0;  // P(i, c) at P[i + ldl c]
-  double acc[4][4];
+  double acc[TM][TM];
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < TM; ++m)
 #pragma unroll
-    for (int n = 0; n < 4; ++n) acc[m][n] = 0.0;
+    for (int n = 0; n < TM; ++n) acc[m][n] = 0.0;
   for (int c0 = 0; c0 < bs; c0 += KC) {
     const int kc = min(KC, bs - c0);
     for (int idx = t; idx < KC * TS; idx += NT) {
@@ -225,32 +244,33 @@ __global__ void __launch_bounds__((TS / 4) * (TS / 4)) k_trail_update(double* L,
     __syncthreads();
 #pragma unroll 4
     for (int c = 0; c < KC; ++c) {
-      double a[4], b[4];
+      double a[TM], b[TM];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
+      for (int m = 0; m < TM; ++m) {
         a[m] = As[c][tx + Q * m];
         b[m] = Bs[c][ty + Q * m];
       }
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
+      for (int m = 0; m < TM; ++m)
 #pragma unroll
-        for (int n = 0; n < 4; ++n) acc[m][n] = fma(a[m], b[n], acc[m][n]);
+        for (int n = 0; n < TM; ++n) acc[m][n] = fma(a[m], b[n], acc[m][n]);
     }
     __syncthreads();
   }
   double* C = L + r0 + ldl * r0;
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < TM; ++m)
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
+    for (int n = 0; n < TM; ++n) {
       const int i = i0 + tx + Q * m, k = k0 + ty + Q * n;
       if (i < rem && k < rem && (ti != tj || i >= k)) C[i + ldl * (long long)k] -= acc[m][n];
     }
 }
 
-// Tile width of a trailing update: 64 while there are at least three waves
-// of 64-wide tiles, else 32 (four times the tiles, so that the late, small
-// updates still spread over the SMs).
+// Tile width of a trailing update: 64 (4 x 4 per thread) while the 64-wide
+// tiles fill the SMs, else 32 (2 x 2 per thread, still 256 threads): the
+// late, small updates then use four times the SMs, each tile a quarter of
+// the work with the same number of warps.
 static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int rem, int batch, const int* fail,
                                 long long sL, cudaStream_t s) {
   auto tiles = [](int m, int ts) {
@@ -266,10 +286,10 @@ static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int re
   }
   KernelTimer kt(KF_FP64_GEMM, s, (double)rem * (rem + 1) * bs * batch);  // lower triangle, 2 flops per term
   note_launch();
-  if (tiles(rem, 64) * batch >= 3LL * sms) {
-    k_trail_update<64><<<dim3((unsigned)tiles(rem, 64), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
+  if (tiles(rem, 64) * batch >= sms) {
+    k_trail_update<64, 4><<<dim3((unsigned)tiles(rem, 64), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
   } else {
-    k_trail_update<32><<<dim3((unsigned)tiles(rem, 32), batch), 64, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
+    k_trail_update<32, 2><<<dim3((unsigned)tiles(rem, 32), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
   }
   return cudaGetLastError();
 }
