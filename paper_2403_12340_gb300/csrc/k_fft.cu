@@ -483,6 +483,95 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_slices_ct(FftGrid g, cons
   }
 }
 
+// ---- z pass in registers --------------------------------------------------
+// Frequency held by position p of an in-place decimation-in-frequency
+// transform of length n whose stages take the radices first_radix(n),
+// first_radix(n / R1), ...: p = m (n / R1) + p' holds the frequency
+// m + R1 freq(p') of the length n / R1 transform of sub-array m.
+__host__ __device__ constexpr int dif_freq(int p, int n) {
+  int f = 0, mult = 1;
+  while (n > 1) {
+    const int R = first_radix(n), sub = n / R;
+    f += (p / sub) * mult;
+    mult *= R;
+    p %= sub;
+    n = sub;
+  }
+  return f;
+}
+
+// In-place decimation-in-frequency stages on a register array: blocks of
+// length L, radix R = first_radix(L), M = L / R; each R-point DFT over the
+// stride-M elements of a block is followed by the twiddles W_L^(j m).
+template <int N, int L, int DIR, class C>
+__device__ __forceinline__ void dif_stages(C (&v)[N], const C* tw) {
+  if constexpr (L > 1) {
+    constexpr int R = first_radix(L), M = L / R;
+#pragma unroll
+    for (int b = 0; b < N / L; ++b) {
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        C x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = v[b * L + j + m * M];
+        bfly<R, DIR>(x, tw, N);
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[b * L + j + m * M] = (j * m == 0) ? x[m] : cmul(x[m], twid<DIR>(tw, (j * m * (N / L)) % N));
+      }
+    }
+    dif_stages<N, M, DIR>(v, tw);
+  }
+}
+
+// The z pass of the FP32 forward transform with the BF16 slices of the
+// weighted spectrum out (the same output as k_fft_z_slices_ct): one thread
+// per z line, the whole line in registers, so there is no shared-memory
+// traffic and no block barrier between the radix stages; a warp's loads and
+// stores of one z row are contiguous.
+constexpr int FFT_ZREG_THREADS = 128;
+template <int N>
+__global__ void __launch_bounds__(FFT_ZREG_THREADS) k_fft_z_slices_reg(FftGrid g, const float* S, long long lds,
+                                                                      const double* __restrict__ wt,
+                                                                      __nv_bfloat16* out, int rows_pad, int kp,
+                                                                      int nsl) {
+  using C = float2;
+  constexpr int H = N / 2 + 1, PLANE = N * H;
+  __shared__ C twz[N];
+  for (int t = threadIdx.x; t < N; t += blockDim.x) twz[t] = from_tw<C>(((const double2*)g.ax[2].tw)[t]);
+  __syncthreads();
+  const int col = blockIdx.y;
+  const int q = blockIdx.x * FFT_ZREG_THREADS + threadIdx.x;  // line of the x-y half plane
+  if (q >= PLANE) return;
+  const C* base = (const C*)(S + lds * (long long)col);
+  C v[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) v[z] = base[(long long)z * PLANE + q];
+  dif_stages<N, N, -1>(v, twz);
+  const long long sstr = (long long)rows_pad * kp;
+  __nv_bfloat16* o0 = out + (long long)col * kp;
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const long long qq = (long long)dif_freq(p, N) * PLANE + q;
+    const float w = to_real<float>(wt[qq]);
+    const float vv[2] = {v[p].x * w, v[p].y * w};
+    __nv_bfloat162 x0, x1, x2;
+    __nv_bfloat16* p0 = reinterpret_cast<__nv_bfloat16*>(&x0);
+    __nv_bfloat16* p1 = reinterpret_cast<__nv_bfloat16*>(&x1);
+    __nv_bfloat16* p2 = reinterpret_cast<__nv_bfloat16*>(&x2);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      p0[h] = __float2bfloat16_rn(vv[h]);
+      const float r1 = vv[h] - __bfloat162float(p0[h]);
+      p1[h] = __float2bfloat16_rn(r1);
+      p2[h] = __float2bfloat16_rn(r1 - __bfloat162float(p1[h]));
+    }
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(o0 + 2 * qq);
+    o[0] = x0;
+    if (nsl > 1) o[sstr / 2] = x1;
+    if (nsl > 2) o[sstr] = x2;
+  }
+}
+
 template <int N>
 static cudaError_t fft_slices_ct(const FftGrid& g, const double* X, long long ldx, int ncols, float* S32, long long lds32,
                                  const double* wt, __nv_bfloat16* out, int rows_pad, int kp, int nsl, cudaStream_t s) {
@@ -494,9 +583,14 @@ static cudaError_t fft_slices_ct(const FftGrid& g, const double* X, long long ld
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   constexpr int PLANE = N * (N / 2 + 1);
-  dim3 gz((PLANE + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
   note_launch();
-  k_fft_z_slices_ct<N><<<gz, FFT_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
+  if constexpr (N <= 64) {
+    dim3 gz((PLANE + FFT_ZREG_THREADS - 1) / FFT_ZREG_THREADS, ncols);
+    k_fft_z_slices_reg<N><<<gz, FFT_ZREG_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
+  } else {
+    dim3 gz((PLANE + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
+    k_fft_z_slices_ct<N><<<gz, FFT_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
+  }
   return cudaGetLastError();
 }
 
