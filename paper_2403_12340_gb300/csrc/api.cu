@@ -28,6 +28,10 @@ static thread_local std::string g_create_err;
 // about 14 or more) the mixed path whitens D in pair space.
 static constexpr double kPairWhitenMean = 4.0;
 
+// SMs that the tensor-core GEMMs leave to the FP64 factorisations running
+// beside them on the second stream (fit and polarizability).
+static constexpr int kFp64Sms = 12;
+
 using PhaseScope = isdf::PhaseTimer;
 
 static int fail(isdf_ctx* c, int code, const std::string& msg) {
@@ -376,6 +380,7 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   // the given order, which is the pivot order whenever the blocked
   // factorisation succeeds
   if (prec == ISDF_PREC_MIXED) {
+    isdf::TcSmReserve keep(kFp64Sms);  // the Cholesky on the second stream keeps some SMs
     CK(isdf::mixed_fit_gram(c, phi, c->phimu.p, n_v, n_c, n_mu));
   } else {
     PhaseScope ph(c, ISDF_PH_FIT_GRAM);
@@ -647,6 +652,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     }
     // G = theta^T V theta (main stream)
     if (c->prec == ISDF_PREC_MIXED) {
+      isdf::TcSmReserve keep(kFp64Sms);  // the factorisations of D(w) on the second stream keep some SMs
       CK(isdf::mixed_polar_G(c));
     } else {
       {

@@ -561,7 +561,8 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   }
   // one block per SM (the stage ring takes most of the shared memory), each looping over units
-  dim3 grid((unsigned)std::min<long long>(units, sms));
+  const int avail = std::max(1, sms - std::max(0, tl_tc_sm_reserve));
+  dim3 grid((unsigned)std::min<long long>(units, avail));
   KernelTimer kt(KF_TC_GEMM, st, mma_flops);
   note_launch();
   k_tc_gemm<BN, NACC, EPI><<<grid, TC_THREADS, smem, st>>>(ma, mb, a);
@@ -578,6 +579,8 @@ static void split_k(int k_iters, int tiles, int num_sms, int max_split, int& spl
   per = (k_iters + want - 1) / want;
   splits = (k_iters + per - 1) / per;
 }
+
+thread_local int tl_tc_sm_reserve = 0;
 
 // ------------------------------------------------------------ tile autotuner
 //

@@ -20,6 +20,16 @@ long long launch_count();
 // only looks up its table.
 extern thread_local bool tl_capture;
 
+// SMs that a persistent tensor-core GEMM launched from this thread leaves
+// free (0: none), so that latency-bound FP64 kernels queued on another
+// stream keep running beside it (k_tc_gemm.cu; TcSmReserve sets it).
+extern thread_local int tl_tc_sm_reserve;
+struct TcSmReserve {
+  int prev;
+  explicit TcSmReserve(int n) : prev(tl_tc_sm_reserve) { tl_tc_sm_reserve = n; }
+  ~TcSmReserve() { tl_tc_sm_reserve = prev; }
+};
+
 // Per-launch timing by kernel family.  While an API call on a context with
 // profiling on is inside one of its phases, a KernelTimer records CUDA
 // events around the launch on the launch's own stream, tagged with the
