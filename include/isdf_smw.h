@@ -312,8 +312,10 @@ ISDF_API int isdf_batch_run(isdf_batch* batch, const double* omega, int n_omega,
  * batch eagerly at the frequencies omega (host, n_omega), which sizes every
  * workspace and fixes each system's rank, then captures the device work of
  * all systems (fit, polarizability at every frequency, SMW) into one graph:
- * the systems are parallel branches off one origin stream, each system's
- * two streams forked and joined inside its branch.  Every fit must have been
+ * the systems run in as many parallel lanes as the batch has workers
+ * (largest first, each onto the lane with the least estimated work so
+ * far, like the host threads of isdf_batch_run), each system's two streams
+ * forked and joined inside its branch.  Every fit must have been
  * unpivoted at full rank (else ISDF_ERR_STATE: a pivoted fit decides on the
  * host).  isdf_batch_replay launches that graph once (one cudaGraphLaunch,
  * no host work between the systems), synchronises, then checks each

@@ -47,7 +47,8 @@ struct isdf_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev_start = nullptr, ev_link = nullptr;
-  std::vector<cudaEvent_t> ev_end;  // one per system, recorded at the end of its branch
+  std::vector<cudaEvent_t> ev_end;   // one per system, recorded at the end of its branch
+  std::vector<cudaEvent_t> ev_lane;  // the end of the last system of each lane
   std::vector<double> g_omega;
 };
 
@@ -68,6 +69,7 @@ void free_batch(isdf_batch* b) {
   if (b->ev_start) cudaEventDestroy(b->ev_start);
   if (b->ev_link) cudaEventDestroy(b->ev_link);
   for (cudaEvent_t e : b->ev_end) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->ev_lane) cudaEventDestroy(e);
   if (b->origin) cudaStreamDestroy(b->origin);
   for (auto& s : b->sys) {
     if (s.ctx) isdf_destroy(s.ctx);
@@ -242,11 +244,19 @@ int capture_systems(isdf_batch* b, const double* omega, int n_omega) {
   cudaError_t e = cudaEventRecordWithFlags(b->ev_start, b->origin, cudaEventRecordExternal);
   if (e != cudaSuccess) return cuda_err(e, "start event");
   if ((e = cudaEventRecord(b->ev_link, b->origin)) != cudaSuccess) return cuda_err(e, "fork event");
-  for (auto& s : b->sys)
-    if ((e = cudaStreamWaitEvent(s.stream, b->ev_link, 0)) != cudaSuccess) return cuda_err(e, "fork");
+  // lanes: as many systems in flight as the batch has workers; each system,
+  // largest first, follows the lane with the least estimated work so far
+  const int nl = (int)b->ev_lane.size();
+  std::vector<double> load(nl, 0.0);
+  std::vector<char> used(nl, 0);
   for (int j = 0; j < (int)b->order.size(); ++j) {
     const int i = b->order[j];
     auto& s = b->sys[i];
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    e = cudaStreamWaitEvent(s.stream, used[l] ? b->ev_lane[l] : b->ev_link, 0);
+    if (e != cudaSuccess) return cuda_err(e, "fork");
+    load[l] += s.cost;
+    used[l] = 1;
     int rank = 0;
     int rc = isdf_fit(s.ctx, s.d.phi, s.d.n_v, s.d.n_c, s.d.mu_idx, s.d.n_mu, b->prec, s.theta, &rank);
     if (rc == ISDF_OK) rc = build_polarizability(s.ctx, s.d.energies, omega, n_omega, nullptr, nullptr);
@@ -257,9 +267,10 @@ int capture_systems(isdf_batch* b, const double* omega, int n_omega) {
     }
     if ((e = cudaEventRecordWithFlags(b->ev_end[i], s.stream, cudaEventRecordExternal)) != cudaSuccess)
       return cuda_err(e, "end event");
-    if ((e = cudaEventRecord(b->ev_link, s.stream)) != cudaSuccess) return cuda_err(e, "join event");
-    if ((e = cudaStreamWaitEvent(b->origin, b->ev_link, 0)) != cudaSuccess) return cuda_err(e, "join");
+    if ((e = cudaEventRecord(b->ev_lane[l], s.stream)) != cudaSuccess) return cuda_err(e, "lane event");
   }
+  for (int l = 0; l < nl; ++l)
+    if (used[l] && (e = cudaStreamWaitEvent(b->origin, b->ev_lane[l], 0)) != cudaSuccess) return cuda_err(e, "join");
   return ISDF_OK;
 }
 
@@ -298,6 +309,12 @@ extern "C" int isdf_batch_capture(isdf_batch* b, const double* omega, int n_omeg
     cudaEvent_t x = nullptr;
     e = cudaEventCreate(&x);
     if (e == cudaSuccess) b->ev_end.push_back(x);
+  }
+  const size_t lanes = (size_t)std::max(1, std::min(b->n_workers, (int)b->sys.size()));
+  while (e == cudaSuccess && b->ev_lane.size() < lanes) {
+    cudaEvent_t x = nullptr;
+    e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev_lane.push_back(x);
   }
   if (e != cudaSuccess) {
     b->err = std::string("isdf_batch_capture: ") + cudaGetErrorString(e);
