@@ -214,8 +214,10 @@ extern "C" int isdf_create(isdf_ctx** out, int n1, int n2, int n3, double L1, do
     int lo = 0, hi = 0;
     e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s3, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(e, "stream / event creation");
   }
   c->d_bar = c->d_status + 8;
@@ -233,8 +235,14 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
     cudaStreamSynchronize(c->s2);
     cudaStreamDestroy(c->s2);
   }
+  if (c->s3) {
+    cudaStreamSynchronize(c->s3);
+    cudaStreamDestroy(c->s3);
+  }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_join3) cudaEventDestroy(c->ev_join3);
+  for (cudaEvent_t e : c->ev_chol) cudaEventDestroy(e);
   if (c->d_fail) cudaFree(c->d_fail);
   if (c->b_fail) cudaFree(c->b_fail);
   DevBuf* bufs[] = {&c->phimu, &c->phimu_p, &c->A, &c->Lr, &c->Lc, &c->Bf, &c->chol_d, &c->chol_part,
@@ -244,7 +252,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->kappa_work};
+                    &c->m_pairs_t, &c->swf, &c->kappa_work, &c->inv_work};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
@@ -312,6 +320,21 @@ static int join_s2(isdf_ctx* c) {
   return ISDF_OK;
 }
 
+// Workspace of launch_cholesky_and_inverse for an n x n factor: its step
+// events and the Y / split-K buffer (sized before any fork: a resize frees).
+static int chol_inverse_workspace(isdf_ctx* c, int n) {
+  const size_t steps = (size_t)(n + 63) / 64;
+  while (c->ev_chol.size() < steps) {
+    if (isdf::tl_capture) return fail(c, ISDF_ERR_STATE, "factorisation events: a captured call needs an eager call first");
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->ev_chol.push_back(e);
+  }
+  if (c->inv_work.cap < (size_t)9 * 64 * n) SYNC(c->stream);
+  CK(ensure(c->inv_work, (size_t)9 * 64 * n));
+  return ISDF_OK;
+}
+
 extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const int64_t* mu_idx,
                         int n_mu, int prec, double* theta, int* rank_out) {
   if (!c) return ISDF_ERR_ARG;
@@ -369,12 +392,26 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   // Cholesky of C C^T in the given point order (blocked, on the second
   // stream: it is a latency-bound FP64 chain); if a pivot falls to the rank
   // threshold it is redone below with diagonal pivoting (rank-deficient C)
+  // mixed path: L^-1 (for the whitened basis) is built on a third stream
+  // beside the factorisation, block row by block row
+  const bool fuse_inv = prec == ISDF_PREC_MIXED;
+  if (fuse_inv) {
+    rc0 = chol_inverse_workspace(c, n_mu);
+    if (rc0 != ISDF_OK) return rc0;
+    CK(ensure(c->m_linv, (size_t)n_mu * n_mu));
+  }
   rc0 = fork_s2(c);
   if (rc0 != ISDF_OK) return rc0;
+  if (fuse_inv) CK(cudaStreamWaitEvent(c->s3, c->ev_fork, 0));
   {
     PhaseScope ph(c, ISDF_PH_POINTS, c->s2);
-    rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1, c->s2);
-    if (rc0 != ISDF_OK) return rc0;
+    if (fuse_inv) {
+      CK(launch_cholesky_and_inverse(c->A.p, n_mu, n_mu, tol, c->Lc.p, n_mu, c->m_linv.p, n_mu, c->cb_work.p,
+                                     c->d_ints + 1, c->inv_work.p, c->s2, c->s3, c->ev_chol.data()));
+    } else {
+      rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1, c->s2);
+      if (rc0 != ISDF_OK) return rc0;
+    }
   }
   // meanwhile, speculatively, the face-split Gram M C^T with the points in
   // the given order, which is the pivot order whenever the blocked
@@ -389,6 +426,10 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   }
   rc0 = join_s2(c);
   if (rc0 != ISDF_OK) return rc0;
+  if (fuse_inv) {
+    CK(cudaEventRecord(c->ev_join3, c->s3));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join3, 0));
+  }
   int rc;
   int fail = -1, rank = 0;
   if (!isdf::tl_capture) {  // captured: the flags are read after the replay (graph_check)
@@ -436,7 +477,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
     if (prec == ISDF_PREC_MIXED) {
       if (!gram_done) CK(isdf::mixed_fit_gram(c, phi, c->phimu_p.p, n_v, n_c, r));
-      CK(isdf::mixed_fit_solve(c, theta, r));
+      // the inverse built beside the factorisation holds for the unpivoted full-rank factor
+      CK(isdf::mixed_fit_solve(c, theta, r, fuse_inv && gram_done));
       // ||L||_F^2 = tr(C C^T) and ||L^-1||_F^2 = tr((C C^T)^-1), read by build_polarizability
       CK(ensure(c->kappa_work, 2 + 256));
       CK(launch_sumsq(c->Lc.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p, c->stream));
@@ -738,11 +780,18 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
     CK(launch_symmetrize(c->T.p, r, r, c->stream));
   }
   // T = U U^T; Q = R U^-T; K = -Q Q^T
-  int rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, failT, c->stream);
-  if (rc != ISDF_OK) return rc;
   if (c->prec == ISDF_PREC_MIXED) {
-    CK(isdf::mixed_smw_products_K(c, Kk));
+    // U^-1 into Q on the second stream, block row by block row, beside the factorisation
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+    CK(launch_cholesky_and_inverse(c->T.p, r, r, 0.0, c->W1.p, r, c->Q.p, r, c->cb_work.p, failT, c->inv_work.p,
+                                   c->stream, c->s2, c->ev_chol.data()));
+    CK(cudaEventRecord(c->ev_join, c->s2));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    CK(isdf::mixed_smw_products_K(c, Kk, true));
   } else {
+    int rc = cholesky_blocked(c, c->T.p, r, r, 0.0, c->W1.p, failT, c->stream);
+    if (rc != ISDF_OK) return rc;
     CK(launch_trsm_prep(c->W1.p, r, r, c->Bf.p + 0, r, c->stream));
     CK(cudaMemcpyAsync(c->Q.p, c->R.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CK(launch_trsm_right_lt(c->Q.p, r, r, c->Bf.p, r, r, c->stream));
@@ -767,6 +816,7 @@ static int smw_workspace(isdf_ctx* c) {
   CK(ensure(c->W1, rr));
   CK(ensure(c->Q, rr));
   CK(ensure(c->partial, (size_t)sp * rr));
+  if (c->prec == ISDF_PREC_MIXED) return chol_inverse_workspace(c, r);
   return ISDF_OK;
 }
 

@@ -70,6 +70,12 @@ struct isdf_ctx {
   // tensor-core / FFT work of the main stream; fork / join by events
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // a third stream that builds a triangular inverse block row by block row
+  // beside the factorisation producing it (launch_cholesky_and_inverse)
+  cudaStream_t s3 = nullptr;
+  cudaEvent_t ev_join3 = nullptr;
+  std::vector<cudaEvent_t> ev_chol;  // one per 64-wide factorisation step
+  DevBuf inv_work;
   DevBuf Rw;             // Cholesky factors of D(w), one r x r block per frequency
   int* d_fail = nullptr; // their failure flags
   size_t cap_fail = 0;
@@ -175,13 +181,13 @@ struct PhaseTimer {
 
 // mixed.cu
 cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p, int n_v, int n_c, int r);
-cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r);
+cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r, bool linv_ready);
 cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega);
 cudaError_t mixed_whiten_D(isdf_ctx* c, const double* Dpp, double* Dk);
 cudaError_t mixed_polar_D_pairspace(isdf_ctx* c, const float* swf, int n_omega);
 cudaError_t mixed_polar_G(isdf_ctx* c);
 cudaError_t mixed_smw_products_T(isdf_ctx* c);
-cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk);
+cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk, bool uinv_ready);
 cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc);
 // All frequencies at once: D(w_k) for k < n_omega (chunked to a memory
 // budget), and K(w_k) from the factors R(w_k) in c->Rw (T factors and

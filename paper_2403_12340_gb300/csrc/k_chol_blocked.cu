@@ -9,6 +9,8 @@
 // first failing column goes to *fail and every later kernel of the sequence
 // does nothing.  The caller decides what that means (not positive definite,
 // or: fall back to the pivoted factorisation for a rank-deficient C C^T).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -328,6 +330,63 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles)
+    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g((n + 127) / 128, n);
+  note_launch();
+  k_zero_upper<<<g, 128, 0, s>>>(L, ldl, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, double tol_rel, double* L,
+                                        long long ldl, double* Li, long long ldi, double* dmax, int* fail,
+                                        double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, n * sizeof(double), n, aux);
+  if (e != cudaSuccess) return e;
+  if (L != W) {
+    e = cudaMemcpy2DAsync(L, ldl * sizeof(double), W, ldw * sizeof(double), n * sizeof(double), n,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  note_launch();
+  k_diag_max<<<1, 256, 0, s>>>(L, ldl, n, dmax, fail);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  double* Y = work;               // 64 x n: L[J, 0:J] Li[0:J, 0:J]
+  double* part = work + 64ll * n;  // split-K partials of Y, 8 x 64 x n
+  for (int j0 = 0, jb = 0; j0 < n; j0 += CB, ++jb) {
+    const int bs = min(CB, n - j0);
+    {
+      KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0);
+      note_launch();
+      k_chol_diag<<<1, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // row block jb of the inverse, beside the rest of the factorisation
+    if ((e = cudaEventRecord(ev[jb], s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(aux, ev[jb], 0)) != cudaSuccess) return e;
+    double* Ljj = L + j0 + ldl * (long long)j0;
+    double* Lijj = Li + j0 + ldi * (long long)j0;
+    if ((e = launch_diag_inverse_block(Ljj, ldl, bs, Lijj, ldi, aux)) != cudaSuccess) return e;
+    if (j0 > 0) {
+      const long long tiles = (long long)((bs + 63) / 64) * ((j0 + 63) / 64);
+      const int sp = (int)std::max(1LL, std::min<long long>(8, (2 * 152 + tiles - 1) / tiles));
+      e = launch_gemm(L + j0, ldl, false, Li, ldi, true, bs, j0, j0, 1.0, 0.0, Y, bs, false, sp, part, false, aux,
+                      TRI_B_LOWER_T);
+      if (e != cudaSuccess) return e;
+      e = launch_gemm(Lijj, ldi, false, Y, bs, true, bs, j0, bs, -1.0, 0.0, Li + j0, ldi, false, 1, nullptr, false, aux,
+                      TRI_A_LOWER);
+      if (e != cudaSuccess) return e;
+    }
+    const int rem = n - j0 - bs;
+    if (rem <= 0) break;
+    {
+      KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs);
+      note_launch();
+      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s);
     if (e != cudaSuccess) return e;
   }

@@ -611,6 +611,15 @@ __global__ void __launch_bounds__(256) k_trsm_offdiag(const double* __restrict__
   }
 }
 
+cudaError_t launch_diag_inverse_block(const double* L, long long ldl, int bs, double* Li, long long ldi,
+                                      cudaStream_t s) {
+  if (bs <= 0) return cudaSuccess;
+  if (bs > TRSM_NB) return cudaErrorInvalidValue;
+  note_launch();
+  k_diag_inverse<<<1, DINV_THREADS, 0, s>>>(L, ldl, bs, Li, ldi);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trsm_prep(const double* L, long long ldl, int r, double* Bf, long long ldb,
                              cudaStream_t s) {
   if (r <= 0) return cudaSuccess;

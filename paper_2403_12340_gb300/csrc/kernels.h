@@ -148,6 +148,21 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
                                     double* dmax, int* fail, cudaStream_t s);
 // The same for `batch` equal-size matrices W + z sW -> L + z sL; dmax and
 // fail: batch entries.
+// The inverse of one lower-triangular block of at most 64 x 64 (L, ld ldl)
+// into Li (ld ldi; strict upper part zeroed): one thread block.
+cudaError_t launch_diag_inverse_block(const double* L, long long ldl, int bs, double* Li, long long ldi,
+                                      cudaStream_t s);
+// launch_cholesky_blocked on stream s, and the inverse Li = L^-1 built
+// block row by block row on stream aux while the factorisation proceeds:
+// once the diagonal block J is factored, row block J of Li is
+//   Li[J, J] = L_JJ^-1,  Li[J, 0:J] = -L_JJ^-1 (L[J, 0:J] Li[0:J, 0:J]),
+// which needs only rows of L that earlier steps finished.  The caller orders
+// aux after everything Li and work depend on, and joins aux before Li is
+// used.  ev: at least ceil(n / 64) events; work: 64 n + 8 * 64 n doubles.
+// If the factorisation stops (fail >= 0), Li is undefined.
+cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, double tol_rel, double* L,
+                                        long long ldl, double* Li, long long ldi, double* dmax, int* fail,
+                                        double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev);
 cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
                                             double tol_rel, double* L, long long ldl, long long sL, double* dmax,
                                             int* fail, cudaStream_t s);

@@ -100,8 +100,9 @@ cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p
 }
 
 // theta (N_r x r, ld N_r) = (M C_r^T) L^-T from c->m_zs and the Cholesky
-// factor c->Lc (r x r, ld r).
-cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r) {
+// factor c->Lc (r x r, ld r); linv_ready: c->m_linv already holds L^-1
+// (built beside the factorisation).
+cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r, bool linv_ready) {
   cudaStream_t st = c->stream;
   const long long nr = c->n_r;
   const int nrp = pad(nr, 128), rp = pad(r, 128), rk = pad(r, 64);
@@ -109,7 +110,7 @@ cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r) {
   MK(ensure(c->m_linv, (size_t)r * r));
   const size_t wq = (size_t)(r / 2 + 64) * (r / 2 + 64);
   MK(ensure(c->m_work, 5 * wq));
-  MK(launch_tri_inverse(c->Lc.p, r, r, c->m_linv.p, r, c->m_work.p, c->m_work.p + wq, st));
+  if (!linv_ready) MK(launch_tri_inverse(c->Lc.p, r, r, c->m_linv.p, r, c->m_work.p, c->m_work.p + wq, st));
   MK(slices_cm(c->m_linvs, c->m_linv.p, r, r, r, rp, rk, st));
   MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, 1.0, 0.0, theta, nr, false, true,
                  nullptr, 1, c->num_sms, c->d_status, st));
@@ -344,8 +345,8 @@ cudaError_t mixed_smw_products_T(isdf_ctx* c) {
   return launch_symmetrize(c->T.p, r, r, st);
 }
 
-cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk) {
-  // U in c->W1: Q = R U^-T, K = -Q Q^T
+cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk, bool uinv_ready) {
+  // U in c->W1 (and U^-1 in c->Q when uinv_ready): Q = R U^-T, K = -Q Q^T
   cudaStream_t st = c->stream;
   const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
   const size_t rr = (size_t)r * r;
@@ -353,7 +354,7 @@ cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk) {
   const size_t wq = (size_t)(r / 2 + 64) * (r / 2 + 64);
   MK(ensure(c->m_work, 5 * wq));
   MK(ensure(c->partial, (size_t)max_split * rr));
-  MK(launch_tri_inverse(c->W1.p, r, r, c->Q.p, r, c->m_work.p, c->m_work.p + wq, st));  // Q <- U^-1
+  if (!uinv_ready) MK(launch_tri_inverse(c->W1.p, r, r, c->Q.p, r, c->m_work.p, c->m_work.p + wq, st));  // Q <- U^-1
   MK(slices_cm(c->m_sa, c->R.p, r, r, r, rp, rk, st));
   MK(slices_cm(c->m_sb, c->Q.p, r, r, r, rp, rk, st));
   MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sb, rp, rk), r, r, 1.0, 0.0, c->Q.p, r, false, true, nullptr, 1,
