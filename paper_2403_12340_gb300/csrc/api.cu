@@ -252,7 +252,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->kappa_work, &c->inv_work};
+                    &c->m_pairs_t, &c->swf, &c->kappa_work, &c->inv_work, &c->m_ths};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {

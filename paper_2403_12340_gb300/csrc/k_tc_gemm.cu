@@ -269,10 +269,12 @@ struct TcArgs {
   long long zs_bstride;        // elements between the output slices of consecutive problems
   const float* colscale;       // EPI_SCALE_SLICES: column n of problem b scaled by colscale[b cs_bstride + n]
   long long cs_bstride;
+  __nv_bfloat16* zt;           // EPI_F64_SLICES2: slices of C transposed, element (n, m) at zt[n zt_kp + m]
+  int zt_rows_pad, zt_kp;
   unsigned* status;
 };
 
-enum { EPI_F64 = 0, EPI_HAD_F64 = 1, EPI_HAD_SLICES = 2, EPI_SCALE_SLICES = 3 };
+enum { EPI_F64 = 0, EPI_HAD_F64 = 1, EPI_HAD_SLICES = 2, EPI_SCALE_SLICES = 3, EPI_F64_SLICES2 = 4 };
 
 // One work unit: a 128 x BN output tile of one problem over one K range.
 struct TcUnit {
@@ -448,6 +450,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int i = 0; i < 16; ++i) v1[i] = 0.f;
         }
         if (m >= a.M) continue;
+        if (EPI == EPI_F64_SLICES2) {
+          // C in FP64 (alpha 1, beta 0), and its BF16 slices twice: row-major
+          // (m, n) into zs and transposed (n, m) into zt
+          const long long sstr = (long long)a.zs_rows_pad * a.zs_kp, tstr = (long long)a.zt_rows_pad * a.zt_kp;
+          const bool whole = w.n0 + c + 16 <= a.N;
+          if (whole) {
+            __nv_bfloat16* dst = a.zs + (long long)m * a.zs_kp + w.n0 + c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float v[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[e] = v0[8 * h + e];
+              store_slices8(v, dst + 8 * h, sstr, a.s);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = w.n0 + c + i;
+            if (n >= a.N) break;
+            Cb[m + a.ldc * n] = tc::f2d(v0[i]);
+            __nv_bfloat16 x0, x1, x2;
+            split3f(v0[i], x0, x1, x2);
+            if (!whole) {
+              const long long base = (long long)m * a.zs_kp + n;
+              a.zs[base] = x0;
+              if (a.s > 1) a.zs[base + sstr] = x1;
+              if (a.s > 2) a.zs[base + 2 * sstr] = x2;
+            }
+            const long long tb = (long long)n * a.zt_kp + m;
+            a.zt[tb] = x0;
+            if (a.s > 1) a.zt[tb + tstr] = x1;
+            if (a.s > 2) a.zt[tb + 2 * tstr] = x2;
+          }
+          continue;
+        }
         const float* cs = (EPI == EPI_SCALE_SLICES) ? a.colscale + a.cs_bstride * w.bidx : nullptr;
         if ((EPI == EPI_HAD_SLICES || EPI == EPI_SCALE_SLICES) && w.n0 + c + 16 <= a.N) {
           // whole 16-column chunk: two 16-byte stores per slice
@@ -774,6 +811,37 @@ cudaError_t tc_scaled_slices(const TcOperand& A, const TcOperand& B, int M, int 
   a.cs_bstride = cs_bstride;
   const double mma = 2.0 * 0.5 * a.s * (a.s + 1) * (double)M * N * (double)A.kp * bt.count;
   return tc_launch<128, 1, EPI_SCALE_SLICES>(A, B, a, 1, bt.count, mma, st);
+}
+
+cudaError_t tc_gemm_f64_slices(const TcOperand& A, const TcOperand& B, int M, int N, double* C, long long ldc,
+                               bool tri_b, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, __nv_bfloat16* zt,
+                               int zt_rows_pad, int zt_kp, unsigned* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (A.s != B.s || A.kp != B.kp || A.kp % TC_BK || (zs_kp % 8) || M > zt_kp || N > zt_rows_pad || M > zs_rows_pad ||
+      N > zs_kp)
+    return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.a_rows_pad = A.rows_pad;
+  a.b_rows_pad = B.rows_pad;
+  a.s = A.s;
+  a.k_iters = A.kp / TC_BK;
+  a.k_per_split = a.k_iters;
+  a.tri_b = tri_b ? 1 : 0;
+  a.alpha = 1.0;
+  a.C = C;
+  a.ldc = ldc;
+  a.zs = zs;
+  a.zs_rows_pad = zs_rows_pad;
+  a.zs_kp = zs_kp;
+  a.zt = zt;
+  a.zt_rows_pad = zt_rows_pad;
+  a.zt_kp = zt_kp;
+  a.status = status;
+  const double prods = 0.5 * a.s * (a.s + 1);
+  const double outk = tri_b ? (double)M * 0.5 * N * (N + 1.0) : (double)M * N * (double)A.kp;
+  return tc_launch<128, 1, EPI_F64_SLICES2>(A, B, a, 1, 1, 2.0 * prods * outk, st);
 }
 
 cudaError_t tc_facesplit(const TcOperand& A, const TcOperand& B, int M, int N, int kv_iters, double* C,

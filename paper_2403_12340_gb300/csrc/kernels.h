@@ -278,6 +278,13 @@ struct TcBatch {
 cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
                                 double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
                                 int num_sms, unsigned* status, cudaStream_t st, const TcBatch& bt);
+// C = A B^T in FP64 (M x N, column-major), and the BF16 slices of C twice:
+// row-major (element (m, n) at zs[m zs_kp + n], slice stride zs_rows_pad
+// zs_kp) and transposed (element (n, m) at zt[n zt_kp + m], slice stride
+// zt_rows_pad zt_kp); no split-K.  Padding entries of zs / zt are not written.
+cudaError_t tc_gemm_f64_slices(const TcOperand& A, const TcOperand& B, int M, int N, double* C, long long ldc,
+                               bool tri_b, __nv_bfloat16* zs, int zs_rows_pad, int zs_kp, __nv_bfloat16* zt,
+                               int zt_rows_pad, int zt_kp, unsigned* status, cudaStream_t st);
 // Face-split Gram (A_v B_v^T) .* (A_c B_c^T): chunks [0, kv_iters) feed the
 // first accumulator, the rest the second.  Output FP64 column-major (C) or,
 // with zs non-null, BF16 slices (row-major M x N, zs_rows_pad x zs_kp).

@@ -112,11 +112,16 @@ cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r, bool linv_ready) 
   MK(ensure(c->m_work, 5 * wq));
   if (!linv_ready) MK(launch_tri_inverse(c->Lc.p, r, r, c->m_linv.p, r, c->m_work.p, c->m_work.p + wq, st));
   MK(slices_cm(c->m_linvs, c->m_linv.p, r, r, r, rp, rk, st));
-  MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, 1.0, 0.0, theta, nr, false, true,
-                 nullptr, 1, c->num_sms, c->d_status, st));
-  // slices of theta for the apply: K-major over the grid (theta^T X) and over mu (theta T2)
-  MK(slices_rm(c->m_thetas_t, theta, nr, r, (int)nr, rp, pad(nr, 64), st));
-  MK(slices_cm(c->m_zs, theta, nr, (int)nr, r, nrp, rk, st));
+  // theta in FP64 and, from the same epilogue, its slices for the apply:
+  // K-major over mu (theta T2, m_ths) and over the grid (theta^T X, m_thetas_t)
+  const int kpg = pad(nr, 64);
+  const size_t nth = (size_t)NSL * nrp * rk, ntt = (size_t)NSL * rp * kpg;
+  MK(ensure_bf16(c->m_ths, nth));
+  MK(ensure_bf16(c->m_thetas_t, ntt));
+  if (nrp != nr || rk != r) MK(cudaMemsetAsync(c->m_ths.p, 0, nth * 2, st));  // zero padding
+  if (rp != r || kpg != nr) MK(cudaMemsetAsync(c->m_thetas_t.p, 0, ntt * 2, st));
+  MK(tc_gemm_f64_slices(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, theta, nr, true, c->m_ths.bf(), nrp,
+                        rk, c->m_thetas_t.bf(), rp, kpg, c->d_status, st));
   return cudaSuccess;
 }
 
@@ -385,7 +390,7 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
                  st));
   // T3 = theta T2
   MK(slices_rm(c->m_xs, c->tmp2.p, r, nc, r, ncp, rk, st));
-  MK(tc_gemm_f64(op(c->m_zs, nrp, rk), op(c->m_xs, ncp, rk), (int)nr, nc, 1.0, 0.0, c->tmp3.p, nr, false, false,
+  MK(tc_gemm_f64(op(c->m_ths, nrp, rk), op(c->m_xs, ncp, rk), (int)nr, nc, 1.0, 0.0, c->tmp3.p, nr, false, false,
                  nullptr, 1, c->num_sms, c->d_status, st));
   // Y = X + V T3
   const long long lds = 2 * c->n_half;
