@@ -29,8 +29,11 @@ static thread_local std::string g_create_err;
 static constexpr double kPairWhitenMean = 4.0;
 
 // SMs that the tensor-core GEMMs leave to the FP64 factorisations running
-// beside them on the second stream (fit and polarizability).
-static constexpr int kFp64Sms = 12;
+// beside them on the second stream (fit and polarizability).  Measured at
+// 48^3 / N_mu = 1536 (ms per solve): 4 -> 25.8, 12 -> 25.4, 32 -> 25.0,
+// 64 -> 24.8, 80 -> 25.4, 100 -> 27.1: the factorisations are the longer
+// chain, so the GEMMs beside them give up SMs until they become the longer.
+static constexpr int kFp64Sms = 64;
 
 using PhaseScope = isdf::PhaseTimer;
 
