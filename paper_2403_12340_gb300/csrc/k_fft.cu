@@ -572,6 +572,70 @@ __global__ void __launch_bounds__(FFT_ZREG_THREADS) k_fft_z_slices_reg(FftGrid g
   }
 }
 
+// BF16 slices of w v into the row of column `col` (the common store of the
+// z passes): element q of the half spectrum at out[col kp + 2 q], slices nsl.
+__device__ __forceinline__ void store_spectrum_slices(float2 v, float w, __nv_bfloat16* row, long long q,
+                                                      long long sstr, int nsl) {
+  const float vv[2] = {v.x * w, v.y * w};
+  __nv_bfloat162 x0, x1, x2;
+  __nv_bfloat16* p0 = reinterpret_cast<__nv_bfloat16*>(&x0);
+  __nv_bfloat16* p1 = reinterpret_cast<__nv_bfloat16*>(&x1);
+  __nv_bfloat16* p2 = reinterpret_cast<__nv_bfloat16*>(&x2);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    p0[h] = __float2bfloat16_rn(vv[h]);
+    const float r1 = vv[h] - __bfloat162float(p0[h]);
+    p1[h] = __float2bfloat16_rn(r1);
+    p2[h] = __float2bfloat16_rn(r1 - __bfloat162float(p1[h]));
+  }
+  __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(row + 2 * q);
+  o[0] = x0;
+  if (nsl > 1) o[sstr / 2] = x1;
+  if (nsl > 2) o[sstr] = x2;
+}
+
+// The z pass with each line split over two threads (lanes l and l + 16 of a
+// warp, N even): one radix-2 decimation-in-frequency step across the pair by
+// shuffles -- lane l keeps a_j + b_j, lane l + 16 keeps (a_j - b_j) W_N^j,
+// a = the first half of the line, b = the second -- then a length-N/2
+// transform in each thread's registers.  Lane l ends with the even
+// frequencies, lane l + 16 with the odd ones.  Half the registers of
+// k_fft_z_slices_reg, so twice the warps per SM to hide its latencies.
+template <int N>
+__global__ void __launch_bounds__(FFT_ZREG_THREADS) k_fft_z_slices_reg2(FftGrid g, const float* S, long long lds,
+                                                                       const double* __restrict__ wt,
+                                                                       __nv_bfloat16* out, int rows_pad, int kp,
+                                                                       int nsl) {
+  using C = float2;
+  constexpr int H = N / 2 + 1, PLANE = N * H, HN = N / 2;
+  static_assert(N % 2 == 0, "two threads per line need an even length");
+  __shared__ C twz[N], tw2[HN];
+  for (int t = threadIdx.x; t < N; t += blockDim.x) twz[t] = from_tw<C>(((const double2*)g.ax[2].tw)[t]);
+  for (int t = threadIdx.x; t < HN; t += blockDim.x) tw2[t] = from_tw<C>(((const double2*)g.ax[2].tw)[2 * t]);
+  __syncthreads();
+  const int col = blockIdx.y, lane = threadIdx.x & 31, half = lane >> 4;
+  const int q = blockIdx.x * (FFT_ZREG_THREADS / 2) + (threadIdx.x >> 5) * 16 + (lane & 15);
+  const bool active = q < PLANE;  // every lane stays for the shuffles
+  const C* base = (const C*)(S + lds * (long long)col);
+  C v[HN];
+#pragma unroll
+  for (int j = 0; j < HN; ++j) v[j] = active ? base[(long long)(j + half * HN) * PLANE + q] : mk<C>(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < HN; ++j) {
+    const C o = mk<C>(__shfl_xor_sync(0xffffffffu, v[j].x, 16), __shfl_xor_sync(0xffffffffu, v[j].y, 16));
+    v[j] = half == 0 ? cadd(v[j], o) : cmul(csub(o, v[j]), twid<-1>(twz, j));
+  }
+  dif_stages<HN, HN, -1>(v, tw2);
+  if (!active) return;
+  const long long sstr = (long long)rows_pad * kp;
+  __nv_bfloat16* row = out + (long long)col * kp;
+#pragma unroll
+  for (int p = 0; p < HN; ++p) {
+    const long long qq = (long long)(half + 2 * dif_freq(p, HN)) * PLANE + q;
+    store_spectrum_slices(v[p], to_real<float>(wt[qq]), row, qq, sstr, nsl);
+  }
+}
+
 template <int N>
 static cudaError_t fft_slices_ct(const FftGrid& g, const double* X, long long ldx, int ncols, float* S32, long long lds32,
                                  const double* wt, __nv_bfloat16* out, int rows_pad, int kp, int nsl, cudaStream_t s) {
@@ -584,7 +648,10 @@ static cudaError_t fft_slices_ct(const FftGrid& g, const double* X, long long ld
   if (e != cudaSuccess) return e;
   constexpr int PLANE = N * (N / 2 + 1);
   note_launch();
-  if constexpr (N <= 64) {
+  if constexpr (N % 2 == 0) {
+    dim3 gz((PLANE + FFT_ZREG_THREADS / 2 - 1) / (FFT_ZREG_THREADS / 2), ncols);
+    k_fft_z_slices_reg2<N><<<gz, FFT_ZREG_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
+  } else if constexpr (N <= 64) {
     dim3 gz((PLANE + FFT_ZREG_THREADS - 1) / FFT_ZREG_THREADS, ncols);
     k_fft_z_slices_reg<N><<<gz, FFT_ZREG_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
   } else {
