@@ -28,12 +28,20 @@ static thread_local std::string g_create_err;
 // about 14 or more) the mixed path whitens D in pair space.
 static constexpr double kPairWhitenMean = 4.0;
 
-// SMs that the tensor-core GEMMs leave to the FP64 factorisations running
-// beside them on the second stream (fit and polarizability).  Measured at
-// 48^3 / N_mu = 1536 (ms per solve): 4 -> 25.8, 12 -> 25.4, 32 -> 25.0,
-// 64 -> 24.8, 80 -> 25.4, 100 -> 27.1: the factorisations are the longer
-// chain, so the GEMMs beside them give up SMs until they become the longer.
+// SMs that a tensor-core GEMM leaves to the FP64 factorisations running
+// beside it on the second stream (fit and polarizability) -- only where the
+// factorisations' latency-bound chain of r / 64 steps (about 0.1 ms each,
+// on a few SMs) is long next to the GEMM (its issued BF16 flops at about
+// 0.7 PFLOP/s); their throughput-bound updates gain nothing from SMs held
+// back.  Measured (ms per solve): 48^3 / N_mu = 1536 with 4, 12, 32, 64, 80,
+// 100 SMs left: 25.8, 25.4, 25.0, 24.8, 25.4, 27.1; 72^3 / N_mu = 6144 (s
+// per solve) with 0, 24, 64: 1.05, 1.08, 1.17.
 static constexpr int kFp64Sms = 64;
+static int fp64_sms_to_leave(int r, double gemm_flops) {
+  const double chain_ms = std::ceil(r / 64.0) * 0.1;
+  const double gemm_ms = gemm_flops / 0.7e12;
+  return chain_ms > 0.5 * gemm_ms ? kFp64Sms : 0;
+}
 
 using PhaseScope = isdf::PhaseTimer;
 
@@ -420,7 +428,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   // the given order, which is the pivot order whenever the blocked
   // factorisation succeeds
   if (prec == ISDF_PREC_MIXED) {
-    isdf::TcSmReserve keep(kFp64Sms);  // the Cholesky on the second stream keeps some SMs
+    // the Cholesky on the second stream keeps some SMs (the Gram: 6 slice products, 2 N_r n_mu N_e each)
+    isdf::TcSmReserve keep(fp64_sms_to_leave(n_mu, 12.0 * c->n_r * n_mu * (n_v + n_c)));
     CK(isdf::mixed_fit_gram(c, phi, c->phimu.p, n_v, n_c, n_mu));
   } else {
     PhaseScope ph(c, ISDF_PH_FIT_GRAM);
@@ -697,7 +706,8 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     }
     // G = theta^T V theta (main stream)
     if (c->prec == ISDF_PREC_MIXED) {
-      isdf::TcSmReserve keep(kFp64Sms);  // the factorisations of D(w) on the second stream keep some SMs
+      // the factorisations of D(w) on the second stream keep some SMs (the SYRK of G: 6 r^2 K)
+      isdf::TcSmReserve keep(fp64_sms_to_leave(r, 6.0 * r * (double)r * lds));
       CK(isdf::mixed_polar_G(c));
     } else {
       {
