@@ -10,6 +10,7 @@
 // does nothing.  The caller decides what that means (not positive definite,
 // or: fall back to the pivoted factorisation for a rank-deficient C C^T).
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -279,12 +280,14 @@ static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int re
     const long long T = (m + ts - 1) / ts;
     return T * (T + 1) / 2;
   };
-  static int sms = 0;
+  static std::atomic<int> sms_cache{0};
+  int sms = sms_cache.load(std::memory_order_relaxed);
   if (!sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    sms_cache.store(sms, std::memory_order_relaxed);
   }
   KernelTimer kt(KF_FP64_GEMM, s, (double)rem * (rem + 1) * bs * batch);  // lower triangle, 2 flops per term
   note_launch();

@@ -440,49 +440,6 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_xy_fwd_ct(FftGrid g, const 
   for (int idx = threadIdx.x; idx < N * H; idx += blockDim.x) out[idx] = Q[idx];
 }
 
-template <int N>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_slices_ct(FftGrid g, const float* S, long long lds,
-                                                                 const double* __restrict__ wt, __nv_bfloat16* out,
-                                                                 int rows_pad, int kp, int nsl) {
-  using C = float2;
-  constexpr int H = N / 2 + 1, PLANE = N * H;
-  __shared__ C twz[N];
-  __shared__ C b0[N * FFT_ZCHUNK], b1[N * FFT_ZCHUNK];
-  const int q0 = blockIdx.x * FFT_ZCHUNK, col = blockIdx.y;
-  const int nq = min(FFT_ZCHUNK, PLANE - q0);
-  for (int t = threadIdx.x; t < N; t += blockDim.x) twz[t] = from_tw<C>(((const double2*)g.ax[2].tw)[t]);
-  const C* base = (const C*)(S + lds * (long long)col);
-  for (int idx = threadIdx.x; idx < N * FFT_ZCHUNK; idx += blockDim.x) {
-    const int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
-    b0[idx] = c < nq ? base[(long long)z * PLANE + q0 + c] : mk<C>(0.f, 0.f);
-  }
-  __syncthreads();
-  C* R = fft_lines_ct<N, 1, N, -1>(b0, b1, twz, FFT_ZCHUNK, FFT_ZCHUNK, 1);
-  const long long sstr = (long long)rows_pad * kp;
-  for (int idx = threadIdx.x; idx < N * FFT_ZCHUNK; idx += blockDim.x) {
-    const int z = idx / FFT_ZCHUNK, c = idx - z * FFT_ZCHUNK;
-    if (c >= nq) continue;
-    const long long q = (long long)z * PLANE + q0 + c;
-    const float w = to_real<float>(wt[q]);
-    const float v[2] = {R[idx].x * w, R[idx].y * w};
-    __nv_bfloat162 x0, x1, x2;
-    __nv_bfloat16* p0 = reinterpret_cast<__nv_bfloat16*>(&x0);
-    __nv_bfloat16* p1 = reinterpret_cast<__nv_bfloat16*>(&x1);
-    __nv_bfloat16* p2 = reinterpret_cast<__nv_bfloat16*>(&x2);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      p0[h] = __float2bfloat16_rn(v[h]);
-      const float r1 = v[h] - __bfloat162float(p0[h]);
-      p1[h] = __float2bfloat16_rn(r1);
-      p2[h] = __float2bfloat16_rn(r1 - __bfloat162float(p1[h]));
-    }
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + (long long)col * kp + 2 * q);
-    o[0] = x0;
-    if (nsl > 1) o[sstr / 2] = x1;
-    if (nsl > 2) o[sstr] = x2;
-  }
-}
-
 // ---- z pass in registers --------------------------------------------------
 // Frequency held by position p of an in-place decimation-in-frequency
 // transform of length n whose stages take the radices first_radix(n),
@@ -524,7 +481,8 @@ __device__ __forceinline__ void dif_stages(C (&v)[N], const C* tw) {
 }
 
 // The z pass of the FP32 forward transform with the BF16 slices of the
-// weighted spectrum out (the same output as k_fft_z_slices_ct): one thread
+// weighted spectrum out (row col of the slice matrix holds column col's
+// half spectrum times the SYRK weights, 3 slices): one thread
 // per z line, the whole line in registers, so there is no shared-memory
 // traffic and no block barrier between the radix stages; a warp's loads and
 // stores of one z row are contiguous.
@@ -651,12 +609,10 @@ static cudaError_t fft_slices_ct(const FftGrid& g, const double* X, long long ld
   if constexpr (N % 2 == 0) {
     dim3 gz((PLANE + FFT_ZREG_THREADS / 2 - 1) / (FFT_ZREG_THREADS / 2), ncols);
     k_fft_z_slices_reg2<N><<<gz, FFT_ZREG_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
-  } else if constexpr (N <= 64) {
+  } else {
+    static_assert(N <= 64, "an odd compile-time length keeps its whole z line in one thread's registers");
     dim3 gz((PLANE + FFT_ZREG_THREADS - 1) / FFT_ZREG_THREADS, ncols);
     k_fft_z_slices_reg<N><<<gz, FFT_ZREG_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
-  } else {
-    dim3 gz((PLANE + FFT_ZCHUNK - 1) / FFT_ZCHUNK, ncols);
-    k_fft_z_slices_ct<N><<<gz, FFT_THREADS, 0, s>>>(g, S32, lds32, wt, out, rows_pad, kp, nsl);
   }
   return cudaGetLastError();
 }

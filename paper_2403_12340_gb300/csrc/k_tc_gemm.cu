@@ -576,12 +576,14 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
   e = make_map(&mb, B.p, B.kp, brows, BN);
   if (e != cudaSuccess) return e;
   const int smem = tc_stages(a.s, BN) * tc_stage_bytes(a.s, BN) + 1024 + 256;
-  static bool configured = false;
-  if (!configured) {
+  // once per kernel (host threads of a batch may arrive together: setting it twice is harmless,
+  // and a thread that reads true finds it set)
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(k_tc_gemm<BN, NACC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TC_SMEM_LIMIT - 2048);  // leaves room for the static shared variables
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   if (smem > TC_SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
   const int tm = (a.M + TC_BM - 1) / TC_BM, tn = (a.N + BN - 1) / BN;
@@ -591,11 +593,13 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
   a.count = batch;
   const long long tiles = a.lower_only ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
   const long long units = tiles * splits * batch;
-  static int sms = 0;
+  static std::atomic<int> sms_cache{0};
+  int sms = sms_cache.load(std::memory_order_relaxed);
   if (!sms) {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    sms_cache.store(sms, std::memory_order_relaxed);
   }
   // one block per SM (the stage ring takes most of the shared memory), each looping over units
   const int avail = std::max(1, sms - std::max(0, tl_tc_sm_reserve));
