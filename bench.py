@@ -44,6 +44,9 @@ N_RHS = 16
 # 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2070 MHz maximum SM clock.  A DFMA
 # throughput microbenchmark on this machine measured 1.20 TFLOP/s at ~1.97 GHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# double-float products on the FP32 pipe: 128 lanes per SM, 12 FP32
+# instructions per product (1 mul, 3 fma, 8 add / sub), 2 flops counted
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 
 
 def measured_peaks():
@@ -88,6 +91,13 @@ def kernel_roofline(fam, phase, ms, cnt, work, steps, peaks):
                      "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe)",
                      "work": "FP64 flops"})
+    elif fam == "df_gemm":
+        ach = work / sec / 1e12
+        cell.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(DF_PEAK_TFLOPS, 4),
+                     "unit": "TFLOP/s", "frac": round(ach / DF_PEAK_TFLOPS, 4),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz / 12 FP32 instructions per "
+                                    "double-float product x 2 flops (FP32 pipe)",
+                     "work": "flops of the FP64 update, carried in double-float"})
     else:
         ach = work / sec / 1e9
         cell.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
@@ -241,7 +251,8 @@ PREC_DETAIL = {
     "fp64": "every step in float64 on the FP64 pipe",
     "mixed": ("large contractions on tcgen05 tensor cores with operands cut into 3 BF16 slices "
               "(FP32 accumulation, FP64 sums over K blocks), FFT of theta in FP32; Cholesky "
-              "factorisations and triangular inverses in FP64"),
+              "factorisations and triangular inverses in FP64, their trailing updates in "
+              "double-float (FP32 pairs, about 2^-46 relative)"),
 }
 
 

@@ -415,7 +415,8 @@ enum {
   ISDF_KF_CHOL_DIAG = 2, /* 64 x 64 diagonal-block Cholesky + inverse; work = flops */
   ISDF_KF_FFT = 3,       /* batched 3-D FFTs; work = bytes (input read + output write) */
   ISDF_KF_SLICE = 4,     /* FP64 -> BF16 slicing; work = bytes */
-  ISDF_NUM_KERNEL_FAMILIES = 5
+  ISDF_KF_DF_GEMM = 5,   /* double-float Cholesky trailing updates on the FP32 pipe (mixed path); work = flops */
+  ISDF_NUM_KERNEL_FAMILIES = 6
 };
 /* Synchronises the device, then writes per (family, phase) cell, index
  * family * ISDF_NUM_PHASES + phase, the summed milliseconds, launch count

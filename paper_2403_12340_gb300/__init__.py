@@ -41,7 +41,7 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "isdf_batch_replay", "isdf_set_autotune", "isdf_autotune_size", "isdf_autotune_entry",
             "isdf_autotune_clear"]
 NUM_PHASES = 9
-NUM_KERNEL_FAMILIES = 5
+NUM_KERNEL_FAMILIES = 6
 
 
 class IsdfError(RuntimeError):

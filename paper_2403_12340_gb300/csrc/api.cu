@@ -263,7 +263,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->kappa_work, &c->inv_work, &c->m_ths};
+                    &c->m_pairs_t, &c->swf, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
@@ -312,9 +312,15 @@ static int cholesky(isdf_ctx* c, const double* W, long long ldw, int n, int pivo
 
 // Blocked Cholesky (no pivoting) of W into Lout (ld n); *fail (device) = -1
 // on success, else the first column whose pivot fell to tol_rel * max diag.
+// The mixed path's trailing updates run in double-float arithmetic from
+// the split panel in cb_split (sized by the caller's workspace step).
+static float2* split_panel(isdf_ctx* c, size_t need) {
+  return c->prec == ISDF_PREC_MIXED && c->cb_split.cap >= need ? reinterpret_cast<float2*>(c->cb_split.p) : nullptr;
+}
+
 static int cholesky_blocked(isdf_ctx* c, const double* W, long long ldw, int n, double tol_rel, double* Lout,
                             int* fail, cudaStream_t st) {
-  CK(launch_cholesky_blocked(W, ldw, n, tol_rel, Lout, n, c->cb_work.p, fail, st));
+  CK(launch_cholesky_blocked(W, ldw, n, tol_rel, Lout, n, c->cb_work.p, fail, st, split_panel(c, (size_t)64 * n)));
   return ISDF_OK;
 }
 
@@ -341,8 +347,9 @@ static int chol_inverse_workspace(isdf_ctx* c, int n) {
     CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->ev_chol.push_back(e);
   }
-  if (c->inv_work.cap < (size_t)9 * 64 * n) SYNC(c->stream);
+  if (c->inv_work.cap < (size_t)9 * 64 * n || c->cb_split.cap < (size_t)64 * n) SYNC(c->stream);
   CK(ensure(c->inv_work, (size_t)9 * 64 * n));
+  CK(ensure(c->cb_split, (size_t)64 * n));
   return ISDF_OK;
 }
 
@@ -418,7 +425,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     PhaseScope ph(c, ISDF_PH_POINTS, c->s2);
     if (fuse_inv) {
       CK(launch_cholesky_and_inverse(c->A.p, n_mu, n_mu, tol, c->Lc.p, n_mu, c->m_linv.p, n_mu, c->cb_work.p,
-                                     c->d_ints + 1, c->inv_work.p, c->s2, c->s3, c->ev_chol.data()));
+                                     c->d_ints + 1, c->inv_work.p, c->s2, c->s3, c->ev_chol.data(),
+                                     reinterpret_cast<float2*>(c->cb_split.p)));
     } else {
       rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1, c->s2);
       if (rc0 != ISDF_OK) return rc0;
@@ -623,6 +631,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     CK(ensure(c->sw, npair * n_omega));
     CK(ensure(c->tmp1, rr));
     if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)n_omega));
+    if (c->prec == ISDF_PREC_MIXED) CK(ensure(c->cb_split, (size_t)64 * r * n_omega));
     if (n_nodes > 0) CK(ensure(c->ctab, (size_t)2 * n_nodes * (n_e + 1)));
     if (c->pair_whiten) CK(ensure(c->swf, (npair * n_omega + 1) / 2));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
@@ -698,7 +707,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
       PhaseScope ph(c, ISDF_PH_SMW, c->s2);
       if (n_omega > 1) {  // all frequencies in one factorisation sequence
         CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr,
-                                           c->b_cbd.p, c->d_fail, c->s2));
+                                           c->b_cbd.p, c->d_fail, c->s2, split_panel(c, (size_t)64 * r * n_omega)));
       } else {
         rc0 = cholesky_blocked(c, c->D.p, r, r, 0.0, c->Rw.p, c->d_fail, c->s2);
         if (rc0 != ISDF_OK) return rc0;
@@ -798,7 +807,7 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
     CK(launch_cholesky_and_inverse(c->T.p, r, r, 0.0, c->W1.p, r, c->Q.p, r, c->cb_work.p, failT, c->inv_work.p,
-                                   c->stream, c->s2, c->ev_chol.data()));
+                                   c->stream, c->s2, c->ev_chol.data(), reinterpret_cast<float2*>(c->cb_split.p)));
     CK(cudaEventRecord(c->ev_join, c->s2));
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     CK(isdf::mixed_smw_products_K(c, Kk, true));
@@ -1028,7 +1037,7 @@ isdf::KernelTimer::~KernelTimer() {
 }
 
 static_assert(KF_COUNT == ISDF_NUM_KERNEL_FAMILIES, "kernel families of the header and the launchers differ");
-static const char* kFamilyNames[KF_COUNT] = {"tc_gemm", "fp64_gemm", "chol_diag", "fft", "slice"};
+static const char* kFamilyNames[KF_COUNT] = {"tc_gemm", "fp64_gemm", "chol_diag", "fft", "slice", "df_gemm"};
 
 extern "C" const char* isdf_kernel_family_name(int fam) {
   return (fam >= 0 && fam < KF_COUNT) ? kFamilyNames[fam] : nullptr;

@@ -76,6 +76,10 @@ struct isdf_ctx {
   cudaEvent_t ev_join3 = nullptr;
   std::vector<cudaEvent_t> ev_chol;  // one per 64-wide factorisation step
   DevBuf inv_work;
+  // split panels (float pairs, one per double) of the mixed path's
+  // double-float trailing updates: one factorisation at a time (cb_split),
+  // the batched T of smw_inverse_all (b_split)
+  DevBuf cb_split, b_split;
   DevBuf m_ths;  // BF16 slices of theta (rows = grid points), written by the epilogue of the fit's TRSM
   DevBuf Rw;             // Cholesky factors of D(w), one r x r block per frequency
   int* d_fail = nullptr; // their failure flags

@@ -5,6 +5,17 @@
 // substitution, one warp per row over every SM; the trailing matrix gets a
 // lower SYRK update, which carries nearly all of the O(n^3) work.
 //
+// With a split-panel buffer (the mixed path) the trailing update runs in
+// double-float arithmetic on the FP32 pipes instead: each panel entry is
+// stored once as a pair of floats (hi + lo, 48 significant bits), products
+// keep their exact FMA error and the cross terms, and the sums carry their
+// rounding error in a second float (two-sum), about 2^-46 relative per
+// update; the factor itself stays FP64 in memory, and the diagonal blocks
+// and panels are FP64.  On this part the FP64 pipe issues one warp
+// instruction per 64 cycles per sub-partition and the FP32 pipe one per
+// cycle, so twelve FP32 instructions per product still run several times
+// faster than one FP64 FMA.
+//
 // A pivot at or below tol_rel * max(diag) stops the factorisation: the
 // first failing column goes to *fail and every later kernel of the sequence
 // does nothing.  The caller decides what that means (not positive definite,
@@ -18,6 +29,47 @@
 namespace isdf {
 
 constexpr int CB = 64;
+
+// ---- double-float helpers ---------------------------------------------------
+
+// An FP32 value as FP64 from its bit fields (exact for normal values; zero
+// and subnormals give a signed zero, infinities and NaN stay what they are).
+__device__ __forceinline__ double f32_as_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
+  if (ex == 0) return __longlong_as_double((long long)sgn);
+  const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);  // 1023 - 127
+  return __longlong_as_double((long long)(sgn | (e64 << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// x = hi + lo to 48 significant bits
+__device__ __forceinline__ float2 split_f64(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - f32_as_f64(h)));
+}
+
+// (hi, lo) += a b: the product's exact FP32 error and both cross terms go to
+// lo (a.lo b.lo, 2^-48 relative, is dropped); hi + p by Knuth's two-sum.
+// The _rn intrinsics keep the compiler from fusing the error-free steps.
+__device__ __forceinline__ void df_fma(float2 a, float2 b, float& hi, float& lo) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// (hi, lo) <- hi + lo renormalised (|hi| >= |lo| or hi = 0 after a chunk)
+__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
 
 __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, double* out, int* fail,
                            long long sW = 0) {
@@ -154,8 +206,11 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
 // one warp per row, lane l holding columns l and l + 32 of the row; forward
 // substitution by columns, each solved value broadcast by a shuffle.  Rows
 // are independent, so every SM takes part however short the panel is.
+// With Sp, the solved panel is also written as float pairs: row `row` of
+// the panel, column c at Sp[row + lds c] (problem y at Sp + y sS).
 __global__ void __launch_bounds__(256) k_panel_trsm(double* A, long long lda, int j0, int bs, int rem,
-                                                   const int* fail, long long sA = 0) {
+                                                   const int* fail, long long sA = 0, float2* Sp = nullptr,
+                                                   long long lds = 0, long long sS = 0) {
   __shared__ double Lt[CB][CB + 1];  // Lt[c][k] = L_jj(c, k), zero outside the lower triangle
   __shared__ double inv[CB];
   A += sA * blockIdx.y;  // problem blockIdx.y of a batch
@@ -187,6 +242,11 @@ __global__ void __launch_bounds__(256) k_panel_trsm(double* A, long long lda, in
     }
     if (lane < bs) a[lda * lane] = x0;
     if (lane + 32 < bs) a[lda * (lane + 32)] = x1;
+    if (Sp) {
+      float2* sp = Sp + sS * blockIdx.y + row;
+      if (lane < bs) sp[lds * lane] = split_f64(x0);
+      if (lane + 32 < bs) sp[lds * (lane + 32)] = split_f64(x1);
+    }
   }
 }
 
@@ -270,12 +330,79 @@ __global__ void __launch_bounds__((TS / TM) * (TS / TM)) k_trail_update(double* 
     }
 }
 
+// The same trailing update in double-float arithmetic from the split panel
+// Sp (rows of the panel, ld lds, problem y at Sp + y sS): FP32 shared tiles
+// of float pairs, a (hi, lo) accumulator pair per output, renormalised after
+// every K chunk; C -= hi + lo in FP64 at the end.
+template <int TS, int TM>
+__global__ void __launch_bounds__((TS / TM) * (TS / TM)) k_trail_update_df(const float2* __restrict__ Sp, long long lds,
+                                                                          long long sS, double* L, long long ldl,
+                                                                          int j0, int bs, int rem, const int* fail,
+                                                                          long long sL) {
+  constexpr int Q = TS / TM, NT = Q * Q, KC = 32;
+  __shared__ float2 As[KC][TS], Bs[KC][TS];
+  L += sL * blockIdx.y;
+  Sp += sS * blockIdx.y;
+  if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
+  const int tile = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+  while (ti * (ti + 1) / 2 > tile) --ti;
+  const int tj = tile - ti * (ti + 1) / 2;
+  const int i0 = ti * TS, k0 = tj * TS;
+  const int t = threadIdx.x, tx = t % Q, ty = t / Q;
+  const long long r0 = j0 + bs;
+  float hi[TM][TM], lo[TM][TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int n = 0; n < TM; ++n) hi[m][n] = lo[m][n] = 0.0f;
+  for (int c0 = 0; c0 < bs; c0 += KC) {
+    const int kc = min(KC, bs - c0);
+    for (int idx = t; idx < KC * TS; idx += NT) {
+      const int i = idx % TS, c = idx / TS;
+      const bool in_k = c < kc;
+      As[c][i] = (in_k && i0 + i < rem) ? Sp[(i0 + i) + lds * (c0 + c)] : make_float2(0.0f, 0.0f);
+      Bs[c][i] = (in_k && k0 + i < rem) ? Sp[(k0 + i) + lds * (c0 + c)] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int c = 0; c < KC; ++c) {
+      float2 a[TM], b[TM];
+#pragma unroll
+      for (int m = 0; m < TM; ++m) {
+        a[m] = As[c][tx + Q * m];
+        b[m] = Bs[c][ty + Q * m];
+      }
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int n = 0; n < TM; ++n) df_fma(a[m], b[n], hi[m][n], lo[m][n]);
+    }
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int n = 0; n < TM; ++n) df_renorm(hi[m][n], lo[m][n]);
+    __syncthreads();
+  }
+  double* C = L + r0 + ldl * r0;
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int n = 0; n < TM; ++n) {
+      const int i = i0 + tx + Q * m, k = k0 + ty + Q * n;
+      if (i < rem && k < rem && (ti != tj || i >= k))
+        C[i + ldl * (long long)k] -= f32_as_f64(hi[m][n]) + f32_as_f64(lo[m][n]);
+    }
+}
+
 // Tile width of a trailing update: 64 (4 x 4 per thread) while the 64-wide
 // tiles fill the SMs, else 32 (2 x 2 per thread, still 256 threads): the
 // late, small updates then use four times the SMs, each tile a quarter of
 // the work with the same number of warps.
 static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int rem, int batch, const int* fail,
-                                long long sL, cudaStream_t s) {
+                                long long sL, cudaStream_t s, const float2* Sp = nullptr, long long lds = 0,
+                                long long sS = 0) {
   auto tiles = [](int m, int ts) {
     const long long T = (m + ts - 1) / ts;
     return T * (T + 1) / 2;
@@ -289,9 +416,17 @@ static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int re
     if (e != cudaSuccess) return e;
     sms_cache.store(sms, std::memory_order_relaxed);
   }
-  KernelTimer kt(KF_FP64_GEMM, s, (double)rem * (rem + 1) * bs * batch);  // lower triangle, 2 flops per term
+  KernelTimer kt(Sp ? KF_DF_GEMM : KF_FP64_GEMM, s, (double)rem * (rem + 1) * bs * batch);  // lower triangle, 2 flops per term
   note_launch();
-  if (tiles(rem, 64) * batch >= sms) {
+  if (Sp) {
+    if (tiles(rem, 64) * batch >= sms) {
+      k_trail_update_df<64, 4><<<dim3((unsigned)tiles(rem, 64), batch), 256, 0, s>>>(Sp, lds, sS, L, ldl, j0, bs,
+                                                                                     rem, fail, sL);
+    } else {
+      k_trail_update_df<32, 2><<<dim3((unsigned)tiles(rem, 32), batch), 256, 0, s>>>(Sp, lds, sS, L, ldl, j0, bs,
+                                                                                     rem, fail, sL);
+    }
+  } else if (tiles(rem, 64) * batch >= sms) {
     k_trail_update<64, 4><<<dim3((unsigned)tiles(rem, 64), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
   } else {
     k_trail_update<32, 2><<<dim3((unsigned)tiles(rem, 32), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
@@ -305,7 +440,7 @@ static unsigned panel_blocks(int rem) {
 }
 
 cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
-                                    double* dmax, int* fail, cudaStream_t s) {
+                                    double* dmax, int* fail, cudaStream_t s, float2* split) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
   if (L != W) {
@@ -329,11 +464,11 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
     {
       KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs);  // triangular solve, rem bs^2 flops
       note_launch();
-      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail);
+      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, 0, split, n, 0);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles)
-    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s);
+    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s, split, n, 0);
     if (e != cudaSuccess) return e;
   }
   dim3 g((n + 127) / 128, n);
@@ -344,7 +479,8 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
 
 cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, double tol_rel, double* L,
                                         long long ldl, double* Li, long long ldi, double* dmax, int* fail,
-                                        double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev) {
+                                        double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev,
+                                        float2* split) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, n * sizeof(double), n, aux);
   if (e != cudaSuccess) return e;
@@ -387,10 +523,10 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
     {
       KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs);
       note_launch();
-      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail);
+      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, 0, split, n, 0);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s);
+    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s, split, n, 0);
     if (e != cudaSuccess) return e;
   }
   dim3 g((n + 127) / 128, n);
@@ -404,7 +540,7 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
 // fail: batch entries.
 cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
                                             double tol_rel, double* L, long long ldl, long long sL, double* dmax,
-                                            int* fail, cudaStream_t s) {
+                                            int* fail, cudaStream_t s, float2* split) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -429,10 +565,11 @@ cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long
     {
       KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs * batch);
       note_launch();
-      k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL);
+      k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, split, n,
+                                                                  (long long)n * CB);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    e = trail_update(L, ldl, j0, bs, rem, batch, fail, sL, s);
+    e = trail_update(L, ldl, j0, bs, rem, batch, fail, sL, s, split, n, (long long)n * CB);
     if (e != cudaSuccess) return e;
   }
   note_launch();

@@ -36,7 +36,7 @@ struct TcSmReserve {
 // family, the phase and the launch's algorithmic work (flops for the GEMM
 // and Cholesky families, bytes for the FFT and slicing families; for
 // KF_TC_GEMM the BF16 MMA flops of the slice products).
-enum { KF_TC_GEMM = 0, KF_FP64_GEMM = 1, KF_CHOL_DIAG = 2, KF_FFT = 3, KF_SLICE = 4, KF_COUNT = 5 };
+enum { KF_TC_GEMM = 0, KF_FP64_GEMM = 1, KF_CHOL_DIAG = 2, KF_FFT = 3, KF_SLICE = 4, KF_DF_GEMM = 5, KF_COUNT = 6 };
 struct KernelTimer {
   KernelTimer(int fam, cudaStream_t s, double work);
   ~KernelTimer();
@@ -144,10 +144,11 @@ cudaError_t launch_contour_polarizability(const double* phimu, long long ldp, in
 // lower part read) into L (may equal W).  *fail = -1 on success, else the
 // first column whose pivot is <= tol_rel * max(diag W) (later steps are
 // skipped); dmax: one double of scratch.
+// split: nullptr for FP64 trailing updates, else 64 n float pairs of
+// scratch for the double-float trailing updates (about 2^-46 relative per
+// update instead of 2^-53; the mixed path).
 cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, double tol_rel, double* L, long long ldl,
-                                    double* dmax, int* fail, cudaStream_t s);
-// The same for `batch` equal-size matrices W + z sW -> L + z sL; dmax and
-// fail: batch entries.
+                                    double* dmax, int* fail, cudaStream_t s, float2* split = nullptr);
 // The inverse of one lower-triangular block of at most 64 x 64 (L, ld ldl)
 // into Li (ld ldi; strict upper part zeroed): one thread block.
 cudaError_t launch_diag_inverse_block(const double* L, long long ldl, int bs, double* Li, long long ldi,
@@ -162,10 +163,13 @@ cudaError_t launch_diag_inverse_block(const double* L, long long ldl, int bs, do
 // If the factorisation stops (fail >= 0), Li is undefined.
 cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, double tol_rel, double* L,
                                         long long ldl, double* Li, long long ldi, double* dmax, int* fail,
-                                        double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev);
+                                        double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev,
+                                        float2* split = nullptr);
+// launch_cholesky_blocked for `batch` equal-size matrices W + z sW -> L + z sL;
+// dmax and fail: batch entries; split: nullptr or batch x 64 n float pairs.
 cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
                                             double tol_rel, double* L, long long ldl, long long sL, double* dmax,
-                                            int* fail, cudaStream_t s);
+                                            int* fail, cudaStream_t s, float2* split = nullptr);
 
 // ---- k_chol.cu ------------------------------------------------------------
 struct CholWork {

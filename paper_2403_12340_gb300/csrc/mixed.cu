@@ -309,6 +309,7 @@ cudaError_t mixed_smw_batched(isdf_ctx* c, int nw, int* fail_T) {
   MK(ensure_bf16(c->b_s3, per_sq));
   MK(ensure(c->b_work, wq * nw));
   MK(ensure(c->b_cb, (size_t)nw));
+  MK(ensure(c->b_split, (size_t)64 * r * nw));
   const double* R = c->Rw.p;
   // T = I + R^T (G R)
   MK(slices_cm(c->b_s3, c->G.p, r, r, r, rp, rk, st));
@@ -322,7 +323,8 @@ cudaError_t mixed_smw_batched(isdf_ctx* c, int nw, int* fail_T) {
                          1, c->num_sms, c->d_status, st, TcBatch{nw, sr, sr, srr}));
   MK(launch_symmetrize(c->bT.p, r, r, st, nw, srr));
   // T = U U^T (FP64), U^-1, Q = R U^-T, K = -Q Q^T
-  MK(launch_cholesky_blocked_batched(c->bT.p, r, srr, r, nw, 0.0, c->bU.p, r, srr, c->b_cb.p, fail_T, st));
+  MK(launch_cholesky_blocked_batched(c->bT.p, r, srr, r, nw, 0.0, c->bU.p, r, srr, c->b_cb.p, fail_T, st,
+                                     reinterpret_cast<float2*>(c->b_split.p)));
   MK(launch_tri_inverse_batched(c->bU.p, r, srr, r, nw, c->bQ.p, r, srr, c->b_work.p, st));
   MK(slices_cm_b(c->b_s1, R, r, srr, r, r, rp, rk, nw, st));
   MK(slices_cm_b(c->b_s2, c->bQ.p, r, srr, r, r, rp, rk, nw, st));
