@@ -111,6 +111,47 @@ struct Operand {
   }
 };
 
+// ---- double-float helpers (the mixed path's FP64-grade work on the FP32 pipe) ----
+
+// An FP32 value as FP64 from its bit fields (exact for normal values; zero
+// and subnormals give a signed zero, infinities and NaN stay what they are).
+__device__ __forceinline__ double f32_as_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
+  if (ex == 0) return __longlong_as_double((long long)sgn);
+  const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);  // 1023 - 127
+  return __longlong_as_double((long long)(sgn | (e64 << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// x = hi + lo to 48 significant bits
+__device__ __forceinline__ float2 split_f64(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - f32_as_f64(h)));
+}
+
+// (hi, lo) += a b: the product's exact FP32 error and both cross terms go to
+// lo (a.lo b.lo, 2^-48 relative, is dropped); hi + p by Knuth's two-sum.
+// The _rn intrinsics keep the compiler from fusing the error-free steps.
+__device__ __forceinline__ void df_fma(float2 a, float2 b, float& hi, float& lo) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// (hi, lo) <- hi + lo renormalised (|hi| >= |lo| or hi = 0 after a chunk)
+__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
+
 template <int BM, int BN, int TM, int TN>
 struct Tile {
   static constexpr int kBM = BM, kBN = BN, kTM = TM, kTN = TN;
@@ -118,6 +159,10 @@ struct Tile {
   struct Smem {
     double a[GT_BK][BM + 1];
     double b[GT_BK][BN + 1];
+  };
+  struct SmemDf {  // the same tiles as float pairs (double-float mode)
+    float2 a[GT_BK][BM + 1];
+    float2 b[GT_BK][BN + 1];
   };
 };
 
@@ -177,6 +222,70 @@ __device__ __forceinline__ void gemm_mainloop(double (&acc)[T::kTM][T::kTN], typ
     mma_slice<T>(acc, s);
     __syncthreads();
   }
+}
+
+// The double-float form of the main loop: each operand element is split
+// into a float pair as it is staged (hi = fl32(x), lo = fl32(x - hi)), the
+// products accumulate in (hi, lo) pairs on the FP32 pipe (df_fma),
+// renormalised after every K slice, and acc = hi + lo in FP64 at the end
+// (about 2^-46 relative per product sum instead of 2^-53).
+template <int NT, int ROWS, class Op>
+__device__ __forceinline__ void load_slice_df(float2 (*sm)[ROWS + 1], const Op& op, int row0, int k0, int kend) {
+  const int t = threadIdx.x;
+  constexpr int PER = (ROWS * GT_BK + NT - 1) / NT;
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    int idx = t + s * NT;
+    if (idx >= ROWS * GT_BK) break;
+    int r, k;
+    if (!Op::kcontig) {
+      r = idx % ROWS;
+      k = idx / ROWS;
+    } else {
+      k = idx % GT_BK;
+      r = idx / GT_BK;
+    }
+    int gr = row0 + r, gk = k0 + k;
+    sm[k][r] = (gr < op.rows && gk < kend) ? split_f64(op.get(gr, gk)) : make_float2(0.0f, 0.0f);
+  }
+}
+
+template <class T, class OpA, class OpB>
+__device__ __forceinline__ void gemm_mainloop_df(double (&acc)[T::kTM][T::kTN], typename T::SmemDf& s,
+                                                 const OpA& A, const OpB& B, int m0, int n0, int kbeg,
+                                                 int kend) {
+  const int tx = threadIdx.x % T::XT, ty = threadIdx.x / T::XT;
+  float hi[T::kTM][T::kTN], lo[T::kTM][T::kTN];
+#pragma unroll
+  for (int i = 0; i < T::kTM; ++i)
+#pragma unroll
+    for (int j = 0; j < T::kTN; ++j) hi[i][j] = lo[i][j] = 0.0f;
+  for (int k0 = kbeg; k0 < kend; k0 += GT_BK) {
+    load_slice_df<T::NT, T::kBM>(s.a, A, m0, k0, kend);
+    load_slice_df<T::NT, T::kBN>(s.b, B, n0, k0, kend);
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < GT_BK; ++kk) {
+      float2 a[T::kTM], b[T::kTN];
+#pragma unroll
+      for (int i = 0; i < T::kTM; ++i) a[i] = s.a[kk][tx + T::XT * i];
+#pragma unroll
+      for (int j = 0; j < T::kTN; ++j) b[j] = s.b[kk][ty + T::YT * j];
+#pragma unroll
+      for (int i = 0; i < T::kTM; ++i)
+#pragma unroll
+        for (int j = 0; j < T::kTN; ++j) df_fma(a[i], b[j], hi[i][j], lo[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < T::kTM; ++i)
+#pragma unroll
+      for (int j = 0; j < T::kTN; ++j) df_renorm(hi[i][j], lo[i][j]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < T::kTM; ++i)
+#pragma unroll
+    for (int j = 0; j < T::kTN; ++j) acc[i][j] = f32_as_f64(hi[i][j]) + f32_as_f64(lo[i][j]);
 }
 
 template <class T>

@@ -30,47 +30,6 @@ namespace isdf {
 
 constexpr int CB = 64;
 
-// ---- double-float helpers ---------------------------------------------------
-
-// An FP32 value as FP64 from its bit fields (exact for normal values; zero
-// and subnormals give a signed zero, infinities and NaN stay what they are).
-__device__ __forceinline__ double f32_as_f64(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned ex = (b >> 23) & 0xffu;
-  const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
-  if (ex == 0) return __longlong_as_double((long long)sgn);
-  const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);  // 1023 - 127
-  return __longlong_as_double((long long)(sgn | (e64 << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
-}
-
-// x = hi + lo to 48 significant bits
-__device__ __forceinline__ float2 split_f64(double x) {
-  const float h = __double2float_rn(x);
-  return make_float2(h, __double2float_rn(x - f32_as_f64(h)));
-}
-
-// (hi, lo) += a b: the product's exact FP32 error and both cross terms go to
-// lo (a.lo b.lo, 2^-48 relative, is dropped); hi + p by Knuth's two-sum.
-// The _rn intrinsics keep the compiler from fusing the error-free steps.
-__device__ __forceinline__ void df_fma(float2 a, float2 b, float& hi, float& lo) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  const float s = __fadd_rn(hi, p);
-  const float v = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, e));
-}
-
-// (hi, lo) <- hi + lo renormalised (|hi| >= |lo| or hi = 0 after a chunk)
-__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
-  const float s = __fadd_rn(hi, lo);
-  lo = __fsub_rn(lo, __fsub_rn(s, hi));
-  hi = s;
-}
-
 __global__ void k_diag_max(const double* __restrict__ W, long long ldw, int n, double* out, int* fail,
                            long long sW = 0) {
   __shared__ double red[256];
@@ -482,6 +441,7 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
                                         double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev,
                                         float2* split) {
   if (n <= 0) return cudaSuccess;
+  DfGemm df(split != nullptr);  // the inverse rows in the same arithmetic as the trailing updates
   cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, n * sizeof(double), n, aux);
   if (e != cudaSuccess) return e;
   if (L != W) {

@@ -3,11 +3,15 @@
 // polarizability C Omega^-1 C^T with on-the-fly pair operands, and a blocked
 // in-place right triangular solve.
 #include <atomic>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
 
 namespace isdf {
+
+thread_local bool tl_gemm_df = false;
+
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -200,11 +204,11 @@ __device__ __forceinline__ void store_tile(const double (&acc)[T::kTM][T::kTN], 
   }
 }
 
-template <class T, class OpA, class OpB>
+template <class T, class OpA, class OpB, bool DF>
 __global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int K, int klen,
                                                 double alpha, double beta, double* C, long long ldc,
                                                 double* partial, int lower_only, int tri) {
-  __shared__ typename T::Smem s;
+  __shared__ typename std::conditional<DF, typename T::SmemDf, typename T::Smem>::type s;
   int mt, nt;
   if (lower_only) {
     lower_tile(blockIdx.x, mt, nt);
@@ -221,7 +225,11 @@ __global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int 
   if (tri & TRI_A_LOWER) kend = min(kend, m0 + T::kBM);
   double acc[T::kTM][T::kTN];
   zero_acc<T>(acc);
-  gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  if constexpr (DF) {
+    gemm_mainloop_df<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  } else {
+    gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  }
   if (partial) {
     double* P = partial + (long long)blockIdx.z * M * N;
     store_tile<T>(acc, m0, n0, M, N, 1.0, 0.0, P, M, false);
@@ -254,10 +262,10 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, 
   C[m + ldc * n] = v;
 }
 
-template <class T, class OpA, class OpB>
+template <class T, class OpA, class OpB, bool DF>
 __global__ void __launch_bounds__(T::NT) k_gemm_batched(OpA A, OpB B, GemmBatch bt, int M, int N, int K, double alpha,
                                                         double beta, double* C, long long ldc, int tri, int lower) {
-  __shared__ typename T::Smem s;
+  __shared__ typename std::conditional<DF, typename T::SmemDf, typename T::Smem>::type s;
   const int z = blockIdx.z;
   const int z1 = z % bt.b1, z2 = z / bt.b1;
   A.p += bt.sA1 * z1 + bt.sA2 * z2;
@@ -275,7 +283,11 @@ __global__ void __launch_bounds__(T::NT) k_gemm_batched(OpA A, OpB B, GemmBatch 
   const int kend = (tri & TRI_A_LOWER) ? min(K, m0 + T::kBM) : K;
   double acc[T::kTM][T::kTN];
   zero_acc<T>(acc);
-  gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  if constexpr (DF) {
+    gemm_mainloop_df<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  } else {
+    gemm_mainloop<T>(acc, s, A, B, m0, n0, kbeg, kend);
+  }
   store_tile<T>(acc, m0, n0, M, N, alpha, beta, C, ldc, lower && mt != nt);
 }
 
@@ -304,10 +316,15 @@ static cudaError_t gemm_batched_dispatch(const double* A, long long lda, const d
   const int tm = (M + T::kBM - 1) / T::kBM;
   const int nb = bt.b1 * bt.b2;
   dim3 grid = lower ? dim3(tm * (tm + 1) / 2, 1, nb) : dim3(tm, (N + T::kBN - 1) / T::kBN, nb);
-  KernelTimer kt(KF_FP64_GEMM, s, 2.0 * nb * gemm_terms(M, N, K, lower, tri));
+  KernelTimer kt(tl_gemm_df ? KF_DF_GEMM : KF_FP64_GEMM, s, 2.0 * nb * gemm_terms(M, N, K, lower, tri));
   note_launch();
-  k_gemm_batched<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(Operand<KA>{A, lda, M}, Operand<KB>{B, ldb, N},
-                                                                    bt, M, N, K, alpha, beta, C, ldc, tri, lower);
+  if (tl_gemm_df) {
+    k_gemm_batched<T, Operand<KA>, Operand<KB>, true><<<grid, T::NT, 0, s>>>(
+        Operand<KA>{A, lda, M}, Operand<KB>{B, ldb, N}, bt, M, N, K, alpha, beta, C, ldc, tri, lower);
+  } else {
+    k_gemm_batched<T, Operand<KA>, Operand<KB>, false><<<grid, T::NT, 0, s>>>(
+        Operand<KA>{A, lda, M}, Operand<KB>{B, ldb, N}, bt, M, N, K, alpha, beta, C, ldc, tri, lower);
+  }
   return cudaGetLastError();
 }
 
@@ -375,11 +392,17 @@ static cudaError_t gemm_dispatch(const double* A, long long lda, const double* B
   }
   cudaError_t e;
   {
-    KernelTimer kt(KF_FP64_GEMM, s, 2.0 * gemm_terms(M, N, K, lower_only, tri));
+    KernelTimer kt(tl_gemm_df ? KF_DF_GEMM : KF_FP64_GEMM, s, 2.0 * gemm_terms(M, N, K, lower_only, tri));
     note_launch();
-    k_gemm<T, Operand<KA>, Operand<KB>><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
-                                                              use_partial ? partial : nullptr,
-                                                              lower_only ? 1 : 0, tri);
+    if (tl_gemm_df) {
+      k_gemm<T, Operand<KA>, Operand<KB>, true><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
+                                                                      use_partial ? partial : nullptr,
+                                                                      lower_only ? 1 : 0, tri);
+    } else {
+      k_gemm<T, Operand<KA>, Operand<KB>, false><<<grid, T::NT, 0, s>>>(oa, ob, M, N, K, klen, alpha, beta, C, ldc,
+                                                                       use_partial ? partial : nullptr,
+                                                                       lower_only ? 1 : 0, tri);
+    }
     e = cudaGetLastError();
   }
   if (e != cudaSuccess || !use_partial) return e;

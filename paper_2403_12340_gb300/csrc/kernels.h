@@ -24,6 +24,16 @@ extern thread_local bool tl_capture;
 // free (0: none), so that latency-bound FP64 kernels queued on another
 // stream keep running beside it (k_tc_gemm.cu; TcSmReserve sets it).
 extern thread_local int tl_tc_sm_reserve;
+// While a DfGemm scope with `on` is alive on this thread, the tiled GEMMs
+// (launch_gemm, launch_gemm_batched, launch_gemm_batched2) run their
+// products in double-float arithmetic on the FP32 pipe (about 2^-46
+// relative per product sum; the mixed path's triangular inverses).
+extern thread_local bool tl_gemm_df;
+struct DfGemm {
+  bool prev;
+  explicit DfGemm(bool on) : prev(tl_gemm_df) { tl_gemm_df = on; }
+  ~DfGemm() { tl_gemm_df = prev; }
+};
 struct TcSmReserve {
   int prev;
   explicit TcSmReserve(int n) : prev(tl_tc_sm_reserve) { tl_tc_sm_reserve = n; }

@@ -325,7 +325,10 @@ cudaError_t mixed_smw_batched(isdf_ctx* c, int nw, int* fail_T) {
   // T = U U^T (FP64), U^-1, Q = R U^-T, K = -Q Q^T
   MK(launch_cholesky_blocked_batched(c->bT.p, r, srr, r, nw, 0.0, c->bU.p, r, srr, c->b_cb.p, fail_T, st,
                                      reinterpret_cast<float2*>(c->b_split.p)));
-  MK(launch_tri_inverse_batched(c->bU.p, r, srr, r, nw, c->bQ.p, r, srr, c->b_work.p, st));
+  {
+    DfGemm df(true);
+    MK(launch_tri_inverse_batched(c->bU.p, r, srr, r, nw, c->bQ.p, r, srr, c->b_work.p, st));
+  }
   MK(slices_cm_b(c->b_s1, R, r, srr, r, r, rp, rk, nw, st));
   MK(slices_cm_b(c->b_s2, c->bQ.p, r, srr, r, r, rp, rk, nw, st));
   MK(tc_gemm_f64_batched(op(c->b_s1, rp, rk), op(c->b_s2, rp, rk), r, r, 1.0, 0.0, c->bW1.p, r, false, true, nullptr,
