@@ -80,9 +80,12 @@ enum {
  * the fit as a GEMM with the FP64 inverse factor, G, D and the capacitance
  * products, theta^T X and theta T) on the tensor cores with operands cut into
  * three BF16 slices and FP32 accumulation, the Coulomb transform of theta
- * in FP32; the Cholesky factorisations, triangular inverses and the FFT of
- * the probe block stay in FP64.  Results agree with FP64 to about 1e-6
- * relative on well-conditioned systems. */
+ * in FP32; the Cholesky factorisations and triangular inverses keep FP64
+ * storage, FP64 diagonal blocks and panels, with their trailing updates and
+ * block-row GEMMs in double-float arithmetic on the FP32 pipe (float pairs,
+ * about 2^-46 relative per product sum); the FFT of the probe block stays in
+ * FP64.  Results agree with FP64 to about 1e-6 relative on well-conditioned
+ * systems. */
 enum { ISDF_PREC_FP64 = 0, ISDF_PREC_MIXED = 1, ISDF_PREC_MIXED_PAIRS = 2 };
 /* MIXED whitens D as L_r^-1 (C_r Omega^-1 C_r^T) L_r^-T, which multiplies
  * the FP32-grade error of the pair products by cond(C C^T); when the fit's
@@ -415,7 +418,7 @@ enum {
   ISDF_KF_CHOL_DIAG = 2, /* 64 x 64 diagonal-block Cholesky + inverse; work = flops */
   ISDF_KF_FFT = 3,       /* batched 3-D FFTs; work = bytes (input read + output write) */
   ISDF_KF_SLICE = 4,     /* FP64 -> BF16 slicing; work = bytes */
-  ISDF_KF_DF_GEMM = 5,   /* double-float Cholesky trailing updates on the FP32 pipe (mixed path); work = flops */
+  ISDF_KF_DF_GEMM = 5,   /* double-float trailing updates and inverse GEMMs on the FP32 pipe (mixed path); work = flops */
   ISDF_NUM_KERNEL_FAMILIES = 6
 };
 /* Synchronises the device, then writes per (family, phase) cell, index
