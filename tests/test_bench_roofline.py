@@ -1,0 +1,36 @@
+"""Host logic of bench.py's roofline cells: each kernel family is measured
+against the peak of the unit that bounds it, achieved = work per launch /
+average launch time, frac = achieved / peak.  CPU only."""
+import pytest
+
+import bench
+
+PEAKS = {"hbm_gbs": 6779.0, "bf16_tflops": 1936.2, "source": "of measured"}
+
+
+@pytest.mark.parametrize("fam,bound,unit,peak", [
+    ("tc_gemm", "tensor", "TFLOP/s", PEAKS["bf16_tflops"]),
+    ("fp64_gemm", "alu", "TFLOP/s", bench.FP64_PEAK_TFLOPS),
+    ("chol_diag", "alu", "TFLOP/s", bench.FP64_PEAK_TFLOPS),
+    ("df_gemm", "alu", "TFLOP/s", bench.DF_PEAK_TFLOPS),
+    ("fft", "hbm", "GB/s", PEAKS["hbm_gbs"]),
+    ("slice", "hbm", "GB/s", PEAKS["hbm_gbs"]),
+])
+def test_cell_units_and_fraction(fam, bound, unit, peak):
+    # 20 launches over 2 steps, 10 ms in all, 3e12 flops (or 3e10 bytes) of work
+    work = 3e12 if unit == "TFLOP/s" else 3e10
+    c = bench.kernel_roofline(fam, "smw", 10.0, 20, work, 2, PEAKS)
+    assert c["kernel"] == f"{fam}:smw"
+    assert c["bound"] == bound and c["unit"] == unit
+    assert c["launches_per_step"] == 10.0 and c["ms_per_step"] == 5.0 and c["ms_per_launch"] == 0.5
+    achieved = work / 0.010 / (1e12 if unit == "TFLOP/s" else 1e9)
+    assert c["achieved"] == pytest.approx(achieved, rel=1e-3)
+    assert c["peak"] == pytest.approx(peak, rel=1e-4)
+    assert c["frac"] == pytest.approx(achieved / peak, rel=1e-3)
+    assert c["traffic"] is None
+
+
+def test_derived_peaks():
+    # 152 SMs at 2070 MHz: 4 FP64 flop/clk; 128 FP32 lanes / 12 instructions x 2 flops
+    assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.2586, rel=1e-4)
+    assert bench.DF_PEAK_TFLOPS == pytest.approx(6.7123, rel=1e-4)
