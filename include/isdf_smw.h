@@ -85,7 +85,9 @@ enum {
  * block-row GEMMs in double-float arithmetic on the FP32 pipe (float pairs,
  * about 2^-46 relative per product sum); the FFT of the probe block stays in
  * FP64.  Results agree with FP64 to about 1e-6 relative on well-conditioned
- * systems. */
+ * systems.  Both the BF16 slices and the float pairs keep FP32's exponent
+ * range: entries of the matrices they carry must lie within about 1e-30 to
+ * 1e30 in magnitude (or be zero); use FP64 for inputs scaled beyond it. */
 enum { ISDF_PREC_FP64 = 0, ISDF_PREC_MIXED = 1, ISDF_PREC_MIXED_PAIRS = 2 };
 /* MIXED whitens D as L_r^-1 (C_r Omega^-1 C_r^T) L_r^-T, which multiplies
  * the FP32-grade error of the pair products by cond(C C^T); when the fit's
