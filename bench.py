@@ -110,7 +110,10 @@ def kernel_roofline(fam, phase, ms, cnt, work, steps, peaks):
 
 def algorithmic_flops(n_r, n_e, pairs, r, n_rhs, n_half2):
     """Flops each phase performs by the arithmetic of the method (not counting
-    padding or wasted tile work): GEMM 2mnk, SYRK mnk... see the design doc."""
+    padding, wasted tile work or the extra products of the split precision):
+    a GEMM m x n x k counts 2 m n k, a SYRK (lower triangle) m^2 k, a
+    triangular solve m n^2, a Cholesky n^3 / 3 and a real 3-D FFT of length
+    N 2.5 N log2 N per column (half of the complex 5 N log2 N)."""
     log2nr = math.log2(n_r)
     return {
         "points_chol": 2.0 * r * r * n_e + r ** 3 / 3.0,
