@@ -116,7 +116,11 @@ ISDF_API int isdf_destroy(isdf_ctx* ctx);
  *            orbitals, the first n_v occupied.  Read now and by
  *            build_polarizability.
  *   n_v,n_c  numbers of occupied / unoccupied orbitals (>= 1 each).
- *   mu_idx   host, n_mu int64 grid indices in [0, N_r), distinct.
+ *   mu_idx   host or device (told apart by cudaPointerGetAttributes), n_mu
+ *            int64 grid indices in [0, N_r), distinct.  A device array is
+ *            read after the context stream has synchronised, then copied to
+ *            the host, where the indices are checked and the pivot order is
+ *            kept; not a device array while a graph is captured.
  *   n_mu     number of interpolation points, 1 <= n_mu <= N_r.
  *   prec     ISDF_PREC_FP64 or ISDF_PREC_MIXED; later calls use the same mode.
  *   theta    device, N_r x n_mu float64 out (ld = N_r); must not alias phi.
@@ -194,15 +198,20 @@ ISDF_API int apply_eps_inv(isdf_ctx* ctx, int omega_index, const double* X, int 
  * a component that is not allowed to own memory.  Everything else needed
  * (theta, K, the Coulomb tables) was allocated earlier by isdf_create,
  * isdf_fit and build_polarizability.
- *   Arguments and result: as apply_eps_inv (same kernels, same numbers up to
- *   the order of the split-K sums).
+ *   Arguments and result: as apply_eps_inv.  The arithmetic is always FP64:
+ *   on an FP64 context it is the same kernels as apply_eps_inv (same numbers
+ *   up to the order of the split-K sums); on a MIXED context it applies the
+ *   context's FP64 theta and K with those FP64 kernels, while apply_eps_inv
+ *   there runs theta^T X and theta T on the tensor cores, so the two agree
+ *   to the mixed path's accuracy (about 1e-7 relative), not bit for bit.
  *   Scratch: a file-scope device array of 8 MiB (2^20 doubles), one per GPU
  *   that loads this library, held until the process exits.  A probe column
  *   needs 2 N_mu + N_r + 2 h n2 n3 + 64 N_mu doubles (h = n1/2 + 1, each
  *   term rounded up to 256 bytes); columns are processed as many at a time
  *   as fit.  If one column does not fit the call returns ISDF_ERR_SHAPE and
  *   writes nothing (apply_eps_inv has no such limit).
- *   The first call on a device looks up the array's device address
+ *   The first call on a device (and the first after a cudaDeviceReset, which
+ *   gives the device a new CUDA context) looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.
  *   Every call on a device shares the one array and leaves its contents
@@ -435,6 +444,22 @@ ISDF_API const char* isdf_kernel_family_name(int family);
 /* Number of kernel launches issued by this library in this process so far
  * (all contexts). */
 ISDF_API long long isdf_launch_count(void);
+/* Number of device allocations (cudaMalloc / cudaMallocAsync) this library
+ * has made in this process so far (all contexts and threads).  The paper
+ * has no counterpart; it lets a caller check that a call allocated nothing. */
+ISDF_API long long isdf_device_allocations(void);
+
+/* Diagnostic of the bounded device-side waits (the paper has no
+ * counterpart).  Runs the library's grid barrier (the wait of the pivoted
+ * factorisation's cooperative kernel) on the context stream with a barrier
+ * that is never completed: its arrival counter is preset past the grid
+ * size, so no block is the last to arrive.  Each block gives up after
+ * limit_ns nanoseconds (1e3 .. 1e10), the kernel returns, and the call
+ * reports ISDF_ERR_TIMEOUT as any entry point does when one of its device
+ * waits runs out.  The barrier and the status word are then cleared, so the
+ * context stays usable.  A return of ISDF_ERR_STATE means the barrier
+ * completed, i.e. the bound failed.  Synchronises the context stream. */
+ISDF_API int isdf_check_device_wait(isdf_ctx* ctx, long long limit_ns);
 
 /* Message for the last error on this context ("" if none).  With ctx NULL,
  * the last error of isdf_create on this thread. */

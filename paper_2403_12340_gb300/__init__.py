@@ -39,7 +39,7 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error",
             "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex", "isdf_batch_capture",
             "isdf_batch_replay", "isdf_set_autotune", "isdf_autotune_size", "isdf_autotune_entry",
-            "isdf_autotune_clear"]
+            "isdf_autotune_clear", "isdf_device_allocations", "isdf_check_device_wait"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 6
 
@@ -121,6 +121,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_kernel_family_name.restype = ctypes.c_char_p
     lib.isdf_launch_count.argtypes = []
     lib.isdf_launch_count.restype = ctypes.c_longlong
+    lib.isdf_check_device_wait.argtypes = [P, ctypes.c_longlong]
+    lib.isdf_check_device_wait.restype = I
+    lib.isdf_device_allocations.argtypes = []
+    lib.isdf_device_allocations.restype = ctypes.c_longlong
     for name in ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "smw_inverse",
                  "apply_eps_inv", "isdf_fit_factor", "isdf_set_profiling", "isdf_read_profile"]:
         getattr(lib, name).restype = I
@@ -199,14 +203,28 @@ def isdf_destroy(ctx) -> None:
     _check(load_library().isdf_destroy(ctx), None)
 
 
+def _is_cuda_tensor(t) -> bool:
+    return type(t).__module__.startswith("torch") and getattr(t, "is_cuda", False)
+
+
 def isdf_fit(ctx, phi, n_v: int, n_c: int, mu_idx, theta, n_r: int, prec: int = ISDF_PREC_FP64) -> int:
-    """ISDF fit; writes theta (N_r x N_mu) and returns the numerical rank."""
-    mu = np.ascontiguousarray(np.asarray(mu_idx, dtype=np.int64))
+    """ISDF fit; writes theta (N_r x N_mu) and returns the numerical rank.
+    mu_idx: host indices (anything numpy takes) or a contiguous int64 CUDA
+    tensor, which the library reads from device memory."""
+    if _is_cuda_tensor(mu_idx):
+        import torch
+
+        if mu_idx.dtype != torch.int64 or mu_idx.dim() != 1 or not mu_idx.is_contiguous():
+            raise TypeError("mu_idx on the device must be a contiguous 1-D int64 tensor")
+        pm, n_mu, keep = mu_idx.data_ptr(), int(mu_idx.shape[0]), mu_idx
+    else:
+        keep = np.ascontiguousarray(np.asarray(mu_idx, dtype=np.int64))
+        pm, n_mu = keep.ctypes.data, int(keep.shape[0])
     pp = _dev_ptr(phi, n_r, n_v + n_c, "phi")
-    pt = _dev_ptr(theta, n_r, mu.shape[0], "theta")
+    pt = _dev_ptr(theta, n_r, n_mu, "theta")
     rank = ctypes.c_int(0)
-    _check(load_library().isdf_fit(ctx, pp, int(n_v), int(n_c), mu.ctypes.data, int(mu.shape[0]),
-                                   int(prec), pt, ctypes.byref(rank)), ctx)
+    _check(load_library().isdf_fit(ctx, pp, int(n_v), int(n_c), pm, n_mu, int(prec), pt, ctypes.byref(rank)), ctx)
+    del keep
     return rank.value
 
 
@@ -365,6 +383,18 @@ def isdf_launch_count() -> int:
     return int(load_library().isdf_launch_count())
 
 
+def isdf_check_device_wait(ctx, limit_ns: int) -> int:
+    """Run the library's bounded grid barrier on a barrier that never
+    completes; returns the status code (ISDF_ERR_TIMEOUT, -7, when the bound
+    works) without raising."""
+    return int(load_library().isdf_check_device_wait(ctx, int(limit_ns)))
+
+
+def isdf_device_allocations() -> int:
+    """Device allocations the library has made in this process so far."""
+    return int(load_library().isdf_device_allocations())
+
+
 class IsdfSmw:
     """One context bound to one grid; thin convenience over the C ABI."""
 
@@ -397,11 +427,11 @@ class IsdfSmw:
             pass
 
     def fit(self, phi, n_v, n_c, mu_idx, theta=None, prec=ISDF_PREC_FP64):
-        mu = np.asarray(mu_idx, dtype=np.int64)
+        mu = mu_idx if _is_cuda_tensor(mu_idx) else np.asarray(mu_idx, dtype=np.int64)
         if theta is None:
             theta = fortran_empty(self.n_r, mu.shape[0], phi.device)
         self.rank = isdf_fit(self.ctx, phi, n_v, n_c, mu, theta, self.n_r, prec)
-        self.n_mu = mu.shape[0]
+        self.n_mu = int(mu.shape[0])
         self.theta = theta
         return theta, self.rank
 

@@ -75,7 +75,7 @@ cudaError_t isdf::ensure(DevBuf& b, size_t n) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;
-  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(n, 1) * sizeof(double));
+  cudaError_t e = isdf::dev_malloc(&b.p, std::max<size_t>(n, 1) * sizeof(double));
   if (e == cudaSuccess) b.cap = n;
   return e;
 }
@@ -212,14 +212,14 @@ extern "C" int isdf_create(isdf_ctx** out, int n1, int n2, int n3, double L1, do
         tab[ntw + q] = std::sqrt(wx * vg / ((double)c->n_r * c->dv));
         tab[ntw + nh + q] = vg / (c->dv * (double)c->n_r);
       }
-  e = cudaMalloc(&c->d_tables, tab.size() * sizeof(double));
+  e = isdf::dev_malloc(&c->d_tables, tab.size() * sizeof(double));
   if (e != cudaSuccess) return bail(e, "cudaMalloc tables");
   e = cudaMemcpy(c->d_tables, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(e, "cudaMemcpy tables");
   for (int a = 0; a < 3; ++a) c->fft.ax[a].tw = c->d_tables + tw_off[a];
   c->d_wsyrk = c->d_tables + ntw;
   c->d_wconv = c->d_tables + ntw + nh;
-  e = cudaMalloc(&c->d_status, 64 * sizeof(unsigned));
+  e = isdf::dev_malloc(&c->d_status, 64 * sizeof(unsigned));
   if (e != cudaSuccess) return bail(e, "cudaMalloc status");
   {
     int lo = 0, hi = 0;
@@ -263,7 +263,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
+                    &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
@@ -286,7 +286,7 @@ static cudaError_t ensure_ints(int*& p, size_t& cap, size_t n) {
   if (p) cudaFree(p);
   p = nullptr;
   cap = 0;
-  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(int));
+  cudaError_t e = isdf::dev_malloc(&p, std::max<size_t>(n, 1) * sizeof(int));
   if (e == cudaSuccess) cap = n;
   return e;
 }
@@ -301,7 +301,7 @@ static int cholesky(isdf_ctx* c, const double* W, long long ldw, int n, int pivo
   size_t cap_used = c->cap_used;
   CK(ensure_ints(c->d_used, cap_used, (size_t)n));
   c->cap_used = cap_used;
-  if (!c->d_part_idx) CK(cudaMalloc(&c->d_part_idx, 2 * kMaxGrid * sizeof(int)));
+  if (!c->d_part_idx) CK(isdf::dev_malloc(&c->d_part_idx, 2 * kMaxGrid * sizeof(int)));
   CholWork w{c->chol_d.p, c->chol_part.p, c->d_part_idx, c->d_used, c->d_bar, kMaxGrid};
   CK(cudaMemsetAsync(c->d_ints, 0, sizeof(int), c->stream));
   CK(launch_cholesky(W, ldw, n, pivot, tol_rel, c->Lr.p, d_perm, c->d_ints, c->d_status, w,
@@ -372,6 +372,23 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   const double* tend = theta + c->n_r * n_mu;
   const double* pend = phi + c->n_r * (long long)(n_v + n_c);
   if (theta < pend && phi < tend) return fail(c, ISDF_ERR_ARG, "isdf_fit: theta overlaps phi");
+  // the points may sit in host or in device memory; the checks and the pivot
+  // bookkeeping below are host work, so a device array is copied over first
+  // (the fit synchronises the stream once anyway)
+  std::vector<int64_t> mu_host;
+  {
+    cudaPointerAttributes at{};
+    const cudaError_t pe = cudaPointerGetAttributes(&at, mu_idx);
+    if (pe != cudaSuccess) cudaGetLastError();  // an unknown host pointer on an old runtime: host memory
+    if (pe == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+      if (isdf::tl_capture)
+        return fail(c, ISDF_ERR_STATE, "isdf_fit: a captured fit takes its points from host memory");
+      mu_host.resize(n_mu);
+      CK(cudaStreamSynchronize(c->stream));  // the caller may have written the points on this stream
+      CK(cudaMemcpy(mu_host.data(), mu_idx, (size_t)n_mu * sizeof(int64_t), cudaMemcpyDefault));
+      mu_idx = mu_host.data();
+    }
+  }
   std::vector<int64_t> sorted(mu_idx, mu_idx + n_mu);
   std::sort(sorted.begin(), sorted.end());
   if (sorted.front() < 0 || sorted.back() >= c->n_r)
@@ -614,7 +631,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     if (c->d_fail) cudaFree(c->d_fail);
     c->d_fail = nullptr;
     c->cap_fail = 0;
-    CK(cudaMalloc(&c->d_fail, n_omega * sizeof(int)));
+    CK(isdf::dev_malloc(&c->d_fail, n_omega * sizeof(int)));
     c->cap_fail = n_omega;
   }
   if (r > 0) {
@@ -633,18 +650,31 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)n_omega));
     if (c->prec == ISDF_PREC_MIXED) CK(ensure(c->cb_split, (size_t)64 * r * n_omega));
     if (n_nodes > 0) CK(ensure(c->ctab, (size_t)2 * n_nodes * (n_e + 1)));
-    if (c->pair_whiten) CK(ensure(c->swf, (npair * n_omega + 1) / 2));
-    // sqrt(-2 Omega(iw)^-1) for every pair and frequency, one upload
-    std::vector<double> sw(cap ? 0 : npair * n_omega);
-    for (int k = 0; k < (cap ? 0 : n_omega); ++k) {
-      const double w2 = omega[k] * omega[k];
-      for (int i = 0; i < n_v; ++i)
-        for (int j = 0; j < n_c; ++j) {
-          double d = energies[i] - energies[n_v + j];
-          sw[npair * k + (size_t)i * n_c + j] = std::sqrt(-2.0 * d / (d * d + w2));
-        }
+    // mixed, one frequency: R^-1 and D^-1 beside the Coulomb work
+    const bool dinv = c->prec == ISDF_PREC_MIXED && n_omega == 1;
+    c->dinv_ready = false;
+    if (dinv) {
+      const int rp = (r + 127) / 128 * 128, rk = (r + 63) / 64 * 64;
+      CK(ensure(c->Rinv, rr));
+      CK(ensure(c->Dinv, rr));
+      CK(ensure_bf16(c->m_sd, (size_t)3 * rp * rk));
+      int rc0 = chol_inverse_workspace(c, r);
+      if (rc0 != ISDF_OK) return rc0;
     }
-    if (!cap) CK(cudaMemcpyAsync(c->sw.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (c->pair_whiten) CK(ensure(c->swf, (npair * n_omega + 1) / 2));
+    CK(ensure(c->ew, (size_t)n_e + n_omega));
+    // sqrt(-2 Omega(iw)^-1) for every pair and frequency, on the device from
+    // the energies and frequencies (one small upload; a captured call reuses
+    // the eager call's, which are the same)
+    if (!cap) {
+      c->ew_host.assign(energies, energies + n_e);
+      c->ew_host.insert(c->ew_host.end(), omega, omega + n_omega);
+      CK(cudaMemcpyAsync(c->ew.p, c->ew_host.data(), c->ew_host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream));
+    }
+    CK(launch_pair_weights(c->ew.p, n_v, n_c, n_omega, c->sw.p,
+                           c->prec == ISDF_PREC_MIXED && c->pair_whiten ? reinterpret_cast<float*>(c->swf.p) : nullptr,
+                           c->stream));
     // D(w) for every frequency (main stream)
     if (n_nodes > 0) {
       // static D by the contour integral: resolvent weights of every node
@@ -672,11 +702,6 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
         CK(cudaMemcpyAsync(c->D.p, c->tmp1.p, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       }
     } else if (c->prec == ISDF_PREC_MIXED && c->pair_whiten) {
-      if (!cap) {
-        std::vector<float> swf(sw.begin(), sw.end());
-        CK(cudaMemcpyAsync(c->swf.p, swf.data(), swf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
-      }
       CK(isdf::mixed_polar_D_pairspace(c, reinterpret_cast<const float*>(c->swf.p), n_omega));
     } else if (c->prec == ISDF_PREC_MIXED) {
       if (n_omega > 1) {
@@ -708,6 +733,16 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
       if (n_omega > 1) {  // all frequencies in one factorisation sequence
         CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr,
                                            c->b_cbd.p, c->d_fail, c->s2, split_panel(c, (size_t)64 * r * n_omega)));
+      } else if (dinv) {
+        // D = R R^T with R^-1 built on the third stream beside it, then
+        // D^-1 = R^-T R^-1 for the capacitance K = -(D^-1 + G)^-1
+        CK(cudaStreamWaitEvent(c->s3, c->ev_fork, 0));
+        CK(launch_cholesky_and_inverse(c->D.p, r, r, 0.0, c->Rw.p, r, c->Rinv.p, r, c->cb_work.p, c->d_fail,
+                                       c->inv_work.p, c->s2, c->s3, c->ev_chol.data(),
+                                       reinterpret_cast<float2*>(c->cb_split.p)));
+        CK(cudaEventRecord(c->ev_join3, c->s3));
+        CK(cudaStreamWaitEvent(c->s2, c->ev_join3, 0));
+        CK(isdf::mixed_dinv(c, c->s2));
       } else {
         rc0 = cholesky_blocked(c, c->D.p, r, r, 0.0, c->Rw.p, c->d_fail, c->s2);
         if (rc0 != ISDF_OK) return rc0;
@@ -748,6 +783,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
   c->energies.assign(energies, energies + n_e);
   c->k_ready.assign(n_omega, 0);
   c->polar_ready = true;
+  c->dinv_ready = c->prec == ISDF_PREC_MIXED && n_omega == 1 && r > 0;
   c->polar_whiten = c->pair_whiten;
   c->polar_nodes = n_nodes;
   return ISDF_OK;
@@ -787,6 +823,20 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
   long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
   int sp = split_for(tiles, std::max(r, 1), c->num_sms);
   PhaseScope ph(c, ISDF_PH_SMW);
+  if (c->prec == ISDF_PREC_MIXED && c->dinv_ready) {
+    // K = -(D^-1 + G)^-1 with D^-1 from build_polarizability: A = D^-1 + G =
+    // U U^T (U^-1 into Q on the second stream, block row by block row,
+    // beside the factorisation), K = -U^-T U^-1
+    CK(launch_add(c->Dinv.p, c->G.p, c->T.p, (long long)rr, c->stream));
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+    CK(launch_cholesky_and_inverse(c->T.p, r, r, 0.0, c->W1.p, r, c->Q.p, r, c->cb_work.p, failT, c->inv_work.p,
+                                   c->stream, c->s2, c->ev_chol.data(), reinterpret_cast<float2*>(c->cb_split.p)));
+    CK(cudaEventRecord(c->ev_join, c->s2));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    CK(isdf::mixed_k_from_uinv(c, Kk));
+    return ISDF_OK;
+  }
   // D = R R^T: factored by build_polarizability on the second stream
   CK(cudaMemcpyAsync(c->R.p, c->Rw.p + rr * k, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   // T = I + R^T G R
@@ -920,7 +970,7 @@ extern "C" int smw_inverse_all(isdf_ctx* c, double* K_out) {
     if (c->b_fail) cudaFree(c->b_fail);
     c->b_fail = nullptr;
     c->cap_bfail = 0;
-    CK(cudaMalloc(&c->b_fail, nw * sizeof(int)));
+    CK(isdf::dev_malloc(&c->b_fail, nw * sizeof(int)));
     c->cap_bfail = nw;
   }
   if (r > 0) {
@@ -999,6 +1049,25 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
   return ISDF_OK;
 }
 
+extern "C" int isdf_check_device_wait(isdf_ctx* c, long long limit_ns) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  if (limit_ns < 1000 || limit_ns > 10000000000ll)
+    return fail(c, ISDF_ERR_ARG, "isdf_check_device_wait: limit_ns must be in [1e3, 1e10]");
+  if (isdf::tl_capture) return fail(c, ISDF_ERR_STATE, "isdf_check_device_wait: not while a graph is captured");
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+  CK(launch_wait_check(c->d_bar, c->d_status, (uint64_t)limit_ns, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int rc = check_status(c, "isdf_check_device_wait");
+  // leave the barrier and the status word as a fresh context has them
+  CK(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (rc == ISDF_OK) return fail(c, ISDF_ERR_STATE, "isdf_check_device_wait: the never-completed barrier completed");
+  return rc;
+}
+
 static const char* kPhaseNames[ISDF_NUM_PHASES] = {"points_chol", "fit_gram", "fit_trsm", "coulomb_fft",
                                                    "coulomb_syrk", "polar_d", "whiten_d", "smw", "apply"};
 
@@ -1007,6 +1076,8 @@ extern "C" const char* isdf_phase_name(int phase) {
 }
 
 extern "C" long long isdf_launch_count(void) { return launch_count(); }
+
+extern "C" long long isdf_device_allocations(void) { return isdf::device_allocation_count(); }
 
 extern "C" int isdf_set_profiling(isdf_ctx* c, int on) {
   if (!c) return ISDF_ERR_ARG;

@@ -128,7 +128,7 @@ extern "C" int isdf_batch_create(isdf_batch** out, const isdf_system* systems, i
     s.d.energies = s.energies.data();
     cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     const long long nr = (long long)d.n1 * d.n2 * d.n3;
-    if (e == cudaSuccess) e = cudaMalloc(&s.theta, (size_t)nr * d.n_mu * sizeof(double));
+    if (e == cudaSuccess) e = isdf::dev_malloc(&s.theta, (size_t)nr * d.n_mu * sizeof(double));
     if (e != cudaSuccess) {
       free_batch(b);
       g_batch_create_err = std::string("isdf_batch_create: ") + cudaGetErrorString(e);

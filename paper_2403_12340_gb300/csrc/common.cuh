@@ -152,6 +152,43 @@ __device__ __forceinline__ void df_renorm(float& hi, float& lo) {
   hi = s;
 }
 
+// ---- double-float scalar arithmetic (latency-bound chains on the FP32 pipe) ----
+// A value is a float2 (x = hi, y = lo) with |lo| <= ulp(hi) / 2 after df_norm.
+
+__device__ __forceinline__ float2 df_norm(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+}
+
+__device__ __forceinline__ double df_to_f64(float2 a) { return f32_as_f64(a.x) + f32_as_f64(a.y); }
+
+// a b to about 2^-47 relative (a.lo b.lo dropped)
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return df_norm(p, e);
+}
+
+// c - a b, with the sum by Knuth's two-sum
+__device__ __forceinline__ float2 df_fms(float2 c, float2 a, float2 b) {
+  float hi = c.x, lo = c.y;
+  df_fma(make_float2(-a.x, -a.y), b, hi, lo);
+  return df_norm(hi, lo);
+}
+
+// 1 / d: the correctly rounded FP32 reciprocal of d.hi, then one Newton step
+// r + r (1 - d r) with the residual 1 - d r formed exactly from an FMA (the
+// step doubles the 24 correct bits to about 47).
+__device__ __forceinline__ float2 df_recip(float2 d) {
+  const float r = __frcp_rn(d.x);
+  const float p = __fmul_rn(d.x, r);
+  const float pe = fmaf(d.x, r, -p);
+  const float e = fmaf(-d.y, r, __fsub_rn(__fsub_rn(1.0f, p), pe));
+  return df_norm(r, __fmul_rn(r, e));
+}
+
 template <int BM, int BN, int TM, int TN>
 struct Tile {
   static constexpr int kBM = BM, kBN = BN, kTM = TM, kTN = TN;

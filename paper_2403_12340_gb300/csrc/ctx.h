@@ -104,6 +104,12 @@ struct isdf_ctx {
   DevBuf ctab;  // contour-integral polarizability: resolvent weights and node weights
   DevBuf cx[12];  // COHSEX (cohsex.cu): spectra, cross products, scratch
   DevBuf m_pairs_t, swf;  // pair-space whitening: transposed pair slices, FP32 pair weights
+  DevBuf ew;                     // energies and frequencies of the last polarizability, on the device
+  // mixed path, one frequency: R^-1 of D = R R^T, D^-1 = R^-T R^-1 and the
+  // BF16 slices of R^-1, built beside the Coulomb work of build_polarizability
+  DevBuf Rinv, Dinv, m_sd;
+  bool dinv_ready = false;
+  std::vector<double> ew_host;   // their host copy (the source of the asynchronous upload)
   bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
   int pair_mode = 0;         // the precision argument of the last fit
   DevBuf kappa_work;         // [0] ||L||_F^2, [1] ||L^-1||_F^2, [2..] reduction scratch
@@ -194,6 +200,10 @@ cudaError_t mixed_polar_G(isdf_ctx* c);
 cudaError_t mixed_smw_products_T(isdf_ctx* c);
 cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk, bool uinv_ready);
 cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc);
+// D^-1 = R^-T R^-1 from c->Rinv into c->Dinv, on stream st
+cudaError_t mixed_dinv(isdf_ctx* c, cudaStream_t st);
+// K = -U^-T U^-1 from U^-1 in c->Q into Kk
+cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk);
 // All frequencies at once: D(w_k) for k < n_omega (chunked to a memory
 // budget), and K(w_k) from the factors R(w_k) in c->Rw (T factors and
 // their failure flags in c->bU / fail_T).

@@ -222,4 +222,23 @@ cudaError_t launch_cholesky(const double* W, long long ldw, int n, int pivot, do
   return cudaLaunchCooperativeKernel((const void*)k_cholesky, dim3(blocks), dim3(256), args, 0, s);
 }
 
+// Diagnostic of the bounded grid barrier: every block enters grid_sync on a
+// barrier whose arrival counter the caller preset past the grid size, so no
+// block is the last to arrive and the generation never moves; each block
+// gives up after limit_ns, sets ST_TIMEOUT and returns.
+__global__ void k_wait_check(GridBarrier bar, unsigned* status, uint64_t limit_ns) {
+  if (!grid_sync(bar, status, limit_ns)) return;
+}
+
+cudaError_t launch_wait_check(unsigned* bar, unsigned* status, uint64_t limit_ns, cudaStream_t s) {
+  // counter 0x40404040, generation 0: no arrival count reaches gridDim - 1
+  cudaError_t e = cudaMemsetAsync(bar, 0x40, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar + 1, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  GridBarrier b{bar, bar + 1};
+  void* args[] = {&b, &status, &limit_ns};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void*)k_wait_check, dim3(2), dim3(32), args, 0, s);
+}
+
 }  // namespace isdf

@@ -161,6 +161,92 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
   }
 }
 
+// k_chol_diag in double-float arithmetic on the FP32 pipe (the mixed path):
+// the same LDL^T chain of one warp beside twelve update warps, with every
+// element a float pair (about 2^-47 relative per operation).  One dependent
+// double-float step costs a few FP32 latencies (4 cycles each) instead of
+// the FP64 pipe's ~64 cycles per dependent instruction, and the updates of
+// the twelve warps issue on the FP32 pipe at 32 lanes per cycle per
+// sub-partition.  A pivot is accepted when its high part exceeds the
+// threshold (tol_rel * max diag in FP32).  Loads split each FP64 entry
+// (hi = fl32(x), lo = fl32(x - hi)); the factor is written back in FP64.
+__global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long long lda, int j0, int bs,
+                                                              const double* dmax, double tol_rel, int* fail,
+                                                              long long sA = 0) {
+  __shared__ float2 Ls[CB][CB + 1];  // the block, unscaled LDL^T columns
+  __shared__ float2 lc[2][CB];       // l_j and l_{j-1}
+  __shared__ float2 piv[CB];         // d_j
+  __shared__ double q[CB];           // d_j^-1/2
+  __shared__ int s_bad;
+  A += sA * blockIdx.x;
+  dmax += blockIdx.x;
+  fail += blockIdx.x;
+  if (*(volatile int*)fail >= 0) return;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int idx = t; idx < CB * CB; idx += blockDim.x) {
+    int i = idx & (CB - 1), k = idx >> 6;
+    Ls[i][k] = (i < bs && k <= i) ? split_f64(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.0f, 0.0f);
+  }
+  const bool bulk = (warp & 3) != 0;
+  int own[DIAG_EPT];
+  {
+    const int b = (warp - 1 - (warp >> 2)) * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < DIAG_EPT; ++q) {
+      const int e = b + DIAG_BULK * q;
+      own[q] = -1;
+      if (bulk && e < CB * (CB + 1) / 2) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        while (a * (a + 1) / 2 > e) --a;
+        own[q] = a * CB + (e - a * (a + 1) / 2);
+      }
+    }
+  }
+  if (t == 0) s_bad = -1;
+  const float thresh = (float)(tol_rel * (*dmax));
+  __syncthreads();
+  for (int j = 0; j < bs; ++j) {
+    const float2* lp = lc[(j + 1) & 1];  // l_{j-1}
+    if (warp == 0) {
+      if (j > 0) {
+        const float2 ajj1 = Ls[j][j - 1];
+        for (int i = j + lane; i < bs; i += 32) Ls[i][j] = df_fms(Ls[i][j], lp[i], ajj1);
+        __syncwarp();
+      }
+      const float2 d = Ls[j][j];
+      if (!(d.x > thresh)) {  // the same value in every lane; also catches NaN
+        if (lane == 0) s_bad = j;
+      } else {
+        const float2 r = df_recip(d);
+        if (lane == 0) piv[j] = d;
+        float2* lj = lc[j & 1];
+        for (int i = j + 1 + lane; i < bs; i += 32) lj[i] = df_mul(Ls[i][j], r);
+      }
+    } else if (bulk && j > 0) {
+#pragma unroll
+      for (int q = 0; q < DIAG_EPT; ++q) {
+        const int o = own[q];
+        const int i = o >> 6, k = o & (CB - 1);
+        if (o >= 0 && k > j && i < bs) Ls[i][k] = df_fms(Ls[i][k], lp[i], Ls[k][j - 1]);
+      }
+    }
+    __syncthreads();
+    if (s_bad >= 0) break;
+  }
+  if (s_bad >= 0) {
+    if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
+    return;
+  }
+  if (t < bs) q[t] = rsqrt_newton(df_to_f64(piv[t]));
+  __syncthreads();
+  for (int idx = t; idx < bs * bs; idx += blockDim.x) {
+    const int i = idx % bs, k = idx / bs;
+    const double v = (k < i) ? df_to_f64(Ls[i][k]) * q[k] : (k == i ? df_to_f64(piv[i]) * q[i] : 0.0);
+    A[(j0 + i) + lda * (long long)(j0 + k)] = v;
+  }
+}
+
 // The panel below a factored diagonal block, A21 <- A21 L_jj^-T, in place:
 // one warp per row, lane l holding columns l and l + 32 of the row; forward
 // substitution by columns, each solved value broadcast by a shuffle.  Rows
@@ -206,6 +292,54 @@ __global__ void __launch_bounds__(256) k_panel_trsm(double* A, long long lda, in
       if (lane < bs) sp[lds * lane] = split_f64(x0);
       if (lane + 32 < bs) sp[lds * (lane + 32)] = split_f64(x1);
     }
+  }
+}
+
+// k_panel_trsm in double-float arithmetic (the mixed path): the diagonal
+// block and each row are split into float pairs as they are loaded, the
+// forward substitution runs on the FP32 pipe, and the solved row goes out
+// in FP64 to A and, unchanged, as the float pairs of the split panel Sp
+// that the double-float trailing update reads.
+__global__ void __launch_bounds__(256) k_panel_trsm_df(double* A, long long lda, int j0, int bs, int rem,
+                                                      const int* fail, long long sA, float2* Sp, long long lds,
+                                                      long long sS) {
+  __shared__ float2 Lt[CB][CB + 1];
+  __shared__ float2 inv[CB];
+  A += sA * blockIdx.y;
+  if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < CB * CB; idx += blockDim.x) {
+    const int i = idx & (CB - 1), k = idx >> 6;
+    Lt[i][k] = (i < bs && k <= i) ? split_f64(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  if (t < bs) inv[t] = df_recip(Lt[t][t]);
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+  const float2 zero = make_float2(0.0f, 0.0f);
+  for (int row = blockIdx.x * 8 + warp; row < rem; row += gridDim.x * 8) {
+    double* a = A + (j0 + bs + row) + lda * (long long)j0;
+    float2 x0 = lane < bs ? split_f64(a[lda * lane]) : zero;
+    float2 x1 = lane + 32 < bs ? split_f64(a[lda * (lane + 32)]) : zero;
+    for (int k = 0; k < bs; ++k) {
+      float2 xk;
+      if (k < 32) {
+        if (lane == k) x0 = df_mul(x0, inv[k]);
+        xk.x = __shfl_sync(0xffffffffu, x0.x, k);
+        xk.y = __shfl_sync(0xffffffffu, x0.y, k);
+      } else {
+        if (lane == k - 32) x1 = df_mul(x1, inv[k]);
+        xk.x = __shfl_sync(0xffffffffu, x1.x, k - 32);
+        xk.y = __shfl_sync(0xffffffffu, x1.y, k - 32);
+      }
+      if (lane > k) x0 = df_fms(x0, xk, Lt[lane][k]);
+      if (lane + 32 > k) x1 = df_fms(x1, xk, Lt[lane + 32][k]);
+    }
+    if (lane < bs) a[lda * lane] = df_to_f64(x0);
+    if (lane + 32 < bs) a[lda * (lane + 32)] = df_to_f64(x1);
+    float2* sp = Sp + sS * blockIdx.y + row;
+    if (lane < bs) sp[lds * lane] = x0;
+    if (lane + 32 < bs) sp[lds * (lane + 32)] = x1;
   }
 }
 
@@ -393,6 +527,40 @@ static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int re
   return cudaGetLastError();
 }
 
+// The mixed path (a split-panel buffer given) factors in double-float
+// arithmetic throughout; its rank test then accepts pivots above
+// 2^-40 max diag at least (double-float rounding is ~2^-47 per operation, so
+// the FP64 threshold of a rank-deficient C C^T could pass noise; a matrix
+// that fails here goes to the FP64 pivoted factorisation).
+constexpr double kDfPivotTol = 0x1p-40;
+static double df_tol(double tol_rel, const float2* split) {
+  return split && tol_rel > 0.0 ? std::max(tol_rel, kDfPivotTol) : tol_rel;
+}
+
+static cudaError_t diag_step(double* L, long long ldl, int j0, int bs, const double* dmax, double tol_rel, int* fail,
+                             long long sL, int batch, bool df, cudaStream_t s) {
+  KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0 * batch);  // bs^3 / 3 flops (FP64 or double-float)
+  note_launch();
+  if (df)
+    k_chol_diag_df<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
+  else
+    k_chol_diag<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
+  return cudaGetLastError();
+}
+
+static unsigned panel_blocks(int rem);
+
+static cudaError_t panel_step(double* L, long long ldl, int j0, int bs, int rem, const int* fail, long long sL,
+                              int batch, float2* split, long long lds, long long sS, cudaStream_t s) {
+  KernelTimer kt(split ? KF_DF_GEMM : KF_FP64_GEMM, s, (double)rem * bs * bs * batch);  // rem bs^2 flops
+  note_launch();
+  if (split)
+    k_panel_trsm_df<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, split, lds, sS);
+  else
+    k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, nullptr, lds, sS);
+  return cudaGetLastError();
+}
+
 static unsigned panel_blocks(int rem) {
   const int b = (rem + 7) / 8;
   return (unsigned)(b < 4 * 152 ? b : 4 * 152);
@@ -410,22 +578,13 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
   note_launch();
   k_diag_max<<<1, 256, 0, s>>>(L, ldl, n, dmax, fail);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tol_rel = df_tol(tol_rel, split);
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
-    {
-      KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0);  // bs^3 / 3 flops
-      note_launch();
-      k_chol_diag<<<1, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split != nullptr, s)) != cudaSuccess) return e;
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
-    {
-      KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs);  // triangular solve, rem bs^2 flops
-      note_launch();
-      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, 0, split, n, 0);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = panel_step(L, ldl, j0, bs, rem, fail, 0, 1, split, n, 0, s)) != cudaSuccess) return e;
     // trailing: A[j0+bs:, j0+bs:] -= L_panel L_panel^T (lower tiles)
     e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s, split, n, 0);
     if (e != cudaSuccess) return e;
@@ -454,14 +613,10 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   double* Y = work;               // 64 x n: L[J, 0:J] Li[0:J, 0:J]
   double* part = work + 64ll * n;  // split-K partials of Y, 8 x 64 x n
+  tol_rel = df_tol(tol_rel, split);
   for (int j0 = 0, jb = 0; j0 < n; j0 += CB, ++jb) {
     const int bs = min(CB, n - j0);
-    {
-      KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0);
-      note_launch();
-      k_chol_diag<<<1, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split != nullptr, s)) != cudaSuccess) return e;
     // row block jb of the inverse, beside the rest of the factorisation
     if ((e = cudaEventRecord(ev[jb], s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(aux, ev[jb], 0)) != cudaSuccess) return e;
@@ -480,12 +635,7 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
     }
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
-    {
-      KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs);
-      note_launch();
-      k_panel_trsm<<<panel_blocks(rem), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, 0, split, n, 0);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = panel_step(L, ldl, j0, bs, rem, fail, 0, 1, split, n, 0, s)) != cudaSuccess) return e;
     e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s, split, n, 0);
     if (e != cudaSuccess) return e;
   }
@@ -512,23 +662,14 @@ cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long
   note_launch();
   k_diag_max<<<batch, 256, 0, s>>>(L, ldl, n, dmax, fail, sL);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tol_rel = df_tol(tol_rel, split);
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
-    {
-      KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0 * batch);
-      note_launch();
-      k_chol_diag<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, sL, batch, split != nullptr, s)) != cudaSuccess) return e;
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
-    {
-      KernelTimer kt(KF_FP64_GEMM, s, (double)rem * bs * bs * batch);
-      note_launch();
-      k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, split, n,
-                                                                  (long long)n * CB);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = panel_step(L, ldl, j0, bs, rem, fail, sL, batch, split, n, (long long)n * CB, s)) != cudaSuccess)
+      return e;
     e = trail_update(L, ldl, j0, bs, rem, batch, fail, sL, s, split, n, (long long)n * CB);
     if (e != cudaSuccess) return e;
   }

@@ -2,6 +2,7 @@
 // fit right-hand side M C^T), generic GEMM / SYRK with deterministic split-K,
 // polarizability C Omega^-1 C^T with on-the-fly pair operands, and a blocked
 // in-place right triangular solve.
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -16,6 +17,17 @@ thread_local bool tl_gemm_df = false;
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+static std::atomic<long long> g_allocs{0};
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return cudaMalloc(p, bytes);
+}
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return cudaMallocAsync(p, bytes, s);
+}
+long long device_allocation_count() { return g_allocs.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- utilities
 
@@ -97,6 +109,26 @@ cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, i
   return cudaGetLastError();
 }
 
+// c = a + b over n contiguous doubles (problem z at + z stride)
+__global__ void k_add(const double* a, const double* b, double* c, long long n,
+                      long long stride) {
+  a += stride * blockIdx.y;
+  b += stride * blockIdx.y;
+  c += stride * blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c[i] = a[i] + b[i];
+}
+
+cudaError_t launch_add(const double* a, const double* b, double* c, long long n, cudaStream_t s, int batch,
+                       long long stride) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  const long long blocks = std::min<long long>((n + 255) / 256, 1024);
+  note_launch();
+  k_add<<<dim3((unsigned)blocks, batch), 256, 0, s>>>(a, b, c, n, stride);
+  return cudaGetLastError();
+}
+
 __global__ void k_add_identity(double* A, long long lda, int n, double v, long long sA = 0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   A += sA * blockIdx.y;
@@ -108,6 +140,37 @@ cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaS
   if (batch > 65535) return cudaErrorInvalidValue;
   note_launch();
   k_add_identity<<<dim3((n + 127) / 128, batch), 128, 0, s>>>(A, lda, n, v, sA);
+  return cudaGetLastError();
+}
+
+// Pair weights of the polarizability, sqrt(-2 Omega(i w_k)^-1) with
+// Omega(i w)^-1 = D / (D^2 + w^2), D = e_i - e_(n_v + j) < 0 (Eq. Hedin_fourier
+// on the imaginary axis): sw[k npair + i n_c + j], and the same in FP32 in
+// swf when it is given.  ew = [energies (n_v + n_c) | frequencies (n_omega)].
+__global__ void k_pair_weights(const double* __restrict__ ew, int n_v, int n_c, int n_omega, double* __restrict__ sw,
+                               float* __restrict__ swf) {
+  const long long npair = (long long)n_v * n_c;
+  const long long total = npair * n_omega;
+  const double* om = ew + n_v + n_c;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / npair);
+    const long long p = idx - (long long)k * npair;
+    const int i = (int)(p / n_c), j = (int)(p - (long long)i * n_c);
+    const double d = ew[i] - ew[n_v + j];
+    const double v = sqrt(-2.0 * d / (d * d + om[k] * om[k]));
+    sw[idx] = v;
+    if (swf) swf[idx] = __double2float_rn(v);
+  }
+}
+
+cudaError_t launch_pair_weights(const double* ew, int n_v, int n_c, int n_omega, double* sw, float* swf,
+                                cudaStream_t s) {
+  const long long total = (long long)n_v * n_c * n_omega;
+  if (total <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+  note_launch();
+  k_pair_weights<<<(unsigned)blocks, 256, 0, s>>>(ew, n_v, n_c, n_omega, sw, swf);
   return cudaGetLastError();
 }
 

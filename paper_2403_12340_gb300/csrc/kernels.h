@@ -13,6 +13,20 @@ namespace isdf {
 void note_launch();
 long long launch_count();
 
+// Every device allocation of the library goes through these two (plain
+// cudaMalloc / cudaMallocAsync), which count them (all contexts, threads).
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
+long long device_allocation_count();
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t s) {
+  return dev_malloc_async(reinterpret_cast<void**>(p), bytes, s);
+}
+
 // True on a thread that is capturing a CUDA graph of the entry points
 // (batch.cu): the entry points then skip their host synchronisations and
 // host reads, take the shapes, rank and uploaded tables of the eager run
@@ -96,6 +110,14 @@ cudaError_t launch_transpose(const double* src, long long lds, int M, int N, dou
 cudaError_t launch_sumsq(const double* a, long long n, double* scratch, double* out, cudaStream_t s);
 // batch > 1: matrices A + z sA
 cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, int batch = 1, long long sA = 0);
+// sqrt(-2 Omega(i w_k)^-1) of every pair (i, j) and frequency k from the
+// device array ew = [energies | frequencies] into sw (and swf in FP32, if
+// not null), index k n_v n_c + i n_c + j.
+cudaError_t launch_pair_weights(const double* ew, int n_v, int n_c, int n_omega, double* sw, float* swf,
+                                cudaStream_t s);
+// c = a + b, n doubles (c may be a or b); batch problems at + z stride
+cudaError_t launch_add(const double* a, const double* b, double* c, long long n, cudaStream_t s, int batch = 1,
+                       long long stride = 0);
 cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s, int batch = 1,
                                 long long sA = 0);
 // Two-level batch of GEMMs: problem (z1, z2), z1 < b1, z2 < b2, has
@@ -198,6 +220,10 @@ struct CholWork {
 cudaError_t launch_cholesky(const double* W, long long ldw, int n, int pivot, double tol_rel,
                             double* Lr, int* perm, int* rank, unsigned* status, const CholWork& w,
                             int num_sms, uint64_t limit_ns, cudaStream_t s);
+// Two co-resident blocks wait on a grid barrier that never completes (the
+// counter at bar[0] is preset past the grid size) with the wait bound
+// limit_ns: both give up, ST_TIMEOUT goes to *status.  bar: 2 words.
+cudaError_t launch_wait_check(unsigned* bar, unsigned* status, uint64_t limit_ns, cudaStream_t s);
 
 // ---- k_fft.cu -------------------------------------------------------------
 constexpr int FFT_MAX_FACTORS = 16;

@@ -374,6 +374,26 @@ cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk, bool uinv_ready) {
                      max_split, c->num_sms, c->d_status, st);
 }
 
+// D^-1 = R^-T R^-1 (the SMW capacitance in the form K = -(D^-1 + G)^-1):
+// rows of the slice matrix are the columns of R^-1, one tensor-core SYRK.
+cudaError_t mixed_dinv(isdf_ctx* c, cudaStream_t st) {
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  MK(slices_rm(c->m_sd, c->Rinv.p, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sd, rp, rk), r, r, 1.0, 0.0, c->Dinv.p, r, true, false, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  return launch_symmetrize(c->Dinv.p, r, r, st);
+}
+
+// K = -A^-1 = -U^-T U^-1 for A = D^-1 + G = U U^T, U^-1 in c->Q.
+cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  MK(slices_rm(c->m_sa, c->Q.p, r, r, r, rp, rk, st));
+  MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 0.0, Kk, r, true, false, nullptr, 1,
+                 c->num_sms, c->d_status, st));
+  return launch_symmetrize(Kk, r, r, st);
+}
+
 // Y = X + V theta K theta^T X for one chunk of nc columns.
 cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc) {
   cudaStream_t st = c->stream;

@@ -3,9 +3,13 @@
 // no device memory.  The paper has no counterpart; this exists for callers
 // that must not allocate at call time (see include/isdf_smw.h).
 //
-// Same kernels and arithmetic as apply_eps_inv (split-K theta^T X, K T1,
-// theta T2, Coulomb convolution by FFT), with its workspace carved out of
-// g_apply_scratch instead of the context's lazily grown buffers.
+// The kernels and arithmetic of apply_eps_inv on an FP64 context (split-K
+// theta^T X, K T1, theta T2, Coulomb convolution by FFT, all FP64), with the
+// workspace carved out of g_apply_scratch instead of the context's lazily
+// grown buffers.  On a mixed-precision context it runs the same FP64
+// kernels on that context's theta (kept in FP64) and K: the tensor-core
+// form of apply_eps_inv needs BF16 slices of the probe block padded to 128
+// columns, 6 N_r bytes per padded column, far beyond a modest static pool.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -24,27 +28,68 @@ static __device__ __align__(256) double g_apply_scratch[kPoolDoubles];
 constexpr int kMaxDevices = 64;
 constexpr int kMaxSplits = 64;
 std::mutex g_mu;
+// per device: the array's device address and the id of the CUDA context it
+// was looked up in (a context id is never reused within a process)
 double* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx_id[kMaxDevices] = {0};
 
-// Device address of g_apply_scratch on `dev`, looked up once per device with
-// that device current.  In host code the array's name is only a host-side
-// stand-in; the kernels must get this address instead.
+// Id of the current CUDA context (the device's primary context once the
+// runtime has made it current), through the driver entry points the
+// runtime hands out, so that the library needs no link to the driver.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess)
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorSymbolNotFound;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+  return get_id(ctx, id) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of g_apply_scratch on `dev`, looked up with that device
+// current, once per device and CUDA context (after a cudaDeviceReset the
+// device gets a new primary context, the library's module is loaded again
+// and the array may sit elsewhere: the new context's id triggers a new
+// lookup).  In host code the array's name is only a host-side stand-in;
+// the kernels must get this address instead.
 cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (g_addr[dev]) {
-    *out = g_addr[dev];
-    return cudaSuccess;
-  }
   int cur = -1;
   cudaError_t e = cudaGetDevice(&cur);
   if (e != cudaSuccess) return e;
   if (cur != dev && (e = cudaSetDevice(dev)) != cudaSuccess) return e;
-  double* p = nullptr;
-  e = cudaGetSymbolAddress((void**)&p, g_apply_scratch);
+  // a thread that has not used the runtime yet may have no current context:
+  // then the lookup itself (which binds the primary context) comes first
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id) == cudaSuccess;
+  if (!have_id || !(g_addr[dev] && g_ctx_id[dev] == id)) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_apply_scratch);
+    if (e == cudaSuccess) {
+      if (!have_id) have_id = current_context_id(&id) == cudaSuccess;
+      g_addr[dev] = have_id ? p : nullptr;  // without a context id: look it up on every call
+      g_ctx_id[dev] = id;
+      *out = p;
+    }
+    if (cur != dev) cudaSetDevice(cur);
+    return e;
+  }
   if (cur != dev) cudaSetDevice(cur);
   if (e != cudaSuccess) return e;
-  g_addr[dev] = p;
-  *out = p;
+  *out = g_addr[dev];
   return cudaSuccess;
 }
 

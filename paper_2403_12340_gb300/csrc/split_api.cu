@@ -39,10 +39,10 @@ extern "C" int isdf_dgemm_split(int M, int N, int K, double alpha, const double*
   __nv_bfloat16 *sa = nullptr, *sb = nullptr;
   double* part = nullptr;
   unsigned* status = nullptr;
-  cudaError_t e = cudaMallocAsync(&sa, na * 2, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&sb, nb * 2, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&part, npart * 8, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&status, 16, st);
+  cudaError_t e = isdf::dev_malloc_async(&sa, na * 2, st);
+  if (e == cudaSuccess) e = isdf::dev_malloc_async(&sb, nb * 2, st);
+  if (e == cudaSuccess) e = isdf::dev_malloc_async(&part, npart * 8, st);
+  if (e == cudaSuccess) e = isdf::dev_malloc_async(&status, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sa, 0, na * 2, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sb, 0, nb * 2, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 16, st);

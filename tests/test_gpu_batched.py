@@ -81,6 +81,25 @@ def test_batched_config4_systems_sampled():
             assert rel_fro(ys[k], ref.y) < TOL[1], (i, k)
 
 
+def test_batched_config4_largest_system_two_frequencies():
+    """The largest system of the 16-system set (60^3, N_v = 160, N_c = 1120,
+    N_mu = 1920): every one of the 32 frequencies through the batched mixed
+    path (smw_inverse_all), the first and the last checked against the
+    oracle (fit and G once, B and K per frequency)."""
+    omegas, _ = synth.gauss_legendre_frequencies(32)
+    s = synth.batch_system(len(synth.BATCH_SYSTEMS) - 1)
+    x = synth.probe_block(s.n_r, 4)
+    _, ys = _run(s, omegas, x, 1)
+    theta, rank = O.isdf_fit(s.phi, s.n_v, s.mu_idx)
+    assert rank == s.n_mu
+    g = O.coulomb_in_basis(theta, s.n, s.cell)
+    pm = s.phi[np.asarray(s.mu_idx)]
+    for k in (0, len(omegas) - 1):
+        kk = O.capacitance(g, O.polarizability(pm, s.energies, s.n_v, float(omegas[k])))
+        ref = O.apply_eps_inv(theta, kk, x, s.n, s.cell)
+        assert rel_fro(ys[k], ref) < TOL[1], k
+
+
 def test_smw_inverse_all_state_errors():
     import paper_2403_12340_gb300 as pkg
 

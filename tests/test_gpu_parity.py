@@ -191,3 +191,32 @@ def test_context_reuse_across_systems():
     for sysm, y in zip((a, b, a), ys):
         ref = O.isdf_smw_solve(sysm.phi, sysm.energies, sysm.n_v, sysm.mu_idx, sysm.n, sysm.cell, xa)
         assert rel_fro(y, ref.y) < TOL
+
+
+def test_points_from_device_memory():
+    """Interpolation points passed as an int64 device array give the same
+    fit and eps^-1 X as the same points in host memory; a bad index in
+    device memory is refused like one in host memory."""
+    import torch
+
+    import paper_2403_12340_gb300 as pkg
+
+    s = small_system((12, 10, 14), 4, 9, 30, seed_index=6)
+    x = synth.probe_block(s.n_r, 3)
+    ref = O.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x)
+    ys = []
+    for on_device in (False, True):
+        with pkg.IsdfSmw(s.n, s.cell) as ctx:
+            mu = torch.as_tensor(s.mu_idx, dtype=torch.int64, device="cuda") if on_device else s.mu_idx
+            _, rank = ctx.fit(pkg.to_fortran(s.phi), s.n_v, s.n_c, mu)
+            assert rank == ref.rank
+            ctx.polarizability(s.energies, [0.0])
+            ctx.smw(0)
+            ys.append(ctx.apply(pkg.to_fortran(x), 0).cpu().numpy())
+            if on_device:
+                bad = mu.clone()
+                bad[2] = s.n_r
+                with pytest.raises(pkg.IsdfError, match="ISDF_ERR_INDEX"):
+                    ctx.fit(pkg.to_fortran(s.phi), s.n_v, s.n_c, bad)
+    assert np.array_equal(ys[0], ys[1])
+    assert rel_fro(ys[1], ref.y) < TOL
