@@ -36,9 +36,11 @@ from typing import Tuple
 
 import numpy as np
 
-from .isdf_oracle import capacitance, omega_inverse, pair_matrix, polarizability
+from .isdf_oracle import (apply_coulomb, capacitance, coulomb_in_basis, isdf_fit, omega_inverse, pair_matrix,
+                          polarizability)
 
-__all__ = ["screened_coulomb_basis", "screened_loss", "screened_loss_grad", "random_projector"]
+__all__ = ["screened_coulomb_basis", "screened_loss", "screened_loss_grad", "random_projector", "fit_loss",
+           "fit_loss_grad"]
 
 
 def screened_coulomb_basis(g: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -92,3 +94,67 @@ def random_projector(n: int, seed: int = 13) -> np.ndarray:
     rng = np.random.default_rng(seed)
     q, _ = np.linalg.qr(rng.standard_normal((n, n // 2)))
     return q @ q.T
+
+
+# ---------------------------------------------------------------------------
+# Through the fit: L as a function of the orbitals on the whole grid.
+#
+# P is now the least-squares ISDF vectors of Phi itself (full rank),
+#     P = Z A^-1,  Z = M C^T = Zv .* Zc,  A = C C^T = Av .* Ac,
+#     Zv = Phi_v Phi_v,mu^T, Zc = Phi_c Phi_c,mu^T, Av = Phi_v,mu Phi_v,mu^T,
+#     Ac = Phi_c,mu Phi_c,mu^T (Eq. MatrixExpressionISDF with the Hadamard
+#     identity), and G = P^T V P depends on Phi through P.  With
+#     W_P = G + G K G = (G^-1 + D)^-1:
+#     dL/dG = E^T Wbar E,  E = I + G K           (dW = W G^-1 dG G^-1 W, W G^-1 = E^T)
+#     dL/dP = 2 V P dL/dG
+#     dL/dZ = dL/dP A^-1,  dL/dA = -sym(A^-1 (dL/dP)^T P)
+#     dL/dPhi_v = (dL/dZ .* Zc) Phi_v,mu,  dL/dPhi_v,mu += (dL/dZ .* Zc)^T Phi_v
+#         + 2 (dL/dA .* Ac) Phi_v,mu  (and v <-> c),
+# and the rows mu of dL/dPhi also collect dL/dphi_mu through D (above).
+
+
+def fit_loss(phi: np.ndarray, energies: np.ndarray, n_v: int, mu_idx, n, cell, pj: np.ndarray,
+             omega: float = 0.0) -> float:
+    """L(Phi) = tr(W_P Pj), every step of W_P recomputed from the orbitals."""
+    mu = np.asarray(mu_idx)
+    p, _ = isdf_fit(phi, n_v, mu)
+    g = coulomb_in_basis(p, n, cell)
+    b = polarizability(phi[mu], energies, n_v, omega)
+    return float(np.trace(screened_coulomb_basis(g, b) @ pj))
+
+
+def fit_loss_grad(phi: np.ndarray, energies: np.ndarray, n_v: int, mu_idx, n, cell, wbar: np.ndarray,
+                  omega: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+    """(dL/de, dL/dPhi) of L(W_P(Phi, e)) for dL/dW_P = wbar (symmetric),
+    dL/dPhi over the whole grid (N_r x N_e).  Needs C C^T of full rank."""
+    mu = np.asarray(mu_idx)
+    pm = phi[mu]
+    p, rank = isdf_fit(phi, n_v, mu)
+    if rank != len(mu):
+        raise ValueError("fit_loss_grad needs a full-rank C C^T")
+    g = coulomb_in_basis(p, n, cell)
+    b = polarizability(pm, energies, n_v, omega)
+    k = capacitance(g, b)
+    e = np.eye(g.shape[0]) + g @ k
+    # through D, P held fixed
+    grad_e, gpm = screened_loss_grad(g, pm, energies, n_v, wbar, omega)
+    # through G and P
+    gbar = e.T @ wbar @ e
+    pbar = 2.0 * apply_coulomb(p @ gbar, n, cell)
+    pv, pc = phi[:, :n_v], phi[:, n_v:]
+    pmv, pmc = pm[:, :n_v], pm[:, n_v:]
+    av, ac = pmv @ pmv.T, pmc @ pmc.T
+    ainv = np.linalg.inv(av * ac)
+    zbar = pbar @ ainv
+    abar = -ainv @ pbar.T @ p
+    abar = 0.5 * (abar + abar.T)
+    zv, zc = pv @ pmv.T, pc @ pmc.T
+    zbv, zbc = zbar * zc, zbar * zv
+    grad_phi = np.zeros_like(phi)
+    grad_phi[:, :n_v] = zbv @ pmv
+    grad_phi[:, n_v:] = zbc @ pmc
+    gpm = gpm.copy()
+    gpm[:, :n_v] += zbv.T @ pv + 2.0 * (abar * ac) @ pmv
+    gpm[:, n_v:] += zbc.T @ pc + 2.0 * (abar * av) @ pmc
+    grad_phi[mu] += gpm
+    return grad_e, grad_phi

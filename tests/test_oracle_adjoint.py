@@ -78,3 +78,60 @@ def test_projector_is_a_symmetric_projector():
     assert np.allclose(pj, pj.T, atol=1e-15)
     assert np.allclose(pj @ pj, pj, atol=1e-14)
     assert abs(np.trace(pj) - 5) < 1e-12
+
+
+# ---- through the fit: dL/dPhi over the whole grid -----------------------
+
+def _fit_case(omega, seed_index=63):
+    s = small_system((5, 6, 7), 2, 4, n_mu=7, seed_index=seed_index)
+    pj = A.random_projector(7, seed=13)
+    return s, pj
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.3])
+def test_fit_gradients_match_central_differences(omega):
+    """Every entry of dL/dPhi (grid rows and point rows) and dL/de of
+    L(Phi, e) = tr(W_P Pj), with P refitted for every perturbed Phi."""
+    s, pj = _fit_case(omega)
+    ge, gphi = A.fit_loss_grad(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, pj, omega)
+    h = 1e-6
+
+    def loss(p, e):
+        return A.fit_loss(p, e, s.n_v, s.mu_idx, s.n, s.cell, pj, omega)
+
+    fphi = np.empty_like(gphi)
+    for a in range(s.phi.shape[0]):
+        for i in range(s.phi.shape[1]):
+            pp, pm = s.phi.copy(), s.phi.copy()
+            pp[a, i] += h
+            pm[a, i] -= h
+            fphi[a, i] = (loss(pp, s.energies) - loss(pm, s.energies)) / (2 * h)
+    fe = np.empty_like(ge)
+    for i in range(len(ge)):
+        ep, em = s.energies.copy(), s.energies.copy()
+        ep[i] += h
+        em[i] -= h
+        fe[i] = (loss(s.phi, ep) - loss(s.phi, em)) / (2 * h)
+    assert rel_fro(gphi, fphi) < 1e-6
+    assert rel_fro(ge, fe) < 1e-6
+    # the grid rows away from the points carry gradient only through P
+    off = np.setdiff1d(np.arange(s.phi.shape[0]), np.asarray(s.mu_idx))
+    assert np.abs(gphi[off]).max() > 1e-3 * np.abs(gphi).max()
+
+
+def test_fit_gradient_scale_identity():
+    """P = Z A^-1 is unchanged when Phi is scaled (Z and A both scale with
+    the fourth power), so only D carries the scaling: at w = 0,
+    sum Phi * dL/dPhi = -4 sum e * dL/de, and the part through P alone sums
+    to zero."""
+    s, pj = _fit_case(0.0, seed_index=64)
+    ge, gphi = A.fit_loss_grad(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, pj, 0.0)
+    lhs = float(np.sum(s.phi * gphi))
+    rhs = -4.0 * float(np.dot(s.energies, ge))
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs)
+    theta, _ = O.isdf_fit(s.phi, s.n_v, s.mu_idx)
+    g = O.coulomb_in_basis(theta, s.n, s.cell)
+    pm = s.phi[np.asarray(s.mu_idx)]
+    _, gpm = A.screened_loss_grad(g, pm, s.energies, s.n_v, pj, 0.0)
+    through_p = float(np.sum(s.phi * gphi) - np.sum(pm * gpm))
+    assert abs(through_p) < 1e-10 * float(np.abs(s.phi * gphi).sum())
