@@ -257,6 +257,28 @@ ISDF_API int isdf_screened_basis(isdf_ctx* ctx, int omega_index, double* W_out);
 ISDF_API int isdf_adjoint(isdf_ctx* ctx, int omega_index, const double* W_bar, double* grad_energies,
                           double* grad_phimu);
 
+/* Reverse mode through the ISDF fit: the same loss, now with the ISDF
+ * vectors P = M C^T (C C^T)^-1 a function of the orbitals on the whole grid
+ * (Eq. MatrixExpressionISDF, least-squares reading), so that dL/dPhi also
+ * carries the change of P, through G = P^T V P:
+ *   dL/dG_P = E^T Wbar E (E = I + G_P K_P),  dL/dP = 2 V P dL/dG_P,
+ *   dL/dZ = dL/dP A^-1, dL/dA = -sym(A^-1 dL/dP^T P) for Z = M C^T =
+ *   (Phi_v Phi_v,mu^T) .* (Phi_c Phi_c,mu^T) and A = C C^T, and on to Phi.
+ * theta and the fit's factor are the checkpoint of the forward pass: the
+ * backward recomputes the face-split factors, V theta and the rest from
+ * the orbitals of the fit, in FP64.
+ *   W_bar         device, n_mu x n_mu float64 (points order), dL/dW_P.
+ *   grad_energies device, n_v + n_c float64 out (as isdf_adjoint).
+ *   grad_phi      device, N_r x (n_v + n_c) float64 out, column-major
+ *                 (ld N_r): dL/dPhi on every grid point (the rows of the
+ *                 interpolation points include the part through D).
+ * Needs a fit of full rank (ISDF_ERR_STATE otherwise) and, like
+ * isdf_adjoint, the state of the last build_polarizability and smw_inverse
+ * for omega_index.  Workspace: 3 N_r n_mu + O(n_mu^2 + n_mu N_e) doubles.
+ * Synchronises the context stream. */
+ISDF_API int isdf_adjoint_fit(isdf_ctx* ctx, int omega_index, const double* W_bar, double* grad_energies,
+                              double* grad_phi);
+
 /* ---- Static COHSEX self-energies (Algorithm 3 steps 4-7) -------------------
  * Band self-energies of the static COHSEX approximation (Section "GW
  * approximation": Sigma_SEX_X, Sigma_X, Sigma_COH of every band n) from
@@ -439,6 +461,16 @@ enum {
  * NULL) and clears the record.  Work counts the method's arithmetic on the
  * launch's true sizes, not tile padding. */
 ISDF_API int isdf_read_kernel_profile(isdf_ctx* ctx, double* ms, int* counts, double* work);
+/* The same records launch by launch (tracing): synchronises the device,
+ * then writes for the first min(max, recorded) launches since the last read
+ * their start and end (ms, from the earliest recorded start; CUDA events on
+ * each launch's own stream, so a launch queued behind work of other
+ * streams shows its wait), family, phase, work and stream (0 the context
+ * stream, 1 and 2 its two helper streams, 3 another) into host arrays of
+ * max entries (any may be NULL); clears the record and returns the number
+ * written (negative ISDF_ERR_* on error). */
+ISDF_API int isdf_read_kernel_trace(isdf_ctx* ctx, int max, double* t_start, double* t_end, int* family, int* phase,
+                                    double* work, int* stream);
 /* Short name of a kernel family, or NULL. */
 ISDF_API const char* isdf_kernel_family_name(int family);
 /* Number of kernel launches issued by this library in this process so far

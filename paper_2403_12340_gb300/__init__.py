@@ -39,7 +39,8 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "isdf_batch_destroy", "isdf_batch_run", "isdf_batch_context", "isdf_batch_last_error",
             "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex", "isdf_batch_capture",
             "isdf_batch_replay", "isdf_set_autotune", "isdf_autotune_size", "isdf_autotune_entry",
-            "isdf_autotune_clear", "isdf_device_allocations", "isdf_check_device_wait"]
+            "isdf_autotune_clear", "isdf_device_allocations", "isdf_check_device_wait",
+            "isdf_adjoint_fit", "isdf_read_kernel_trace"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 6
 
@@ -113,8 +114,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_set_point_orbitals.argtypes = [P, P, LL]
     lib.isdf_screened_basis.argtypes = [P, I, P]
     lib.isdf_adjoint.argtypes = [P, I, P, P, P]
-    for name in ["isdf_set_point_orbitals", "isdf_screened_basis", "isdf_adjoint"]:
+    lib.isdf_adjoint_fit.argtypes = [P, I, P, P, P]
+    for name in ["isdf_set_point_orbitals", "isdf_screened_basis", "isdf_adjoint", "isdf_adjoint_fit"]:
         getattr(lib, name).restype = I
+    lib.isdf_read_kernel_trace.argtypes = [P, I, P, P, P, P, P, P]
+    lib.isdf_read_kernel_trace.restype = I
     lib.isdf_read_kernel_profile.argtypes = [P, P, P, P]
     lib.isdf_read_kernel_profile.restype = I
     lib.isdf_kernel_family_name.argtypes = [I]
@@ -320,6 +324,12 @@ def isdf_adjoint(ctx, omega_index: int, W_bar, grad_e, grad_phimu, n_mu: int, n_
                                        _dev_ptr(grad_phimu, n_mu, n_e, "grad_phimu")), ctx)
 
 
+def isdf_adjoint_fit(ctx, omega_index: int, W_bar, grad_e, grad_phi, n_mu: int, n_r: int, n_e: int) -> None:
+    _check(load_library().isdf_adjoint_fit(ctx, int(omega_index), _dev_ptr(W_bar, n_mu, n_mu, "W_bar"),
+                                           _dev_ptr(grad_e, name="grad_energies"),
+                                           _dev_ptr(grad_phi, n_r, n_e, "grad_phi")), ctx)
+
+
 def isdf_fit_factor(ctx, n_mu: int, L_out=None):
     """Pivot order (host int32 array) of the last fit; fills L_out if given."""
     piv = np.zeros(n_mu, dtype=np.int32)
@@ -359,6 +369,26 @@ def isdf_read_kernel_profile(ctx):
                 out[(lib.isdf_kernel_family_name(f).decode(), lib.isdf_phase_name(p).decode())] = (
                     float(ms[i]), int(cnt[i]), float(work[i]))
     return out
+
+
+def isdf_read_kernel_trace(ctx, max_records: int = 100000):
+    """Launch-by-launch record of the timed kernels since the last read:
+    a list of (start_ms, end_ms, family, phase, work, stream)."""
+    lib = load_library()
+    t0 = np.zeros(max_records)
+    t1 = np.zeros(max_records)
+    fam = np.zeros(max_records, dtype=np.int32)
+    ph = np.zeros(max_records, dtype=np.int32)
+    wk = np.zeros(max_records)
+    st = np.zeros(max_records, dtype=np.int32)
+    n = lib.isdf_read_kernel_trace(ctx, int(max_records), t0.ctypes.data, t1.ctypes.data, fam.ctypes.data,
+                                   ph.ctypes.data, wk.ctypes.data, st.ctypes.data)
+    if n < 0:
+        raise IsdfError(n, isdf_last_error(ctx))
+    fn = [lib.isdf_kernel_family_name(i).decode() for i in range(NUM_KERNEL_FAMILIES)]
+    pn = [lib.isdf_phase_name(i).decode() for i in range(NUM_PHASES)]
+    return [(float(t0[i]), float(t1[i]), fn[fam[i]], pn[ph[i]] if 0 <= ph[i] < NUM_PHASES else "?", float(wk[i]),
+             int(st[i])) for i in range(n)]
 
 
 def isdf_dgemm_split(A, B, C, alpha=1.0, beta=0.0, nslices=3, stream=None) -> None:
@@ -432,6 +462,7 @@ class IsdfSmw:
             theta = fortran_empty(self.n_r, mu.shape[0], phi.device)
         self.rank = isdf_fit(self.ctx, phi, n_v, n_c, mu, theta, self.n_r, prec)
         self.n_mu = int(mu.shape[0])
+        self.phi = phi  # the library reads the orbitals again after the fit
         self.theta = theta
         return theta, self.rank
 
@@ -498,6 +529,17 @@ class IsdfSmw:
         isdf_adjoint(self.ctx, omega_index, wb, ge, gp, self.n_mu, n_e)
         return ge, gp
 
+    def adjoint_fit(self, W_bar, n_e, omega_index=0):
+        """(dL/de, dL/dPhi over the grid) for dL/dW_P = W_bar, with the ISDF
+        vectors differentiated through the fit."""
+        import torch
+
+        wb = W_bar if (W_bar.dim() == 2 and W_bar.stride() == (1, self.n_mu)) else to_fortran(W_bar, W_bar.device)
+        ge = torch.empty(n_e, dtype=torch.float64, device=self.theta.device)
+        gphi = fortran_empty(self.n_r, n_e, self.theta.device)
+        isdf_adjoint_fit(self.ctx, omega_index, wb, ge, gphi, self.n_mu, self.n_r, n_e)
+        return ge, gphi
+
     def factor(self, want_L=False):
         import torch
 
@@ -534,6 +576,40 @@ def _autograd_function():
             return None, ge.to(fctx.e_device), gp, None
 
     return ScreenedCoulombBasis
+
+
+def _fit_autograd_function():
+    import torch
+
+    class ScreenedCoulombFit(torch.autograd.Function):
+        """W_P(Phi, e) = P^T eps^-1(i w) V P with P refitted from the orbitals
+        on the whole grid (FP64).  forward runs the CUDA fit, polarizability,
+        SMW and projection; backward runs the CUDA adjoint through the fit,
+        which recomputes what it needs from theta (the checkpoint).  Between
+        a forward and its backward the solver must not be refitted."""
+
+        @staticmethod
+        def forward(fctx, solver, phi, energies, n_v, mu_idx, omega):
+            solver.fit(phi.detach(), n_v, phi.shape[1] - n_v, mu_idx)
+            solver.polarizability(energies.detach().cpu().numpy(), [float(omega)])
+            solver.smw(0)
+            fctx.solver = solver
+            fctx.n_e = phi.shape[1]
+            fctx.e_device = energies.device
+            return solver.screened_basis(0)
+
+        @staticmethod
+        def backward(fctx, gW):
+            ge, gphi = fctx.solver.adjoint_fit(gW, fctx.n_e, 0)
+            return None, gphi, ge.to(fctx.e_device), None, None, None
+
+    return ScreenedCoulombFit
+
+
+def screened_coulomb_fit(solver, phi, energies, n_v, mu_idx, omega=0.0):
+    """Differentiable W_P = P^T eps^-1 V P as a function of the orbitals on
+    the grid (column-major N_r x N_e CUDA tensor) and the energies."""
+    return _fit_autograd_function().apply(solver, phi, energies, n_v, mu_idx, omega)
 
 
 def screened_coulomb_basis(solver, energies, phi_mu, omega=0.0):

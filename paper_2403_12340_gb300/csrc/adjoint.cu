@@ -134,6 +134,27 @@ __global__ void k_gather_sym(const double* __restrict__ src, long long lds, int 
   if (i < r) dst[i + (long long)r * j] = src[perm[i] + lds * perm[j]];
 }
 
+// c = a .* b over n doubles (c may be a or b)
+__global__ void k_mul_elem(const double* a, const double* b, double* c, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c[i] = a[i] * b[i];
+}
+
+void mul_elem(const double* a, const double* b, double* c, long long n, cudaStream_t s) {
+  note_launch();
+  k_mul_elem<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(a, b, c, n);
+}
+
+// The rows of the points: g(idx[perm[a]], i) += gp(a, i) + gd(perm[a], i)
+// (gp in pivot order, ld r; gd in points order, ld m; the points distinct)
+__global__ void k_scatter_add_rows(const double* __restrict__ gp, int r, const double* __restrict__ gd, int m,
+                                   const int* __restrict__ perm, const int* __restrict__ idx, double* g, long long ldg) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (a >= r) return;
+  const int pt = perm[a];
+  g[idx[pt] + ldg * i] += gp[a + (long long)r * i] + gd[pt + (long long)m * i];
+}
+
 // C = op(A) op(B)^T with the FP64 engine (r x r operands, ld r)
 cudaError_t mm(const double* A, bool ta, const double* B, bool tb, int r, double alpha, double beta, double* C,
                cudaStream_t s) {
@@ -267,5 +288,106 @@ extern "C" int isdf_adjoint(isdf_ctx* c, int k, const double* W_bar, double* gra
   k_adj_energy<<<n_e, 128, 0, s>>>(c->a_gd.p, c->a_e.p, n_v, n_c, c->omega[k], grad_energies);
   AK(cudaGetLastError());
   AK(cudaStreamSynchronize(s));  // the energies were copied from a host vector that later calls may change
+  return ISDF_OK;
+}
+
+// Adjoint through the fit (see include/isdf_smw.h).  With P = theta L^-1
+// (points basis, full rank) and A = C C^T = L L^T, in the whitened basis:
+//   Pw  = L^-1 Wbar L^-T,  E = I + G K,  Gb = E^T Pw E   (dL/dG_P = L Gb L^T)
+//   dL/dZ = 2 V P dL/dG_P A^-1 = 2 V theta Gb L^-1
+//   dL/dA = -sym(A^-1 (dL/dP)^T P) = -L^-T (Gb G + G Gb) L^-1
+//   Z = Zv .* Zc, Zv = Phi_v Phi_v,mu^T, Zc = Phi_c Phi_c,mu^T (recomputed:
+//   theta is the only checkpoint of the forward pass), A = Av .* Ac:
+//   dL/dPhi_v = (dL/dZ .* Zc) Phi_v,mu,  dL/dPhi_c = (dL/dZ .* Zv) Phi_c,mu,
+//   rows mu: + (dL/dZ .* Zc)^T Phi_v + 2 (dL/dA .* Ac) Phi_v,mu (and v <-> c)
+//   + dL/dphi_mu through D (isdf_adjoint).
+extern "C" int isdf_adjoint_fit(isdf_ctx* c, int k, const double* W_bar, double* grad_energies, double* grad_phi) {
+  if (!c) return ISDF_ERR_ARG;
+  c->err.clear();
+  int rc = check_ready(c, k, "isdf_adjoint_fit");
+  if (rc != ISDF_OK) return rc;
+  if (!W_bar || !grad_energies || !grad_phi)
+    return ctx_fail(c, ISDF_ERR_ARG, "isdf_adjoint_fit: null pointer argument");
+  const int r = c->rank, m = c->n_mu, n_v = c->n_v, n_c = c->n_c, n_e = n_v + n_c;
+  if (r != m) return ctx_fail(c, ISDF_ERR_STATE, "isdf_adjoint_fit: needs a fit of full rank (C C^T invertible)");
+  if (r > 65535 || n_e > 65535) return ctx_fail(c, ISDF_ERR_SHAPE, "isdf_adjoint_fit: rank and n_e must be <= 65535");
+  const long long nr = c->n_r;
+  const size_t rr = (size_t)r * r, big = (size_t)nr * r;
+  const long long lds = 2 * c->n_half;
+  cudaStream_t s = c->stream;
+  // through D at the points, theta held fixed; its point gradient goes to a_gpm
+  AK(ensure(c->a_gpm, (size_t)m * n_e));
+  rc = isdf_adjoint(c, k, W_bar, grad_energies, c->a_gpm.p);
+  if (rc != ISDF_OK) return rc;
+  AK(cudaStreamSynchronize(s));  // the buffers below may grow
+  AK(ensure(c->a_z1, big));
+  AK(ensure(c->a_z2, big));
+  AK(ensure(c->a_z3, big));
+  AK(ensure(c->spec, (size_t)lds * r));
+  AK(ensure(c->a_gpp, (size_t)r * n_e));
+  AK(ensure(c->a_m5, rr));
+  AK(ensure(c->a_m6, rr));
+  const int ks = (int)std::max<long long>(1, std::min<long long>(32, nr / 4096));
+  AK(ensure(c->partial, (size_t)ks * r * n_e));
+  if ((rc = linv(c, r)) != ISDF_OK) return rc;
+  const double* Li = c->a_linv.p;
+  double *M1 = c->a_m1.p, *M2 = c->a_m2.p, *M4 = c->a_m4.p, *M5 = c->a_m5.p, *M6 = c->a_m6.p;
+  const double* G = c->G.p;
+  const double* K = c->K.p + rr * k;
+  const double* phv = c->phimu_p.p;                   // r x n_v, pivot order
+  const double* phc = c->phimu_p.p + (size_t)r * n_v;  // r x n_c
+  note_launch();
+  k_gather_sym<<<dim3((r + 127) / 128, r), 128, 0, s>>>(W_bar, m, r, c->d_perm, M1);
+  AK(cudaGetLastError());
+  AK(mm(Li, false, M1, true, r, 1.0, 0.0, M2, s));    // L^-1 Wbar
+  AK(mm(M2, false, Li, false, r, 1.0, 0.0, M1, s));   // Pw
+  AK(mm(G, false, K, true, r, 1.0, 0.0, M2, s));      // G K
+  AK(launch_add_identity(M2, r, r, 1.0, s));          // E
+  AK(mm(M1, false, M2, true, r, 1.0, 0.0, M4, s));    // Pw E
+  AK(mm(M2, true, M4, true, r, 1.0, 0.0, M5, s));     // Gb = E^T Pw E
+  AK(launch_symmetrize(M5, r, r, s));
+  // H = 2 Gb L^-1, then dL/dZ = V (theta H)
+  AK(mm(M5, false, Li, true, r, 2.0, 0.0, M6, s));
+  AK(launch_gemm(c->theta, nr, false, M6, r, true, (int)nr, r, r, 1.0, 0.0, c->a_z1.p, nr, false, 1, nullptr, false, s));
+  AK(launch_fft_convolve(c->fft, c->a_z1.p, nr, r, c->spec.p, lds, c->d_wconv, nullptr, 0, c->a_z1.p, nr, c->smem_xy,
+                         c->smem_z, s));
+  // dL/dA = -L^-T (Gb G + G Gb) L^-1
+  AK(mm(M5, false, G, true, r, 1.0, 0.0, M1, s));     // Gb G
+  AK(mm(G, false, M5, true, r, 1.0, 1.0, M1, s));     // + G Gb
+  AK(mm(M1, false, Li, true, r, 1.0, 0.0, M2, s));    // (.) L^-1
+  AK(mm(Li, true, M2, true, r, -1.0, 0.0, M6, s));    // Abar = -L^-T (.) L^-1
+  // Zv, Zc, then dL/dZ .* Zc (into Zc) and dL/dZ .* Zv (into Zv)
+  AK(launch_gemm(c->phi, nr, false, phv, r, false, (int)nr, r, n_v, 1.0, 0.0, c->a_z2.p, nr, false, 1, nullptr, false,
+                 s));
+  AK(launch_gemm(c->phi + (size_t)nr * n_v, nr, false, phc, r, false, (int)nr, r, n_c, 1.0, 0.0, c->a_z3.p, nr, false,
+                 1, nullptr, false, s));
+  mul_elem(c->a_z1.p, c->a_z3.p, c->a_z3.p, (long long)big, s);  // Zbv = Zbar .* Zc
+  mul_elem(c->a_z1.p, c->a_z2.p, c->a_z2.p, (long long)big, s);  // Zbc = Zbar .* Zv
+  AK(cudaGetLastError());
+  // grid rows: dL/dPhi_v = Zbv Phi_v,mu, dL/dPhi_c = Zbc Phi_c,mu
+  AK(launch_gemm(c->a_z3.p, nr, false, phv, r, true, (int)nr, n_v, r, 1.0, 0.0, grad_phi, nr, false, 1, nullptr, false,
+                 s));
+  AK(launch_gemm(c->a_z2.p, nr, false, phc, r, true, (int)nr, n_c, r, 1.0, 0.0, grad_phi + (size_t)nr * n_v, nr, false,
+                 1, nullptr, false, s));
+  // point rows (pivot order): Zbv^T Phi_v, Zbc^T Phi_c (split over the grid)
+  double* gpp = c->a_gpp.p;
+  AK(launch_gemm(c->a_z3.p, nr, true, c->phi, nr, true, r, n_v, (int)nr, 1.0, 0.0, gpp, r, false, ks, c->partial.p,
+                 false, s));
+  AK(launch_gemm(c->a_z2.p, nr, true, c->phi + (size_t)nr * n_v, nr, true, r, n_c, (int)nr, 1.0, 0.0,
+                 gpp + (size_t)r * n_v, r, false, ks, c->partial.p, false, s));
+  // + 2 (Abar .* Ac) Phi_v,mu and 2 (Abar .* Av) Phi_c,mu
+  AK(launch_gemm(phc, r, false, phc, r, false, r, r, n_c, 1.0, 0.0, M1, r, false, 1, nullptr, false, s));  // Ac
+  AK(launch_gemm(phv, r, false, phv, r, false, r, r, n_v, 1.0, 0.0, M2, r, false, 1, nullptr, false, s));  // Av
+  mul_elem(M6, M1, M1, (long long)rr, s);  // Abar .* Ac
+  mul_elem(M6, M2, M2, (long long)rr, s);  // Abar .* Av
+  AK(cudaGetLastError());
+  AK(launch_gemm(M1, r, false, phv, r, true, r, n_v, r, 2.0, 1.0, gpp, r, false, 1, nullptr, false, s));
+  AK(launch_gemm(M2, r, false, phc, r, true, r, n_c, r, 2.0, 1.0, gpp + (size_t)r * n_v, r, false, 1, nullptr, false,
+                 s));
+  note_launch();
+  k_scatter_add_rows<<<dim3((r + 127) / 128, n_e), 128, 0, s>>>(gpp, r, c->a_gpm.p, m, c->d_perm, c->d_idx, grad_phi,
+                                                               nr);
+  AK(cudaGetLastError());
+  AK(cudaStreamSynchronize(s));
   return ISDF_OK;
 }

@@ -261,9 +261,10 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->tmp1, &c->tmp2, &c->tmp3, &c->sw, &c->m_phis, &c->m_phimus, &c->m_zs, &c->m_linv,
                     &c->m_linvs, &c->m_work, &c->m_thetas_t, &c->m_s32, &c->m_ss, &c->m_pairs, &c->m_sa,
                     &c->m_sb, &c->m_xs, &c->cb_work, &c->Rw, &c->a_linv, &c->a_m1, &c->a_m2, &c->a_m3,
-                    &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->bW1, &c->bT, &c->bU, &c->bQ,
+                    &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->a_z1, &c->a_z2, &c->a_z3, &c->a_gpm, &c->a_gpp,
+                    &c->a_m5, &c->a_m6, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
+                    &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->ns_bound, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
@@ -814,6 +815,42 @@ extern "C" int isdf_contour_nodes(const double* energies, int n_v, int n_c, doub
   return std::max(1, contour_nodes_recommended(e_lo - e_n, e_hi - e_n, tol));
 }
 
+// Largest pair weight w_p = -2 Omega_p(i w_k)^-1 = 2 |D| / (D^2 + w^2),
+// D = e_v - e_c: the largest eigenvalue D(w) can have (D = C~ diag(w) C~^T
+// with orthonormal rows C~).  As a function of |D| it peaks at |D| = w, so
+// the maximum over the pairs lies at w or at an end of [gap, width].
+static double max_pair_weight(isdf_ctx* c, int k) {
+  const int n_v = c->n_v, n_e = n_v + c->n_c;
+  double emax_v = c->energies[0], emin_v = c->energies[0], emin_c = c->energies[n_v], emax_c = c->energies[n_v];
+  for (int i = 0; i < n_v; ++i) {
+    emax_v = std::max(emax_v, c->energies[i]);
+    emin_v = std::min(emin_v, c->energies[i]);
+  }
+  for (int j = n_v; j < n_e; ++j) {
+    emin_c = std::min(emin_c, c->energies[j]);
+    emax_c = std::max(emax_c, c->energies[j]);
+  }
+  const double w = c->omega[k], gap = emin_c - emax_v, width = emax_c - emin_v;
+  auto f = [w](double d) { return 2.0 * d / (d * d + w * w); };
+  double m = std::max(f(gap), f(width));
+  if (w >= gap && w <= width) m = std::max(m, f(w));
+  return m;
+}
+
+// Newton-Schulz steps that take |I - alpha A| from (k - 1) / (k + 1) (k =
+// hi / lo, alpha = 2 / (lo + hi)) below 2^-26, under the FP32-grade rounding
+// of the products; 0 (use the factorisation) if more than 12.
+static int ns_iterations(double lo, double hi) {
+  if (!(lo > 0.0) || !(hi >= lo) || !std::isfinite(hi)) return 0;
+  const double e0 = (hi - lo) / (hi + lo);
+  if (e0 < 1e-300) return 1;
+  const double need = 26.0 * std::log(2.0) / -std::log(e0);  // 2^k >= need
+  // one step more than the bounds ask for: they come partly from power
+  // iteration estimates
+  const int k = std::max(1, (int)std::ceil(std::log2(std::max(need, 1.0)))) + 1;
+  return k <= 12 ? k : 0;
+}
+
 // Queue the SMW capacitance of frequency k (no synchronisation); the
 // failure flag of the factorisation of I + R^T G R goes to failT.
 static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
@@ -824,10 +861,35 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
   int sp = split_for(tiles, std::max(r, 1), c->num_sms);
   PhaseScope ph(c, ISDF_PH_SMW);
   if (c->prec == ISDF_PREC_MIXED && c->dinv_ready) {
-    // K = -(D^-1 + G)^-1 with D^-1 from build_polarizability: A = D^-1 + G =
-    // U U^T (U^-1 into Q on the second stream, block row by block row,
-    // beside the factorisation), K = -U^-T U^-1
+    // K = -(D^-1 + G)^-1 with D^-1 from build_polarizability
     CK(launch_add(c->Dinv.p, c->G.p, c->T.p, (long long)rr, c->stream));
+    if (!isdf::tl_capture) {
+      // spectrum of A = D^-1 + G: at least 1 / max w (D <= max w, G >= 0),
+      // at most the Gershgorin bound; a condition number small enough for a
+      // few Newton-Schulz steps takes that route
+      // spectrum of A: from above the smaller of the Gershgorin bound and
+      // 1.1 times a power-iteration estimate; from below 1 / lambda_max(D)
+      // (power iteration, times 1.1) and 1 / max w.  Newton-Schulz converges
+      // whenever the largest eigenvalue is below lo + hi, which these
+      // margins keep well inside.
+      double* nb = c->ns_bound.p;
+      CK(launch_row_abs_sum_max(c->T.p, r, r, nb, c->stream));
+      CK(launch_power_estimate(c->T.p, r, r, 10, nb + 4, nb + 1, c->stream));
+      CK(launch_power_estimate(c->D.p + rr * k, r, r, 10, nb + 4, nb + 2, c->stream));
+      double h[3] = {0.0, 0.0, 0.0};
+      CK(cudaMemcpyAsync(h, nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      const double hi = std::min(h[0], 1.1 * h[1]);
+      const double lo = std::max(1.0 / max_pair_weight(c, k), h[2] > 0.0 ? 1.0 / (1.1 * h[2]) : 0.0);
+      const int iters = ns_iterations(lo, hi);
+      if (iters > 0) {
+        CK(cudaMemsetAsync(failT, 0xff, sizeof(int), c->stream));  // no factorisation to fail
+        CK(isdf::mixed_ns_capacitance(c, Kk, 2.0 / (lo + hi), iters));
+        return ISDF_OK;
+      }
+    }
+    // else A = U U^T (U^-1 into Q on the second stream, block row by block
+    // row, beside the factorisation), K = -U^-T U^-1
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
     CK(launch_cholesky_and_inverse(c->T.p, r, r, 0.0, c->W1.p, r, c->Q.p, r, c->cb_work.p, failT, c->inv_work.p,
@@ -888,6 +950,7 @@ static int smw_workspace(isdf_ctx* c) {
   CK(ensure(c->W1, rr));
   CK(ensure(c->Q, rr));
   CK(ensure(c->partial, (size_t)sp * rr));
+  CK(ensure(c->ns_bound, 4 + 2 * (size_t)r));
   if (c->prec == ISDF_PREC_MIXED) return chol_inverse_workspace(c, r);
   return ISDF_OK;
 }
@@ -1104,7 +1167,7 @@ isdf::KernelTimer::~KernelTimer() {
     return;
   }
   cudaEventRecord(e1, st);
-  c->kprof.push_back({fam, tl_prof_phase, e0, e1, work});
+  c->kprof.push_back({fam, tl_prof_phase, e0, e1, work, st});
 }
 
 static_assert(KF_COUNT == ISDF_NUM_KERNEL_FAMILIES, "kernel families of the header and the launchers differ");
@@ -1138,6 +1201,39 @@ extern "C" int isdf_read_kernel_profile(isdf_ctx* c, double* ms, int* counts, do
     if (work) work[i] = wk[i];
   }
   return ISDF_OK;
+}
+
+extern "C" int isdf_read_kernel_trace(isdf_ctx* c, int max, double* t_start, double* t_end, int* family, int* phase,
+                                      double* work, int* stream) {
+  if (!c || max < 0) return ISDF_ERR_ARG;
+  CK(cudaDeviceSynchronize());
+  const int n = (int)std::min<size_t>(c->kprof.size(), (size_t)max);
+  std::vector<double> t0(n, 0.0), t1(n, 0.0);
+  double tmin = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const auto& r = c->kprof[i];
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, c->kprof[0].e0, r.e0) != cudaSuccess) a = 0.f;
+    if (cudaEventElapsedTime(&b, c->kprof[0].e0, r.e1) != cudaSuccess) b = a;
+    t0[i] = a;
+    t1[i] = b;
+    tmin = std::min(tmin, (double)a);
+  }
+  for (int i = 0; i < n; ++i) {
+    const auto& r = c->kprof[i];
+    if (t_start) t_start[i] = t0[i] - tmin;
+    if (t_end) t_end[i] = t1[i] - tmin;
+    if (family) family[i] = r.fam;
+    if (phase) phase[i] = r.ph;
+    if (work) work[i] = r.work;
+    if (stream) stream[i] = r.st == c->stream ? 0 : (r.st == c->s2 ? 1 : (r.st == c->s3 ? 2 : 3));
+  }
+  for (auto& r : c->kprof) {
+    c->ev_pool.push_back(r.e0);
+    c->ev_pool.push_back(r.e1);
+  }
+  c->kprof.clear();
+  return n;
 }
 
 extern "C" int isdf_read_profile(isdf_ctx* c, double* ms, int* counts) {

@@ -130,6 +130,29 @@ __device__ __forceinline__ float2 split_f64(double x) {
   return make_float2(h, __double2float_rn(x - f32_as_f64(h)));
 }
 
+// FP64 -> FP32 rounded to nearest even by integer operations on the bit
+// fields (no FP64-pipe conversion; GB300 issues FP64 instructions, which
+// include the conversions, at 1/64 of the FP32 rate).  Results below the
+// FP32 normal range flush to zero, above it become infinity.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int ef = (int)((b >> 52) & 0x7FFull) - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
+  unsigned int bits = ((unsigned int)ef << 23) | (unsigned int)(m >> 29);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) bits += 1u;  // a carry moves into the exponent
+  return __uint_as_float(sign | bits);
+}
+
+// split_f64 with one FP64 instruction (the subtraction) instead of three
+__device__ __forceinline__ float2 split_f64_fast(double x) {
+  const float h = f64_to_f32_rn(x);
+  return make_float2(h, f64_to_f32_rn(x - f32_as_f64(h)));
+}
+
 // (hi, lo) += a b: the product's exact FP32 error and both cross terms go to
 // lo (a.lo b.lo, 2^-48 relative, is dropped); hi + p by Knuth's two-sum.
 // The _rn intrinsics keep the compiler from fusing the error-free steps.
@@ -176,6 +199,16 @@ __device__ __forceinline__ float2 df_fms(float2 c, float2 a, float2 b) {
   float hi = c.x, lo = c.y;
   df_fma(make_float2(-a.x, -a.y), b, hi, lo);
   return df_norm(hi, lo);
+}
+
+// 1 / sqrt(d): the FP32 estimate, then one Newton step y + y (1 - d y^2) / 2
+// with d y^2 in double-float (about 2^-46 relative)
+__device__ __forceinline__ float2 df_rsqrt(float2 d) {
+  const float y = rsqrtf(d.x);
+  const float2 y2 = make_float2(__fmul_rn(y, y), fmaf(y, y, -__fmul_rn(y, y)));
+  const float2 t = df_mul(d, y2);  // about 1
+  const float e = __fsub_rn(__fsub_rn(1.0f, t.x), t.y);
+  return df_norm(y, __fmul_rn(__fmul_rn(0.5f, y), e));
 }
 
 // 1 / d: the correctly rounded FP32 reciprocal of d.hi, then one Newton step

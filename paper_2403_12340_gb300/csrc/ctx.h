@@ -95,6 +95,7 @@ struct isdf_ctx {
     int fam, ph;
     cudaEvent_t e0, e1;
     double work;
+    cudaStream_t st;
   };
   std::vector<KRec> kprof;
 
@@ -107,7 +108,7 @@ struct isdf_ctx {
   DevBuf ew;                     // energies and frequencies of the last polarizability, on the device
   // mixed path, one frequency: R^-1 of D = R R^T, D^-1 = R^-T R^-1 and the
   // BF16 slices of R^-1, built beside the Coulomb work of build_polarizability
-  DevBuf Rinv, Dinv, m_sd;
+  DevBuf Rinv, Dinv, m_sd, ns_bound;  // ns_bound: the Gershgorin bound of D^-1 + G
   bool dinv_ready = false;
   std::vector<double> ew_host;   // their host copy (the source of the asynchronous upload)
   bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
@@ -119,6 +120,9 @@ struct isdf_ctx {
   // adjoint (adjoint.cu): L_r^-1, r x r products, the pair matrix at the
   // points and its gradient, device copy of the energies
   DevBuf a_linv, a_m1, a_m2, a_m3, a_m4, a_cp, a_y, a_gd, a_e;
+  // adjoint through the fit: three N_r x r blocks (dL/dZ, the face-split
+  // factors), point-row gradients, two more r x r products
+  DevBuf a_z1, a_z2, a_z3, a_gpm, a_gpp, a_m5, a_m6;
 
   // polarizability / SMW state
   bool polar_ready = false;
@@ -204,6 +208,10 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
 cudaError_t mixed_dinv(isdf_ctx* c, cudaStream_t st);
 // K = -U^-T U^-1 from U^-1 in c->Q into Kk
 cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk);
+// K = -A^-1 for the SPD A in c->T by Newton-Schulz iteration on the tensor
+// cores, X <- X (2 I - A X) from X = alpha I, `iters` times (the last
+// product written negated into Kk)
+cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, int iters);
 // All frequencies at once: D(w_k) for k < n_omega (chunked to a memory
 // budget), and K(w_k) from the factors R(w_k) in c->Rw (T factors and
 // their failure flags in c->bU / fail_T).

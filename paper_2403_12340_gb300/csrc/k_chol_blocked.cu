@@ -161,22 +161,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
   }
 }
 
-// k_chol_diag in double-float arithmetic on the FP32 pipe (the mixed path):
-// the same LDL^T chain of one warp beside twelve update warps, with every
-// element a float pair (about 2^-47 relative per operation).  One dependent
-// double-float step costs a few FP32 latencies (4 cycles each) instead of
-// the FP64 pipe's ~64 cycles per dependent instruction, and the updates of
-// the twelve warps issue on the FP32 pipe at 32 lanes per cycle per
-// sub-partition.  A pivot is accepted when its high part exceeds the
-// threshold (tol_rel * max diag in FP32).  Loads split each FP64 entry
-// (hi = fl32(x), lo = fl32(x - hi)); the factor is written back in FP64.
+// k_chol_diag in double-float arithmetic on the FP32 pipe (the mixed path),
+// which also inverts the factor of the block.  The same LDL^T chain of one
+// warp beside twelve update warps, every element a float pair (about 2^-47
+// relative per operation): one dependent double-float step costs a few
+// FP32 latencies (4 cycles each) instead of the FP64 pipe's ~64 cycles per
+// dependent instruction.  The update warps carry the elimination to an
+// identity block too (Gauss-Jordan on the augmented block [A | I]): with
+// A = Lt D Lt^T (Lt unit lower), the row operations of pivot p,
+// row_i -= l_ip row_p for i > p, turn I into B = Lt^-1, so
+// L^-1 = D^-1/2 B comes out of the same pivot loop with no chain of its own.
+// A pivot is accepted when its high part exceeds the threshold
+// (tol_rel * max diag, in FP32).  Entries are split into float pairs as they
+// are loaded; L goes back to A in FP64, L^-1 to Lid (FP64, ld ldi) and / or
+// Lis (float pairs, ld lds) when those are given.
+constexpr int DIAG_EPT_B = (CB * (CB - 1) / 2 + DIAG_BULK - 1) / DIAG_BULK;  // strict lower elements per thread
+
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long long lda, int j0, int bs,
                                                               const double* dmax, double tol_rel, int* fail,
-                                                              long long sA = 0) {
+                                                              long long sA, double* Lid, long long ldi,
+                                                              float2* Lis, long long lds, long long sS) {
   __shared__ float2 Ls[CB][CB + 1];  // the block, unscaled LDL^T columns
+  __shared__ float2 Bs[CB][CB + 1];  // the identity block under the same row operations
   __shared__ float2 lc[2][CB];       // l_j and l_{j-1}
-  __shared__ float2 piv[CB];         // d_j
-  __shared__ double q[CB];           // d_j^-1/2
+  __shared__ float2 piv[CB];         // d_j, then d_j^-1/2
   __shared__ int s_bad;
   A += sA * blockIdx.x;
   dmax += blockIdx.x;
@@ -184,22 +192,37 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long l
   if (*(volatile int*)fail >= 0) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
-    int i = idx & (CB - 1), k = idx >> 6;
-    Ls[i][k] = (i < bs && k <= i) ? split_f64(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.0f, 0.0f);
+    const int i = idx & (CB - 1), k = idx >> 6;
+    Ls[i][k] = (i < bs && k <= i) ? split_f64_fast(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.0f, 0.0f);
+    Bs[i][k] = make_float2(i == k ? 1.0f : 0.0f, 0.0f);
   }
+  // the warps on sub-partitions 1-3 own fixed elements of both blocks,
+  // packed as row * 64 + column: the lower triangle of A, the strict lower
+  // triangle of B
   const bool bulk = (warp & 3) != 0;
-  int own[DIAG_EPT];
+  int ownA[DIAG_EPT], ownB[DIAG_EPT_B];
   {
     const int b = (warp - 1 - (warp >> 2)) * 32 + lane;
 #pragma unroll
     for (int q = 0; q < DIAG_EPT; ++q) {
       const int e = b + DIAG_BULK * q;
-      own[q] = -1;
+      ownA[q] = -1;
       if (bulk && e < CB * (CB + 1) / 2) {
         int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
         while ((a + 1) * (a + 2) / 2 <= e) ++a;
         while (a * (a + 1) / 2 > e) --a;
-        own[q] = a * CB + (e - a * (a + 1) / 2);
+        ownA[q] = a * CB + (e - a * (a + 1) / 2);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < DIAG_EPT_B; ++q) {
+      const int e = b + DIAG_BULK * q;  // row a >= 1 holds e in [a (a - 1) / 2, a (a + 1) / 2)
+      ownB[q] = -1;
+      if (bulk && e < CB * (CB - 1) / 2) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 <= e) ++a;
+        while (a * (a - 1) / 2 > e) --a;
+        ownB[q] = a * CB + (e - a * (a - 1) / 2);
       }
     }
   }
@@ -209,9 +232,20 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long l
   for (int j = 0; j < bs; ++j) {
     const float2* lp = lc[(j + 1) & 1];  // l_{j-1}
     if (warp == 0) {
-      if (j > 0) {
+      if (j > 0) {  // column j gets the update of pivot j - 1
         const float2 ajj1 = Ls[j][j - 1];
-        for (int i = j + lane; i < bs; i += 32) Ls[i][j] = df_fms(Ls[i][j], lp[i], ajj1);
+        const int i0 = j + lane, i1 = j + 32 + lane;
+        float2 x0 = make_float2(0.0f, 0.0f), x1 = x0, l0 = x0, l1 = x0;
+        if (i0 < bs) {
+          x0 = Ls[i0][j];
+          l0 = lp[i0];
+        }
+        if (i1 < bs) {
+          x1 = Ls[i1][j];
+          l1 = lp[i1];
+        }
+        if (i0 < bs) Ls[i0][j] = df_fms(x0, l0, ajj1);
+        if (i1 < bs) Ls[i1][j] = df_fms(x1, l1, ajj1);
         __syncwarp();
       }
       const float2 d = Ls[j][j];
@@ -221,14 +255,56 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long l
         const float2 r = df_recip(d);
         if (lane == 0) piv[j] = d;
         float2* lj = lc[j & 1];
-        for (int i = j + 1 + lane; i < bs; i += 32) lj[i] = df_mul(Ls[i][j], r);
+        const int i0 = j + 1 + lane, i1 = j + 33 + lane;
+        float2 x0 = make_float2(0.0f, 0.0f), x1 = x0;
+        if (i0 < bs) x0 = Ls[i0][j];
+        if (i1 < bs) x1 = Ls[i1][j];
+        if (i0 < bs) lj[i0] = df_mul(x0, r);
+        if (i1 < bs) lj[i1] = df_mul(x1, r);
       }
     } else if (bulk && j > 0) {
+      const int p = j - 1;
+      // A: columns k > j take the update of pivot p
+      {
+        float2 c[DIAG_EPT], a[DIAG_EPT], b[DIAG_EPT];
+        bool on[DIAG_EPT];
 #pragma unroll
-      for (int q = 0; q < DIAG_EPT; ++q) {
-        const int o = own[q];
-        const int i = o >> 6, k = o & (CB - 1);
-        if (o >= 0 && k > j && i < bs) Ls[i][k] = df_fms(Ls[i][k], lp[i], Ls[k][j - 1]);
+        for (int q = 0; q < DIAG_EPT; ++q) {
+          const int o = ownA[q], i = o >> 6, k = o & (CB - 1);
+          on[q] = o >= 0 && k > j && i < bs;
+          if (on[q]) {
+            c[q] = Ls[i][k];
+            a[q] = lp[i];
+            b[q] = Ls[k][p];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < DIAG_EPT; ++q)
+          if (on[q]) {
+            const int o = ownA[q];
+            Ls[o >> 6][o & (CB - 1)] = df_fms(c[q], a[q], b[q]);
+          }
+      }
+      // B: row i >= j takes row p times l_ip (columns m <= p; B_pp = 1)
+      {
+        float2 c[DIAG_EPT_B], a[DIAG_EPT_B], b[DIAG_EPT_B];
+        bool on[DIAG_EPT_B];
+#pragma unroll
+        for (int q = 0; q < DIAG_EPT_B; ++q) {
+          const int o = ownB[q], i = o >> 6, m = o & (CB - 1);
+          on[q] = o >= 0 && m <= p && i >= j && i < bs;
+          if (on[q]) {
+            c[q] = Bs[i][m];
+            a[q] = lp[i];
+            b[q] = Bs[p][m];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < DIAG_EPT_B; ++q)
+          if (on[q]) {
+            const int o = ownB[q];
+            Bs[o >> 6][o & (CB - 1)] = df_fms(c[q], a[q], b[q]);
+          }
       }
     }
     __syncthreads();
@@ -238,12 +314,25 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long l
     if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
     return;
   }
-  if (t < bs) q[t] = rsqrt_newton(df_to_f64(piv[t]));
+  // L = Lt D^1/2: L_ik = u_ik d_k^-1/2 (u = Lt D), L_ii = d_i d_i^-1/2;
+  // L^-1 = D^-1/2 B
+  float2 dq = make_float2(0.0f, 0.0f);
+  if (t < bs) dq = df_rsqrt(piv[t]);
+  __syncthreads();
+  if (t < bs) {
+    lc[0][t] = dq;                     // d^-1/2
+    lc[1][t] = df_mul(piv[t], dq);     // d^1/2
+  }
   __syncthreads();
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
     const int i = idx % bs, k = idx / bs;
-    const double v = (k < i) ? df_to_f64(Ls[i][k]) * q[k] : (k == i ? df_to_f64(piv[i]) * q[i] : 0.0);
+    const double v = (k < i) ? df_to_f64(df_mul(Ls[i][k], lc[0][k])) : (k == i ? df_to_f64(lc[1][i]) : 0.0);
     A[(j0 + i) + lda * (long long)(j0 + k)] = v;
+    if (Lid || Lis) {
+      const float2 w = (k < i) ? df_mul(Bs[i][k], lc[0][i]) : (k == i ? lc[0][i] : make_float2(0.0f, 0.0f));
+      if (Lid) Lid[i + ldi * (long long)k] = df_to_f64(w);
+      if (Lis) Lis[sS * blockIdx.x + i + lds * k] = w;
+    }
   }
 }
 
@@ -295,51 +384,58 @@ __global__ void __launch_bounds__(256) k_panel_trsm(double* A, long long lda, in
   }
 }
 
-// k_panel_trsm in double-float arithmetic (the mixed path): the diagonal
-// block and each row are split into float pairs as they are loaded, the
-// forward substitution runs on the FP32 pipe, and the solved row goes out
-// in FP64 to A and, unchanged, as the float pairs of the split panel Sp
-// that the double-float trailing update reads.
-__global__ void __launch_bounds__(256) k_panel_trsm_df(double* A, long long lda, int j0, int bs, int rem,
+// The panel of the mixed path as a product, A21 <- A21 L_jj^-T, with the
+// float pairs of L_jj^-1 that k_chol_diag_df wrote (Lis, ld lds): each
+// output is an independent dot product, so no substitution chain remains.
+// One block per 16 panel rows (256 threads, a row and four columns each),
+// double-float accumulation on the FP32 pipe; rows are read whole into
+// shared memory before any is written back, in FP64 to A and as the float
+// pairs of the split panel Sp for the trailing update.
+constexpr int PG_ROWS = 16;
+
+__global__ void __launch_bounds__(256) k_panel_gemm_df(double* A, long long lda, int j0, int bs, int rem,
                                                       const int* fail, long long sA, float2* Sp, long long lds,
-                                                      long long sS) {
-  __shared__ float2 Lt[CB][CB + 1];
-  __shared__ float2 inv[CB];
+                                                      long long sS, const float2* __restrict__ Lis) {
+  __shared__ float2 As[PG_ROWS][CB + 1];
+  __shared__ float2 Bs[CB][CB + 1];  // Bs[j][m] = (L_jj^-1)(j, m), zero above the diagonal
   A += sA * blockIdx.y;
+  Sp += sS * blockIdx.y;
+  Lis += sS * blockIdx.y;
   if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
   const int t = threadIdx.x;
+  const int row0 = blockIdx.x * PG_ROWS;
+  const float2 zero = make_float2(0.0f, 0.0f);
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
-    const int i = idx & (CB - 1), k = idx >> 6;
-    Lt[i][k] = (i < bs && k <= i) ? split_f64(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.0f, 0.0f);
+    const int jj = idx & (CB - 1), m = idx >> 6;
+    Bs[jj][m] = (jj < bs && m <= jj) ? Lis[jj + lds * m] : zero;
+  }
+  for (int idx = t; idx < PG_ROWS * CB; idx += blockDim.x) {
+    const int rr = idx % PG_ROWS, m = idx / PG_ROWS;
+    const int row = row0 + rr;
+    As[rr][m] = (row < rem && m < bs) ? split_f64_fast(A[(j0 + bs + row) + lda * (long long)(j0 + m)]) : zero;
   }
   __syncthreads();
-  if (t < bs) inv[t] = df_recip(Lt[t][t]);
-  __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
-  const float2 zero = make_float2(0.0f, 0.0f);
-  for (int row = blockIdx.x * 8 + warp; row < rem; row += gridDim.x * 8) {
-    double* a = A + (j0 + bs + row) + lda * (long long)j0;
-    float2 x0 = lane < bs ? split_f64(a[lda * lane]) : zero;
-    float2 x1 = lane + 32 < bs ? split_f64(a[lda * (lane + 32)]) : zero;
-    for (int k = 0; k < bs; ++k) {
-      float2 xk;
-      if (k < 32) {
-        if (lane == k) x0 = df_mul(x0, inv[k]);
-        xk.x = __shfl_sync(0xffffffffu, x0.x, k);
-        xk.y = __shfl_sync(0xffffffffu, x0.y, k);
-      } else {
-        if (lane == k - 32) x1 = df_mul(x1, inv[k]);
-        xk.x = __shfl_sync(0xffffffffu, x1.x, k - 32);
-        xk.y = __shfl_sync(0xffffffffu, x1.y, k - 32);
-      }
-      if (lane > k) x0 = df_fms(x0, xk, Lt[lane][k]);
-      if (lane + 32 > k) x1 = df_fms(x1, xk, Lt[lane + 32][k]);
+  const int rr = t >> 4, cq = t & 15;
+  float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m0 = 0; m0 < bs; m0 += 32) {
+    const int me = min(bs, m0 + 32);
+    for (int m = m0; m < me; ++m) {
+      const float2 a = As[rr][m];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) df_fma(a, Bs[cq + 16 * q][m], hi[q], lo[q]);
     }
-    if (lane < bs) a[lda * lane] = df_to_f64(x0);
-    if (lane + 32 < bs) a[lda * (lane + 32)] = df_to_f64(x1);
-    float2* sp = Sp + sS * blockIdx.y + row;
-    if (lane < bs) sp[lds * lane] = x0;
-    if (lane + 32 < bs) sp[lds * (lane + 32)] = x1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) df_renorm(hi[q], lo[q]);
+  }
+  const int row = row0 + rr;
+  if (row >= rem) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = cq + 16 * q;
+    if (jj >= bs) continue;
+    const float2 x = df_norm(hi[q], lo[q]);
+    A[(j0 + bs + row) + lda * (long long)(j0 + jj)] = df_to_f64(x);
+    Sp[row + lds * jj] = x;
   }
 }
 
@@ -537,14 +633,22 @@ static double df_tol(double tol_rel, const float2* split) {
   return split && tol_rel > 0.0 ? std::max(tol_rel, kDfPivotTol) : tol_rel;
 }
 
+// One diagonal block.  The mixed path (split != null, split panel of n rows,
+// problem z at + z sS) factors in double-float and leaves L_jj^-1 as float
+// pairs in the last 64 rows of the split panel, rows that no panel reaches
+// (a panel holds at most n - 64 rows); Lid (FP64, ld ldi), if given, gets
+// L_jj^-1 too.
 static cudaError_t diag_step(double* L, long long ldl, int j0, int bs, const double* dmax, double tol_rel, int* fail,
-                             long long sL, int batch, bool df, cudaStream_t s) {
+                             long long sL, int batch, float2* split, long long n, long long sS, double* Lid,
+                             long long ldi, cudaStream_t s) {
   KernelTimer kt(KF_CHOL_DIAG, s, bs * (double)bs * bs / 3.0 * batch);  // bs^3 / 3 flops (FP64 or double-float)
   note_launch();
-  if (df)
-    k_chol_diag_df<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
-  else
+  if (split) {
+    float2* lis = n > CB ? split + (n - CB) : nullptr;  // n <= 64: one block, no panel
+    k_chol_diag_df<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL, Lid, ldi, lis, n, sS);
+  } else {
     k_chol_diag<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
+  }
   return cudaGetLastError();
 }
 
@@ -555,7 +659,8 @@ static cudaError_t panel_step(double* L, long long ldl, int j0, int bs, int rem,
   KernelTimer kt(split ? KF_DF_GEMM : KF_FP64_GEMM, s, (double)rem * bs * bs * batch);  // rem bs^2 flops
   note_launch();
   if (split)
-    k_panel_trsm_df<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, split, lds, sS);
+    k_panel_gemm_df<<<dim3((rem + PG_ROWS - 1) / PG_ROWS, batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, split,
+                                                                              lds, sS, split + (lds - CB));
   else
     k_panel_trsm<<<dim3(panel_blocks(rem), batch), 256, 0, s>>>(L, ldl, j0, bs, rem, fail, sL, nullptr, lds, sS);
   return cudaGetLastError();
@@ -581,7 +686,8 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
   tol_rel = df_tol(tol_rel, split);
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
-    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split != nullptr, s)) != cudaSuccess) return e;
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split, n, 0, nullptr, 0, s)) != cudaSuccess)
+      return e;
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
     if ((e = panel_step(L, ldl, j0, bs, rem, fail, 0, 1, split, n, 0, s)) != cudaSuccess) return e;
@@ -601,7 +707,8 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
                                         float2* split) {
   if (n <= 0) return cudaSuccess;
   DfGemm df(split != nullptr);  // the inverse rows in the same arithmetic as the trailing updates
-  cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, n * sizeof(double), n, aux);
+  // on s: with double-float blocks the diagonal blocks of Li are written from s
+  cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, n * sizeof(double), n, split ? s : aux);
   if (e != cudaSuccess) return e;
   if (L != W) {
     e = cudaMemcpy2DAsync(L, ldl * sizeof(double), W, ldw * sizeof(double), n * sizeof(double), n,
@@ -616,13 +723,16 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
   tol_rel = df_tol(tol_rel, split);
   for (int j0 = 0, jb = 0; j0 < n; j0 += CB, ++jb) {
     const int bs = min(CB, n - j0);
-    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split != nullptr, s)) != cudaSuccess) return e;
+    double* Ljj = L + j0 + ldl * (long long)j0;
+    double* Lijj = Li + j0 + ldi * (long long)j0;
+    // the double-float block factorisation writes L_jj^-1 into Li itself
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split, n, 0, split ? Lijj : nullptr, ldi, s)) !=
+        cudaSuccess)
+      return e;
     // row block jb of the inverse, beside the rest of the factorisation
     if ((e = cudaEventRecord(ev[jb], s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(aux, ev[jb], 0)) != cudaSuccess) return e;
-    double* Ljj = L + j0 + ldl * (long long)j0;
-    double* Lijj = Li + j0 + ldi * (long long)j0;
-    if ((e = launch_diag_inverse_block(Ljj, ldl, bs, Lijj, ldi, aux)) != cudaSuccess) return e;
+    if (!split && (e = launch_diag_inverse_block(Ljj, ldl, bs, Lijj, ldi, aux)) != cudaSuccess) return e;
     if (j0 > 0) {
       const long long tiles = (long long)((bs + 63) / 64) * ((j0 + 63) / 64);
       const int sp = (int)std::max(1LL, std::min<long long>(8, (2 * 152 + tiles - 1) / tiles));
@@ -665,7 +775,9 @@ cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long
   tol_rel = df_tol(tol_rel, split);
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int bs = min(CB, n - j0);
-    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, sL, batch, split != nullptr, s)) != cudaSuccess) return e;
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, sL, batch, split, n, (long long)n * CB, nullptr, 0, s)) !=
+        cudaSuccess)
+      return e;
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
     if ((e = panel_step(L, ldl, j0, bs, rem, fail, sL, batch, split, n, (long long)n * CB, s)) != cudaSuccess)

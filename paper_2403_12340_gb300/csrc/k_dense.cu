@@ -109,6 +109,97 @@ cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, i
   return cudaGetLastError();
 }
 
+// *out = max_i sum_j |A(i, j)| (Gershgorin bound of the spectrum of a
+// symmetric A); *out must hold +0.0 before the launch.  Row sums are
+// non-negative, so their bit patterns order like their values.
+__global__ void k_row_abs_sum_max(const double* __restrict__ A, long long lda, int n, unsigned long long* out) {
+  __shared__ double red[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (i < n)
+    for (int j = 0; j < n; ++j) acc += fabs(A[i + lda * (long long)j]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+cudaError_t launch_row_abs_sum_max(const double* A, long long lda, int n, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess || n <= 0) return e;
+  note_launch();
+  k_row_abs_sum_max<<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
+// Power iteration for the largest eigenvalue of a symmetric positive
+// semidefinite A (n x n, ld lda) in FP32 (an estimate is all it gives):
+// x_0 = 1 / sqrt(n) in every entry, then x <- A x / |A x|, one launch per
+// step.  Step k reads y_{k-1}, normalises it on the fly (every block
+// recomputes its norm), accumulates y_k = A x over column chunks with
+// atomics, and zeroes y_{k+1} for the next step (three rotating vectors).
+// *lam = |y_k| of the last step, which approaches the largest eigenvalue
+// from below.  work: 3 n + 2 floats.
+__global__ void k_power_step(const double* __restrict__ A, long long lda, int n, float* y, int k) {
+  __shared__ float red[256];
+  __shared__ float s_inv;
+  float* yp = y + (size_t)((k + 2) % 3) * n;  // y_{k-1}
+  float* yk = y + (size_t)(k % 3) * n;
+  float* yn = y + (size_t)((k + 1) % 3) * n;  // y_{k+1}
+  float acc = 0.0f;
+  if (k > 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += yp[i] * yp[i];
+  red[threadIdx.x] = k > 0 ? acc : (threadIdx.x == 0 ? (float)n : 0.0f);
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s_inv = red[0] > 0.0f ? rsqrtf(red[0]) : 0.0f;
+  __syncthreads();
+  const float inv = s_inv;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cw = (n + gridDim.y - 1) / gridDim.y;
+  const int j0 = blockIdx.y * cw, j1 = min(n, j0 + cw);
+  if (i < n) {
+    float a = 0.0f;
+    for (int j = j0; j < j1; ++j) a = fmaf(f64_to_f32_rn(A[i + lda * (long long)j]), k > 0 ? yp[j] * inv : inv, a);
+    atomicAdd(yk + i, a);
+    if (blockIdx.y == 0) yn[i] = 0.0f;
+  }
+}
+
+__global__ void k_power_norm(const float* __restrict__ y, int n, double* lam) {
+  __shared__ float red[1024];
+  float acc = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += y[i] * y[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *lam = sqrt((double)red[0]);
+}
+
+cudaError_t launch_power_estimate(const double* A, long long lda, int n, int steps, double* work, double* lam,
+                                  cudaStream_t s) {
+  if (n <= 0 || steps < 1) return cudaErrorInvalidValue;
+  float* y = reinterpret_cast<float*>(work);
+  cudaError_t e = cudaMemsetAsync(y, 0, 3 * (size_t)n * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < steps; ++k) {
+    note_launch();
+    k_power_step<<<dim3((n + 255) / 256, 16), 256, 0, s>>>(A, lda, n, y, k);
+  }
+  note_launch();
+  k_power_norm<<<1, 1024, 0, s>>>(y + (size_t)((steps - 1) % 3) * n, n, lam);
+  return cudaGetLastError();
+}
+
 // c = a + b over n contiguous doubles (problem z at + z stride)
 __global__ void k_add(const double* a, const double* b, double* c, long long n,
                       long long stride) {

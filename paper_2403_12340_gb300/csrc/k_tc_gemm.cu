@@ -255,6 +255,7 @@ struct TcArgs {
   int kv_iters;                // NACC == 2: chunks of the first accumulator
   int lower_only;              // M == N; only tiles with n-tile <= m-tile
   int tri_b;                   // B(n, k) == 0 for k > n: skip chunks beyond the tile's last n
+  int group;                   // NACC == 1: 64-wide K chunks per FP32 accumulation run (0: the whole unit)
   int tiles_m, tiles_n;        // tiles along M and N
   int count;                   // problems of the batch
   int splits;                  // K splits per problem (units: problem, split, tile)
@@ -321,6 +322,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   __shared__ int s_abort;
   constexpr uint32_t ACC_COLS = NACC * BN;
+  // Grouped accumulation (NACC == 1, a.group > 0): each unit's K range runs
+  // as groups of a.group chunks, each summed in FP32 in one accumulator
+  // buffer, and the epilogue adds every group into a double-float running
+  // sum (hi, lo) kept in two more TMEM column blocks; the FP32 rounding then
+  // builds up over a.group * 64 terms at most instead of the whole range.
+  const bool grouped = NACC == 1 && a.group > 0;
+  const uint32_t tcols = grouped ? 2 * ACC_COLS + 2 * BN : 2 * ACC_COLS;  // 512 or 256 for BN 128 / 64
+  const uint32_t df_hi = 2 * ACC_COLS, df_lo = 2 * ACC_COLS + BN;       // column offsets of the running sum
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles = a.lower_only ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc::fence_mbar_init();
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, 2 * ACC_COLS);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, tcols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -374,20 +383,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- MMA issuer
     constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_BM, BN);
     uint32_t g = 0;
-    int li = 0;  // units done by this block
-    for (long long u = blockIdx.x; u < units && !s_abort; u += gridDim.x, ++li) {
+    uint32_t gi = 0;  // accumulation groups issued by this block (one per unit unless grouped)
+    bool stop = false;
+    for (long long u = blockIdx.x; u < units && !s_abort && !stop; u += gridDim.x) {
       const TcUnit w = tc_unit(a, u, tiles, BN);
-      const int buf = li & 1;
-      // the epilogue has read this buffer's previous unit (two units ago)
-      if (!tc::mbar_wait(&tempty[buf], ((uint32_t)(li >> 1) & 1u) ^ 1u, a.status)) {
+      const int ng = (grouped && w.ke > w.kb) ? (w.ke - w.kb + a.group - 1) / a.group : 1;
+      int kc = w.kb;
+      for (int gr = 0; gr < ng; ++gr, ++gi) {
+      const int buf = (int)(gi & 1u);
+      // the epilogue has read this buffer's previous group (two groups ago)
+      if (!tc::mbar_wait(&tempty[buf], ((gi >> 1) & 1u) ^ 1u, a.status)) {
         s_abort = 1;
+        stop = true;
         break;
       }
       tc::fence_after_sync();
       const uint32_t dbase = tmem + (uint32_t)buf * ACC_COLS;
       bool first[2] = {true, true};
       bool ok = true;
-      for (int kc = w.kb; kc < w.ke; ++kc, ++g) {
+      const int kg0 = kc;
+      const int kend = grouped ? min(w.ke, kc + a.group) : w.ke;
+      for (; kc < kend; ++kc, ++g) {
         const int st = (int)(g % (uint32_t)S);
         const uint32_t ph = (g / (uint32_t)S) & 1u;
         if (!tc::mbar_wait(&full[st], ph, a.status)) {
@@ -414,36 +430,95 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       if (!ok) {
         s_abort = 1;
+        stop = true;
         break;
       }
-      if (w.ke > w.kb) {
+      if (kend > kg0) {
         tc::mma_commit(&tfull[buf]);
       } else {
         tc::mbar_arrive(&tfull[buf]);
+      }
       }
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: thread <-> tile row (TMEM lane)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
-    int li = 0;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x, ++li) {
+    uint32_t gi = 0;  // accumulation groups consumed, in the MMA warp's order
+    bool stop = false;
+    for (long long u = blockIdx.x; u < units && !stop; u += gridDim.x) {
       const TcUnit w = tc_unit(a, u, tiles, BN);
-      const int buf = li & 1;
-      const bool ok = tc::mbar_wait(&tfull[buf], (uint32_t)(li >> 1) & 1u, a.status);
+      const int ng = (grouped && w.ke > w.kb) ? (w.ke - w.kb + a.group - 1) / a.group : 1;
+      for (int gr = 0; gr < ng; ++gr, ++gi) {
+      const int buf = (int)(gi & 1u);
+      const bool ok = tc::mbar_wait(&tfull[buf], (gi >> 1) & 1u, a.status);
       tc::fence_after_sync();
-      if (!ok || s_abort) break;
+      if (!ok || s_abort) {
+        stop = true;
+        break;
+      }
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+      const uint32_t lane_addr = lane_base + (uint32_t)buf * ACC_COLS;
+      if (grouped && gr + 1 < ng) {
+        // not the unit's last group: fold it into the double-float running sum
+        for (int c = 0; c < BN; c += 16) {
+          float v[16], hi[16], lo[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)c, v);
+          if (gr == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              hi[i] = v[i];
+              lo[i] = 0.f;
+            }
+          } else {
+            tc::tmem_ld16(lane_base + df_hi + (uint32_t)c, hi);
+            tc::tmem_ld16(lane_base + df_lo + (uint32_t)c, lo);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float t = __fadd_rn(hi[i], v[i]);
+              const float bv = __fsub_rn(t, hi[i]);
+              const float err = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(t, bv)), __fsub_rn(v[i], bv));
+              const float l = __fadd_rn(lo[i], err);
+              hi[i] = __fadd_rn(t, l);
+              lo[i] = __fsub_rn(l, __fsub_rn(hi[i], t));
+            }
+          }
+          tc::tmem_st16(lane_base + df_hi + (uint32_t)c, hi);
+          tc::tmem_st16(lane_base + df_lo + (uint32_t)c, lo);
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty[buf]);
+        continue;
+      }
+      const bool with_sum = grouped && gr > 0;  // the unit's result is the running sum plus this group
       const int m = w.m0 + row;
       const bool have = w.ke > w.kb;
       const bool have1 = NACC == 2 && have && w.ke > a.kv_iters;
       const bool have0 = have && (NACC == 1 || w.kb < a.kv_iters);
-      const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * ACC_COLS;
       double* Cb = a.C + a.c_bstride * w.bidx;
       for (int c = 0; c < BN; c += 16) {
-        float v0[16], v1[16];
+        float v0[16], v1[16], w0[16];
         if (have0) tc::tmem_ld16(lane_addr + (uint32_t)c, v0);
         else
           for (int i = 0; i < 16; ++i) v0[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w0[i] = 0.f;
+        if (with_sum) {
+          // (hi, lo) + v0 -> (v0, w0): the value to 48 bits, high part in v0
+          float hi[16], lo[16];
+          tc::tmem_ld16(lane_base + df_hi + (uint32_t)c, hi);
+          tc::tmem_ld16(lane_base + df_lo + (uint32_t)c, lo);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float t = __fadd_rn(hi[i], v0[i]);
+            const float bv = __fsub_rn(t, hi[i]);
+            const float err = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(t, bv)), __fsub_rn(v0[i], bv));
+            const float l = __fadd_rn(lo[i], err);
+            v0[i] = __fadd_rn(t, l);
+            w0[i] = __fsub_rn(l, __fsub_rn(v0[i], t));
+          }
+        }
         if (NACC == 2) {
           if (have1) tc::tmem_ld16(lane_addr + (uint32_t)(BN + c), v1);
           else
@@ -469,7 +544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int i = 0; i < 16; ++i) {
             const int n = w.n0 + c + i;
             if (n >= a.N) break;
-            Cb[m + a.ldc * n] = tc::f2d(v0[i]);
+            Cb[m + a.ldc * n] = with_sum ? tc::f2d(v0[i]) + tc::f2d(w0[i]) : tc::f2d(v0[i]);
             __nv_bfloat16 x0, x1, x2;
             split3f(v0[i], x0, x1, x2);
             if (!whole) {
@@ -514,10 +589,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (a.s > 1) a.zs[base + sstr] = x1;
             if (a.s > 2) a.zs[base + 2 * sstr] = x2;
           } else if (a.partial) {
-            a.partial[((long long)w.bidx * a.splits + w.split) * a.M * a.N + m + (long long)a.M * n] = tc::f2d(vf);
+            a.partial[((long long)w.bidx * a.splits + w.split) * a.M * a.N + m + (long long)a.M * n] =
+                with_sum ? tc::f2d(vf) + tc::f2d(w0[i]) : tc::f2d(vf);
           } else {
-            // alpha = 1, beta = 0 (the common case) needs no FP64 arithmetic
-            double o = (a.alpha == 1.0) ? tc::f2d(vf) : a.alpha * tc::f2d(vf);
+            // alpha = 1, beta = 0 and no running sum (the common case) need no FP64 arithmetic
+            const double vd = with_sum ? tc::f2d(vf) + tc::f2d(w0[i]) : tc::f2d(vf);
+            double o = (a.alpha == 1.0) ? vd : a.alpha * vd;
             if (a.beta != 0.0) o += a.beta * Cb[m + a.ldc * n];
             Cb[m + a.ldc * n] = o;
             if (a.lower_only && w.mt != w.nt) Cb[n + a.ldc * m] = o;
@@ -528,11 +605,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[buf]);
+      }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, 2 * ACC_COLS);
+  if (warp == 1) tc::tmem_dealloc(tmem, tcols);
 }
 
 // ------------------------------------------------------------ host side
@@ -587,6 +665,7 @@ static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, i
   }
   if (smem > TC_SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
   const int tm = (a.M + TC_BM - 1) / TC_BM, tn = (a.N + BN - 1) / BN;
+  a.group = NACC == 1 ? tl_tc_group : 0;
   a.tiles_m = tm;
   a.tiles_n = tn;
   a.splits = splits;
@@ -622,6 +701,7 @@ static void split_k(int k_iters, int tiles, int num_sms, int max_split, int& spl
 }
 
 thread_local int tl_tc_sm_reserve = 0;
+thread_local int tl_tc_group = kTcGroupChunks;
 
 // ------------------------------------------------------------ tile autotuner
 //

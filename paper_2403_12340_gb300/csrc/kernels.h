@@ -48,6 +48,24 @@ struct DfGemm {
   explicit DfGemm(bool on) : prev(tl_gemm_df) { tl_gemm_df = on; }
   ~DfGemm() { tl_gemm_df = prev; }
 };
+// Chunks per FP32 accumulation run of the tensor-core GEMMs launched from
+// this thread (kTcGroupChunks unless a TcGroup scope says otherwise; 0:
+// one run per block's K range).
+// The FP32 accumulator of a block restarts every this many chunks (512
+// terms) and the runs are summed in double-float arithmetic in tensor
+// memory (GEMMs with one accumulator): the tensor cores' FP32 sums of long
+// same-sign runs otherwise lose about 2^-24 per term, which left D = S S^T
+// (a sum over all pairs) at 5e-5 relative.  Two products skip it (TcGroup(0)):
+// the fit's triangular GEMM, whose epilogue writes three outputs and whose
+// error is set by the Gram it reads, and the SYRK of G, whose error is set
+// by the FP32 transform of theta.
+constexpr int kTcGroupChunks = 8;
+extern thread_local int tl_tc_group;
+struct TcGroup {
+  int prev;
+  explicit TcGroup(int n) : prev(tl_tc_group) { tl_tc_group = n; }
+  ~TcGroup() { tl_tc_group = prev; }
+};
 struct TcSmReserve {
   int prev;
   explicit TcSmReserve(int n) : prev(tl_tc_sm_reserve) { tl_tc_sm_reserve = n; }
@@ -115,6 +133,14 @@ cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, i
 // not null), index k n_v n_c + i n_c + j.
 cudaError_t launch_pair_weights(const double* ew, int n_v, int n_c, int n_omega, double* sw, float* swf,
                                 cudaStream_t s);
+// *out (device double) = max_i sum_j |A(i, j)|, the Gershgorin bound of a
+// symmetric A's spectrum
+cudaError_t launch_row_abs_sum_max(const double* A, long long lda, int n, double* out, cudaStream_t s);
+// *lam (device) = an estimate of the largest eigenvalue of a symmetric
+// positive semidefinite A by `steps` FP32 power iterations (from below;
+// work: 2 n doubles)
+cudaError_t launch_power_estimate(const double* A, long long lda, int n, int steps, double* work, double* lam,
+                                  cudaStream_t s);
 // c = a + b, n doubles (c may be a or b); batch problems at + z stride
 cudaError_t launch_add(const double* a, const double* b, double* c, long long n, cudaStream_t s, int batch = 1,
                        long long stride = 0);

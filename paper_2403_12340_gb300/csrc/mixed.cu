@@ -120,6 +120,7 @@ cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r, bool linv_ready) 
   MK(ensure_bf16(c->m_thetas_t, ntt));
   if (nrp != nr || rk != r) MK(cudaMemsetAsync(c->m_ths.p, 0, nth * 2, st));  // zero padding
   if (rp != r || kpg != nr) MK(cudaMemsetAsync(c->m_thetas_t.p, 0, ntt * 2, st));
+  TcGroup whole_runs(0);
   MK(tc_gemm_f64_slices(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, theta, nr, true, c->m_ths.bf(), nrp,
                         rk, c->m_thetas_t.bf(), rp, kpg, c->d_status, st));
   return cudaSuccess;
@@ -146,6 +147,7 @@ cudaError_t mixed_polar_G(isdf_ctx* c) {
   }
   {
     PhaseTimer ph(c, ISDF_PH_SYRK_G);
+    TcGroup whole_runs(0);
     MK(tc_gemm_f64(op(c->m_ss, rp, kps), op(c->m_ss, rp, kps), r, r, 1.0, 0.0, c->G.p, r, true, false,
                    c->partial.p, max_split, c->num_sms, c->d_status, st));
   }
@@ -392,6 +394,40 @@ cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk) {
   MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 0.0, Kk, r, true, false, nullptr, 1,
                  c->num_sms, c->d_status, st));
   return launch_symmetrize(Kk, r, r, st);
+}
+
+// K = -A^-1 by Newton-Schulz iteration, X_{k+1} = X_k (2 I - A X_k) from
+// X_0 = alpha I, on the tensor cores.  Every iterate is a polynomial in the
+// symmetric A, so X and Y = 2 I - A X are symmetric and one slice layout
+// serves both sides of each product.  The error contracts quadratically,
+// |I - A X_k| = |I - alpha A|^(2^k), down to the FP32-grade rounding of the
+// products; in the whitened basis A = D^-1 + G has a spectrum within
+// [1 / max w, 1 / min w + |G|] (w the pair weights), a condition number of
+// a few, so a handful of iterations reach that level.
+cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, int iters) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const size_t rr = (size_t)r * r;
+  double* X = c->Q.p;
+  double* X2 = c->W1.p;
+  double* Y = c->R.p;
+  MK(slices_cm(c->m_sd, c->T.p, r, r, r, rp, rk, st));  // A, once
+  MK(cudaMemsetAsync(X, 0, rr * sizeof(double), st));
+  MK(launch_add_identity(X, r, r, alpha, st));
+  for (int it = 0; it < iters; ++it) {
+    const bool last = it + 1 == iters;
+    MK(slices_cm(c->m_sa, X, r, r, r, rp, rk, st));
+    MK(cudaMemsetAsync(Y, 0, rr * sizeof(double), st));
+    MK(launch_add_identity(Y, r, r, 2.0, st));
+    MK(tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 1.0, Y, r, true, false, nullptr, 1,
+                   c->num_sms, c->d_status, st));  // Y = 2 I - A X (symmetric: lower tiles, mirrored)
+    MK(slices_cm(c->m_sb, Y, r, r, r, rp, rk, st));
+    double* out = last ? Kk : X2;
+    MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sb, rp, rk), r, r, last ? -1.0 : 1.0, 0.0, out, r, true, false,
+                   nullptr, 1, c->num_sms, c->d_status, st));  // X Y, symmetric (negated at the end: K)
+    std::swap(X, X2);
+  }
+  return cudaSuccess;
 }
 
 // Y = X + V theta K theta^T X for one chunk of nc columns.

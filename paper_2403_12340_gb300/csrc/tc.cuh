@@ -139,24 +139,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 16 consecutive FP32 columns into TMEM (lane = thread's row);
+// complete before the call returns.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // ---- FP64 <-> FP32 without the FP64 pipe ----------------------------------
 // GB300 runs FP64 arithmetic (conversions included) at 1/64 of the FP32
 // rate, so the slicing and epilogue code converts with integer operations on
 // the IEEE 754 bit patterns.  Round to nearest even; results below the FP32
 // normal range flush to zero and results above it become infinity (inputs
 // are finite and well inside the range: they are checked earlier).
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 63) << 31;
-  const int ef = (int)((b >> 52) & 0x7FFull) - 1023 + 127;
-  if (ef <= 0) return __uint_as_float(sign);
-  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
-  unsigned int bits = ((unsigned int)ef << 23) | (unsigned int)(m >> 29);
-  if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) bits += 1u;  // a carry moves into the exponent
-  return __uint_as_float(sign | bits);
-}
+__device__ __forceinline__ float d2f(double x) { return f64_to_f32_rn(x); }
 // exact FP32 -> FP64 (zero and FP32 subnormals map to signed zero)
 __device__ __forceinline__ double f2d(float x) {
   const unsigned int b = __float_as_uint(x);

@@ -173,3 +173,109 @@ def test_adjoint_config_48():
     assert rel_fro(w_g, w_o) < TOL
     assert rel_fro(ge_g, ge_o) < TOL
     assert rel_fro(gp_g, gp_o) < TOL
+
+
+# ---- through the fit: dL/dPhi over the whole grid -------------------------
+
+def _gpu_fit(s, omega, pj):
+    import torch
+    import paper_2403_12340_gb300 as pkg
+
+    phi = pkg.to_fortran(s.phi)  # the fit keeps reading it: it must outlive the backward
+    with pkg.IsdfSmw(s.n, s.cell) as sol:
+        sol.fit(phi, s.n_v, s.n_c, s.mu_idx)
+        sol.polarizability(s.energies, [omega])
+        sol.smw(0)
+        ge, gphi = sol.adjoint_fit(pkg.to_fortran(pj.T), s.n_v + s.n_c)
+        torch.cuda.synchronize()
+        return ge.cpu().numpy(), gphi.cpu().numpy()
+
+
+FIT_CASES = [  # (grid, n_v, n_c, n_mu, seed index, omega)
+    (12, 3, 9, 20, 71, 0.0),
+    ((10, 12, 9), 2, 10, 16, 72, 0.35),
+    (16, 4, 12, 40, 73, 1.5),
+]
+
+
+@pytest.mark.parametrize("case", FIT_CASES, ids=[f"{c[0]}-{c[1]}-{c[2]}-{c[3]}-w{c[5]}" for c in FIT_CASES])
+def test_adjoint_fit_matches_oracle(case):
+    n, n_v, n_c, n_mu, seed, omega = case
+    s = small_system(n, n_v, n_c, n_mu=n_mu, seed_index=seed)
+    pj = A.random_projector(n_mu, seed=13)
+    ge_o, gp_o = A.fit_loss_grad(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, pj.T, omega)
+    ge_g, gp_g = _gpu_fit(s, omega, pj)
+    assert rel_fro(ge_g, ge_o) < TOL
+    assert rel_fro(gp_g, gp_o) < TOL
+
+
+def test_adjoint_fit_autograd_and_rank_check():
+    """torch.autograd through screened_coulomb_fit equals the direct call;
+    a rank-deficient fit is refused."""
+    import torch
+    import paper_2403_12340_gb300 as pkg
+
+    s = small_system(12, 3, 9, n_mu=20, seed_index=77)
+    pj = A.random_projector(20, seed=13)
+    ge_o, gp_o = A.fit_loss_grad(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, pj.T, 0.2)
+    with pkg.IsdfSmw(s.n, s.cell) as sol:
+        phi = pkg.to_fortran(s.phi).requires_grad_(True)
+        e = torch.tensor(s.energies, dtype=torch.float64, requires_grad=True)
+        W = pkg.screened_coulomb_fit(sol, phi, e, s.n_v, s.mu_idx, 0.2)
+        (W * torch.as_tensor(pj.T, device=W.device)).sum().backward()
+        torch.cuda.synchronize()
+        assert rel_fro(phi.grad.cpu().numpy(), gp_o) < TOL
+        assert rel_fro(e.grad.numpy(), ge_o) < TOL
+    d = small_system((8, 8, 8), 2, 3, 9, seed_index=78)  # 9 points > 6 pairs
+    with pkg.IsdfSmw(d.n, d.cell) as sol:
+        _, rank = sol.fit(pkg.to_fortran(d.phi), d.n_v, d.n_c, d.mu_idx)
+        assert rank < 9
+        sol.polarizability(d.energies, [0.0])
+        sol.smw(0)
+        with pytest.raises(pkg.IsdfError) as ei:
+            sol.adjoint_fit(pkg.to_fortran(np.eye(9)), d.n_e)
+        assert ei.value.code == -9
+
+
+def test_adjoint_fit_config_48():
+    """Config 5 (48^3, N_mu = 1536, FP64 forward, static): dL/dPhi over the
+    grid and dL/de against the oracle, and central differences (h = 1e-6)
+    of the CUDA forward on sampled orbital entries at interpolation points
+    and elsewhere on the grid."""
+    import torch
+    import paper_2403_12340_gb300 as pkg
+
+    s = synth.workload("isdf48")
+    pj = A.random_projector(len(s.mu_idx), seed=13)
+    ge_o, gp_o = A.fit_loss_grad(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, pj.T, 0.0)
+    ge_g, gp_g = _gpu_fit(s, 0.0, pj)
+    assert rel_fro(ge_g, ge_o) < TOL
+    assert rel_fro(gp_g, gp_o) < TOL
+    h = 1e-6
+    mu = np.asarray(s.mu_idx)
+    rng = np.random.default_rng(5)
+    rows = list(rng.choice(mu, 5, replace=False)) + list(rng.choice(np.setdiff1d(np.arange(s.n_r), mu), 5,
+                                                                    replace=False))
+    picks = [(int(a), int(i)) for a, i in zip(rows, rng.integers(0, s.n_e, 10))]
+    pj_t = torch.as_tensor(pj.T, device="cuda")
+    phi_d = pkg.to_fortran(s.phi)
+    fd = []
+    with pkg.IsdfSmw(s.n, s.cell) as sol:
+
+        def loss():
+            sol.fit(phi_d, s.n_v, s.n_c, mu)
+            sol.polarizability(s.energies, [0.0])
+            sol.smw(0)
+            return float((sol.screened_basis(0) * pj_t).sum())
+
+        for a, i in picks:
+            v = float(s.phi[a, i])
+            phi_d[a, i] = v + h
+            lp = loss()
+            phi_d[a, i] = v - h
+            lm = loss()
+            phi_d[a, i] = v
+            fd.append((lp - lm) / (2 * h))
+    err = rel_fro(np.array([gp_g[a, i] for a, i in picks]), np.array(fd))
+    print(f"\nisdf48 dL/dPhi through the fit: vs oracle {rel_fro(gp_g, gp_o):.2e}, sampled central differences {err:.2e}")
+    assert err < 1e-6
