@@ -264,7 +264,8 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->a_z1, &c->a_z2, &c->a_z3, &c->a_gpm, &c->a_gpp,
                     &c->a_m5, &c->a_m6, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->ns_bound, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
+                    &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->ns_bound, &c->ns_alpha, &c->ns_work,
+                    &c->b_s4, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
@@ -635,6 +636,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     CK(isdf::dev_malloc(&c->d_fail, n_omega * sizeof(int)));
     c->cap_fail = n_omega;
   }
+  c->dinv_ns = false;
   if (r > 0) {
     // G = theta^T V theta = S^T S with S the weighted half spectrum (Parseval)
     const long long lds = 2 * c->n_half;
@@ -651,18 +653,35 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)n_omega));
     if (c->prec == ISDF_PREC_MIXED) CK(ensure(c->cb_split, (size_t)64 * r * n_omega));
     if (n_nodes > 0) CK(ensure(c->ctab, (size_t)2 * n_nodes * (n_e + 1)));
-    // mixed, one frequency: R^-1 and D^-1 beside the Coulomb work
+    // mixed, one frequency: D^-1 beside the Coulomb work
     const bool dinv = c->prec == ISDF_PREC_MIXED && n_omega == 1;
     c->dinv_ready = false;
+    // D^-1 by Newton-Schulz when the pair weights bound the spectrum of D
+    // tightly enough (no synchronisation: the bounds are host arithmetic)
+    isdf::NsPlan dplan;
+    double dwmin = 0.0, dwmax = 0.0;
+    if (dinv) {
+      isdf::pair_weight_bounds(energies, n_v, n_c, omega[0], &dwmin, &dwmax);
+      if (!(dwmin > 0.0) || !(dwmax >= dwmin) || !isdf::ns_plan((dwmax - dwmin) / (dwmax + dwmin), dplan))
+        dplan.beta.clear();
+    }
+    const bool dinv_ns = dinv && dplan.steps() > 0;
+    c->dinv_ns = dinv_ns;
     if (dinv) {
       const int rp = (r + 127) / 128 * 128, rk = (r + 63) / 64 * 64;
       CK(ensure(c->Rinv, rr));
       CK(ensure(c->Dinv, rr));
       CK(ensure_bf16(c->m_sd, (size_t)3 * rp * rk));
+      if (dinv_ns) {
+        CK(ensure(c->Q, rr));
+        CK(ensure(c->R, rr));
+        CK(ensure_bf16(c->m_sa, (size_t)3 * rp * rk));
+        CK(ensure_bf16(c->m_sb, (size_t)3 * rp * rk));
+      }
       int rc0 = chol_inverse_workspace(c, r);
       if (rc0 != ISDF_OK) return rc0;
     }
-    if (c->pair_whiten) CK(ensure(c->swf, (npair * n_omega + 1) / 2));
+    if (c->prec == ISDF_PREC_MIXED) CK(ensure(c->swf, (npair * n_omega + 1) / 2));  // the weights in FP32
     CK(ensure(c->ew, (size_t)n_e + n_omega));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, on the device from
     // the energies and frequencies (one small upload; a captured call reuses
@@ -674,7 +693,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
                          c->stream));
     }
     CK(launch_pair_weights(c->ew.p, n_v, n_c, n_omega, c->sw.p,
-                           c->prec == ISDF_PREC_MIXED && c->pair_whiten ? reinterpret_cast<float*>(c->swf.p) : nullptr,
+                           c->prec == ISDF_PREC_MIXED ? reinterpret_cast<float*>(c->swf.p) : nullptr,
                            c->stream));
     // D(w) for every frequency (main stream)
     if (n_nodes > 0) {
@@ -706,9 +725,9 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
       CK(isdf::mixed_polar_D_pairspace(c, reinterpret_cast<const float*>(c->swf.p), n_omega));
     } else if (c->prec == ISDF_PREC_MIXED) {
       if (n_omega > 1) {
-        CK(isdf::mixed_polar_D_batched(c, c->sw.p, n_omega));
+        CK(isdf::mixed_polar_D_batched(c, reinterpret_cast<const float*>(c->swf.p), n_omega));
       } else {
-        CK(isdf::mixed_polar_D(c, c->sw.p, n_omega));
+        CK(isdf::mixed_polar_D(c, reinterpret_cast<const float*>(c->swf.p), n_omega));
       }
     } else {
       for (int k = 0; k < n_omega; ++k) {
@@ -731,9 +750,19 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
       int rc0 = fork_s2(c);
       if (rc0 != ISDF_OK) return rc0;
       PhaseScope ph(c, ISDF_PH_SMW, c->s2);
-      if (n_omega > 1) {  // all frequencies in one factorisation sequence
+      if (n_omega > 1 && c->prec == ISDF_PREC_MIXED) {
+        // all frequencies: smw_inverse_all inverts D(w) by Newton-Schulz (and
+        // factors it only if the spectral bounds do not allow that)
+        CK(cudaMemsetAsync(c->d_fail, 0xff, n_omega * sizeof(int), c->s2));
+        c->rw_ready = false;
+      } else if (n_omega > 1) {  // all frequencies in one factorisation sequence
         CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr,
                                            c->b_cbd.p, c->d_fail, c->s2, split_panel(c, (size_t)64 * r * n_omega)));
+      } else if (dinv_ns) {
+        // D^-1 for the capacitance K = -(D^-1 + G)^-1 by Newton-Schulz on the
+        // tensor cores, beside the FFT of theta; D is left unfactored
+        CK(cudaMemsetAsync(c->d_fail, 0xff, sizeof(int), c->s2));
+        CK(isdf::mixed_ns_inverse(c, c->D.p, c->Dinv.p, 1.0, 2.0 / (dwmin + dwmax), dplan, c->s2));
       } else if (dinv) {
         // D = R R^T with R^-1 built on the third stream beside it, then
         // D^-1 = R^-T R^-1 for the capacitance K = -(D^-1 + G)^-1
@@ -751,8 +780,10 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     }
     // G = theta^T V theta (main stream)
     if (c->prec == ISDF_PREC_MIXED) {
-      // the factorisations of D(w) on the second stream keep some SMs (the SYRK of G: 6 r^2 K)
-      isdf::TcSmReserve keep(fp64_sms_to_leave(r, 6.0 * r * (double)r * lds));
+      // the factorisations of D(w) on the second stream keep some SMs (the
+      // SYRK of G: 6 r^2 K); the Newton-Schulz route shares them instead
+      const bool factoring = !(n_omega > 1 || dinv_ns);
+      isdf::TcSmReserve keep(factoring ? fp64_sms_to_leave(r, 6.0 * r * (double)r * lds) : 0);
       CK(isdf::mixed_polar_G(c));
     } else {
       {
@@ -785,6 +816,8 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
   c->k_ready.assign(n_omega, 0);
   c->polar_ready = true;
   c->dinv_ready = c->prec == ISDF_PREC_MIXED && n_omega == 1 && r > 0;
+  // D(w) factored unless a Newton-Schulz route inverts it (smw_enqueue factors on demand)
+  c->rw_ready = !(c->prec == ISDF_PREC_MIXED && (n_omega > 1 || c->dinv_ns));
   c->polar_whiten = c->pair_whiten;
   c->polar_nodes = n_nodes;
   return ISDF_OK;
@@ -815,42 +848,6 @@ extern "C" int isdf_contour_nodes(const double* energies, int n_v, int n_c, doub
   return std::max(1, contour_nodes_recommended(e_lo - e_n, e_hi - e_n, tol));
 }
 
-// Largest pair weight w_p = -2 Omega_p(i w_k)^-1 = 2 |D| / (D^2 + w^2),
-// D = e_v - e_c: the largest eigenvalue D(w) can have (D = C~ diag(w) C~^T
-// with orthonormal rows C~).  As a function of |D| it peaks at |D| = w, so
-// the maximum over the pairs lies at w or at an end of [gap, width].
-static double max_pair_weight(isdf_ctx* c, int k) {
-  const int n_v = c->n_v, n_e = n_v + c->n_c;
-  double emax_v = c->energies[0], emin_v = c->energies[0], emin_c = c->energies[n_v], emax_c = c->energies[n_v];
-  for (int i = 0; i < n_v; ++i) {
-    emax_v = std::max(emax_v, c->energies[i]);
-    emin_v = std::min(emin_v, c->energies[i]);
-  }
-  for (int j = n_v; j < n_e; ++j) {
-    emin_c = std::min(emin_c, c->energies[j]);
-    emax_c = std::max(emax_c, c->energies[j]);
-  }
-  const double w = c->omega[k], gap = emin_c - emax_v, width = emax_c - emin_v;
-  auto f = [w](double d) { return 2.0 * d / (d * d + w * w); };
-  double m = std::max(f(gap), f(width));
-  if (w >= gap && w <= width) m = std::max(m, f(w));
-  return m;
-}
-
-// Newton-Schulz steps that take |I - alpha A| from (k - 1) / (k + 1) (k =
-// hi / lo, alpha = 2 / (lo + hi)) below 2^-26, under the FP32-grade rounding
-// of the products; 0 (use the factorisation) if more than 12.
-static int ns_iterations(double lo, double hi) {
-  if (!(lo > 0.0) || !(hi >= lo) || !std::isfinite(hi)) return 0;
-  const double e0 = (hi - lo) / (hi + lo);
-  if (e0 < 1e-300) return 1;
-  const double need = 26.0 * std::log(2.0) / -std::log(e0);  // 2^k >= need
-  // one step more than the bounds ask for: they come partly from power
-  // iteration estimates
-  const int k = std::max(1, (int)std::ceil(std::log2(std::max(need, 1.0)))) + 1;
-  return k <= 12 ? k : 0;
-}
-
 // Queue the SMW capacitance of frequency k (no synchronisation); the
 // failure flag of the factorisation of I + R^T G R goes to failT.
 static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
@@ -867,24 +864,24 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
       // spectrum of A = D^-1 + G: at least 1 / max w (D <= max w, G >= 0),
       // at most the Gershgorin bound; a condition number small enough for a
       // few Newton-Schulz steps takes that route
-      // spectrum of A: from above the smaller of the Gershgorin bound and
-      // 1.1 times a power-iteration estimate; from below 1 / lambda_max(D)
-      // (power iteration, times 1.1) and 1 / max w.  Newton-Schulz converges
-      // whenever the largest eigenvalue is below lo + hi, which these
-      // margins keep well inside.
       double* nb = c->ns_bound.p;
-      CK(launch_row_abs_sum_max(c->T.p, r, r, nb, c->stream));
-      CK(launch_power_estimate(c->T.p, r, r, 10, nb + 4, nb + 1, c->stream));
-      CK(launch_power_estimate(c->D.p + rr * k, r, r, 10, nb + 4, nb + 2, c->stream));
+      CK(launch_row_abs_sum_max(c->T.p, r, r, nb, nb + 4, c->stream));
+      CK(launch_row_abs_sum_max(c->G.p, r, r, nb + 1, nb + 4, c->stream));
+      CK(launch_row_abs_sum_max(c->D.p + rr * k, r, r, nb + 2, nb + 4, c->stream));
       double h[3] = {0.0, 0.0, 0.0};
       CK(cudaMemcpyAsync(h, nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
-      const double hi = std::min(h[0], 1.1 * h[1]);
-      const double lo = std::max(1.0 / max_pair_weight(c, k), h[2] > 0.0 ? 1.0 / (1.1 * h[2]) : 0.0);
-      const int iters = ns_iterations(lo, hi);
-      if (iters > 0) {
+      // rigorous bounds only (a step count planned from an estimate could
+      // leave a mode unconverged): lambda(A) <= min(Gershgorin(A), 1 / w_min
+      // + Gershgorin(G)) and >= 1 / min(w_max, Gershgorin(D))
+      double wmin = 0.0, wmax = 0.0;
+      isdf::pair_weight_bounds(c->energies.data(), c->n_v, c->n_c, c->omega[k], &wmin, &wmax);
+      const double hi = std::min(h[0], 1.0 / wmin + h[1]);
+      const double lo = 1.0 / std::min(wmax, h[2]);
+      isdf::NsPlan plan;
+      if (lo > 0.0 && hi >= lo && std::isfinite(hi) && isdf::ns_plan((hi - lo) / (hi + lo), plan)) {
         CK(cudaMemsetAsync(failT, 0xff, sizeof(int), c->stream));  // no factorisation to fail
-        CK(isdf::mixed_ns_capacitance(c, Kk, 2.0 / (lo + hi), iters));
+        CK(isdf::mixed_ns_capacitance(c, Kk, 2.0 / (lo + hi), plan));
         return ISDF_OK;
       }
     }
@@ -899,7 +896,13 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
     CK(isdf::mixed_k_from_uinv(c, Kk));
     return ISDF_OK;
   }
-  // D = R R^T: factored by build_polarizability on the second stream
+  // D = R R^T: factored by build_polarizability on the second stream, or
+  // here (a mixed context whose polarizability holds several frequencies
+  // leaves D(w) unfactored for the Newton-Schulz route of smw_inverse_all)
+  if (!c->rw_ready) {
+    int rc = cholesky_blocked(c, c->D.p + rr * k, r, r, 0.0, c->Rw.p + rr * k, c->d_fail + k, c->stream);
+    if (rc != ISDF_OK) return rc;
+  }
   CK(cudaMemcpyAsync(c->R.p, c->Rw.p + rr * k, rr * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   // T = I + R^T G R
   CK(cudaMemsetAsync(c->T.p, 0, rr * sizeof(double), c->stream));
@@ -950,7 +953,7 @@ static int smw_workspace(isdf_ctx* c) {
   CK(ensure(c->W1, rr));
   CK(ensure(c->Q, rr));
   CK(ensure(c->partial, (size_t)sp * rr));
-  CK(ensure(c->ns_bound, 4 + 2 * (size_t)r));
+  CK(ensure(c->ns_bound, 4 + row_abs_sum_work(r, 1)));
   if (c->prec == ISDF_PREC_MIXED) return chol_inverse_workspace(c, r);
   return ISDF_OK;
 }
@@ -1042,7 +1045,22 @@ extern "C" int smw_inverse_all(isdf_ctx* c, double* K_out) {
     CK(cudaMemsetAsync(c->b_fail, 0xff, nw * sizeof(int), c->stream));
     if (c->prec == ISDF_PREC_MIXED && nw > 1) {
       PhaseScope ph(c, ISDF_PH_SMW);
-      CK(isdf::mixed_smw_batched(c, nw, c->b_fail));
+      bool ns = false;
+      CK(isdf::mixed_smw_batched_ns(c, nw, c->b_fail, &ns));
+      if (!ns) {
+        // the bounds ask for too many Newton-Schulz steps: factor D(w) here,
+        // then the factorisation route
+        if (c->b_cbd.cap < (size_t)nw || c->cb_split.cap < (size_t)64 * r * nw) {
+          if (isdf::tl_capture) return fail(c, ISDF_ERR_STATE, "smw_inverse_all: a captured call needs an eager call first");
+          CK(cudaStreamSynchronize(c->stream));
+          CK(ensure(c->b_cbd, (size_t)nw));
+          CK(ensure(c->cb_split, (size_t)64 * r * nw));
+        }
+        CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, nw, 0.0, c->Rw.p, r, (long long)rr, c->b_cbd.p,
+                                           c->d_fail, c->stream, split_panel(c, (size_t)64 * r * nw)));
+        c->rw_ready = true;
+        CK(isdf::mixed_smw_batched(c, nw, c->b_fail));
+      }
     } else {
       int rc = smw_workspace(c);
       if (rc != ISDF_OK) return rc;

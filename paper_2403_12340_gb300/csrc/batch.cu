@@ -50,6 +50,11 @@ struct isdf_batch {
   std::vector<cudaEvent_t> ev_end;   // one per system, recorded at the end of its branch
   std::vector<cudaEvent_t> ev_lane;  // the end of the last system of each lane
   std::vector<double> g_omega;
+  // the capacitance stage of every system in grouped launches (graph form)
+  bool grouped_smw = false;
+  void* ns_work = nullptr;
+  size_t ns_ws = 0, ns_bytes = 0;
+  std::vector<std::vector<unsigned char>> ns_staged;
 };
 
 namespace {
@@ -71,6 +76,7 @@ void free_batch(isdf_batch* b) {
   for (cudaEvent_t e : b->ev_end) cudaEventDestroy(e);
   for (cudaEvent_t e : b->ev_lane) cudaEventDestroy(e);
   if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->ns_work) cudaFree(b->ns_work);
   for (auto& s : b->sys) {
     if (s.ctx) isdf_destroy(s.ctx);
     if (s.theta) cudaFree(s.theta);
@@ -260,7 +266,7 @@ int capture_systems(isdf_batch* b, const double* omega, int n_omega) {
     int rank = 0;
     int rc = isdf_fit(s.ctx, s.d.phi, s.d.n_v, s.d.n_c, s.d.mu_idx, s.d.n_mu, b->prec, s.theta, &rank);
     if (rc == ISDF_OK) rc = build_polarizability(s.ctx, s.d.energies, omega, n_omega, nullptr, nullptr);
-    if (rc == ISDF_OK) rc = smw_inverse_all(s.ctx, nullptr);
+    if (rc == ISDF_OK && !b->grouped_smw) rc = smw_inverse_all(s.ctx, nullptr);
     if (rc != ISDF_OK) {
       b->err = "isdf_batch_capture: system " + std::to_string(i) + ": " + isdf_last_error(s.ctx);
       return rc;
@@ -271,6 +277,55 @@ int capture_systems(isdf_batch* b, const double* omega, int n_omega) {
   }
   for (int l = 0; l < nl; ++l)
     if (used[l] && (e = cudaStreamWaitEvent(b->origin, b->ev_lane[l], 0)) != cudaSuccess) return cuda_err(e, "join");
+  if (b->grouped_smw) {
+    // every system's capacitance, all frequencies, in grouped persistent
+    // launches over (system, frequency, tile): one per Newton-Schulz product
+    std::vector<isdf_ctx*> cs;
+    for (auto& s : b->sys) cs.push_back(s.ctx);
+    e = isdf::ns_stage_grouped(cs.data(), (int)cs.size(), b->origin, b->ns_work, b->ns_ws, b->ns_staged);
+    if (e != cudaSuccess) return cuda_err(e, "grouped capacitance stage");
+    for (size_t i = 0; i < b->sys.size(); ++i)
+      if ((e = cudaEventRecordWithFlags(b->ev_end[i], b->origin, cudaEventRecordExternal)) != cudaSuccess)
+        return cuda_err(e, "end event");
+  }
+  return ISDF_OK;
+}
+
+// Whether the captured graph can run the capacitance stage of all systems
+// together (mixed precision, several frequencies, every system's eager
+// smw_inverse_all on the Newton-Schulz route, at most 32 systems); if so,
+// size the descriptor workspace and run the stage once eagerly, which
+// uploads the descriptors the captured launches reuse.
+int prepare_grouped_smw(isdf_batch* b, int n_omega) {
+  b->grouped_smw = false;
+  if (b->prec != ISDF_PREC_MIXED || n_omega < 2 || b->sys.size() > 32) return ISDF_OK;
+  for (auto& s : b->sys) {
+    isdf_ctx* c = s.ctx;
+    if (c->rank <= 0 || c->ns_nw != n_omega || c->ns_e0_d < 0.0 || c->ns_e0_a < 0.0) return ISDF_OK;
+  }
+  const size_t ws = (isdf::tc_grouped_workspace_bytes((int)b->sys.size()) + 255) / 256 * 256;
+  const size_t need = ws * (size_t)isdf::ns_stage_slots();
+  if (need > b->ns_bytes) {
+    if (b->ns_work) cudaFree(b->ns_work);
+    b->ns_work = nullptr;
+    b->ns_bytes = 0;
+    b->ns_staged.clear();
+    if (isdf::dev_malloc(&b->ns_work, need) != cudaSuccess) {
+      b->err = "isdf_batch_capture: descriptor workspace allocation failed";
+      return ISDF_ERR_NOMEM;
+    }
+    b->ns_bytes = need;
+  }
+  b->ns_ws = ws;
+  std::vector<isdf_ctx*> cs;
+  for (auto& s : b->sys) cs.push_back(s.ctx);
+  cudaError_t e = isdf::ns_stage_grouped(cs.data(), (int)cs.size(), b->origin, b->ns_work, ws, b->ns_staged);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
+  if (e != cudaSuccess) {
+    b->err = std::string("isdf_batch_capture: grouped capacitance stage: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  b->grouped_smw = true;
   return ISDF_OK;
 }
 
@@ -321,6 +376,8 @@ extern "C" int isdf_batch_capture(isdf_batch* b, const double* omega, int n_omeg
     return ISDF_ERR_CUDA;
   }
   for (auto& s : b->sys) cudaStreamSynchronize(s.stream);
+  rc = prepare_grouped_smw(b, n_omega);
+  if (rc != ISDF_OK) return rc;
   // the capture itself: entry points in capture mode on this thread only
   e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {

@@ -104,12 +104,21 @@ struct isdf_ctx {
   DevBuf bW1, bT, bU, bQ, b_s1, b_s2, b_s3, b_work, b_cb, b_dtmp, b_cbd;
   DevBuf ctab;  // contour-integral polarizability: resolvent weights and node weights
   DevBuf cx[12];  // COHSEX (cohsex.cu): spectra, cross products, scratch
-  DevBuf m_pairs_t, swf;  // pair-space whitening: transposed pair slices, FP32 pair weights
+  DevBuf m_pairs_t, swf;  // pair-space whitening: transposed pair slices; the pair weights in FP32 (mixed path)
   DevBuf ew;                     // energies and frequencies of the last polarizability, on the device
   // mixed path, one frequency: R^-1 of D = R R^T, D^-1 = R^-T R^-1 and the
   // BF16 slices of R^-1, built beside the Coulomb work of build_polarizability
-  DevBuf Rinv, Dinv, m_sd, ns_bound;  // ns_bound: the Gershgorin bound of D^-1 + G
+  DevBuf Rinv, Dinv, m_sd, ns_bound;  // ns_bound: Gershgorin bounds (and their workspace)
+  // all frequencies by Newton-Schulz (mixed_smw_batched_ns): step counts and
+  // per-frequency start scales of the last eager call (a captured call
+  // replays them), the grouped-GEMM descriptor slots and their host copies
+  double ns_e0_d = -1.0, ns_e0_a = -1.0;  // the largest e0 over the frequencies (see NsPlan)
+  int ns_nw = 0;
+  bool rw_ready = false;  // c->Rw holds the Cholesky factors of every D(w)
+  DevBuf ns_alpha, ns_work, b_s4;
+  std::vector<std::vector<unsigned char>> ns_staged;
   bool dinv_ready = false;
+  bool dinv_ns = false;  // the last polarizability inverted D by Newton-Schulz (D left unfactored)
   std::vector<double> ew_host;   // their host copy (the source of the asynchronous upload)
   bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
   int pair_mode = 0;         // the precision argument of the last fit
@@ -197,7 +206,7 @@ struct PhaseTimer {
 // mixed.cu
 cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p, int n_v, int n_c, int r);
 cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r, bool linv_ready);
-cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_polar_D(isdf_ctx* c, const float* swf, int n_omega);
 cudaError_t mixed_whiten_D(isdf_ctx* c, const double* Dpp, double* Dk);
 cudaError_t mixed_polar_D_pairspace(isdf_ctx* c, const float* swf, int n_omega);
 cudaError_t mixed_polar_G(isdf_ctx* c);
@@ -208,14 +217,47 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
 cudaError_t mixed_dinv(isdf_ctx* c, cudaStream_t st);
 // K = -U^-T U^-1 from U^-1 in c->Q into Kk
 cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk);
+// K(w_k) for every frequency by Newton-Schulz (K = -(D^-1 + G)^-1 with
+// D(w)^-1 itself by Newton-Schulz), each step one grouped persistent GEMM
+// over every (frequency, tile); *used = false if the spectral bounds ask for
+// too many steps (the caller then factors).
+cudaError_t mixed_smw_batched_ns(isdf_ctx* c, int nw, int* fail_T, bool* used);
+// The same for n systems at once (each after an eager smw_inverse_all that
+// took the Newton-Schulz route), one grouped launch per step over every
+// (system, frequency, tile), on stream st; work holds 4 max_steps slots of
+// ws bytes (tc_grouped_workspace_bytes(n), rounded up to 256).
+int ns_stage_slots();  // descriptor slots of ns_stage_grouped's workspace
+cudaError_t ns_stage_grouped(isdf_ctx** cs, int n, cudaStream_t st, void* work, size_t ws,
+                             std::vector<std::vector<unsigned char>>& staged);
 // K = -A^-1 for the SPD A in c->T by Newton-Schulz iteration on the tensor
 // cores, X <- X (2 I - A X) from X = alpha I, `iters` times (the last
 // product written negated into Kk)
-cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, int iters);
+// Newton-Schulz schedule: for each step the scale beta of
+// X <- beta (2 X - X M X) and the BF16 slices of its products (ns_plan).
+struct NsPlan {
+  std::vector<double> beta;
+  std::vector<int> s;
+  int steps() const { return (int)beta.size(); }
+};
+// e0 = (hi - lo) / (hi + lo) for a spectrum of M within [lo, hi]; false if
+// the iteration needs more than 12 steps.
+bool ns_plan(double e0, NsPlan& p);
+// out = sign M^-1 for a symmetric positive definite r x r M (ld r) by the
+// Newton-Schulz steps of `plan` from X = alpha I, on stream st (scratch:
+// c->Q, c->R and the slices c->m_sd, m_sa, m_sb)
+cudaError_t mixed_ns_inverse(isdf_ctx* c, const double* M, double* out, double sign, double alpha, const NsPlan& plan,
+                             cudaStream_t st);
+// K = -(c->T)^-1 on the main stream
+cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, const NsPlan& plan);
+// Range [wmin, wmax] of the pair weights w = 2 |dE| / (dE^2 + w^2) over the
+// valence-conduction pairs, from the band edges (the weight is unimodal in
+// |dE|, peaking at |dE| = w): in the whitened basis the spectrum of D(w)
+// lies within it.
+void pair_weight_bounds(const double* energies, int n_v, int n_c, double w, double* wmin, double* wmax);
 // All frequencies at once: D(w_k) for k < n_omega (chunked to a memory
 // budget), and K(w_k) from the factors R(w_k) in c->Rw (T factors and
 // their failure flags in c->bU / fail_T).
-cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega);
+cudaError_t mixed_polar_D_batched(isdf_ctx* c, const float* swf, int n_omega);
 cudaError_t mixed_smw_batched(isdf_ctx* c, int n_omega, int* fail_T);
 
 // api.cu: after a captured graph of isdf_fit, build_polarizability and

@@ -109,114 +109,95 @@ cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, i
   return cudaGetLastError();
 }
 
-// *out = max_i sum_j |A(i, j)| (Gershgorin bound of the spectrum of a
-// symmetric A); *out must hold +0.0 before the launch.  Row sums are
-// non-negative, so their bit patterns order like their values.
-__global__ void k_row_abs_sum_max(const double* __restrict__ A, long long lda, int n, unsigned long long* out) {
-  __shared__ double red[256];
+// out[z] = max_i sum_j |A_z(i, j)| (the Gershgorin bound of the spectrum of
+// a symmetric A_z) in two passes with a fixed summation order, so the bound
+// is the same on every run: pass 1 sums |A(i, j)| over one of RA_CHUNKS
+// column chunks per block (a thread per row, loads coalesced down the
+// columns, many blocks in flight where one thread per whole row would chain
+// n dependent FP64 adds); pass 2 adds the chunks of each row in order and
+// takes the maximum over the rows.
+constexpr int RA_CHUNKS = 16;
+
+__global__ void k_row_abs_partial(const double* __restrict__ A, long long lda, int n, double* __restrict__ part,
+                                  long long sA) {
+  A += sA * blockIdx.z;
+  part += (size_t)RA_CHUNKS * n * blockIdx.z;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int len = (n + RA_CHUNKS - 1) / RA_CHUNKS, j0 = blockIdx.y * len, j1 = min(n, j0 + len);
+  if (i >= n) return;
   double acc = 0.0;
-  if (i < n)
-    for (int j = 0; j < n; ++j) acc += fabs(A[i + lda * (long long)j]);
-  red[threadIdx.x] = acc;
+  for (int j = j0; j < j1; ++j) acc += fabs(A[i + lda * (long long)j]);
+  part[(size_t)blockIdx.y * n + i] = acc;
+}
+
+__global__ void k_row_abs_max(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  part += (size_t)RA_CHUNKS * n * blockIdx.x;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < RA_CHUNKS; ++c) s += part[(size_t)c * n + i];
+    m = fmax(m, s);
+  }
+  red[threadIdx.x] = m;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(red[0]));
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
-cudaError_t launch_row_abs_sum_max(const double* A, long long lda, int n, double* out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
-  if (e != cudaSuccess || n <= 0) return e;
+size_t row_abs_sum_work(int n, int batch) { return (size_t)RA_CHUNKS * std::max(n, 0) * std::max(batch, 0); }
+
+cudaError_t launch_row_abs_sum_max(const double* A, long long lda, int n, double* out, double* work, cudaStream_t s,
+                                   int batch, long long sA) {
+  if (batch < 1 || batch > 65535) return cudaErrorInvalidValue;
+  if (n <= 0) return cudaMemsetAsync(out, 0, batch * sizeof(double), s);
   note_launch();
-  k_row_abs_sum_max<<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, reinterpret_cast<unsigned long long*>(out));
+  k_row_abs_partial<<<dim3((n + 127) / 128, RA_CHUNKS, batch), 128, 0, s>>>(A, lda, n, work, sA);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  note_launch();
+  k_row_abs_max<<<batch, 256, 0, s>>>(work, n, out);
   return cudaGetLastError();
 }
 
-// Power iteration for the largest eigenvalue of a symmetric positive
-// semidefinite A (n x n, ld lda) in FP32 (an estimate is all it gives):
-// x_0 = 1 / sqrt(n) in every entry, then x <- A x / |A x|, one launch per
-// step.  Step k reads y_{k-1}, normalises it on the fly (every block
-// recomputes its norm), accumulates y_k = A x over column chunks with
-// atomics, and zeroes y_{k+1} for the next step (three rotating vectors).
-// *lam = |y_k| of the last step, which approaches the largest eigenvalue
-// from below.  work: 3 n + 2 floats.
-__global__ void k_power_step(const double* __restrict__ A, long long lda, int n, float* y, int k) {
-  __shared__ float red[256];
-  __shared__ float s_inv;
-  float* yp = y + (size_t)((k + 2) % 3) * n;  // y_{k-1}
-  float* yk = y + (size_t)(k % 3) * n;
-  float* yn = y + (size_t)((k + 1) % 3) * n;  // y_{k+1}
-  float acc = 0.0f;
-  if (k > 0)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += yp[i] * yp[i];
-  red[threadIdx.x] = k > 0 ? acc : (threadIdx.x == 0 ? (float)n : 0.0f);
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) s_inv = red[0] > 0.0f ? rsqrtf(red[0]) : 0.0f;
-  __syncthreads();
-  const float inv = s_inv;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int cw = (n + gridDim.y - 1) / gridDim.y;
-  const int j0 = blockIdx.y * cw, j1 = min(n, j0 + cw);
-  if (i < n) {
-    float a = 0.0f;
-    for (int j = j0; j < j1; ++j) a = fmaf(f64_to_f32_rn(A[i + lda * (long long)j]), k > 0 ? yp[j] * inv : inv, a);
-    atomicAdd(yk + i, a);
-    if (blockIdx.y == 0) yn[i] = 0.0f;
-  }
+// X_z = alpha[z] I (n x n, ld n, matrix z at X + z n^2)
+__global__ void k_scaled_identity(double* X, int n, const double* __restrict__ alpha) {
+  const long long nn = (long long)n * n;
+  double* x = X + nn * blockIdx.y;
+  const double a = alpha[blockIdx.y];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+    x[i] = (i % (n + 1) == 0) ? a : 0.0;
 }
 
-__global__ void k_power_norm(const float* __restrict__ y, int n, double* lam) {
-  __shared__ float red[1024];
-  float acc = 0.0f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += y[i] * y[i];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *lam = sqrt((double)red[0]);
-}
-
-cudaError_t launch_power_estimate(const double* A, long long lda, int n, int steps, double* work, double* lam,
-                                  cudaStream_t s) {
-  if (n <= 0 || steps < 1) return cudaErrorInvalidValue;
-  float* y = reinterpret_cast<float*>(work);
-  cudaError_t e = cudaMemsetAsync(y, 0, 3 * (size_t)n * sizeof(float), s);
-  if (e != cudaSuccess) return e;
-  for (int k = 0; k < steps; ++k) {
-    note_launch();
-    k_power_step<<<dim3((n + 255) / 256, 16), 256, 0, s>>>(A, lda, n, y, k);
-  }
+cudaError_t launch_scaled_identity(double* X, int n, int batch, const double* alpha, cudaStream_t s) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  const long long nn = (long long)n * n;
   note_launch();
-  k_power_norm<<<1, 1024, 0, s>>>(y + (size_t)((steps - 1) % 3) * n, n, lam);
+  k_scaled_identity<<<dim3((unsigned)std::min<long long>((nn + 255) / 256, 1024), batch), 256, 0, s>>>(X, n, alpha);
   return cudaGetLastError();
 }
 
 // c = a + b over n contiguous doubles (problem z at + z stride)
 __global__ void k_add(const double* a, const double* b, double* c, long long n,
-                      long long stride) {
+                      long long stride, long long stride_b) {
   a += stride * blockIdx.y;
-  b += stride * blockIdx.y;
+  b += stride_b * blockIdx.y;
   c += stride * blockIdx.y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     c[i] = a[i] + b[i];
 }
 
 cudaError_t launch_add(const double* a, const double* b, double* c, long long n, cudaStream_t s, int batch,
-                       long long stride) {
+                       long long stride, long long stride_b) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
   const long long blocks = std::min<long long>((n + 255) / 256, 1024);
   note_launch();
-  k_add<<<dim3((unsigned)blocks, batch), 256, 0, s>>>(a, b, c, n, stride);
+  k_add<<<dim3((unsigned)blocks, batch), 256, 0, s>>>(a, b, c, n, stride, stride_b < 0 ? stride : stride_b);
   return cudaGetLastError();
 }
 
@@ -392,8 +373,9 @@ __global__ void __launch_bounds__(T::NT) k_gemm(OpA A, OpB B, int M, int N, int 
   }
 }
 
-// C = alpha * sum_z partial[z] + beta * C; for lower_only the upper tiles are
-// read mirrored from the lower ones.
+// C = alpha * sum_z partial[z] + beta * C; for lower_only (the partials hold
+// the lower tiles) the upper triangle is read mirrored from the lower one,
+// so C comes out exactly symmetric.
 // Batched over blockIdx.z: partials of problem z start at z * splits * M * N,
 // its C at C + z * sC.
 __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, int M, int N,
@@ -405,7 +387,7 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splits, 
   partial += (long long)blockIdx.z * splits * M * N;
   C += sC * blockIdx.z;
   int pm = m, pn = n;
-  if (lower_only && (m / tile) < (n / tile)) {
+  if (lower_only && m < n) {  // the upper triangle mirrors the lower one: C exactly symmetric
     pm = n;
     pn = m;
   }

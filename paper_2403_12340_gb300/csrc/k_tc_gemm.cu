@@ -176,23 +176,53 @@ cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K
 
 // Slices of the pair operand of the polarizability at the points:
 // S(a, i n_c + j) = phimu(a, i) phimu(a, n_v + j) sw[i n_c + j], a < r
-// (the columns of C, Eq. MatrixExpressionISDF, scaled by sqrt(-2 Omega^-1)).
-__global__ void k_pair_slices(const double* __restrict__ phimu, long long ldp, int r, int n_v, int n_c,
-                              const double* __restrict__ sw, __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s,
-                              long long dstride) {
-  const int a = blockIdx.y;
-  sw += (long long)n_v * n_c * blockIdx.z;
+// (the columns of C, Eq. MatrixExpressionISDF, scaled by sqrt(-2 Omega^-1)),
+// and zero in the padding (rows r..Rp, columns K..Kp), so the destination
+// needs no clearing.  A block converts PS_ROWS rows of phimu to FP32 into
+// shared memory once, then each thread writes eight consecutive pairs of
+// all PS_ROWS rows: the weights (FP32, the same rounding as before) are read
+// once for PS_ROWS rows and every slice store is 16 bytes.  The kernel is
+// bound by its writes, 2 s bytes per element.
+constexpr int PS_ROWS = 4;
+
+__global__ void __launch_bounds__(256) k_pair_slices(const double* __restrict__ phimu, long long ldp, int r, int n_v,
+                                                     int n_c, const float* __restrict__ swf,
+                                                     __nv_bfloat16* __restrict__ dst, int Rp, int Kp, int s,
+                                                     long long dstride) {
+  extern __shared__ float ps_rows[];  // PS_ROWS x n_e
+  const int n_e = n_v + n_c, K = n_v * n_c;
+  const int a0 = blockIdx.y * PS_ROWS;
+  swf += (long long)K * blockIdx.z;
   dst += dstride * blockIdx.z;
-  const int K = n_v * n_c;
-  for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk < K; kk += gridDim.x * blockDim.x) {
-    const int i = kk / n_c, j = kk - i * n_c;
-    const float v = tc::d2f(phimu[a + ldp * i]) * tc::d2f(phimu[a + ldp * (long long)(n_v + j)]) * tc::d2f(sw[kk]);
-    __nv_bfloat16 x0, x1, x2;
-    split3f(v, x0, x1, x2);
-    long long base = (long long)a * Kp + kk;
-    dst[base] = x0;
-    if (s > 1) dst[base + (long long)Rp * Kp] = x1;
-    if (s > 2) dst[base + 2ll * Rp * Kp] = x2;
+  for (int idx = threadIdx.x; idx < PS_ROWS * n_e; idx += blockDim.x) {
+    const int q = idx / n_e, e = idx - q * n_e;
+    ps_rows[idx] = (a0 + q < r) ? tc::d2f(phimu[(a0 + q) + ldp * (long long)e]) : 0.f;
+  }
+  __syncthreads();
+  const long long sstr = (long long)Rp * Kp;
+  for (int k8 = (blockIdx.x * blockDim.x + threadIdx.x) * 8; k8 < Kp; k8 += gridDim.x * blockDim.x * 8) {
+    float w[8];
+    int iv[8], jc[8];
+    int i = k8 / n_c, j = k8 - i * n_c;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool in = k8 + q < K;
+      w[q] = in ? swf[k8 + q] : 0.f;
+      iv[q] = in ? i : 0;
+      jc[q] = in ? j : 0;
+      if (++j == n_c) {
+        j = 0;
+        ++i;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PS_ROWS; ++q) {
+      const float* row = ps_rows + q * n_e;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = row[iv[e]] * row[n_v + jc[e]] * w[e];
+      store_slices8(v, dst + (long long)(a0 + q) * Kp + k8, sstr, s);
+    }
   }
 }
 
@@ -228,19 +258,27 @@ cudaError_t launch_pair_slices_t(const double* phimu, long long ldp, int r, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
+cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const float* swf,
                                __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch,
                                long long dstride) {
   if (r <= 0 || batch <= 0) return cudaSuccess;
-  if (r > 65535 || batch > 65535) return cudaErrorInvalidValue;
-  int K = n_v * n_c;
-  int bx = (K + 255) / 256;
-  if (bx > 128) bx = 128;
-  dim3 grid(bx, r, batch);
-  KernelTimer kt(KF_SLICE, st,
-                 ((double)r * (n_v + n_c) * 8.0 + (double)K * 8.0 + (double)r * K * 2.0 * s) * batch);
+  const int K = n_v * n_c, n_e = n_v + n_c;
+  if (batch > 65535 || Rp % PS_ROWS || Rp < r || Rp / PS_ROWS > 65535 || Kp % 8 || Kp < K || (dstride % 8))
+    return cudaErrorInvalidValue;
+  const size_t smem = (size_t)PS_ROWS * n_e * sizeof(float);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static size_t smem_set = 48 * 1024;
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_pair_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    smem_set = 200 * 1024;
+  }
+  const int bx = std::min((Kp + 2047) / 2048, 8);
+  dim3 grid(bx, Rp / PS_ROWS, batch);
+  KernelTimer kt(KF_SLICE, st, ((double)r * n_e * 8.0 + (double)K * 4.0 * (Rp / PS_ROWS) +
+                                (double)Rp * Kp * 2.0 * s) * batch);
   note_launch();
-  k_pair_slices<<<grid, 256, 0, st>>>(phimu, ldp, r, n_v, n_c, sw, dst, Rp, Kp, s, dstride);
+  k_pair_slices<<<grid, 256, smem, st>>>(phimu, ldp, r, n_v, n_c, swf, dst, Rp, Kp, s, dstride);
   return cudaGetLastError();
 }
 
@@ -575,6 +613,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           continue;
         }
+        // beta C: the chunk's 16 loads issued together, ahead of the stores
+        // (one memory round trip per chunk instead of one per element)
+        double cin[16];
+        const bool rd = (EPI == EPI_F64 || EPI == EPI_HAD_F64) && !a.partial && a.beta != 0.0;
+        if (rd) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = w.n0 + c + i;
+            cin[i] = (n < a.N && !(a.lower_only && n > m)) ? Cb[m + a.ldc * n] : 0.0;
+          }
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int n = w.n0 + c + i;
@@ -592,12 +641,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             a.partial[((long long)w.bidx * a.splits + w.split) * a.M * a.N + m + (long long)a.M * n] =
                 with_sum ? tc::f2d(vf) + tc::f2d(w0[i]) : tc::f2d(vf);
           } else {
+            // lower-only: the lower triangle, mirrored (an exactly symmetric C;
+            // beta reads only the lower triangle of C)
+            if (a.lower_only && n > m) break;
             // alpha = 1, beta = 0 and no running sum (the common case) need no FP64 arithmetic
             const double vd = with_sum ? tc::f2d(vf) + tc::f2d(w0[i]) : tc::f2d(vf);
             double o = (a.alpha == 1.0) ? vd : a.alpha * vd;
-            if (a.beta != 0.0) o += a.beta * Cb[m + a.ldc * n];
+            if (rd) o += a.beta * cin[i];
             Cb[m + a.ldc * n] = o;
-            if (a.lower_only && w.mt != w.nt) Cb[n + a.ldc * m] = o;
+            if (a.lower_only && n < m) Cb[n + a.ldc * m] = o;
           }
         }
       }

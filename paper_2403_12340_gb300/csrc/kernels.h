@@ -133,17 +133,18 @@ cudaError_t launch_symmetrize(double* A, long long lda, int n, cudaStream_t s, i
 // not null), index k n_v n_c + i n_c + j.
 cudaError_t launch_pair_weights(const double* ew, int n_v, int n_c, int n_omega, double* sw, float* swf,
                                 cudaStream_t s);
-// *out (device double) = max_i sum_j |A(i, j)|, the Gershgorin bound of a
-// symmetric A's spectrum
-cudaError_t launch_row_abs_sum_max(const double* A, long long lda, int n, double* out, cudaStream_t s);
-// *lam (device) = an estimate of the largest eigenvalue of a symmetric
-// positive semidefinite A by `steps` FP32 power iterations (from below;
-// work: 2 n doubles)
-cudaError_t launch_power_estimate(const double* A, long long lda, int n, int steps, double* work, double* lam,
-                                  cudaStream_t s);
+// out[z] (device) = max_i sum_j |A_z(i, j)|, the Gershgorin bound of a
+// symmetric A_z's spectrum, for the batch matrices at A + z sA; work: at
+// least row_abs_sum_work(n, batch) device doubles.  Deterministic.
+size_t row_abs_sum_work(int n, int batch);
+cudaError_t launch_row_abs_sum_max(const double* A, long long lda, int n, double* out, double* work, cudaStream_t s,
+                                   int batch = 1, long long sA = 0);
+// X_z = alpha[z] I for z < batch (n x n, ld n, matrix z at X + z n^2; alpha on the device)
+cudaError_t launch_scaled_identity(double* X, int n, int batch, const double* alpha, cudaStream_t s);
 // c = a + b, n doubles (c may be a or b); batch problems at + z stride
+// (b at + z stride_b; stride_b < 0: the same stride)
 cudaError_t launch_add(const double* a, const double* b, double* c, long long n, cudaStream_t s, int batch = 1,
-                       long long stride = 0);
+                       long long stride = 0, long long stride_b = -1);
 cudaError_t launch_add_identity(double* A, long long lda, int n, double v, cudaStream_t s, int batch = 1,
                                 long long sA = 0);
 // Two-level batch of GEMMs: problem (z1, z2), z1 < b1, z2 < b2, has
@@ -309,9 +310,11 @@ cudaError_t launch_slice_rowmajor(const double* src, long long lds, int R, int K
                                   int Kp, int s, cudaStream_t st, int batch = 1, long long sstride = 0,
                                   long long dstride = 0);
 // Slices of the pair operand at the points, S(a, i n_c + j) =
-// phimu(a, i) phimu(a, n_v + j) sw[i n_c + j] (r rows, K = n_v n_c); for
-// batch > 1, problem z uses sw + z n_v n_c.
-cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const double* sw,
+// phimu(a, i) phimu(a, n_v + j) swf[i n_c + j] (r rows, K = n_v n_c, FP32
+// weights), zero in the padding up to Rp x Kp (Rp a multiple of 4, Kp of
+// 8): the destination needs no clearing; for batch > 1, problem z uses
+// swf + z n_v n_c.
+cudaError_t launch_pair_slices(const double* phimu, long long ldp, int r, int n_v, int n_c, const float* swf,
                                __nv_bfloat16* dst, int Rp, int Kp, int s, cudaStream_t st, int batch = 1,
                                long long dstride = 0);
 // Unscaled pair operand transposed: slices with rows p = i n_c + j (Pp rows
@@ -344,6 +347,27 @@ struct TcBatch {
 cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, int N, double alpha, double beta,
                                 double* C, long long ldc, bool lower_only, bool tri_b, double* partial, int max_split,
                                 int num_sms, unsigned* status, cudaStream_t st, const TcBatch& bt);
+// Grouped persistent form (k_tc_grouped.cu): up to 32 problems, each a
+// batch as tc_gemm_f64_batched takes it (no split-K; FP64 output with
+// alpha / beta; lower: square problems with mirrored lower tiles), all in
+// one launch whose blocks claim 128 x 128 output tiles from a device work
+// queue.  dev_work: tc_grouped_workspace_bytes(n) bytes of device memory
+// that holds the tensor maps, problem records and the queue counter;
+// `staged` keeps the host copy of what was last uploaded there (an upload
+// synchronises the stream, and none happens while a graph is captured: a
+// captured call needs an eager call with the same problems first).
+struct TcGroupProblem {
+  TcOperand A, B;
+  int M, N;
+  double alpha, beta;
+  double* C;
+  long long ldc;
+  bool lower;
+  TcBatch bt;
+};
+size_t tc_grouped_workspace_bytes(int nprob);
+cudaError_t tc_gemm_f64_grouped(const TcGroupProblem* probs, int nprob, void* dev_work, size_t work_bytes,
+                                std::vector<unsigned char>& staged, int num_sms, unsigned* status, cudaStream_t st);
 // C = A B^T in FP64 (M x N, column-major), and the BF16 slices of C twice:
 // row-major (element (m, n) at zs[m zs_kp + n], slice stride zs_rows_pad
 // zs_kp) and transposed (element (n, m) at zt[n zt_kp + m], slice stride

@@ -15,7 +15,9 @@
 //   apply : theta^T X and theta T2 on the tensor cores, the Coulomb
 //           convolution of the n_rhs columns in FP64.
 #include <algorithm>
+#include <cmath>
 #include <string>
+#include <vector>
 
 #include "../../include/isdf_smw.h"
 #include "ctx.h"
@@ -49,6 +51,8 @@ inline cudaError_t slices_rm(DevBuf& buf, const double* src, long long lds, int 
 }
 
 inline TcOperand op(const DevBuf& b, int rows_pad, int kp) { return TcOperand{b.bf(), rows_pad, kp, NSL}; }
+// the first s slices of the stack (products i + j < s)
+inline TcOperand op_s(const DevBuf& b, int rows_pad, int kp, int s) { return TcOperand{b.bf(), rows_pad, kp, s}; }
 
 // Slices of `count` matrices src + z sstride; problem z's slice stack starts
 // at row z NSL rows_pad of buf.  buf must already hold count stacks.
@@ -155,7 +159,7 @@ cudaError_t mixed_polar_G(isdf_ctx* c) {
 }
 
 // D(w_k) for all frequencies, whitened, into c->D.
-cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega) {
+cudaError_t mixed_polar_D(isdf_ctx* c, const float* swf, int n_omega) {
   cudaStream_t st = c->stream;
   const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
   const size_t rr = (size_t)r * r;
@@ -170,12 +174,11 @@ cudaError_t mixed_polar_D(isdf_ctx* c, const double* sw, int n_omega) {
   MK(ensure(c->tmp2, rr));
   const size_t np = (size_t)NSL * rp * kpp;
   MK(ensure_bf16(c->m_pairs, np));
-  MK(cudaMemsetAsync(c->m_pairs.p, 0, np * 2, st));
   for (int k = 0; k < n_omega; ++k) {
     double* Dk = c->D.p + rr * k;
     {
       PhaseTimer ph(c, ISDF_PH_POLAR_D);
-      MK(launch_pair_slices(c->phimu_p.p, r, r, n_v, n_c, sw + (size_t)npair * k, c->m_pairs.bf(), rp, kpp, NSL,
+      MK(launch_pair_slices(c->phimu_p.p, r, r, n_v, n_c, swf + (size_t)npair * k, c->m_pairs.bf(), rp, kpp, NSL,
                             st));
       MK(tc_gemm_f64(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, c->tmp1.p, r, true, false,
                      c->partial.p, max_split, c->num_sms, c->d_status, st));
@@ -205,7 +208,7 @@ cudaError_t mixed_whiten_D(isdf_ctx* c, const double* Dpp, double* Dk) {
 
 // D(w_k) for all frequencies: the same products as mixed_polar_D, each one
 // launch for a chunk of frequencies whose pair slices fit the budget.
-cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
+cudaError_t mixed_polar_D_batched(isdf_ctx* c, const float* swf, int n_omega) {
   cudaStream_t st = c->stream;
   const int r = c->rank, n_v = c->n_v, n_c = c->n_c;
   const size_t rr = (size_t)r * r;
@@ -227,9 +230,8 @@ cudaError_t mixed_polar_D_batched(isdf_ctx* c, const double* sw, int n_omega) {
     const int nb = std::min(chunk, n_omega - k0);
     {
       PhaseTimer ph(c, ISDF_PH_POLAR_D);
-      MK(cudaMemsetAsync(c->m_pairs.p, 0, per_pair * nb * 2, st));
-      MK(launch_pair_slices(c->phimu_p.p, r, r, n_v, n_c, sw + (size_t)npair * k0, c->m_pairs.bf(), rp, kpp, NSL, st,
-                            nb, (long long)per_pair));
+      MK(launch_pair_slices(c->phimu_p.p, r, r, n_v, n_c, swf + (size_t)npair * k0, c->m_pairs.bf(), rp, kpp, NSL,
+                            st, nb, (long long)per_pair));
       const int pr = NSL * rp;
       MK(tc_gemm_f64_batched(op(c->m_pairs, rp, kpp), op(c->m_pairs, rp, kpp), r, r, 1.0, 0.0, Dpp, r, true, false,
                              ms > 1 ? c->partial.p : nullptr, ms, c->num_sms, c->d_status, st,
@@ -396,37 +398,294 @@ cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk) {
   return launch_symmetrize(Kk, r, r, st);
 }
 
-// K = -A^-1 by Newton-Schulz iteration, X_{k+1} = X_k (2 I - A X_k) from
-// X_0 = alpha I, on the tensor cores.  Every iterate is a polynomial in the
-// symmetric A, so X and Y = 2 I - A X are symmetric and one slice layout
-// serves both sides of each product.  The error contracts quadratically,
-// |I - A X_k| = |I - alpha A|^(2^k), down to the FP32-grade rounding of the
-// products; in the whitened basis A = D^-1 + G has a spectrum within
-// [1 / max w, 1 / min w + |G|] (w the pair weights), a condition number of
-// a few, so a handful of iterations reach that level.
-cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, int iters) {
-  cudaStream_t st = c->stream;
+// The Newton-Schulz schedule for a spectrum of alpha M within [1 - e0,
+// 1 + e0] (alpha = 2 / (lo + hi), e0 = (hi - lo) / (hi + lo)).  A step maps
+// each eigenvalue t of M X to t (2 - t), so [1 - e, 1 + e] goes to
+// [1 - e^2, 1]; the scale beta = 2 / (2 - e^2) centres it again, and
+// e <- e^2 / (2 - e^2) (from e0 = 0.84, kappa 11.5: 5 steps instead of 7).
+// Each step's products take the fewest BF16 slices whose rounding (about
+// 2^(1 - 8 s) kappa relative, kappa = hi / lo) stays below a quarter of the
+// error the step leaves; the last two take all three, so the result carries
+// the three-slice rounding only (the iteration corrects the rounding of the
+// earlier steps like any other error).  Stops when e < 2^-26.
+bool ns_plan(double e0, NsPlan& p) {
+  p.beta.clear();
+  p.s.clear();
+  if (!(e0 >= 0.0) || !(e0 < 1.0)) return false;
+  const double kappa = (1.0 + e0) / (1.0 - e0);
+  double e = e0;
+  while (e > 0x1p-26) {
+    if (p.steps() >= 12) return false;
+    p.beta.push_back(2.0 / (2.0 - e * e));
+    e = e * e / (2.0 - e * e);
+    p.s.push_back(kappa * 0x1p-7 <= 0.25 * e ? 1 : (kappa * 0x1p-15 <= 0.25 * e ? 2 : NSL));
+  }
+  if (p.beta.empty()) {  // alpha M = I to 2^-26 already: one full step
+    p.beta.push_back(1.0);
+    p.s.push_back(NSL);
+  }
+  for (int k = std::max(0, p.steps() - 2); k < p.steps(); ++k) p.s[k] = NSL;
+  return true;
+}
+
+// K = -A^-1 by Newton-Schulz iteration on the tensor cores, in the form
+// X_{k+1} = beta_k (2 X_k - X_k (A X_k)) from X_0 = alpha I (schedule of
+// ns_plan).  The error contracts quadratically down to the FP32-grade
+// rounding of the products; in the whitened basis A = D^-1 + G has a
+// spectrum within [1 / max w, 1 / min w + |G|] (w the pair weights), a
+// condition number of a few, so a handful of steps reach that level.  The
+// form matters under rounding: 2 X - X A X is symmetric for every symmetric
+// X, so its lower triangle, mirrored, is exact up to rounding, and a
+// perturbation P of X enters the next iterate as 2 P - P A X - X A P = 0 to
+// first order at X = A^-1 whatever P is.  X (2 I - A X) with a symmetrised
+// 2 I - A X instead maps P to about (P - A^-1 P A) / 2, whose modes grow by
+// up to cond(A) / 4 per step once the iteration has converged.
+// Per step: Z = A X (full), then X <- beta (2 X - X Z) (lower triangle, in
+// place: the tile epilogue reads and writes each lower element once, and
+// its mirrored stores touch only the upper triangle, which nothing reads).
+cudaError_t mixed_ns_inverse(isdf_ctx* c, const double* M, double* out, double sign, double alpha, const NsPlan& plan,
+                             cudaStream_t st) {
   const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
   const size_t rr = (size_t)r * r;
   double* X = c->Q.p;
-  double* X2 = c->W1.p;
-  double* Y = c->R.p;
-  MK(slices_cm(c->m_sd, c->T.p, r, r, r, rp, rk, st));  // A, once
+  double* Z = c->R.p;
+  MK(slices_cm(c->m_sd, M, r, r, r, rp, rk, st));  // M, once
   MK(cudaMemsetAsync(X, 0, rr * sizeof(double), st));
   MK(launch_add_identity(X, r, r, alpha, st));
-  for (int it = 0; it < iters; ++it) {
-    const bool last = it + 1 == iters;
-    MK(slices_cm(c->m_sa, X, r, r, r, rp, rk, st));
-    MK(cudaMemsetAsync(Y, 0, rr * sizeof(double), st));
-    MK(launch_add_identity(Y, r, r, 2.0, st));
-    MK(tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 1.0, Y, r, true, false, nullptr, 1,
-                   c->num_sms, c->d_status, st));  // Y = 2 I - A X (symmetric: lower tiles, mirrored)
-    MK(slices_cm(c->m_sb, Y, r, r, r, rp, rk, st));
-    double* out = last ? Kk : X2;
-    MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sb, rp, rk), r, r, last ? -1.0 : 1.0, 0.0, out, r, true, false,
-                   nullptr, 1, c->num_sms, c->d_status, st));  // X Y, symmetric (negated at the end: K)
-    std::swap(X, X2);
+  for (int it = 0; it < plan.steps(); ++it) {
+    const bool last = it + 1 == plan.steps();
+    const int s = plan.s[it];
+    const double b = plan.beta[it], f = last ? sign * b : b;
+    MK(slices_cm(c->m_sa, X, r, r, r, rp, rk, st));  // rows of X (= its columns)
+    MK(tc_gemm_f64(op_s(c->m_sd, rp, rk, s), op_s(c->m_sa, rp, rk, s), r, r, 1.0, 0.0, Z, r, false, false, nullptr, 1,
+                   c->num_sms, c->d_status, st));  // Z = M X
+    MK(slices_rm(c->m_sb, Z, r, r, r, rp, rk, st));  // rows: the columns of Z
+    double* dst = X;
+    if (last) {  // out = sign beta (2 X - X Z)
+      MK(cudaMemcpyAsync(out, X, rr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      dst = out;
+    }
+    MK(tc_gemm_f64(op_s(c->m_sa, rp, rk, s), op_s(c->m_sb, rp, rk, s), r, r, -f, 2.0 * f, dst, r, true, false, nullptr,
+                   1, c->num_sms, c->d_status, st));
   }
+  return cudaSuccess;
+}
+
+cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, const NsPlan& plan) {
+  return mixed_ns_inverse(c, c->T.p, Kk, -1.0, alpha, plan, c->stream);
+}
+
+void pair_weight_bounds(const double* energies, int n_v, int n_c, double w, double* wmin, double* wmax) {
+  double emax_v = energies[0], emin_v = energies[0], emin_c = energies[n_v], emax_c = energies[n_v];
+  for (int i = 0; i < n_v; ++i) {
+    emax_v = std::max(emax_v, energies[i]);
+    emin_v = std::min(emin_v, energies[i]);
+  }
+  for (int j = n_v; j < n_v + n_c; ++j) {
+    emin_c = std::min(emin_c, energies[j]);
+    emax_c = std::max(emax_c, energies[j]);
+  }
+  const double gap = emin_c - emax_v, width = emax_c - emin_v;
+  auto f = [w](double d) { return 2.0 * d / (d * d + w * w); };
+  *wmin = std::min(f(gap), f(width));
+  *wmax = std::max(f(gap), f(width));
+  if (w >= gap && w <= width) *wmax = std::max(*wmax, f(w));
+}
+
+namespace {
+
+void pair_weight_range(const isdf_ctx* c, int k, double* wmin, double* wmax) {
+  pair_weight_bounds(c->energies.data(), c->n_v, c->n_c, c->omega[k], wmin, wmax);
+}
+
+// Grouped-GEMM descriptor slot of (stage, step, kind): kind 0 the full
+// Z = M X, kind 1 the lower-triangle update (each step has its own scale and
+// slice count, so its own descriptors).
+inline int ns_slot(int stage, int step, int kind) { return (stage * 12 + step) * 2 + kind; }
+constexpr int kNsSlots = 2 * 12 * 2;
+
+// nw symmetric positive definite r x r matrices M (stride r^2): out = sign M^-1
+// by the Newton-Schulz steps of `plan`, X <- beta (2 X - X (M X)) from
+// X = alpha[z] I (the stable form of mixed_ns_capacitance).  Each product
+// is one grouped persistent GEMM over every (matrix, tile).
+cudaError_t ns_batched(isdf_ctx* c, const double* M, double* out, double sign, const double* alpha,
+                       const NsPlan& plan, int nw, int stage) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), sr = NSL * rp;
+  const long long rr = (long long)r * r;
+  const size_t ws = (tc_grouped_workspace_bytes(1) + 255) / 256 * 256;
+  unsigned char* wk = reinterpret_cast<unsigned char*>(c->ns_work.p);
+  double* X = c->bW1.p;
+  double* Z = c->bT.p;
+  MK(slices_cm_b(c->b_s1, M, r, rr, r, r, rp, rk, nw, st));
+  MK(launch_scaled_identity(X, r, nw, alpha, st));
+  for (int it = 0; it < plan.steps(); ++it) {
+    const bool last = it + 1 == plan.steps();
+    const int s = plan.s[it];
+    const double b = plan.beta[it];
+    MK(slices_cm_b(c->b_s2, X, r, rr, r, r, rp, rk, nw, st));
+    TcGroupProblem pz{op_s(c->b_s1, rp, rk, s), op_s(c->b_s2, rp, rk, s), r, r, 1.0, 0.0, Z, r, false,
+                      TcBatch{nw, sr, sr, rr}};
+    const int sz = ns_slot(stage, it, 0), sx = ns_slot(stage, it, 1);
+    MK(tc_gemm_f64_grouped(&pz, 1, wk + sz * ws, ws, c->ns_staged[sz], c->num_sms, c->d_status, st));
+    MK(slices_rm_b(c->b_s4, Z, r, rr, r, r, rp, rk, nw, st));
+    double* dst = X;
+    if (last) {
+      MK(cudaMemcpyAsync(out, X, (size_t)rr * nw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      dst = out;
+    }
+    const double f = last ? sign * b : b;
+    TcGroupProblem px{op_s(c->b_s2, rp, rk, s), op_s(c->b_s4, rp, rk, s), r, r, -f, 2.0 * f, dst, r, true,
+                      TcBatch{nw, sr, sr, rr}};
+    MK(tc_gemm_f64_grouped(&px, 1, wk + sx * ws, ws, c->ns_staged[sx], c->num_sms, c->d_status, st));
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t mixed_smw_batched_ns(isdf_ctx* c, int nw, int* fail_T, bool* used) {
+  cudaStream_t st = c->stream;
+  *used = false;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const size_t rr = (size_t)r * r, per_sq = (size_t)NSL * rp * rk;
+  const size_t ws = (tc_grouped_workspace_bytes(1) + 255) / 256 * 256;
+  if (!tl_capture) {
+    MK(cudaStreamSynchronize(st));  // the buffers below may grow
+    MK(ensure(c->bW1, rr * nw));
+    MK(ensure(c->bT, rr * nw));
+    MK(ensure(c->bQ, rr * nw));
+    MK(ensure_bf16(c->b_s1, per_sq * nw));
+    MK(ensure_bf16(c->b_s2, per_sq * nw));
+    MK(ensure_bf16(c->b_s4, per_sq * nw));
+    MK(ensure(c->ns_work, (kNsSlots * ws + 7) / 8));
+    if (c->ns_staged.size() < (size_t)kNsSlots) c->ns_staged.resize(kNsSlots);
+    MK(ensure(c->ns_alpha, 2 * (size_t)nw));
+    const size_t bw = row_abs_sum_work(r, nw);
+    MK(ensure(c->ns_bound, bw + 3 * (size_t)nw + 8));
+    // spectra: rigorous bounds only (Gershgorin for every D(w) and for G,
+    // the pair-weight range): a schedule planned from an estimate could
+    // leave a mode unconverged
+    double* nb = c->ns_bound.p;
+    double* lam = nb + bw;  // [unused | nw Gershgorin of D | Gershgorin of G], after the workspace
+    MK(launch_row_abs_sum_max(c->D.p, r, r, lam + nw, nb, st, nw, (long long)rr));
+    MK(launch_row_abs_sum_max(c->G.p, r, r, lam + 2 * nw, nb, st));
+    std::vector<double> h(2 * (size_t)nw + 1);
+    MK(cudaMemcpyAsync(h.data(), lam, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MK(cudaStreamSynchronize(st));
+    std::vector<double> alpha(2 * (size_t)nw);
+    double e_d = 0.0, e_a = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      double wmin = 0.0, wmax = 0.0;
+      pair_weight_range(c, k, &wmin, &wmax);
+      // D: spectrum within [w_min, min(w_max, Gershgorin)]
+      const double hd = std::min(wmax, h[nw + k]), ld = wmin;
+      // A = D^-1 + G: at least 1 / lambda_max(D), at most 1 / w_min + lambda_max(G)
+      const double la = 1.0 / hd, ha = 1.0 / wmin + h[2 * nw];
+      if (!(ld > 0.0) || !(hd >= ld) || !std::isfinite(ha)) return cudaSuccess;  // not used: the caller factors
+      alpha[k] = 2.0 / (ld + hd);
+      alpha[nw + k] = 2.0 / (la + ha);
+      // one schedule for every frequency: the largest e0 (a scale sequence
+      // valid for e0 keeps every smaller e0 within the same bounds)
+      e_d = std::max(e_d, (hd - ld) / (hd + ld));
+      e_a = std::max(e_a, (ha - la) / (ha + la));
+    }
+    NsPlan pd, pa;
+    if (!ns_plan(e_d, pd) || !ns_plan(e_a, pa)) return cudaSuccess;  // too many steps: the caller factors
+    MK(cudaMemcpyAsync(c->ns_alpha.p, alpha.data(), alpha.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    MK(cudaStreamSynchronize(st));
+    c->ns_e0_d = e_d;
+    c->ns_e0_a = e_a;
+    c->ns_nw = nw;
+  } else if (c->ns_nw != nw || c->ns_e0_d < 0.0) {
+    return cudaErrorStreamCaptureUnsupported;  // a captured call needs the eager call's plan
+  }
+  NsPlan pd, pa;
+  ns_plan(c->ns_e0_d, pd);
+  ns_plan(c->ns_e0_a, pa);
+  // D(w)^-1, then A(w) = D(w)^-1 + G, then K(w) = -A(w)^-1
+  MK(ns_batched(c, c->D.p, c->bQ.p, 1.0, c->ns_alpha.p, pd, nw, 0));
+  MK(launch_add(c->bQ.p, c->G.p, c->bQ.p, (long long)rr, st, nw, (long long)rr, 0));
+  MK(ns_batched(c, c->bQ.p, c->K.p, -1.0, c->ns_alpha.p + nw, pa, nw, 1));
+  MK(cudaMemsetAsync(fail_T, 0xff, nw * sizeof(int), st));  // nothing to fail
+  *used = true;
+  return cudaSuccess;
+}
+
+// The capacitance stage of smw_inverse_all for several systems at once:
+// every Newton-Schulz product of every system (all frequencies, all tiles)
+// in one grouped persistent launch per step.  Each context must hold the
+// plan of an earlier eager smw_inverse_all on the same polarizability (the
+// start scales on the device, the largest e0 of each stage); every system
+// follows the schedule of the largest e0 over the systems (valid for all
+// of them, and one slice count per launch, as the grouped kernel needs).
+// Descriptor slot (stage, step, kind) lives at work + slot * ws with its
+// host copy in staged[slot]; ns_stage_slots() slots in all.
+int ns_stage_slots() { return kNsSlots; }
+
+cudaError_t ns_stage_grouped(isdf_ctx** cs, int n, cudaStream_t st, void* work, size_t ws,
+                             std::vector<std::vector<unsigned char>>& staged) {
+  if (n <= 0) return cudaSuccess;
+  if (n > 32) return cudaErrorInvalidValue;
+  double e_d = 0.0, e_a = 0.0;
+  for (int i = 0; i < n; ++i) {
+    isdf_ctx* c = cs[i];
+    if (c->prec != ISDF_PREC_MIXED || c->rank <= 0 || c->ns_nw != c->n_omega || c->ns_e0_d < 0.0 || c->ns_e0_a < 0.0)
+      return cudaErrorInvalidValue;
+    e_d = std::max(e_d, c->ns_e0_d);
+    e_a = std::max(e_a, c->ns_e0_a);
+  }
+  NsPlan plan[2];
+  if (!ns_plan(e_d, plan[0]) || !ns_plan(e_a, plan[1])) return cudaErrorInvalidValue;
+  if (staged.size() < (size_t)kNsSlots) staged.resize(kNsSlots);
+  unsigned char* w = static_cast<unsigned char*>(work);
+  std::vector<TcGroupProblem> pz, px;
+  for (int stage = 0; stage < 2; ++stage) {
+    const NsPlan& pl = plan[stage];
+    // stage 0: bQ = D(w)^-1; stage 1: K(w) = -(D(w)^-1 + G)^-1; X in bW1, Z in bT
+    for (int i = 0; i < n; ++i) {
+      isdf_ctx* c = cs[i];
+      const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega;
+      const long long rr = (long long)r * r;
+      if (stage == 1) MK(launch_add(c->bQ.p, c->G.p, c->bQ.p, rr, st, nw, rr, 0));  // A = D^-1 + G
+      MK(slices_cm_b(c->b_s1, stage == 0 ? c->D.p : c->bQ.p, r, rr, r, r, rp, rk, nw, st));
+      MK(launch_scaled_identity(c->bW1.p, r, nw, c->ns_alpha.p + (stage == 0 ? 0 : nw), st));
+    }
+    for (int t = 0; t < pl.steps(); ++t) {
+      const bool last = t + 1 == pl.steps();
+      const int s = pl.s[t];
+      const double sign = stage == 0 ? 1.0 : -1.0, f = last ? sign * pl.beta[t] : pl.beta[t];
+      pz.clear();
+      px.clear();
+      for (int i = 0; i < n; ++i) {
+        isdf_ctx* c = cs[i];
+        const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
+        const long long rr = (long long)r * r;
+        MK(slices_cm_b(c->b_s2, c->bW1.p, r, rr, r, r, rp, rk, nw, st));
+        pz.push_back(TcGroupProblem{op_s(c->b_s1, rp, rk, s), op_s(c->b_s2, rp, rk, s), r, r, 1.0, 0.0, c->bT.p, r,
+                                    false, TcBatch{nw, sr, sr, rr}});
+      }
+      const int sz = ns_slot(stage, t, 0), sx = ns_slot(stage, t, 1);
+      MK(tc_gemm_f64_grouped(pz.data(), (int)pz.size(), w + sz * ws, ws, staged[sz], cs[0]->num_sms, cs[0]->d_status,
+                             st));  // Z = M X
+      for (int i = 0; i < n; ++i) {
+        isdf_ctx* c = cs[i];
+        const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
+        const long long rr = (long long)r * r;
+        MK(slices_rm_b(c->b_s4, c->bT.p, r, rr, r, r, rp, rk, nw, st));
+        double* dst = c->bW1.p;
+        if (last) {
+          dst = stage == 0 ? c->bQ.p : c->K.p;
+          MK(cudaMemcpyAsync(dst, c->bW1.p, (size_t)rr * nw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        px.push_back(TcGroupProblem{op_s(c->b_s2, rp, rk, s), op_s(c->b_s4, rp, rk, s), r, r, -f, 2.0 * f, dst, r,
+                                    true, TcBatch{nw, sr, sr, rr}});
+      }
+      MK(tc_gemm_f64_grouped(px.data(), (int)px.size(), w + sx * ws, ws, staged[sx], cs[0]->num_sms, cs[0]->d_status,
+                             st));  // X <- beta (2 X - X Z) (lower, in place), or the result
+    }
+  }
+  for (int i = 0; i < n; ++i) MK(cudaMemsetAsync(cs[i]->b_fail, 0xff, cs[i]->n_omega * sizeof(int), st));
   return cudaSuccess;
 }
 
