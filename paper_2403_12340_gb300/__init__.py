@@ -40,7 +40,7 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex", "isdf_batch_capture",
             "isdf_batch_replay", "isdf_set_autotune", "isdf_autotune_size", "isdf_autotune_entry",
             "isdf_autotune_clear", "isdf_device_allocations", "isdf_check_device_wait",
-            "isdf_adjoint_fit", "isdf_read_kernel_trace"]
+            "isdf_adjoint_fit", "isdf_read_kernel_trace", "isdf_set_refinement"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 6
 
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isdf_kernel_family_name.restype = ctypes.c_char_p
     lib.isdf_launch_count.argtypes = []
     lib.isdf_launch_count.restype = ctypes.c_longlong
+    lib.isdf_set_refinement.argtypes = [P, I]
+    lib.isdf_set_refinement.restype = I
     lib.isdf_check_device_wait.argtypes = [P, ctypes.c_longlong]
     lib.isdf_check_device_wait.restype = I
     lib.isdf_device_allocations.argtypes = []
@@ -336,6 +338,10 @@ def isdf_fit_factor(ctx, n_mu: int, L_out=None):
     pl = 0 if L_out is None else _dev_ptr(L_out.reshape(-1), name="L_out")
     _check(load_library().isdf_fit_factor(ctx, piv.ctypes.data, pl), ctx)
     return piv
+
+
+def isdf_set_refinement(ctx, steps: int) -> None:
+    _check(load_library().isdf_set_refinement(ctx, int(steps)), ctx)
 
 
 def isdf_set_profiling(ctx, on: bool) -> None:

@@ -265,7 +265,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->a_m5, &c->a_m6, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
                     &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->ns_bound, &c->ns_alpha, &c->ns_work,
-                    &c->b_s4, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split};
+                    &c->b_s4, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split, &c->ref};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
   for (auto& pe : c->prof_ev) {
@@ -1103,6 +1103,10 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
   CK(ensure(c->tmp3, (size_t)nr * nc0));
   CK(ensure(c->spec, (size_t)lds * nc0));
   CK(ensure(c->partial, std::max<size_t>((size_t)sp0 * r * nc0, 1)));
+  if (c->prec == ISDF_PREC_MIXED && c->refine > 0 && c->dinv_ready) {
+    if (c->ref.cap < (size_t)3 * r * nc0) CK(cudaStreamSynchronize(c->stream));
+    CK(ensure(c->ref, std::max<size_t>((size_t)3 * r * nc0, 1)));
+  }
   PhaseScope ph(c, ISDF_PH_APPLY);
   for (int c0 = 0; c0 < n_rhs; c0 += chunk) {
     const int nc = std::min(chunk, n_rhs - c0);
@@ -1159,6 +1163,12 @@ extern "C" const char* isdf_phase_name(int phase) {
 extern "C" long long isdf_launch_count(void) { return launch_count(); }
 
 extern "C" long long isdf_device_allocations(void) { return isdf::device_allocation_count(); }
+
+extern "C" int isdf_set_refinement(isdf_ctx* c, int steps) {
+  if (!c || steps < 0 || steps > 8) return ISDF_ERR_ARG;
+  c->refine = steps;
+  return ISDF_OK;
+}
 
 extern "C" int isdf_set_profiling(isdf_ctx* c, int on) {
   if (!c) return ISDF_ERR_ARG;

@@ -119,6 +119,8 @@ struct isdf_ctx {
   std::vector<std::vector<unsigned char>> ns_staged;
   bool dinv_ready = false;
   bool dinv_ns = false;  // the last polarizability inverted D by Newton-Schulz (D left unfactored)
+  int refine = 0;        // refinement rounds of the SMW solve in the mixed apply (isdf_set_refinement)
+  DevBuf ref;            // their scratch: three r x 64 blocks
   std::vector<double> ew_host;   // their host copy (the source of the asynchronous upload)
   bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
   int pair_mode = 0;         // the precision argument of the last fit

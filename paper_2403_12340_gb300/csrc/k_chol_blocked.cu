@@ -162,29 +162,47 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double* A, long long
 }
 
 // k_chol_diag in double-float arithmetic on the FP32 pipe (the mixed path),
-// which also inverts the factor of the block.  The same LDL^T chain of one
-// warp beside twelve update warps, every element a float pair (about 2^-47
-// relative per operation): one dependent double-float step costs a few
-// FP32 latencies (4 cycles each) instead of the FP64 pipe's ~64 cycles per
-// dependent instruction.  The update warps carry the elimination to an
-// identity block too (Gauss-Jordan on the augmented block [A | I]): with
-// A = Lt D Lt^T (Lt unit lower), the row operations of pivot p,
-// row_i -= l_ip row_p for i > p, turn I into B = Lt^-1, so
-// L^-1 = D^-1/2 B comes out of the same pivot loop with no chain of its own.
-// A pivot is accepted when its high part exceeds the threshold
-// (tol_rel * max diag, in FP32).  Entries are split into float pairs as they
-// are loaded; L goes back to A in FP64, L^-1 to Lid (FP64, ld ldi) and / or
-// Lis (float pairs, ld lds) when those are given.
-constexpr int DIAG_EPT_B = (CB * (CB - 1) / 2 + DIAG_BULK - 1) / DIAG_BULK;  // strict lower elements per thread
+// blocked, which also inverts the factor of the block.  Every element is a
+// float pair (about 2^-47 relative per operation); the block is padded to
+// 64 x 64 with the identity, so padded pivots are 1 and padded rows of the
+// factor are 0.  A = Lt D Lt^T (Lt unit lower) by eight panels of eight
+// columns with look-ahead:
+//  - warp 0 factors a panel: for each pivot j, d_j = A_jj (accepted when its
+//    high part exceeds tol_rel * max diag, in FP32), u_ij = A_ij and
+//    l_ij = u_ij / d_j for the rows below, then the rest of the panel's
+//    columns take the rank-1 update A_ik -= l_ij u_kj (lanes own rows,
+//    __syncwarp between the steps; one warp's chain, no block barrier);
+//  - the other warps meanwhile apply the previous panel's rank-8 update to
+//    the columns beyond the panel being factored (8 x 8 element blocks of
+//    the lower triangle, eight double-float products per element);
+//  - between panels all warps update the next panel's columns first, so
+//    warp 0 can start on it at once.
+// Then B = Lt^-1 by 8 x 8 block rows (diagonal blocks by forward
+// substitution, one thread per column; off-diagonal blocks
+// B_IJ = -B_II sum_K Lt_IK B_KJ), L = Lt D^1/2 back to A in FP64 and
+// L^-1 = D^-1/2 B to Lid (FP64, ld ldi) and / or Lis (float pairs, ld lds).
+// Entries are split into float pairs as they are loaded.
+constexpr int DF_DIAG_THREADS = 256;
+constexpr int DF_PW = 8;  // panel width
 
-__global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long long lda, int j0, int bs,
-                                                              const double* dmax, double tol_rel, int* fail,
-                                                              long long sA, double* Lid, long long ldi,
-                                                              float2* Lis, long long lds, long long sS) {
-  __shared__ float2 Ls[CB][CB + 1];  // the block, unscaled LDL^T columns
-  __shared__ float2 Bs[CB][CB + 1];  // the identity block under the same row operations
-  __shared__ float2 lc[2][CB];       // l_j and l_{j-1}
-  __shared__ float2 piv[CB];         // d_j, then d_j^-1/2
+// 8 x 8 element block (bi, bk) of the lower triangle, bk <= bi: the block
+// count of rows 0..n-1 is n (n + 1) / 2; decode by a short search (n <= 8)
+__device__ __forceinline__ void df_tri_block(int b, int& bi, int& bk) {
+  int i = 0;
+  while ((i + 1) * (i + 2) / 2 <= b) ++i;
+  bi = i;
+  bk = b - i * (i + 1) / 2;
+}
+
+__global__ void __launch_bounds__(DF_DIAG_THREADS) k_chol_diag_df(double* A, long long lda, int j0, int bs,
+                                                                 const double* dmax, double tol_rel, int* fail,
+                                                                 long long sA, double* Lid, long long ldi,
+                                                                 float2* Lis, long long lds, long long sS) {
+  __shared__ float2 Ls[CB][CB + 1];     // the block; after its panel, column j holds l_ij (i > j)
+  __shared__ float2 Bs[CB][CB + 1];     // B = Lt^-1
+  __shared__ float2 Us[2][CB][DF_PW];   // u_kj = l_kj d_j of the last two panels
+  __shared__ float2 piv[CB];            // d_j
+  __shared__ float2 sq[2][CB];          // d^-1/2, d^1/2
   __shared__ int s_bad;
   A += sA * blockIdx.x;
   dmax += blockIdx.x;
@@ -193,143 +211,180 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag_df(double* A, long l
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int idx = t; idx < CB * CB; idx += blockDim.x) {
     const int i = idx & (CB - 1), k = idx >> 6;
-    Ls[i][k] = (i < bs && k <= i) ? split_f64_fast(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.0f, 0.0f);
-    Bs[i][k] = make_float2(i == k ? 1.0f : 0.0f, 0.0f);
-  }
-  // the warps on sub-partitions 1-3 own fixed elements of both blocks,
-  // packed as row * 64 + column: the lower triangle of A, the strict lower
-  // triangle of B
-  const bool bulk = (warp & 3) != 0;
-  int ownA[DIAG_EPT], ownB[DIAG_EPT_B];
-  {
-    const int b = (warp - 1 - (warp >> 2)) * 32 + lane;
-#pragma unroll
-    for (int q = 0; q < DIAG_EPT; ++q) {
-      const int e = b + DIAG_BULK * q;
-      ownA[q] = -1;
-      if (bulk && e < CB * (CB + 1) / 2) {
-        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while ((a + 1) * (a + 2) / 2 <= e) ++a;
-        while (a * (a + 1) / 2 > e) --a;
-        ownA[q] = a * CB + (e - a * (a + 1) / 2);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < DIAG_EPT_B; ++q) {
-      const int e = b + DIAG_BULK * q;  // row a >= 1 holds e in [a (a - 1) / 2, a (a + 1) / 2)
-      ownB[q] = -1;
-      if (bulk && e < CB * (CB - 1) / 2) {
-        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
-        while (a * (a + 1) / 2 <= e) ++a;
-        while (a * (a - 1) / 2 > e) --a;
-        ownB[q] = a * CB + (e - a * (a - 1) / 2);
-      }
-    }
+    float2 v = make_float2(i == k ? 1.0f : 0.0f, 0.0f);  // the identity beyond bs
+    if (i < bs && k < bs) v = k <= i ? split_f64_fast(A[(j0 + i) + lda * (long long)(j0 + k)]) : make_float2(0.f, 0.f);
+    Ls[i][k] = v;
+    Bs[i][k] = make_float2(0.0f, 0.0f);
   }
   if (t == 0) s_bad = -1;
   const float thresh = (float)(tol_rel * (*dmax));
   __syncthreads();
-  for (int j = 0; j < bs; ++j) {
-    const float2* lp = lc[(j + 1) & 1];  // l_{j-1}
+
+  // rank-8 update by panel p (l in Ls columns c0..c0+7, u in Us[p & 1]) of
+  // the lower-triangle 8 x 8 blocks with block column in [kb0, kb1): thread
+  // `tid` of `nth`
+  auto update_blocks = [&](int p, int kb0, int kb1, int tid, int nth) {
+    const int c0 = p * DF_PW;
+    const float2(*U)[DF_PW] = Us[p & 1];
+    // blocks (bi, bk) with kb0 <= bk < kb1 and bk <= bi < 8
+    int nblk = 0;
+    for (int bk = kb0; bk < kb1; ++bk) nblk += 8 - bk;
+    for (int e = tid; e < nblk * 64; e += nth) {
+      int b = e >> 6, bi = 0, bk = kb0;
+      while (b >= 8 - bk) {
+        b -= 8 - bk;
+        ++bk;
+      }
+      bi = bk + b;
+      const int i = bi * 8 + ((e >> 3) & 7), k = bk * 8 + (e & 7);
+      if (k > i) continue;
+      float hi = Ls[i][k].x, lo = Ls[i][k].y;
+#pragma unroll
+      for (int q = 0; q < DF_PW; ++q) {
+        const float2 l = Ls[i][c0 + q];
+        df_fma(make_float2(-l.x, -l.y), U[k][q], hi, lo);
+      }
+      Ls[i][k] = df_norm(hi, lo);
+    }
+  };
+
+  constexpr int NP = CB / DF_PW;
+  for (int p = 0; p < NP; ++p) {
+    const int c0 = p * DF_PW;
     if (warp == 0) {
-      if (j > 0) {  // column j gets the update of pivot j - 1
-        const float2 ajj1 = Ls[j][j - 1];
-        const int i0 = j + lane, i1 = j + 32 + lane;
-        float2 x0 = make_float2(0.0f, 0.0f), x1 = x0, l0 = x0, l1 = x0;
-        if (i0 < bs) {
-          x0 = Ls[i0][j];
-          l0 = lp[i0];
-        }
-        if (i1 < bs) {
-          x1 = Ls[i1][j];
-          l1 = lp[i1];
-        }
-        if (i0 < bs) Ls[i0][j] = df_fms(x0, l0, ajj1);
-        if (i1 < bs) Ls[i1][j] = df_fms(x1, l1, ajj1);
-        __syncwarp();
-      }
-      const float2 d = Ls[j][j];
-      if (!(d.x > thresh)) {  // the same value in every lane; also catches NaN
-        if (lane == 0) s_bad = j;
-      } else {
-        const float2 r = df_recip(d);
-        if (lane == 0) piv[j] = d;
-        float2* lj = lc[j & 1];
-        const int i0 = j + 1 + lane, i1 = j + 33 + lane;
-        float2 x0 = make_float2(0.0f, 0.0f), x1 = x0;
-        if (i0 < bs) x0 = Ls[i0][j];
-        if (i1 < bs) x1 = Ls[i1][j];
-        if (i0 < bs) lj[i0] = df_mul(x0, r);
-        if (i1 < bs) lj[i1] = df_mul(x1, r);
-      }
-    } else if (bulk && j > 0) {
-      const int p = j - 1;
-      // A: columns k > j take the update of pivot p
-      {
-        float2 c[DIAG_EPT], a[DIAG_EPT], b[DIAG_EPT];
-        bool on[DIAG_EPT];
+      // ---- panel p in registers: lane owns rows c0 + lane and c0 + 32 + lane
+      // (v[0], v[1]), columns c0..c0+7; row j = c0 + jq is lane jq's v[0]
+      float2(*U)[DF_PW] = Us[p & 1];
+      float2 v[2][DF_PW];
 #pragma unroll
-        for (int q = 0; q < DIAG_EPT; ++q) {
-          const int o = ownA[q], i = o >> 6, k = o & (CB - 1);
-          on[q] = o >= 0 && k > j && i < bs;
-          if (on[q]) {
-            c[q] = Ls[i][k];
-            a[q] = lp[i];
-            b[q] = Ls[k][p];
+      for (int h = 0; h < 2; ++h) {
+        const int i = c0 + lane + 32 * h;
+#pragma unroll
+        for (int q = 0; q < DF_PW; ++q) v[h][q] = i < CB ? Ls[i][c0 + q] : make_float2(0.f, 0.f);
+      }
+      bool bad = false;
+#pragma unroll
+      for (int jq = 0; jq < DF_PW; ++jq) {
+        const int j = c0 + jq;
+        float2 d;
+        d.x = __shfl_sync(0xffffffffu, v[0][jq].x, jq);
+        d.y = __shfl_sync(0xffffffffu, v[0][jq].y, jq);
+        // u_kj = A_kj of the panel's later rows k = c0 + kq, before scaling
+        float2 uk[DF_PW];
+#pragma unroll
+        for (int kq = jq + 1; kq < DF_PW; ++kq) {
+          uk[kq].x = __shfl_sync(0xffffffffu, v[0][jq].x, kq);
+          uk[kq].y = __shfl_sync(0xffffffffu, v[0][jq].y, kq);
+        }
+        if (!bad) {
+          if (j < bs && !(d.x > thresh)) {  // the same value in every lane; also catches NaN
+            bad = true;
+            if (lane == 0) s_bad = j;
+          } else {
+            const float2 r = df_recip(d);
+            if (lane == 0) piv[j] = d;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int i = c0 + lane + 32 * h;
+              if (i > j && i < CB) {
+                const float2 u = v[h][jq];
+                U[i][jq] = u;
+                const float2 l = df_mul(u, r);
+                v[h][jq] = l;
+#pragma unroll
+                for (int kq = jq + 1; kq < DF_PW; ++kq)
+                  if (c0 + kq <= i) v[h][kq] = df_fms(v[h][kq], l, uk[kq]);
+              }
+            }
           }
         }
-#pragma unroll
-        for (int q = 0; q < DIAG_EPT; ++q)
-          if (on[q]) {
-            const int o = ownA[q];
-            Ls[o >> 6][o & (CB - 1)] = df_fms(c[q], a[q], b[q]);
-          }
       }
-      // B: row i >= j takes row p times l_ip (columns m <= p; B_pp = 1)
-      {
-        float2 c[DIAG_EPT_B], a[DIAG_EPT_B], b[DIAG_EPT_B];
-        bool on[DIAG_EPT_B];
 #pragma unroll
-        for (int q = 0; q < DIAG_EPT_B; ++q) {
-          const int o = ownB[q], i = o >> 6, m = o & (CB - 1);
-          on[q] = o >= 0 && m <= p && i >= j && i < bs;
-          if (on[q]) {
-            c[q] = Bs[i][m];
-            a[q] = lp[i];
-            b[q] = Bs[p][m];
-          }
+      for (int h = 0; h < 2; ++h) {
+        const int i = c0 + lane + 32 * h;
+        if (i < CB) {
+#pragma unroll
+          for (int q = 0; q < DF_PW; ++q) Ls[i][c0 + q] = v[h][q];
         }
-#pragma unroll
-        for (int q = 0; q < DIAG_EPT_B; ++q)
-          if (on[q]) {
-            const int o = ownB[q];
-            Bs[o >> 6][o & (CB - 1)] = df_fms(c[q], a[q], b[q]);
-          }
       }
+    } else if (p > 0 && (warp & 3) != 0) {
+      // ---- the previous panel's update of the columns beyond this panel, by
+      // the warps off warp 0's sub-partition (the chain keeps its issue slots)
+      update_blocks(p - 1, p + 1, NP, (warp - 1 - (warp >> 2)) * 32 + lane, DF_DIAG_THREADS / 4 * 3);
     }
     __syncthreads();
     if (s_bad >= 0) break;
+    // ---- this panel's update of the next panel's columns (look-ahead)
+    if (p + 1 < NP) update_blocks(p, p + 1, p + 2, t, DF_DIAG_THREADS);
+    __syncthreads();
   }
   if (s_bad >= 0) {
     if (t == 0) atomicCAS(fail, -1, j0 + s_bad);
     return;
   }
-  // L = Lt D^1/2: L_ik = u_ik d_k^-1/2 (u = Lt D), L_ii = d_i d_i^-1/2;
-  // L^-1 = D^-1/2 B
-  float2 dq = make_float2(0.0f, 0.0f);
-  if (t < bs) dq = df_rsqrt(piv[t]);
+  // ---- B = Lt^-1: diagonal 8 x 8 blocks, one thread per column
+  if (t < CB) {
+    const int bi = t >> 3, m = t;  // column m of diagonal block bi
+    Bs[m][m] = make_float2(1.0f, 0.0f);
+    for (int i = m + 1; i < bi * 8 + 8; ++i) {
+      float hi = 0.0f, lo = 0.0f;
+      for (int j = m; j < i; ++j) df_fma(Ls[i][j], Bs[j][m], hi, lo);
+      Bs[i][m] = df_norm(-hi, -lo);
+    }
+  }
   __syncthreads();
+  // off-diagonal blocks, block row by block row: W = sum_K Lt_IK B_KJ
+  // (K = J .. I - 1, into the block itself), then B_IJ = -B_II W
+  for (int I = 1; I < NP; ++I) {
+    float2 w[2];
+    int cnt = 0;
+    for (int e = t; e < I * 64; e += blockDim.x, ++cnt) {
+      const int J = e >> 6, i = I * 8 + ((e >> 3) & 7), m = J * 8 + (e & 7);
+      // two interleaved sums halve the dependent chain
+      float hi = 0.0f, lo = 0.0f, hi2 = 0.0f, lo2 = 0.0f;
+      int j = m;
+      for (; j + 1 < I * 8; j += 2) {
+        df_fma(Ls[i][j], Bs[j][m], hi, lo);
+        df_fma(Ls[i][j + 1], Bs[j + 1][m], hi2, lo2);
+      }
+      if (j < I * 8) df_fma(Ls[i][j], Bs[j][m], hi, lo);
+      df_fma(make_float2(hi2, lo2), make_float2(1.0f, 0.0f), hi, lo);
+      w[cnt] = df_norm(hi, lo);
+    }
+    cnt = 0;
+    for (int e = t; e < I * 64; e += blockDim.x, ++cnt) {
+      const int i = I * 8 + ((e >> 3) & 7), m = (e >> 6) * 8 + (e & 7);
+      Bs[i][m] = w[cnt];
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int e = t; e < I * 64; e += blockDim.x, ++cnt) {
+      const int i = I * 8 + ((e >> 3) & 7), m = (e >> 6) * 8 + (e & 7);
+      float hi = 0.0f, lo = 0.0f;
+      for (int j = I * 8; j <= i; ++j) df_fma(Bs[i][j], Bs[j][m], hi, lo);  // B_II W (B_ii = 1)
+      w[cnt] = df_norm(-hi, -lo);
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int e = t; e < I * 64; e += blockDim.x, ++cnt) {
+      const int i = I * 8 + ((e >> 3) & 7), m = (e >> 6) * 8 + (e & 7);
+      Bs[i][m] = w[cnt];
+    }
+    __syncthreads();
+  }
+  // ---- L = Lt D^1/2, L^-1 = D^-1/2 B
   if (t < bs) {
-    lc[0][t] = dq;                     // d^-1/2
-    lc[1][t] = df_mul(piv[t], dq);     // d^1/2
+    const float2 dq = df_rsqrt(piv[t]);
+    sq[0][t] = dq;
+    sq[1][t] = df_mul(piv[t], dq);
   }
   __syncthreads();
   for (int idx = t; idx < bs * bs; idx += blockDim.x) {
     const int i = idx % bs, k = idx / bs;
-    const double v = (k < i) ? df_to_f64(df_mul(Ls[i][k], lc[0][k])) : (k == i ? df_to_f64(lc[1][i]) : 0.0);
+    const double v = (k < i) ? df_to_f64(df_mul(Ls[i][k], sq[1][k])) : (k == i ? df_to_f64(sq[1][i]) : 0.0);
     A[(j0 + i) + lda * (long long)(j0 + k)] = v;
     if (Lid || Lis) {
-      const float2 w = (k < i) ? df_mul(Bs[i][k], lc[0][i]) : (k == i ? lc[0][i] : make_float2(0.0f, 0.0f));
+      const float2 w = (k < i) ? df_mul(Bs[i][k], sq[0][i]) : (k == i ? sq[0][i] : make_float2(0.0f, 0.0f));
       if (Lid) Lid[i + ldi * (long long)k] = df_to_f64(w);
       if (Lis) Lis[sS * blockIdx.x + i + lds * k] = w;
     }
@@ -645,7 +700,7 @@ static cudaError_t diag_step(double* L, long long ldl, int j0, int bs, const dou
   note_launch();
   if (split) {
     float2* lis = n > CB ? split + (n - CB) : nullptr;  // n <= 64: one block, no panel
-    k_chol_diag_df<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL, Lid, ldi, lis, n, sS);
+    k_chol_diag_df<<<batch, DF_DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL, Lid, ldi, lis, n, sS);
   } else {
     k_chol_diag<<<batch, DIAG_THREADS, 0, s>>>(L, ldl, j0, bs, dmax, tol_rel, fail, sL);
   }

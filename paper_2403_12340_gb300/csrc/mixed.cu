@@ -708,6 +708,27 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
   // T2 = K T1 (FP64, small)
   MK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 16, c->partial.p, true,
                  st));
+  if (c->refine > 0 && c->dinv_ready && c->ref.cap >= (size_t)3 * r * nc) {
+    // iterative refinement of T2 = -(D^-1 + G)^-1 T1, i.e. of (I + D G) T2 =
+    // -D T1: R = -D (T1 + G T2) - T2 in FP64, then T2 -= K (D^-1 R) (the
+    // error of T2 solves (I + D G) E = R, and (I + D G)^-1 = -K D^-1)
+    const size_t blk = (size_t)r * nc, bytes = blk * sizeof(double);
+    double* U = c->ref.p;
+    double* R = U + blk;
+    double* V = R + blk;
+    for (int it = 0; it < c->refine; ++it) {
+      MK(cudaMemcpyAsync(U, c->tmp1.p, bytes, cudaMemcpyDeviceToDevice, st));
+      MK(launch_gemm(c->G.p, r, false, c->tmp2.p, r, true, r, nc, r, 1.0, 1.0, U, r, false, 16, c->partial.p, true,
+                     st));  // U = T1 + G T2
+      MK(cudaMemcpyAsync(R, c->tmp2.p, bytes, cudaMemcpyDeviceToDevice, st));
+      MK(launch_gemm(c->D.p, r, false, U, r, true, r, nc, r, -1.0, -1.0, R, r, false, 16, c->partial.p, true,
+                     st));  // R = -D U - T2
+      MK(launch_gemm(c->Dinv.p, r, false, R, r, true, r, nc, r, 1.0, 0.0, V, r, false, 16, c->partial.p, true,
+                     st));  // V = D^-1 R
+      MK(launch_gemm(Kk, r, false, V, r, true, r, nc, r, -1.0, 1.0, c->tmp2.p, r, false, 16, c->partial.p, true,
+                     st));  // T2 -= K V
+    }
+  }
   // T3 = theta T2
   MK(slices_rm(c->m_xs, c->tmp2.p, r, nc, r, ncp, rk, st));
   MK(tc_gemm_f64(op(c->m_ths, nrp, rk), op(c->m_xs, ncp, rk), (int)nr, nc, 1.0, 0.0, c->tmp3.p, nr, false, false,
