@@ -41,3 +41,21 @@ def test_derived_peaks():
     # 152 SMs at 2070 MHz: 4 FP64 flop/clk; 128 FP32 lanes / 12 instructions x 2 flops
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.2586, rel=1e-4)
     assert bench.DF_PEAK_TFLOPS == pytest.approx(6.7123, rel=1e-4)
+
+
+def test_dominant_cell_prefers_tensor_gemm():
+    """The roofline cell is the tensor-core GEMM cell with the most time per
+    step, even when a factorisation chain's cell (timed on its own stream,
+    waits included) reads longer; without a tensor-core cell, the longest
+    cell.  Its traffic comes from the ncu table when the kernel is in it."""
+    import bench
+
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of test"}
+    cells = [bench.kernel_roofline("df_gemm", "points_chol", 30.0, 92, 1e10, 10, peaks),
+             bench.kernel_roofline("tc_gemm", "fit_trsm", 28.0, 10, 1e13, 10, peaks),
+             bench.kernel_roofline("tc_gemm", "coulomb_syrk", 20.0, 10, 1e13, 10, peaks)]
+    roof = bench.dominant_cell(cells)
+    assert roof["kernel"] == "tc_gemm:fit_trsm"
+    assert roof["traffic"] == bench.NCU_DRAM_BYTES["tc_gemm:fit_trsm"]
+    assert bench.dominant_cell(cells[:1])["kernel"] == "df_gemm:points_chol"
+    assert bench.dominant_cell([]) is None

@@ -95,3 +95,36 @@ def test_mixed_ill_conditioned_points():
     ref = O.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x)
     assert g["rank"] == ref.rank
     assert rel_fro(g["y"][0], ref.y) < TOL_MIXED
+
+
+def test_mixed_smw_refinement():
+    """isdf_set_refinement: rounds of FP64 residual correction of the SMW
+    solve in the mixed single-frequency apply.  With 1 and 2 rounds eps^-1 X
+    stays within the mixed bound of the oracle and within 1e-6 of the
+    unrefined result (the Newton-Schulz K is already close to the exact
+    solve with the same D and G); 65 probe vectors cover two apply chunks.
+    Out-of-range round counts are refused."""
+    import torch
+    import paper_2403_12340_gb300 as pkg
+
+    s = small_system(24, 8, 40, n_mu=200, seed_index=61)
+    x = synth.probe_block(s.n_r, 65)
+    ref = O.isdf_smw_solve(s.phi, s.energies, s.n_v, s.mu_idx, s.n, s.cell, x)
+    ys = {}
+    with pkg.IsdfSmw(s.n, s.cell) as sol:
+        sol.fit(pkg.to_fortran(s.phi), s.n_v, s.n_c, s.mu_idx, prec=MIXED)
+        sol.polarizability(s.energies, [0.0])
+        sol.smw(0)
+        X = pkg.to_fortran(x)
+        for steps in (0, 1, 2):
+            pkg.isdf_set_refinement(sol.ctx, steps)
+            ys[steps] = sol.apply(X, 0).cpu().numpy()
+        for bad in (-1, 9):
+            with pytest.raises(pkg.IsdfError) as ei:
+                pkg.isdf_set_refinement(sol.ctx, bad)
+            assert ei.value.code == -1
+        torch.cuda.synchronize()
+    for steps, y in ys.items():
+        assert rel_fro(y, ref.y) < TOL_MIXED, steps
+    assert rel_fro(ys[1], ys[0]) < 1e-6
+    assert rel_fro(ys[2], ys[1]) < 1e-6
