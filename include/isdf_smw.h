@@ -439,13 +439,14 @@ ISDF_API int isdf_set_profiling(isdf_ctx* ctx, int on);
 
 /* Iterative refinement of the SMW solve in apply_eps_inv (mixed precision,
  * one frequency; Eq. epsilon_with_SMW, the capacitance solve of Algorithm 3
- * step 3): after T2 = K T1 with the tensor-core K, `steps` (0..8) rounds of
+ * step 3): after T2 = K T1 with the tensor-core K = -D X, X the
+ * Newton-Schulz (I + G D)^-1, `steps` (0..8) rounds of
  * R = -D (T1 + G T2) - T2 in FP64 (the residual of (I + D G) T2 = -D T1,
- * the capacitance equation multiplied by D) and T2 <- T2 - K (D^-1 R), with
- * the same approximate K and D^-1.  Each round takes the solve's error
- * relative to the exact solve with this D and G from about cond 2^-24 to
- * its square; the error against the FP64 path stays set by D, G and theta.
- * Other contexts (FP64, several frequencies) ignore it.  Default 0.
+ * the capacitance equation multiplied by D) and T2 <- T2 + X^T R.  Each
+ * round takes the solve's error relative to the exact solve with this D and
+ * G from about cond 2^-24 to its square; the error against the FP64 path
+ * stays set by D, G and theta.  Other contexts (FP64, several frequencies,
+ * a K from the factorisation route) ignore it.  Default 0.
  * Errors: ISDF_ERR_ARG (steps outside 0..8). */
 ISDF_API int isdf_set_refinement(isdf_ctx* ctx, int steps);
 /* Synchronises the device, then writes the summed milliseconds and the

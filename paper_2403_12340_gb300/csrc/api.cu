@@ -264,7 +264,7 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
                     &c->a_m4, &c->a_cp, &c->a_y, &c->a_gd, &c->a_e, &c->a_z1, &c->a_z2, &c->a_z3, &c->a_gpm, &c->a_gpp,
                     &c->a_m5, &c->a_m6, &c->bW1, &c->bT, &c->bU, &c->bQ,
                     &c->b_s1, &c->b_s2, &c->b_s3, &c->b_work, &c->b_cb, &c->b_dtmp, &c->b_cbd, &c->ctab,
-                    &c->m_pairs_t, &c->swf, &c->ew, &c->Rinv, &c->Dinv, &c->m_sd, &c->ns_bound, &c->ns_alpha, &c->ns_work,
+                    &c->m_pairs_t, &c->swf, &c->ew, &c->Xgd, &c->m_sd, &c->ns_bound, &c->ns_alpha, &c->ns_work,
                     &c->b_s4, &c->kappa_work, &c->inv_work, &c->m_ths, &c->cb_split, &c->b_split, &c->ref};
   for (DevBuf* b : bufs) release(*b);
   for (DevBuf& b : c->cx) release(b);
@@ -636,7 +636,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     CK(isdf::dev_malloc(&c->d_fail, n_omega * sizeof(int)));
     c->cap_fail = n_omega;
   }
-  c->dinv_ns = false;
+  c->xgd_ready = false;
   if (r > 0) {
     // G = theta^T V theta = S^T S with S the weighted half spectrum (Parseval)
     const long long lds = 2 * c->n_half;
@@ -653,34 +653,6 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     if (n_omega > 1) CK(ensure(c->b_cbd, (size_t)n_omega));
     if (c->prec == ISDF_PREC_MIXED) CK(ensure(c->cb_split, (size_t)64 * r * n_omega));
     if (n_nodes > 0) CK(ensure(c->ctab, (size_t)2 * n_nodes * (n_e + 1)));
-    // mixed, one frequency: D^-1 beside the Coulomb work
-    const bool dinv = c->prec == ISDF_PREC_MIXED && n_omega == 1;
-    c->dinv_ready = false;
-    // D^-1 by Newton-Schulz when the pair weights bound the spectrum of D
-    // tightly enough (no synchronisation: the bounds are host arithmetic)
-    isdf::NsPlan dplan;
-    double dwmin = 0.0, dwmax = 0.0;
-    if (dinv) {
-      isdf::pair_weight_bounds(energies, n_v, n_c, omega[0], &dwmin, &dwmax);
-      if (!(dwmin > 0.0) || !(dwmax >= dwmin) || !isdf::ns_plan((dwmax - dwmin) / (dwmax + dwmin), dplan))
-        dplan.beta.clear();
-    }
-    const bool dinv_ns = dinv && dplan.steps() > 0;
-    c->dinv_ns = dinv_ns;
-    if (dinv) {
-      const int rp = (r + 127) / 128 * 128, rk = (r + 63) / 64 * 64;
-      CK(ensure(c->Rinv, rr));
-      CK(ensure(c->Dinv, rr));
-      CK(ensure_bf16(c->m_sd, (size_t)3 * rp * rk));
-      if (dinv_ns) {
-        CK(ensure(c->Q, rr));
-        CK(ensure(c->R, rr));
-        CK(ensure_bf16(c->m_sa, (size_t)3 * rp * rk));
-        CK(ensure_bf16(c->m_sb, (size_t)3 * rp * rk));
-      }
-      int rc0 = chol_inverse_workspace(c, r);
-      if (rc0 != ISDF_OK) return rc0;
-    }
     if (c->prec == ISDF_PREC_MIXED) CK(ensure(c->swf, (npair * n_omega + 1) / 2));  // the weights in FP32
     CK(ensure(c->ew, (size_t)n_e + n_omega));
     // sqrt(-2 Omega(iw)^-1) for every pair and frequency, on the device from
@@ -750,29 +722,14 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
       int rc0 = fork_s2(c);
       if (rc0 != ISDF_OK) return rc0;
       PhaseScope ph(c, ISDF_PH_SMW, c->s2);
-      if (n_omega > 1 && c->prec == ISDF_PREC_MIXED) {
-        // all frequencies: smw_inverse_all inverts D(w) by Newton-Schulz (and
-        // factors it only if the spectral bounds do not allow that)
+      if (c->prec == ISDF_PREC_MIXED) {
+        // the capacitance K = -D (I + G D)^-1 comes from Newton-Schulz
+        // products (smw_inverse, smw_inverse_all), which factor D only when
+        // the spectral bounds do not allow that
         CK(cudaMemsetAsync(c->d_fail, 0xff, n_omega * sizeof(int), c->s2));
-        c->rw_ready = false;
       } else if (n_omega > 1) {  // all frequencies in one factorisation sequence
         CK(launch_cholesky_blocked_batched(c->D.p, r, (long long)rr, r, n_omega, 0.0, c->Rw.p, r, (long long)rr,
                                            c->b_cbd.p, c->d_fail, c->s2, split_panel(c, (size_t)64 * r * n_omega)));
-      } else if (dinv_ns) {
-        // D^-1 for the capacitance K = -(D^-1 + G)^-1 by Newton-Schulz on the
-        // tensor cores, beside the FFT of theta; D is left unfactored
-        CK(cudaMemsetAsync(c->d_fail, 0xff, sizeof(int), c->s2));
-        CK(isdf::mixed_ns_inverse(c, c->D.p, c->Dinv.p, 1.0, 2.0 / (dwmin + dwmax), dplan, c->s2));
-      } else if (dinv) {
-        // D = R R^T with R^-1 built on the third stream beside it, then
-        // D^-1 = R^-T R^-1 for the capacitance K = -(D^-1 + G)^-1
-        CK(cudaStreamWaitEvent(c->s3, c->ev_fork, 0));
-        CK(launch_cholesky_and_inverse(c->D.p, r, r, 0.0, c->Rw.p, r, c->Rinv.p, r, c->cb_work.p, c->d_fail,
-                                       c->inv_work.p, c->s2, c->s3, c->ev_chol.data(),
-                                       reinterpret_cast<float2*>(c->cb_split.p)));
-        CK(cudaEventRecord(c->ev_join3, c->s3));
-        CK(cudaStreamWaitEvent(c->s2, c->ev_join3, 0));
-        CK(isdf::mixed_dinv(c, c->s2));
       } else {
         rc0 = cholesky_blocked(c, c->D.p, r, r, 0.0, c->Rw.p, c->d_fail, c->s2);
         if (rc0 != ISDF_OK) return rc0;
@@ -780,10 +737,7 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
     }
     // G = theta^T V theta (main stream)
     if (c->prec == ISDF_PREC_MIXED) {
-      // the factorisations of D(w) on the second stream keep some SMs (the
-      // SYRK of G: 6 r^2 K); the Newton-Schulz route shares them instead
-      const bool factoring = !(n_omega > 1 || dinv_ns);
-      isdf::TcSmReserve keep(factoring ? fp64_sms_to_leave(r, 6.0 * r * (double)r * lds) : 0);
+      // nothing runs beside it on the second stream: all SMs
       CK(isdf::mixed_polar_G(c));
     } else {
       {
@@ -815,9 +769,8 @@ static int polar_impl(isdf_ctx* c, const double* energies, const double* omega, 
   c->energies.assign(energies, energies + n_e);
   c->k_ready.assign(n_omega, 0);
   c->polar_ready = true;
-  c->dinv_ready = c->prec == ISDF_PREC_MIXED && n_omega == 1 && r > 0;
-  // D(w) factored unless a Newton-Schulz route inverts it (smw_enqueue factors on demand)
-  c->rw_ready = !(c->prec == ISDF_PREC_MIXED && (n_omega > 1 || c->dinv_ns));
+  // D(w) factored by the FP64 path; the mixed path factors on demand (smw_enqueue)
+  c->rw_ready = c->prec != ISDF_PREC_MIXED;
   c->polar_whiten = c->pair_whiten;
   c->polar_nodes = n_nodes;
   return ISDF_OK;
@@ -857,48 +810,34 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
   long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
   int sp = split_for(tiles, std::max(r, 1), c->num_sms);
   PhaseScope ph(c, ISDF_PH_SMW);
-  if (c->prec == ISDF_PREC_MIXED && c->dinv_ready) {
-    // K = -(D^-1 + G)^-1 with D^-1 from build_polarizability
-    CK(launch_add(c->Dinv.p, c->G.p, c->T.p, (long long)rr, c->stream));
-    if (!isdf::tl_capture) {
-      // spectrum of A = D^-1 + G: at least 1 / max w (D <= max w, G >= 0),
-      // at most the Gershgorin bound; a condition number small enough for a
-      // few Newton-Schulz steps takes that route
-      double* nb = c->ns_bound.p;
-      CK(launch_row_abs_sum_max(c->T.p, r, r, nb, nb + 4, c->stream));
-      CK(launch_row_abs_sum_max(c->G.p, r, r, nb + 1, nb + 4, c->stream));
-      CK(launch_row_abs_sum_max(c->D.p + rr * k, r, r, nb + 2, nb + 4, c->stream));
-      double h[3] = {0.0, 0.0, 0.0};
-      CK(cudaMemcpyAsync(h, nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      CK(cudaStreamSynchronize(c->stream));
-      // rigorous bounds only (a step count planned from an estimate could
-      // leave a mode unconverged): lambda(A) <= min(Gershgorin(A), 1 / w_min
-      // + Gershgorin(G)) and >= 1 / min(w_max, Gershgorin(D))
-      double wmin = 0.0, wmax = 0.0;
-      isdf::pair_weight_bounds(c->energies.data(), c->n_v, c->n_c, c->omega[k], &wmin, &wmax);
-      const double hi = std::min(h[0], 1.0 / wmin + h[1]);
-      const double lo = 1.0 / std::min(wmax, h[2]);
-      isdf::NsPlan plan;
-      if (lo > 0.0 && hi >= lo && std::isfinite(hi) && isdf::ns_plan((hi - lo) / (hi + lo), plan)) {
-        CK(cudaMemsetAsync(failT, 0xff, sizeof(int), c->stream));  // no factorisation to fail
-        CK(isdf::mixed_ns_capacitance(c, Kk, 2.0 / (lo + hi), plan));
-        return ISDF_OK;
-      }
+  if (c->prec == ISDF_PREC_MIXED && !isdf::tl_capture) {
+    // K = -D (I + G D)^-1 by Newton-Schulz on the tensor cores when the
+    // spectral bounds allow a few steps (rigorous bounds only, one host
+    // read): I + G D has real eigenvalues in [1, 1 + |G| |D|], with |G| the
+    // Gershgorin bound of G and |D| the smaller of its Gershgorin bound and
+    // the largest pair weight
+    const double* Dk = c->D.p + rr * k;
+    double* nb = c->ns_bound.p;
+    CK(launch_row_abs_sum_max(c->G.p, r, r, nb, nb + 4, c->stream));
+    CK(launch_row_abs_sum_max(Dk, r, r, nb + 1, nb + 4, c->stream));
+    double h[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(h, nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double wmin = 0.0, wmax = 0.0;
+    isdf::pair_weight_bounds(c->energies.data(), c->n_v, c->n_c, c->omega[k], &wmin, &wmax);
+    const double kappa = isdf::ns_kappa(h[0], std::min(wmax, h[1]));
+    isdf::NsPlan plan;
+    if (std::isfinite(kappa) && isdf::ns_plan((kappa - 1.0) / (kappa + 1.0), plan)) {
+      CK(cudaMemsetAsync(failT, 0xff, sizeof(int), c->stream));  // no factorisation to fail
+      CK(isdf::mixed_ns_capacitance(c, Dk, Kk, 2.0 / (1.0 + kappa), plan));
+      c->xgd_ready = c->n_omega == 1;
+      return ISDF_OK;
     }
-    // else A = U U^T (U^-1 into Q on the second stream, block row by block
-    // row, beside the factorisation), K = -U^-T U^-1
-    CK(cudaEventRecord(c->ev_fork, c->stream));
-    CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
-    CK(launch_cholesky_and_inverse(c->T.p, r, r, 0.0, c->W1.p, r, c->Q.p, r, c->cb_work.p, failT, c->inv_work.p,
-                                   c->stream, c->s2, c->ev_chol.data(), reinterpret_cast<float2*>(c->cb_split.p)));
-    CK(cudaEventRecord(c->ev_join, c->s2));
-    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-    CK(isdf::mixed_k_from_uinv(c, Kk));
-    return ISDF_OK;
   }
-  // D = R R^T: factored by build_polarizability on the second stream, or
-  // here (a mixed context whose polarizability holds several frequencies
-  // leaves D(w) unfactored for the Newton-Schulz route of smw_inverse_all)
+  c->xgd_ready = false;
+  // D = R R^T: factored by build_polarizability on the second stream (FP64
+  // path), or here (the mixed path leaves D(w) unfactored for its
+  // Newton-Schulz route)
   if (!c->rw_ready) {
     int rc = cholesky_blocked(c, c->D.p + rr * k, r, r, 0.0, c->Rw.p + rr * k, c->d_fail + k, c->stream);
     if (rc != ISDF_OK) return rc;
@@ -946,8 +885,11 @@ static int smw_workspace(isdf_ctx* c) {
   const size_t rr = (size_t)r * r;
   long long tiles = (long long)((r + 63) / 64) * ((r + 63) / 64 + 1) / 2;
   int sp = split_for(tiles, std::max(r, 1), c->num_sms);
-  if (c->R.cap < rr || c->T.cap < rr || c->W1.cap < rr || c->Q.cap < rr || c->partial.cap < sp * rr)
+  const bool mixed = c->prec == ISDF_PREC_MIXED;
+  if (c->R.cap < rr || c->T.cap < rr || c->W1.cap < rr || c->Q.cap < rr || c->partial.cap < sp * rr ||
+      (mixed && c->Xgd.cap < rr))
     SYNC(c->stream);  // a resize frees memory that earlier work may read
+  if (mixed) CK(ensure(c->Xgd, rr));
   CK(ensure(c->R, rr));
   CK(ensure(c->T, rr));
   CK(ensure(c->W1, rr));
@@ -1103,9 +1045,9 @@ extern "C" int apply_eps_inv(isdf_ctx* c, int k, const double* X, int n_rhs, dou
   CK(ensure(c->tmp3, (size_t)nr * nc0));
   CK(ensure(c->spec, (size_t)lds * nc0));
   CK(ensure(c->partial, std::max<size_t>((size_t)sp0 * r * nc0, 1)));
-  if (c->prec == ISDF_PREC_MIXED && c->refine > 0 && c->dinv_ready) {
-    if (c->ref.cap < (size_t)3 * r * nc0) CK(cudaStreamSynchronize(c->stream));
-    CK(ensure(c->ref, std::max<size_t>((size_t)3 * r * nc0, 1)));
+  if (c->prec == ISDF_PREC_MIXED && c->refine > 0 && c->xgd_ready) {
+    if (c->ref.cap < (size_t)2 * r * nc0) CK(cudaStreamSynchronize(c->stream));
+    CK(ensure(c->ref, std::max<size_t>((size_t)2 * r * nc0, 1)));
   }
   PhaseScope ph(c, ISDF_PH_APPLY);
   for (int c0 = 0; c0 < n_rhs; c0 += chunk) {

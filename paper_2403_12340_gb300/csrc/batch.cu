@@ -301,7 +301,7 @@ int prepare_grouped_smw(isdf_batch* b, int n_omega) {
   if (b->prec != ISDF_PREC_MIXED || n_omega < 2 || b->sys.size() > 32) return ISDF_OK;
   for (auto& s : b->sys) {
     isdf_ctx* c = s.ctx;
-    if (c->rank <= 0 || c->ns_nw != n_omega || c->ns_e0_d < 0.0 || c->ns_e0_a < 0.0) return ISDF_OK;
+    if (c->rank <= 0 || c->ns_nw != n_omega || c->ns_e0 < 0.0) return ISDF_OK;
   }
   const size_t ws = (isdf::tc_grouped_workspace_bytes((int)b->sys.size()) + 255) / 256 * 256;
   const size_t need = ws * (size_t)isdf::ns_stage_slots();

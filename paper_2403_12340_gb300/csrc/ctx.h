@@ -107,20 +107,20 @@ struct isdf_ctx {
   DevBuf m_pairs_t, swf;  // pair-space whitening: transposed pair slices; the pair weights in FP32 (mixed path)
   DevBuf ew;                     // energies and frequencies of the last polarizability, on the device
   // mixed path, one frequency: R^-1 of D = R R^T, D^-1 = R^-T R^-1 and the
-  // BF16 slices of R^-1, built beside the Coulomb work of build_polarizability
-  DevBuf Rinv, Dinv, m_sd, ns_bound;  // ns_bound: Gershgorin bounds (and their workspace)
-  // all frequencies by Newton-Schulz (mixed_smw_batched_ns): step counts and
+  // Xgd: (I + G D)^-1 of the single-frequency capacitance (kept for the
+  // refinement of the apply); ns_bound: Gershgorin bounds and their workspace
+  DevBuf Xgd, m_sd, ns_bound;
+  // all frequencies by Newton-Schulz (mixed_smw_batched_ns): the schedule and
   // per-frequency start scales of the last eager call (a captured call
   // replays them), the grouped-GEMM descriptor slots and their host copies
-  double ns_e0_d = -1.0, ns_e0_a = -1.0;  // the largest e0 over the frequencies (see NsPlan)
+  double ns_e0 = -1.0;  // the largest e0 over the frequencies (see NsPlan)
   int ns_nw = 0;
   bool rw_ready = false;  // c->Rw holds the Cholesky factors of every D(w)
   DevBuf ns_alpha, ns_work, b_s4;
   std::vector<std::vector<unsigned char>> ns_staged;
-  bool dinv_ready = false;
-  bool dinv_ns = false;  // the last polarizability inverted D by Newton-Schulz (D left unfactored)
+  bool xgd_ready = false;  // K of the single frequency came from Newton-Schulz: Xgd holds (I + G D)^-1
   int refine = 0;        // refinement rounds of the SMW solve in the mixed apply (isdf_set_refinement)
-  DevBuf ref;            // their scratch: three r x 64 blocks
+  DevBuf ref;            // their scratch: two r x 64 blocks
   std::vector<double> ew_host;   // their host copy (the source of the asynchronous upload)
   bool pair_whiten = false;  // mixed path: whiten D in pair space (chosen from the fit's factor)
   int pair_mode = 0;         // the precision argument of the last fit
@@ -215,19 +215,15 @@ cudaError_t mixed_polar_G(isdf_ctx* c);
 cudaError_t mixed_smw_products_T(isdf_ctx* c);
 cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk, bool uinv_ready);
 cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, double* Y, int nc);
-// D^-1 = R^-T R^-1 from c->Rinv into c->Dinv, on stream st
-cudaError_t mixed_dinv(isdf_ctx* c, cudaStream_t st);
-// K = -U^-T U^-1 from U^-1 in c->Q into Kk
-cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk);
-// K(w_k) for every frequency by Newton-Schulz (K = -(D^-1 + G)^-1 with
-// D(w)^-1 itself by Newton-Schulz), each step one grouped persistent GEMM
-// over every (frequency, tile); *used = false if the spectral bounds ask for
-// too many steps (the caller then factors).
+// K(w_k) = -D(w_k) (I + G D(w_k))^-1 for every frequency by Newton-Schulz,
+// each product one grouped persistent GEMM over every (frequency, tile);
+// *used = false if the spectral bounds ask for too many steps (the caller
+// then factors).
 cudaError_t mixed_smw_batched_ns(isdf_ctx* c, int nw, int* fail_T, bool* used);
 // The same for n systems at once (each after an eager smw_inverse_all that
-// took the Newton-Schulz route), one grouped launch per step over every
-// (system, frequency, tile), on stream st; work holds 4 max_steps slots of
-// ws bytes (tc_grouped_workspace_bytes(n), rounded up to 256).
+// took the Newton-Schulz route), one grouped launch per product over every
+// (system, frequency, tile), on stream st; work holds ns_stage_slots()
+// slots of ws bytes (tc_grouped_workspace_bytes(n), rounded up to 256).
 int ns_stage_slots();  // descriptor slots of ns_stage_grouped's workspace
 cudaError_t ns_stage_grouped(isdf_ctx** cs, int n, cudaStream_t st, void* work, size_t ws,
                              std::vector<std::vector<unsigned char>>& staged);
@@ -244,13 +240,14 @@ struct NsPlan {
 // e0 = (hi - lo) / (hi + lo) for a spectrum of M within [lo, hi]; false if
 // the iteration needs more than 12 steps.
 bool ns_plan(double e0, NsPlan& p);
-// out = sign M^-1 for a symmetric positive definite r x r M (ld r) by the
-// Newton-Schulz steps of `plan` from X = alpha I, on stream st (scratch:
-// c->Q, c->R and the slices c->m_sd, m_sa, m_sb)
-cudaError_t mixed_ns_inverse(isdf_ctx* c, const double* M, double* out, double sign, double alpha, const NsPlan& plan,
-                             cudaStream_t st);
-// K = -(c->T)^-1 on the main stream
-cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, const NsPlan& plan);
+// K = -D (I + G D)^-1 for the D at Dk (r x r, ld r) and c->G, into Kk, on
+// the main stream, by the Newton-Schulz steps of `plan` for (I + G D)^-1
+// from X = alpha I (scratch: c->T, c->R, c->Xgd, which keeps X, and the
+// slices c->m_sd, m_sa, m_sb)
+cudaError_t mixed_ns_capacitance(isdf_ctx* c, const double* Dk, double* Kk, double alpha, const NsPlan& plan);
+// Upper end of the spectrum of I + G D, 1 + |G| |D| from bounds of the two
+// spectra (its lower end is 1: G D has the eigenvalues of D^1/2 G D^1/2 >= 0)
+double ns_kappa(double g_bound, double d_bound);
 // Range [wmin, wmax] of the pair weights w = 2 |dE| / (dE^2 + w^2) over the
 // valence-conduction pairs, from the band edges (the weight is unimodal in
 // |dE|, peaking at |dE| = w): in the whitened basis the spectrum of D(w)

@@ -378,26 +378,6 @@ cudaError_t mixed_smw_products_K(isdf_ctx* c, double* Kk, bool uinv_ready) {
                      max_split, c->num_sms, c->d_status, st);
 }
 
-// D^-1 = R^-T R^-1 (the SMW capacitance in the form K = -(D^-1 + G)^-1):
-// rows of the slice matrix are the columns of R^-1, one tensor-core SYRK.
-cudaError_t mixed_dinv(isdf_ctx* c, cudaStream_t st) {
-  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
-  MK(slices_rm(c->m_sd, c->Rinv.p, r, r, r, rp, rk, st));
-  MK(tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sd, rp, rk), r, r, 1.0, 0.0, c->Dinv.p, r, true, false, nullptr, 1,
-                 c->num_sms, c->d_status, st));
-  return launch_symmetrize(c->Dinv.p, r, r, st);
-}
-
-// K = -A^-1 = -U^-T U^-1 for A = D^-1 + G = U U^T, U^-1 in c->Q.
-cudaError_t mixed_k_from_uinv(isdf_ctx* c, double* Kk) {
-  cudaStream_t st = c->stream;
-  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
-  MK(slices_rm(c->m_sa, c->Q.p, r, r, r, rp, rk, st));
-  MK(tc_gemm_f64(op(c->m_sa, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 0.0, Kk, r, true, false, nullptr, 1,
-                 c->num_sms, c->d_status, st));
-  return launch_symmetrize(Kk, r, r, st);
-}
-
 // The Newton-Schulz schedule for a spectrum of alpha M within [1 - e0,
 // 1 + e0] (alpha = 2 / (lo + hi), e0 = (hi - lo) / (hi + lo)).  A step maps
 // each eigenvalue t of M X to t (2 - t), so [1 - e, 1 + e] goes to
@@ -428,53 +408,6 @@ bool ns_plan(double e0, NsPlan& p) {
   return true;
 }
 
-// K = -A^-1 by Newton-Schulz iteration on the tensor cores, in the form
-// X_{k+1} = beta_k (2 X_k - X_k (A X_k)) from X_0 = alpha I (schedule of
-// ns_plan).  The error contracts quadratically down to the FP32-grade
-// rounding of the products; in the whitened basis A = D^-1 + G has a
-// spectrum within [1 / max w, 1 / min w + |G|] (w the pair weights), a
-// condition number of a few, so a handful of steps reach that level.  The
-// form matters under rounding: 2 X - X A X is symmetric for every symmetric
-// X, so its lower triangle, mirrored, is exact up to rounding, and a
-// perturbation P of X enters the next iterate as 2 P - P A X - X A P = 0 to
-// first order at X = A^-1 whatever P is.  X (2 I - A X) with a symmetrised
-// 2 I - A X instead maps P to about (P - A^-1 P A) / 2, whose modes grow by
-// up to cond(A) / 4 per step once the iteration has converged.
-// Per step: Z = A X (full), then X <- beta (2 X - X Z) (lower triangle, in
-// place: the tile epilogue reads and writes each lower element once, and
-// its mirrored stores touch only the upper triangle, which nothing reads).
-cudaError_t mixed_ns_inverse(isdf_ctx* c, const double* M, double* out, double sign, double alpha, const NsPlan& plan,
-                             cudaStream_t st) {
-  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
-  const size_t rr = (size_t)r * r;
-  double* X = c->Q.p;
-  double* Z = c->R.p;
-  MK(slices_cm(c->m_sd, M, r, r, r, rp, rk, st));  // M, once
-  MK(cudaMemsetAsync(X, 0, rr * sizeof(double), st));
-  MK(launch_add_identity(X, r, r, alpha, st));
-  for (int it = 0; it < plan.steps(); ++it) {
-    const bool last = it + 1 == plan.steps();
-    const int s = plan.s[it];
-    const double b = plan.beta[it], f = last ? sign * b : b;
-    MK(slices_cm(c->m_sa, X, r, r, r, rp, rk, st));  // rows of X (= its columns)
-    MK(tc_gemm_f64(op_s(c->m_sd, rp, rk, s), op_s(c->m_sa, rp, rk, s), r, r, 1.0, 0.0, Z, r, false, false, nullptr, 1,
-                   c->num_sms, c->d_status, st));  // Z = M X
-    MK(slices_rm(c->m_sb, Z, r, r, r, rp, rk, st));  // rows: the columns of Z
-    double* dst = X;
-    if (last) {  // out = sign beta (2 X - X Z)
-      MK(cudaMemcpyAsync(out, X, rr * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      dst = out;
-    }
-    MK(tc_gemm_f64(op_s(c->m_sa, rp, rk, s), op_s(c->m_sb, rp, rk, s), r, r, -f, 2.0 * f, dst, r, true, false, nullptr,
-                   1, c->num_sms, c->d_status, st));
-  }
-  return cudaSuccess;
-}
-
-cudaError_t mixed_ns_capacitance(isdf_ctx* c, double* Kk, double alpha, const NsPlan& plan) {
-  return mixed_ns_inverse(c, c->T.p, Kk, -1.0, alpha, plan, c->stream);
-}
-
 void pair_weight_bounds(const double* energies, int n_v, int n_c, double w, double* wmin, double* wmax) {
   double emax_v = energies[0], emin_v = energies[0], emin_c = energies[n_v], emax_c = energies[n_v];
   for (int i = 0; i < n_v; ++i) {
@@ -492,53 +425,144 @@ void pair_weight_bounds(const double* energies, int n_v, int n_c, double w, doub
   if (w >= gap && w <= width) *wmax = std::max(*wmax, f(w));
 }
 
+double ns_kappa(double g_bound, double d_bound) { return 1.0 + std::max(0.0, g_bound) * std::max(0.0, d_bound); }
+
+namespace {
+
+// Grouped-GEMM descriptor slots of the batched capacitance: 0 the products
+// G D(w), 1 the results -D(w) X(w), 2 + 2 step + kind the iteration (kind 0
+// Z = M X, kind 1 X <- beta (2 X - X Z)); each has its own scale, slice
+// count and operands, so its own descriptors.
+inline int ns_slot(int step, int kind) { return 2 + 2 * step + kind; }
+constexpr int kNsSlots = 2 + 2 * 12;
+
+}  // namespace
+
+// K = -D (I + G D)^-1 = -(D^-1 + G)^-1 (reading 20) on the tensor cores:
+// M = I + G D, X -> M^-1 by Newton-Schulz X <- beta_k (2 X - X (M X)) from
+// X = alpha I (schedule of ns_plan), then K = -D X.  G D has the spectrum of
+// D^1/2 G D^1/2, so M has real eigenvalues in [1, kappa], kappa = 1 +
+// |G| |D| (the bounds of ns_kappa), and alpha = 2 / (1 + kappa).  M is not
+// symmetric, and the form is what keeps the iteration stable under
+// rounding: a perturbation P of X enters the next iterate as 2 P - P M X -
+// X M P, which vanishes at X = M^-1 whatever P is, where X (2 I - M X)
+// with a rounded or symmetrised middle factor lets the modes of
+// P - M^-1 P M grow once the iteration has converged.  Every product is a
+// full tensor-core GEMM; K, symmetric in exact arithmetic, is the lower
+// triangle of -D X, mirrored.  X stays in c->Xgd for the refinement of the
+// apply.
+cudaError_t mixed_ns_capacitance(isdf_ctx* c, const double* Dk, double* Kk, double alpha, const NsPlan& plan) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const size_t rr = (size_t)r * r;
+  double* M = c->T.p;
+  double* X = c->Xgd.p;
+  double* Z = c->R.p;
+  MK(cudaMemsetAsync(M, 0, rr * sizeof(double), st));
+  MK(launch_add_identity(M, r, r, 1.0, st));
+  MK(slices_cm(c->m_sd, c->G.p, r, r, r, rp, rk, st));  // rows of G
+  MK(slices_cm(c->m_sa, Dk, r, r, r, rp, rk, st));      // rows of D (= its columns)
+  MK(tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sa, rp, rk), r, r, 1.0, 1.0, M, r, false, false, nullptr, 1,
+                 c->num_sms, c->d_status, st));  // M = I + G D
+  MK(slices_cm(c->m_sd, M, r, r, r, rp, rk, st));  // rows of M, once
+  MK(cudaMemsetAsync(X, 0, rr * sizeof(double), st));
+  MK(launch_add_identity(X, r, r, alpha, st));
+  for (int it = 0; it < plan.steps(); ++it) {
+    const int s = plan.s[it];
+    const double b = plan.beta[it];
+    MK(slices_rm(c->m_sa, X, r, r, r, rp, rk, st));  // columns of X
+    MK(tc_gemm_f64(op_s(c->m_sd, rp, rk, s), op_s(c->m_sa, rp, rk, s), r, r, 1.0, 0.0, Z, r, false, false, nullptr, 1,
+                   c->num_sms, c->d_status, st));  // Z = M X
+    MK(slices_cm(c->m_sa, X, r, r, r, rp, rk, st));  // rows of X
+    MK(slices_rm(c->m_sb, Z, r, r, r, rp, rk, st));  // columns of Z
+    MK(tc_gemm_f64(op_s(c->m_sa, rp, rk, s), op_s(c->m_sb, rp, rk, s), r, r, -b, 2.0 * b, X, r, false, false, nullptr,
+                   1, c->num_sms, c->d_status, st));  // X <- beta (2 X - X Z), in place
+  }
+  MK(slices_cm(c->m_sd, Dk, r, r, r, rp, rk, st));  // rows of D
+  MK(slices_rm(c->m_sa, X, r, r, r, rp, rk, st));   // columns of X
+  return tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sa, rp, rk), r, r, -1.0, 0.0, Kk, r, true, false, nullptr, 1,
+                     c->num_sms, c->d_status, st);  // K = -D X
+}
+
 namespace {
 
 void pair_weight_range(const isdf_ctx* c, int k, double* wmin, double* wmax) {
   pair_weight_bounds(c->energies.data(), c->n_v, c->n_c, c->omega[k], wmin, wmax);
 }
 
-// Grouped-GEMM descriptor slot of (stage, step, kind): kind 0 the full
-// Z = M X, kind 1 the lower-triangle update (each step has its own scale and
-// slice count, so its own descriptors).
-inline int ns_slot(int stage, int step, int kind) { return (stage * 12 + step) * 2 + kind; }
-constexpr int kNsSlots = 2 * 12 * 2;
-
-// nw symmetric positive definite r x r matrices M (stride r^2): out = sign M^-1
-// by the Newton-Schulz steps of `plan`, X <- beta (2 X - X (M X)) from
-// X = alpha[z] I (the stable form of mixed_ns_capacitance).  Each product
-// is one grouped persistent GEMM over every (matrix, tile).
-cudaError_t ns_batched(isdf_ctx* c, const double* M, double* out, double sign, const double* alpha,
-                       const NsPlan& plan, int nw, int stage) {
-  cudaStream_t st = c->stream;
-  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), sr = NSL * rp;
-  const long long rr = (long long)r * r;
-  const size_t ws = (tc_grouped_workspace_bytes(1) + 255) / 256 * 256;
-  unsigned char* wk = reinterpret_cast<unsigned char*>(c->ns_work.p);
-  double* X = c->bW1.p;
-  double* Z = c->bT.p;
-  MK(slices_cm_b(c->b_s1, M, r, rr, r, r, rp, rk, nw, st));
-  MK(launch_scaled_identity(X, r, nw, alpha, st));
+// The capacitance of every frequency of one context (or of several, ncs >
+// 1) by the steps of `plan`: each product of every context, frequency and
+// tile is one work unit of a single grouped persistent launch.  Per
+// context: X(w) in bW1, M(w) in bT, Z(w) in bQ; slices in b_s1, b_s2, b_s4;
+// start scales in ns_alpha.  Descriptor slot q of the launch lives at
+// work + q * ws, its host copy in staged[q].
+cudaError_t ns_capacitance_grouped(isdf_ctx** cs, int ncs, const NsPlan& plan, cudaStream_t st, unsigned char* work,
+                                   size_t ws, std::vector<std::vector<unsigned char>>& staged) {
+  std::vector<TcGroupProblem> pr;
+  isdf_ctx* c0 = cs[0];
+  auto launch = [&](int slot) -> cudaError_t {
+    return tc_gemm_f64_grouped(pr.data(), (int)pr.size(), work + slot * ws, ws, staged[slot], c0->num_sms,
+                               c0->d_status, st);
+  };
+  // M(w) = I + G D(w)
+  pr.clear();
+  for (int i = 0; i < ncs; ++i) {
+    isdf_ctx* c = cs[i];
+    const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
+    const long long rr = (long long)r * r;
+    MK(cudaMemsetAsync(c->bT.p, 0, (size_t)rr * nw * sizeof(double), st));
+    MK(launch_add_identity(c->bT.p, r, r, 1.0, st, nw, rr));
+    MK(slices_cm_b(c->b_s1, c->G.p, r, rr, r, r, rp, rk, 1, st));  // rows of G, shared by every frequency
+    MK(slices_cm_b(c->b_s2, c->D.p, r, rr, r, r, rp, rk, nw, st));
+    pr.push_back(TcGroupProblem{op(c->b_s1, rp, rk), op(c->b_s2, rp, rk), r, r, 1.0, 1.0, c->bT.p, r, false,
+                                TcBatch{nw, 0, sr, rr}});
+  }
+  MK(launch(0));
+  for (int i = 0; i < ncs; ++i) {
+    isdf_ctx* c = cs[i];
+    const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega;
+    const long long rr = (long long)r * r;
+    MK(slices_cm_b(c->b_s1, c->bT.p, r, rr, r, r, rp, rk, nw, st));  // rows of M(w), once
+    MK(launch_scaled_identity(c->bW1.p, r, nw, c->ns_alpha.p, st));
+  }
   for (int it = 0; it < plan.steps(); ++it) {
-    const bool last = it + 1 == plan.steps();
     const int s = plan.s[it];
     const double b = plan.beta[it];
-    MK(slices_cm_b(c->b_s2, X, r, rr, r, r, rp, rk, nw, st));
-    TcGroupProblem pz{op_s(c->b_s1, rp, rk, s), op_s(c->b_s2, rp, rk, s), r, r, 1.0, 0.0, Z, r, false,
-                      TcBatch{nw, sr, sr, rr}};
-    const int sz = ns_slot(stage, it, 0), sx = ns_slot(stage, it, 1);
-    MK(tc_gemm_f64_grouped(&pz, 1, wk + sz * ws, ws, c->ns_staged[sz], c->num_sms, c->d_status, st));
-    MK(slices_rm_b(c->b_s4, Z, r, rr, r, r, rp, rk, nw, st));
-    double* dst = X;
-    if (last) {
-      MK(cudaMemcpyAsync(out, X, (size_t)rr * nw * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      dst = out;
+    pr.clear();
+    for (int i = 0; i < ncs; ++i) {
+      isdf_ctx* c = cs[i];
+      const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
+      const long long rr = (long long)r * r;
+      MK(slices_rm_b(c->b_s2, c->bW1.p, r, rr, r, r, rp, rk, nw, st));  // columns of X
+      pr.push_back(TcGroupProblem{op_s(c->b_s1, rp, rk, s), op_s(c->b_s2, rp, rk, s), r, r, 1.0, 0.0, c->bQ.p, r,
+                                  false, TcBatch{nw, sr, sr, rr}});
     }
-    const double f = last ? sign * b : b;
-    TcGroupProblem px{op_s(c->b_s2, rp, rk, s), op_s(c->b_s4, rp, rk, s), r, r, -f, 2.0 * f, dst, r, true,
-                      TcBatch{nw, sr, sr, rr}};
-    MK(tc_gemm_f64_grouped(&px, 1, wk + sx * ws, ws, c->ns_staged[sx], c->num_sms, c->d_status, st));
+    MK(launch(ns_slot(it, 0)));  // Z = M X
+    pr.clear();
+    for (int i = 0; i < ncs; ++i) {
+      isdf_ctx* c = cs[i];
+      const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
+      const long long rr = (long long)r * r;
+      MK(slices_cm_b(c->b_s2, c->bW1.p, r, rr, r, r, rp, rk, nw, st));  // rows of X
+      MK(slices_rm_b(c->b_s4, c->bQ.p, r, rr, r, r, rp, rk, nw, st));   // columns of Z
+      pr.push_back(TcGroupProblem{op_s(c->b_s2, rp, rk, s), op_s(c->b_s4, rp, rk, s), r, r, -b, 2.0 * b, c->bW1.p, r,
+                                  false, TcBatch{nw, sr, sr, rr}});
+    }
+    MK(launch(ns_slot(it, 1)));  // X <- beta (2 X - X Z), in place
   }
+  // K(w) = -D(w) X(w), the lower triangle mirrored
+  pr.clear();
+  for (int i = 0; i < ncs; ++i) {
+    isdf_ctx* c = cs[i];
+    const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
+    const long long rr = (long long)r * r;
+    MK(slices_cm_b(c->b_s1, c->D.p, r, rr, r, r, rp, rk, nw, st));
+    MK(slices_rm_b(c->b_s2, c->bW1.p, r, rr, r, r, rp, rk, nw, st));
+    pr.push_back(TcGroupProblem{op(c->b_s1, rp, rk), op(c->b_s2, rp, rk), r, r, -1.0, 0.0, c->K.p, r, true,
+                                TcBatch{nw, sr, sr, rr}});
+  }
+  MK(launch(1));
+  for (int i = 0; i < ncs; ++i) MK(cudaMemsetAsync(cs[i]->b_fail, 0xff, cs[i]->n_omega * sizeof(int), st));
   return cudaSuccess;
 }
 
@@ -560,133 +584,74 @@ cudaError_t mixed_smw_batched_ns(isdf_ctx* c, int nw, int* fail_T, bool* used) {
     MK(ensure_bf16(c->b_s4, per_sq * nw));
     MK(ensure(c->ns_work, (kNsSlots * ws + 7) / 8));
     if (c->ns_staged.size() < (size_t)kNsSlots) c->ns_staged.resize(kNsSlots);
-    MK(ensure(c->ns_alpha, 2 * (size_t)nw));
+    MK(ensure(c->ns_alpha, (size_t)nw));
     const size_t bw = row_abs_sum_work(r, nw);
-    MK(ensure(c->ns_bound, bw + 3 * (size_t)nw + 8));
+    MK(ensure(c->ns_bound, bw + (size_t)nw + 8));
     // spectra: rigorous bounds only (Gershgorin for every D(w) and for G,
     // the pair-weight range): a schedule planned from an estimate could
     // leave a mode unconverged
     double* nb = c->ns_bound.p;
-    double* lam = nb + bw;  // [unused | nw Gershgorin of D | Gershgorin of G], after the workspace
-    MK(launch_row_abs_sum_max(c->D.p, r, r, lam + nw, nb, st, nw, (long long)rr));
-    MK(launch_row_abs_sum_max(c->G.p, r, r, lam + 2 * nw, nb, st));
-    std::vector<double> h(2 * (size_t)nw + 1);
+    double* lam = nb + bw;  // [nw Gershgorin of D | Gershgorin of G]
+    MK(launch_row_abs_sum_max(c->D.p, r, r, lam, nb, st, nw, (long long)rr));
+    MK(launch_row_abs_sum_max(c->G.p, r, r, lam + nw, nb, st));
+    std::vector<double> h((size_t)nw + 1);
     MK(cudaMemcpyAsync(h.data(), lam, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     MK(cudaStreamSynchronize(st));
-    std::vector<double> alpha(2 * (size_t)nw);
-    double e_d = 0.0, e_a = 0.0;
+    std::vector<double> alpha((size_t)nw);
+    double e0 = 0.0;
     for (int k = 0; k < nw; ++k) {
       double wmin = 0.0, wmax = 0.0;
       pair_weight_range(c, k, &wmin, &wmax);
-      // D: spectrum within [w_min, min(w_max, Gershgorin)]
-      const double hd = std::min(wmax, h[nw + k]), ld = wmin;
-      // A = D^-1 + G: at least 1 / lambda_max(D), at most 1 / w_min + lambda_max(G)
-      const double la = 1.0 / hd, ha = 1.0 / wmin + h[2 * nw];
-      if (!(ld > 0.0) || !(hd >= ld) || !std::isfinite(ha)) return cudaSuccess;  // not used: the caller factors
-      alpha[k] = 2.0 / (ld + hd);
-      alpha[nw + k] = 2.0 / (la + ha);
+      const double kappa = ns_kappa(h[nw], std::min(wmax, h[k]));
+      if (!std::isfinite(kappa)) return cudaSuccess;  // not used: the caller factors
+      alpha[k] = 2.0 / (1.0 + kappa);
       // one schedule for every frequency: the largest e0 (a scale sequence
       // valid for e0 keeps every smaller e0 within the same bounds)
-      e_d = std::max(e_d, (hd - ld) / (hd + ld));
-      e_a = std::max(e_a, (ha - la) / (ha + la));
+      e0 = std::max(e0, (kappa - 1.0) / (kappa + 1.0));
     }
-    NsPlan pd, pa;
-    if (!ns_plan(e_d, pd) || !ns_plan(e_a, pa)) return cudaSuccess;  // too many steps: the caller factors
+    NsPlan plan;
+    if (!ns_plan(e0, plan)) return cudaSuccess;  // too many steps: the caller factors
     MK(cudaMemcpyAsync(c->ns_alpha.p, alpha.data(), alpha.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     MK(cudaStreamSynchronize(st));
-    c->ns_e0_d = e_d;
-    c->ns_e0_a = e_a;
+    c->ns_e0 = e0;
     c->ns_nw = nw;
-  } else if (c->ns_nw != nw || c->ns_e0_d < 0.0) {
+  } else if (c->ns_nw != nw || c->ns_e0 < 0.0) {
     return cudaErrorStreamCaptureUnsupported;  // a captured call needs the eager call's plan
   }
-  NsPlan pd, pa;
-  ns_plan(c->ns_e0_d, pd);
-  ns_plan(c->ns_e0_a, pa);
-  // D(w)^-1, then A(w) = D(w)^-1 + G, then K(w) = -A(w)^-1
-  MK(ns_batched(c, c->D.p, c->bQ.p, 1.0, c->ns_alpha.p, pd, nw, 0));
-  MK(launch_add(c->bQ.p, c->G.p, c->bQ.p, (long long)rr, st, nw, (long long)rr, 0));
-  MK(ns_batched(c, c->bQ.p, c->K.p, -1.0, c->ns_alpha.p + nw, pa, nw, 1));
-  MK(cudaMemsetAsync(fail_T, 0xff, nw * sizeof(int), st));  // nothing to fail
+  NsPlan plan;
+  ns_plan(c->ns_e0, plan);
+  MK(ns_capacitance_grouped(&c, 1, plan, st, reinterpret_cast<unsigned char*>(c->ns_work.p), ws, c->ns_staged));
+  (void)fail_T;  // set to "nothing failed" with the context's flags
   *used = true;
   return cudaSuccess;
 }
 
 // The capacitance stage of smw_inverse_all for several systems at once:
 // every Newton-Schulz product of every system (all frequencies, all tiles)
-// in one grouped persistent launch per step.  Each context must hold the
+// in one grouped persistent launch per product.  Each context must hold the
 // plan of an earlier eager smw_inverse_all on the same polarizability (the
-// start scales on the device, the largest e0 of each stage); every system
-// follows the schedule of the largest e0 over the systems (valid for all
-// of them, and one slice count per launch, as the grouped kernel needs).
-// Descriptor slot (stage, step, kind) lives at work + slot * ws with its
-// host copy in staged[slot]; ns_stage_slots() slots in all.
+// start scales on the device, the largest e0); every system follows the
+// schedule of the largest e0 over the systems (valid for all of them, and
+// one slice count per launch, as the grouped kernel needs).  Descriptor
+// slot q lives at work + q * ws with its host copy in staged[q];
+// ns_stage_slots() slots in all.
 int ns_stage_slots() { return kNsSlots; }
 
 cudaError_t ns_stage_grouped(isdf_ctx** cs, int n, cudaStream_t st, void* work, size_t ws,
                              std::vector<std::vector<unsigned char>>& staged) {
   if (n <= 0) return cudaSuccess;
   if (n > 32) return cudaErrorInvalidValue;
-  double e_d = 0.0, e_a = 0.0;
+  double e0 = 0.0;
   for (int i = 0; i < n; ++i) {
     isdf_ctx* c = cs[i];
-    if (c->prec != ISDF_PREC_MIXED || c->rank <= 0 || c->ns_nw != c->n_omega || c->ns_e0_d < 0.0 || c->ns_e0_a < 0.0)
+    if (c->prec != ISDF_PREC_MIXED || c->rank <= 0 || c->ns_nw != c->n_omega || c->ns_e0 < 0.0)
       return cudaErrorInvalidValue;
-    e_d = std::max(e_d, c->ns_e0_d);
-    e_a = std::max(e_a, c->ns_e0_a);
+    e0 = std::max(e0, c->ns_e0);
   }
-  NsPlan plan[2];
-  if (!ns_plan(e_d, plan[0]) || !ns_plan(e_a, plan[1])) return cudaErrorInvalidValue;
+  NsPlan plan;
+  if (!ns_plan(e0, plan)) return cudaErrorInvalidValue;
   if (staged.size() < (size_t)kNsSlots) staged.resize(kNsSlots);
-  unsigned char* w = static_cast<unsigned char*>(work);
-  std::vector<TcGroupProblem> pz, px;
-  for (int stage = 0; stage < 2; ++stage) {
-    const NsPlan& pl = plan[stage];
-    // stage 0: bQ = D(w)^-1; stage 1: K(w) = -(D(w)^-1 + G)^-1; X in bW1, Z in bT
-    for (int i = 0; i < n; ++i) {
-      isdf_ctx* c = cs[i];
-      const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega;
-      const long long rr = (long long)r * r;
-      if (stage == 1) MK(launch_add(c->bQ.p, c->G.p, c->bQ.p, rr, st, nw, rr, 0));  // A = D^-1 + G
-      MK(slices_cm_b(c->b_s1, stage == 0 ? c->D.p : c->bQ.p, r, rr, r, r, rp, rk, nw, st));
-      MK(launch_scaled_identity(c->bW1.p, r, nw, c->ns_alpha.p + (stage == 0 ? 0 : nw), st));
-    }
-    for (int t = 0; t < pl.steps(); ++t) {
-      const bool last = t + 1 == pl.steps();
-      const int s = pl.s[t];
-      const double sign = stage == 0 ? 1.0 : -1.0, f = last ? sign * pl.beta[t] : pl.beta[t];
-      pz.clear();
-      px.clear();
-      for (int i = 0; i < n; ++i) {
-        isdf_ctx* c = cs[i];
-        const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
-        const long long rr = (long long)r * r;
-        MK(slices_cm_b(c->b_s2, c->bW1.p, r, rr, r, r, rp, rk, nw, st));
-        pz.push_back(TcGroupProblem{op_s(c->b_s1, rp, rk, s), op_s(c->b_s2, rp, rk, s), r, r, 1.0, 0.0, c->bT.p, r,
-                                    false, TcBatch{nw, sr, sr, rr}});
-      }
-      const int sz = ns_slot(stage, t, 0), sx = ns_slot(stage, t, 1);
-      MK(tc_gemm_f64_grouped(pz.data(), (int)pz.size(), w + sz * ws, ws, staged[sz], cs[0]->num_sms, cs[0]->d_status,
-                             st));  // Z = M X
-      for (int i = 0; i < n; ++i) {
-        isdf_ctx* c = cs[i];
-        const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64), nw = c->n_omega, sr = NSL * rp;
-        const long long rr = (long long)r * r;
-        MK(slices_rm_b(c->b_s4, c->bT.p, r, rr, r, r, rp, rk, nw, st));
-        double* dst = c->bW1.p;
-        if (last) {
-          dst = stage == 0 ? c->bQ.p : c->K.p;
-          MK(cudaMemcpyAsync(dst, c->bW1.p, (size_t)rr * nw * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        }
-        px.push_back(TcGroupProblem{op_s(c->b_s2, rp, rk, s), op_s(c->b_s4, rp, rk, s), r, r, -f, 2.0 * f, dst, r,
-                                    true, TcBatch{nw, sr, sr, rr}});
-      }
-      MK(tc_gemm_f64_grouped(px.data(), (int)px.size(), w + sx * ws, ws, staged[sx], cs[0]->num_sms, cs[0]->d_status,
-                             st));  // X <- beta (2 X - X Z) (lower, in place), or the result
-    }
-  }
-  for (int i = 0; i < n; ++i) MK(cudaMemsetAsync(cs[i]->b_fail, 0xff, cs[i]->n_omega * sizeof(int), st));
-  return cudaSuccess;
+  return ns_capacitance_grouped(cs, n, plan, st, static_cast<unsigned char*>(work), ws, staged);
 }
 
 // Y = X + V theta K theta^T X for one chunk of nc columns.
@@ -708,14 +673,13 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
   // T2 = K T1 (FP64, small)
   MK(launch_gemm(Kk, r, false, c->tmp1.p, r, true, r, nc, r, 1.0, 0.0, c->tmp2.p, r, false, 16, c->partial.p, true,
                  st));
-  if (c->refine > 0 && c->dinv_ready && c->ref.cap >= (size_t)3 * r * nc) {
+  if (c->refine > 0 && c->xgd_ready && c->ref.cap >= (size_t)2 * r * nc) {
     // iterative refinement of T2 = -(D^-1 + G)^-1 T1, i.e. of (I + D G) T2 =
-    // -D T1: R = -D (T1 + G T2) - T2 in FP64, then T2 -= K (D^-1 R) (the
-    // error of T2 solves (I + D G) E = R, and (I + D G)^-1 = -K D^-1)
+    // -D T1: R = -D (T1 + G T2) - T2 in FP64, then T2 += X^T R (the error of
+    // T2 solves (I + D G) E = R, and (I + D G)^-1 = ((I + G D)^-1)^T = X^T)
     const size_t blk = (size_t)r * nc, bytes = blk * sizeof(double);
     double* U = c->ref.p;
     double* R = U + blk;
-    double* V = R + blk;
     for (int it = 0; it < c->refine; ++it) {
       MK(cudaMemcpyAsync(U, c->tmp1.p, bytes, cudaMemcpyDeviceToDevice, st));
       MK(launch_gemm(c->G.p, r, false, c->tmp2.p, r, true, r, nc, r, 1.0, 1.0, U, r, false, 16, c->partial.p, true,
@@ -723,10 +687,8 @@ cudaError_t mixed_apply_chunk(isdf_ctx* c, const double* Kk, const double* X, do
       MK(cudaMemcpyAsync(R, c->tmp2.p, bytes, cudaMemcpyDeviceToDevice, st));
       MK(launch_gemm(c->D.p, r, false, U, r, true, r, nc, r, -1.0, -1.0, R, r, false, 16, c->partial.p, true,
                      st));  // R = -D U - T2
-      MK(launch_gemm(c->Dinv.p, r, false, R, r, true, r, nc, r, 1.0, 0.0, V, r, false, 16, c->partial.p, true,
-                     st));  // V = D^-1 R
-      MK(launch_gemm(Kk, r, false, V, r, true, r, nc, r, -1.0, 1.0, c->tmp2.p, r, false, 16, c->partial.p, true,
-                     st));  // T2 -= K V
+      MK(launch_gemm(c->Xgd.p, r, true, R, r, true, r, nc, r, 1.0, 1.0, c->tmp2.p, r, false, 16, c->partial.p, true,
+                     st));  // T2 += X^T R
     }
   }
   // T3 = theta T2
