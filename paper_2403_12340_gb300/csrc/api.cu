@@ -423,6 +423,8 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   {
     PhaseScope ph(c, ISDF_PH_POINTS);
     CK(launch_gather_rows(phi, c->n_r, c->d_idx, n_mu, n_e, c->phimu.p, n_mu, c->stream));
+    // the mixed path sums in double-float on the FP32 pipe (about 2^-47)
+    isdf::DfGemm df(prec == ISDF_PREC_MIXED);
     CK(launch_facesplit_gram(c->phimu.p, n_mu, n_mu, c->phimu.p, n_mu, n_mu, n_v, n_e, c->A.p, n_mu,
                              c->stream));
   }

@@ -274,19 +274,27 @@ cudaError_t launch_factor_to_colmajor(const double* Lr, int n, const int* perm, 
 // C(m, n) = (sum_{k < n_v} A(m,k) B(n,k)) * (sum_{n_v <= k < n_e} A(m,k) B(n,k)):
 // with A = Phi and B = Phi at the points this is M C^T (Hadamard identity,
 // Eq. Hadamard), with A = B = Phi at the points it is C C^T.
+// DF: both sums in double-float on the FP32 pipe (the DfGemm scope), about
+// 2^-47 relative, for the points' C C^T of the mixed path.
+template <bool DF>
 __global__ void __launch_bounds__(256) k_facesplit_gram(Operand<false> A, Operand<false> B, int n_v,
                                                         int n_e, double* __restrict__ C,
                                                         long long ldc, int sym) {
   using T = TileSq;
-  __shared__ T::Smem s;
+  __shared__ typename std::conditional<DF, T::SmemDf, T::Smem>::type s;
   int mt = blockIdx.x, nt = blockIdx.y;
   if (sym) lower_tile(blockIdx.x, mt, nt);  // A == B: lower tiles, mirrored
   const int m0 = mt * T::kBM, n0 = nt * T::kBN;
   double av[T::kTM][T::kTN], ac[T::kTM][T::kTN];
   zero_acc<T>(av);
   zero_acc<T>(ac);
-  gemm_mainloop<T>(av, s, A, B, m0, n0, 0, n_v);
-  gemm_mainloop<T>(ac, s, A, B, m0, n0, n_v, n_e);
+  if constexpr (DF) {
+    gemm_mainloop_df<T>(av, s, A, B, m0, n0, 0, n_v);
+    gemm_mainloop_df<T>(ac, s, A, B, m0, n0, n_v, n_e);
+  } else {
+    gemm_mainloop<T>(av, s, A, B, m0, n0, 0, n_v);
+    gemm_mainloop<T>(ac, s, A, B, m0, n0, n_v, n_e);
+  }
 #pragma unroll
   for (int j = 0; j < T::kTN; ++j) {
     int n = tile_col<T>(n0, j);
@@ -310,10 +318,14 @@ cudaError_t launch_facesplit_gram(const double* A, long long lda, int M, const d
   const bool sym = (A == B && lda == ldb && M == N);
   const int tm = (M + 63) / 64;
   dim3 grid = sym ? dim3(tm * (tm + 1) / 2, 1) : dim3(tm, (N + 63) / 64);
-  KernelTimer kt(KF_FP64_GEMM, s, 2.0 * n_e * (sym ? 0.5 * M * (M + 1.0) : (double)M * N));
+  KernelTimer kt(tl_gemm_df ? KF_DF_GEMM : KF_FP64_GEMM, s, 2.0 * n_e * (sym ? 0.5 * M * (M + 1.0) : (double)M * N));
   note_launch();
-  k_facesplit_gram<<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v,
-                                        n_e, C, ldc, sym ? 1 : 0);
+  if (tl_gemm_df)
+    k_facesplit_gram<true><<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v, n_e, C,
+                                                ldc, sym ? 1 : 0);
+  else
+    k_facesplit_gram<false><<<grid, 256, 0, s>>>(Operand<false>{A, lda, M}, Operand<false>{B, ldb, N}, n_v, n_e, C,
+                                                 ldc, sym ? 1 : 0);
   return cudaGetLastError();
 }
 
