@@ -165,7 +165,17 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
   const int nR = n / R;
   const int tstep = n / (Ns * R);
   for (int idx = threadIdx.x; idx < nlines * nR; idx += blockDim.x) {
-    int line = idx / nR, j = idx - line * nR;
+    // consecutive threads on consecutive addresses: along the line where its
+    // elements are adjacent (se == 1), across the lines where the lines are
+    // (sl == 1, the y pass of a plane), which keeps shared-memory banks apart
+    int line, j;
+    if (sl == 1 && se != 1) {
+      j = idx / nlines;
+      line = idx - j * nlines;
+    } else {
+      line = idx / nR;
+      j = idx - line * nR;
+    }
     int k = j % Ns;
     C v[R];
 #pragma unroll
