@@ -226,6 +226,7 @@ extern "C" int isdf_create(isdf_ctx** out, int n1, int n2, int n3, double L1, do
     e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s4, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
@@ -245,6 +246,10 @@ extern "C" int isdf_destroy(isdf_ctx* c) {
   if (c->s2) {
     cudaStreamSynchronize(c->s2);
     cudaStreamDestroy(c->s2);
+  }
+  if (c->s4) {
+    cudaStreamSynchronize(c->s4);
+    cudaStreamDestroy(c->s4);
   }
   if (c->s3) {
     cudaStreamSynchronize(c->s3);
@@ -341,17 +346,18 @@ static int join_s2(isdf_ctx* c) {
 
 // Workspace of launch_cholesky_and_inverse for an n x n factor: its step
 // events and the Y / split-K buffer (sized before any fork: a resize frees).
-static int chol_inverse_workspace(isdf_ctx* c, int n) {
-  const size_t steps = (size_t)(n + 63) / 64;
+static int chol_inverse_workspace(isdf_ctx* c, int n, bool ahead = false) {
+  const size_t steps = (size_t)(n + 63) / 64 * 3;  // per step: block, panel, rest (look-ahead)
   while (c->ev_chol.size() < steps) {
     if (isdf::tl_capture) return fail(c, ISDF_ERR_STATE, "factorisation events: a captured call needs an eager call first");
     cudaEvent_t e = nullptr;
     CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->ev_chol.push_back(e);
   }
-  if (c->inv_work.cap < (size_t)9 * 64 * n || c->cb_split.cap < (size_t)64 * n) SYNC(c->stream);
+  const size_t split = (size_t)(ahead ? 128 : 64) * n;  // two alternating split panels with look-ahead
+  if (c->inv_work.cap < (size_t)9 * 64 * n || c->cb_split.cap < split) SYNC(c->stream);
   CK(ensure(c->inv_work, (size_t)9 * 64 * n));
-  CK(ensure(c->cb_split, (size_t)64 * n));
+  CK(ensure(c->cb_split, split));
   return ISDF_OK;
 }
 
@@ -435,7 +441,7 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   // beside the factorisation, block row by block row
   const bool fuse_inv = prec == ISDF_PREC_MIXED;
   if (fuse_inv) {
-    rc0 = chol_inverse_workspace(c, n_mu);
+    rc0 = chol_inverse_workspace(c, n_mu, true);
     if (rc0 != ISDF_OK) return rc0;
     CK(ensure(c->m_linv, (size_t)n_mu * n_mu));
   }
@@ -447,7 +453,7 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     if (fuse_inv) {
       CK(launch_cholesky_and_inverse(c->A.p, n_mu, n_mu, tol, c->Lc.p, n_mu, c->m_linv.p, n_mu, c->cb_work.p,
                                      c->d_ints + 1, c->inv_work.p, c->s2, c->s3, c->ev_chol.data(),
-                                     reinterpret_cast<float2*>(c->cb_split.p)));
+                                     reinterpret_cast<float2*>(c->cb_split.p), c->s4));
     } else {
       rc0 = cholesky_blocked(c, c->A.p, n_mu, n_mu, tol, c->Lc.p, c->d_ints + 1, c->s2);
       if (rc0 != ISDF_OK) return rc0;

@@ -74,6 +74,9 @@ struct isdf_ctx {
   // beside the factorisation producing it (launch_cholesky_and_inverse)
   cudaStream_t s3 = nullptr;
   cudaEvent_t ev_join3 = nullptr;
+  // a fourth stream for the look-ahead of the fit's factorisation (the rest
+  // of each step's trailing update beside the next diagonal block)
+  cudaStream_t s4 = nullptr;
   std::vector<cudaEvent_t> ev_chol;  // one per 64-wide factorisation step
   DevBuf inv_work;
   // split panels (float pairs, one per double) of the mixed path's

@@ -579,20 +579,35 @@ __global__ void __launch_bounds__((TS / TM) * (TS / TM)) k_trail_update(double* 
 // of float pairs, a (hi, lo) accumulator pair per output, renormalised after
 // every K chunk; C -= hi + lo in FP64 at the end.
 template <int TS, int TM>
+// tj0 > 0 or tj1 < T (T tiles per side): only the tile columns [tj0, tj1)
+// of the trailing triangle, enumerated column by column (the look-ahead of
+// launch_cholesky_and_inverse splits one update in two).
 __global__ void __launch_bounds__((TS / TM) * (TS / TM)) k_trail_update_df(const float2* __restrict__ Sp, long long lds,
                                                                           long long sS, double* L, long long ldl,
                                                                           int j0, int bs, int rem, const int* fail,
-                                                                          long long sL) {
+                                                                          long long sL, int tj0 = 0, int tj1 = -1) {
   constexpr int Q = TS / TM, NT = Q * Q, KC = 32;
   __shared__ float2 As[KC][TS], Bs[KC][TS];
   L += sL * blockIdx.y;
   Sp += sS * blockIdx.y;
   if (*(volatile const int*)(fail + blockIdx.y) >= 0) return;
   const int tile = blockIdx.x;
-  int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
-  while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-  while (ti * (ti + 1) / 2 > tile) --ti;
-  const int tj = tile - ti * (ti + 1) / 2;
+  int ti, tj;
+  if (tj1 < 0) {
+    ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    tj = tile - ti * (ti + 1) / 2;
+  } else {
+    const int T = (rem + TS - 1) / TS;
+    int b = tile;
+    tj = tj0;
+    while (b >= T - tj) {
+      b -= T - tj;
+      ++tj;
+    }
+    ti = tj + b;
+  }
   const int i0 = ti * TS, k0 = tj * TS;
   const int t = threadIdx.x, tx = t % Q, ty = t / Q;
   const long long r0 = j0 + bs;
@@ -678,6 +693,36 @@ static cudaError_t trail_update(double* L, long long ldl, int j0, int bs, int re
   return cudaGetLastError();
 }
 
+// Double-float trailing update of one column range of the trailing block:
+// part 1 the first 64 columns (the next diagonal block and its panel),
+// part 2 the rest (see launch_cholesky_and_inverse).
+static cudaError_t trail_update_part(double* L, long long ldl, int j0, int bs, int rem, const int* fail,
+                                     cudaStream_t s, const float2* Sp, long long lds, int part) {
+  if (rem <= 0) return cudaSuccess;
+  constexpr int TS = 32;  // the thin first part needs the parallelism; the rest follows the full rule below
+  const int T = (rem + TS - 1) / TS, split = std::min(T, CB / TS);
+  const int tj0 = part == 1 ? 0 : split, tj1 = part == 1 ? split : T;
+  if (tj0 >= tj1) return cudaSuccess;
+  long long ntiles = 0;
+  for (int tj = tj0; tj < tj1; ++tj) ntiles += T - tj;
+  const long long cols0 = (long long)tj0 * TS, cols1 = std::min<long long>((long long)tj1 * TS, rem);
+  // terms: the lower part of columns [cols0, cols1) of the rem x rem triangle, bs each
+  const double terms = (double)(cols1 - cols0) * (2.0 * rem - cols0 - cols1 + 1) / 2.0 * bs;
+  KernelTimer kt(KF_DF_GEMM, s, 2.0 * terms);
+  note_launch();
+  if (part == 2 && (T / 2) * (T / 2 + 1) / 2 >= 152) {
+    // the wide rest in 64-wide tiles while they fill the GPU (tile columns in 64s)
+    const int T64 = (rem + 63) / 64;
+    long long n64 = 0;
+    for (int tj = 1; tj < T64; ++tj) n64 += T64 - tj;
+    k_trail_update_df<64, 4><<<dim3((unsigned)n64, 1), 256, 0, s>>>(Sp, lds, 0, L, ldl, j0, bs, rem, fail, 0, 1, T64);
+  } else {
+    k_trail_update_df<32, 2><<<dim3((unsigned)ntiles, 1), 256, 0, s>>>(Sp, lds, 0, L, ldl, j0, bs, rem, fail, 0, tj0,
+                                                                       tj1);
+  }
+  return cudaGetLastError();
+}
+
 // The mixed path (a split-panel buffer given) factors in double-float
 // arithmetic throughout; its rank test then accepts pivots above
 // 2^-40 max diag at least (double-float rounding is ~2^-47 per operation, so
@@ -759,8 +804,12 @@ cudaError_t launch_cholesky_blocked(const double* W, long long ldw, int n, doubl
 cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, double tol_rel, double* L,
                                         long long ldl, double* Li, long long ldi, double* dmax, int* fail,
                                         double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev,
-                                        float2* split) {
+                                        float2* split, cudaStream_t aux2) {
   if (n <= 0) return cudaSuccess;
+  const int nsteps = (n + CB - 1) / CB;
+  const bool ahead = split != nullptr && aux2 != nullptr;
+  cudaEvent_t* ev_panel = ev + nsteps;      // panel j written (look-ahead)
+  cudaEvent_t* ev_rest = ev + 2 * nsteps;   // rest of update j applied (look-ahead)
   DfGemm df(split != nullptr);  // the inverse rows in the same arithmetic as the trailing updates
   // on s: with double-float blocks the diagonal blocks of Li are written from s
   cudaError_t e = cudaMemset2DAsync(Li, ldi * sizeof(double), 0, n * sizeof(double), n, split ? s : aux);
@@ -780,8 +829,12 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
     const int bs = min(CB, n - j0);
     double* Ljj = L + j0 + ldl * (long long)j0;
     double* Lijj = Li + j0 + ldi * (long long)j0;
+    // with look-ahead the split panels alternate between two buffers: the
+    // rest of step j's update (aux2) still reads panel j while step j + 1
+    // writes its own; step j + 2 reuses the buffer after s waited for it
+    float2* sp = ahead ? split + (size_t)(jb & 1) * CB * n : split;
     // the double-float block factorisation writes L_jj^-1 into Li itself
-    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, split, n, 0, split ? Lijj : nullptr, ldi, s)) !=
+    if ((e = diag_step(L, ldl, j0, bs, dmax, tol_rel, fail, 0, 1, sp, n, 0, split ? Lijj : nullptr, ldi, s)) !=
         cudaSuccess)
       return e;
     // row block jb of the inverse, beside the rest of the factorisation
@@ -800,10 +853,22 @@ cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, d
     }
     const int rem = n - j0 - bs;
     if (rem <= 0) break;
-    if ((e = panel_step(L, ldl, j0, bs, rem, fail, 0, 1, split, n, 0, s)) != cudaSuccess) return e;
-    e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s, split, n, 0);
-    if (e != cudaSuccess) return e;
+    if ((e = panel_step(L, ldl, j0, bs, rem, fail, 0, 1, sp, n, 0, s)) != cudaSuccess) return e;
+    if (!ahead) {
+      e = trail_update(L, ldl, j0, bs, rem, 1, fail, 0, s, split, n, 0);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    // look-ahead: the rest of the previous step's update (on aux2) has
+    // reached these columns before this step's panel updates them
+    if (jb > 0 && (e = cudaStreamWaitEvent(s, ev_rest[jb - 1], 0)) != cudaSuccess) return e;
+    if ((e = trail_update_part(L, ldl, j0, bs, rem, fail, s, sp, n, 1)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_panel[jb], s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(aux2, ev_panel[jb], 0)) != cudaSuccess) return e;
+    if ((e = trail_update_part(L, ldl, j0, bs, rem, fail, aux2, sp, n, 2)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_rest[jb], aux2)) != cudaSuccess) return e;
   }
+  if (ahead && nsteps > 1 && (e = cudaStreamWaitEvent(s, ev_rest[nsteps - 2], 0)) != cudaSuccess) return e;
   dim3 g((n + 127) / 128, n);
   note_launch();
   k_zero_upper<<<g, 128, 0, s>>>(L, ldl, n);

@@ -218,12 +218,18 @@ cudaError_t launch_diag_inverse_block(const double* L, long long ldl, int bs, do
 //   Li[J, J] = L_JJ^-1,  Li[J, 0:J] = -L_JJ^-1 (L[J, 0:J] Li[0:J, 0:J]),
 // which needs only rows of L that earlier steps finished.  The caller orders
 // aux after everything Li and work depend on, and joins aux before Li is
-// used.  ev: at least ceil(n / 64) events; work: 64 n + 8 * 64 n doubles.
-// If the factorisation stops (fail >= 0), Li is undefined.
+// used.  ev: at least ceil(n / 64) events (3 ceil(n / 64) with aux2);
+// work: 64 n + 8 * 64 n doubles.  If the factorisation stops (fail >= 0),
+// Li is undefined.
+// aux2 (double-float path only): look-ahead.  Each step's trailing update
+// is split: the next 64 columns on s, so the next diagonal block can start
+// at once, and the rest on aux2 beside it; s waits for that rest before it
+// updates the columns the rest also touches.  aux2 is joined into s before
+// the function returns.
 cudaError_t launch_cholesky_and_inverse(const double* W, long long ldw, int n, double tol_rel, double* L,
                                         long long ldl, double* Li, long long ldi, double* dmax, int* fail,
                                         double* work, cudaStream_t s, cudaStream_t aux, cudaEvent_t* ev,
-                                        float2* split = nullptr);
+                                        float2* split = nullptr, cudaStream_t aux2 = nullptr);
 // launch_cholesky_blocked for `batch` equal-size matrices W + z sW -> L + z sL;
 // dmax and fail: batch entries; split: nullptr or batch x 64 n float pairs.
 cudaError_t launch_cholesky_blocked_batched(const double* W, long long ldw, long long sW, int n, int batch,
