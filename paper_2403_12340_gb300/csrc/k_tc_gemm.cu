@@ -332,6 +332,10 @@ __device__ __forceinline__ TcUnit tc_unit(const TcArgs& a, long long u, int tile
   } else {
     w.mt = tile / a.tiles_n;  // n fastest: consecutive units share the A tile (L2 reuse)
     w.nt = tile - w.mt * a.tiles_n;
+    // under tri_b a tile's K range grows with nt; rotating nt by the row
+    // spreads long and short tiles over the persistent blocks (at isdf48
+    // the busiest block then does 5 % more than the mean instead of 25 %)
+    if (a.tri_b) w.nt = (w.nt + w.mt) % a.tiles_n;
   }
   w.m0 = w.mt * TC_BM;
   w.n0 = w.nt * bn;
@@ -793,15 +797,17 @@ static cudaError_t tc_run_plan(const TcOperand& A, const TcOperand& B, TcArgs a,
   a.k_per_split = p.per;
   if (p.splits > 1) {
     a.partial = partial;
-    cudaError_t e = p.bn == 64 ? tc_launch<64, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st)
-                               : tc_launch<128, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st);
+    cudaError_t e = p.bn == 16   ? tc_launch<16, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st)
+                    : p.bn == 64 ? tc_launch<64, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st)
+                                 : tc_launch<128, 1, EPI_F64>(A, B, a, p.splits, bt.count, mma, st);
     if (e != cudaSuccess) return e;
     return launch_splitk_reduce(partial, p.splits, M, N, alpha, beta, C, ldc, lower_only, TC_BM, st, bt.count,
                                 bt.c_stride);
   }
   a.partial = nullptr;
-  return p.bn == 64 ? tc_launch<64, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st)
-                    : tc_launch<128, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st);
+  return p.bn == 16   ? tc_launch<16, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st)
+         : p.bn == 64 ? tc_launch<64, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st)
+                      : tc_launch<128, 1, EPI_F64>(A, B, a, 1, bt.count, mma, st);
 }
 
 static TcPlan plan_for(int k_iters, int splits_wanted, int bn) {
@@ -840,7 +846,10 @@ cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, i
   const bool can_split = partial && !tri_b;
   int splits = 1, per = a.k_iters;
   if (can_split) split_k(a.k_iters, tiles, num_sms, max_split, splits, per);
-  TcPlan plan{128, splits, per};
+  // a narrow B (at most 16 columns, the probe blocks of the apply): 128 x 16
+  // tiles, so the MMAs do not run on padding columns
+  const int bn0 = (!lower_only && N <= 16) ? 16 : 128;
+  TcPlan plan{bn0, splits, per};
   // BF16 MMA flops of the s (s + 1) / 2 slice products over the outputs the
   // method needs (lower triangle of a SYRK; k <= n under tri_b)
   const double prods = 0.5 * a.s * (a.s + 1);
@@ -862,7 +871,7 @@ cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, i
   if (!tuned && g_autotune.load() == 2 && !tl_capture) {
     // the narrowest tile wherever it is allowed, heuristic splits, no timing:
     // runs every tile path of a workload (tests)
-    plan = plan_for(a.k_iters, splits, lower_only ? 128 : 64);
+    plan = plan_for(a.k_iters, splits, lower_only ? 128 : (N <= 16 ? 16 : 64));
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = TuneVal{plan.bn, plan.splits, 0.0f, 0.0f};
   } else if (!tuned && g_autotune.load() == 1 && !tl_capture && beta == 0.0) {
@@ -878,7 +887,7 @@ cudaError_t tc_gemm_f64_batched(const TcOperand& A, const TcOperand& B, int M, i
         if (q.bn == p.bn && q.splits == p.splits) return;
       cand.push_back(p);
     };
-    for (int bn : {128, 64}) {
+    for (int bn : {bn0, 128, 64}) {
       add(splits, bn);
       add(splits * 2, bn);
       add(splits / 2, bn);

@@ -1,5 +1,6 @@
 """The tile autotuner of the tensor-core GEMMs (isdf_set_autotune): timed
-choices and the forced 64-wide tiles both keep the mixed path within its
+choices and the forced narrow tiles (64 wide, 16 for a B of at most 16
+columns) both keep the mixed path within its
 bound against the FP64 oracle, the table records valid choices, and a tuned
 shape gives the same result on every later call.  The table is process-wide,
 so every test leaves the tuner off and the table empty."""
@@ -33,7 +34,9 @@ def pkg():
 def _check_table(table, forced):
     assert table
     for t in table:
-        assert t["bn"] in (64, 128)
+        assert t["bn"] in (16, 64, 128)
+        if t["bn"] == 16:  # 128 x 16 tiles only for a B of at most 16 columns
+            assert t["N"] <= 16 and not t["lower"]
         assert 1 <= t["splits"] <= max(1, t["max_split"])
         # the accumulation-length minimum holds for every choice that may split
         if t["max_split"] > 1:
@@ -41,7 +44,7 @@ def _check_table(table, forced):
         if t["lower"]:
             assert t["bn"] == 128
         if forced:
-            assert t["bn"] == (128 if t["lower"] else 64)
+            assert t["bn"] == (128 if t["lower"] else (16 if t["N"] <= 16 else 64))
         else:
             assert t["ms_best"] <= t["ms_heuristic"] + 1e-6
 
@@ -67,7 +70,8 @@ def test_autotuned_mixed_solve_matches_oracle(pkg, mode):
 
 @pytest.mark.parametrize("M,N,K", [(200, 130, 100), (1000, 600, 4096), (257, 129, 20000), (300, 7, 513)])
 def test_narrow_tiles_dgemm_split(pkg, M, N, K):
-    """isdf_dgemm_split with the 64-wide tiles forced, against float64."""
+    """isdf_dgemm_split with the narrow tiles forced (64 wide; 16 for N <= 16),
+    against float64."""
     import torch
 
     pkg.isdf_set_autotune(2)
@@ -81,7 +85,7 @@ def test_narrow_tiles_dgemm_split(pkg, M, N, K):
     ref = 0.75 * a @ b.T - 0.5 * c0
     scale = 0.75 * np.abs(a) @ np.abs(b).T + 0.5 * np.abs(c0)
     assert (np.abs(C.cpu().numpy() - ref) / scale).max() < 2e-6
-    assert any(t["bn"] == 64 for t in pkg.isdf_autotune_table())
+    assert any(t["bn"] == (16 if N <= 16 else 64) for t in pkg.isdf_autotune_table())
 
 
 def test_autotune_off_records_nothing(pkg):
