@@ -77,14 +77,13 @@ enum {
 
 /* Precision of the path.  FP64: every step in float64 on the FP64 pipe.
  * MIXED: every large contraction (face-split Gram, the triangular solve of
- * the fit as a GEMM with the FP64 inverse factor, G, D and the capacitance
- * products, theta^T X and theta T) on the tensor cores with operands cut into
- * three BF16 slices and FP32 accumulation, the Coulomb transform of theta
- * in FP32; the Cholesky factorisations and triangular inverses keep FP64
- * storage, FP64 diagonal blocks and panels, with their trailing updates and
- * block-row GEMMs in double-float arithmetic on the FP32 pipe (float pairs,
- * about 2^-46 relative per product sum); the FFT of the probe block stays in
- * FP64.  Results agree with FP64 to about 1e-6 relative on well-conditioned
+ * the fit as a GEMM with the inverse factor, G, D, the Newton-Schulz
+ * capacitance products, theta^T X and theta T) on the tensor cores with
+ * operands cut into three BF16 slices and FP32 accumulation, the Coulomb
+ * transform of theta in FP32; the points' C C^T, its Cholesky factorisation
+ * and triangular inverse in double-float arithmetic on the FP32 pipe (float
+ * pairs, about 2^-46 relative per product sum) with FP64 storage; the FFT
+ * of the probe block stays in FP64.  Results agree with FP64 to about 1e-6 relative on well-conditioned
  * systems.  Both the BF16 slices and the float pairs keep FP32's exponent
  * range: entries of the matrices they carry must lie within about 1e-30 to
  * 1e30 in magnitude (or be zero); use FP64 for inputs scaled beyond it. */
@@ -168,18 +167,25 @@ ISDF_API int isdf_contour_nodes(const double* energies, int n_v, int n_c, double
 
 /* SMW capacitance for frequency omega[omega_index] (K of Section "Cubic
  * scaling algorithm", Algorithm 3 step 3), in the singular-B-safe form
- * K = -D (I + G D)^-1 = -Q Q^T, Q = R U^-T, D = R R^T, I + R^T G R = U U^T.
+ * K = -D (I + G D)^-1.  FP64: K = -Q Q^T, Q = R U^-T, D = R R^T,
+ * I + R^T G R = U U^T.  MIXED: X -> (I + G D)^-1 by Newton-Schulz on the
+ * tensor cores, then K = -D X; the step schedule comes from rigorous
+ * bounds of the spectra of G and D (one host read).  When those bounds ask
+ * for more than 12 steps, or during a stream capture, the factorisation
+ * route runs instead.
  *   K_out    device, n_mu x n_mu float64 out, or NULL (K is kept in the
  *            context for apply_eps_inv either way).
- * ISDF_ERR_NOT_SPD if D is not positive definite in floating point. */
+ * ISDF_ERR_NOT_SPD if a factorisation finds D (or I + R^T G R) not positive
+ * definite in floating point. */
 ISDF_API int smw_inverse(isdf_ctx* ctx, int omega_index, double* K_out);
 
 /* smw_inverse for every frequency of the last build_polarizability at once
- * (the full-frequency form of Algorithm 3 step 3): on a MIXED context the
- * products, the FP64 Cholesky factorisations and the triangular inverses
- * of all frequencies run as batched launches (one launch per step for all
- * of them); on an FP64 context the frequencies are queued one after the
- * other.  One synchronisation at the end.
+ * (the full-frequency form of Algorithm 3 step 3).  On a MIXED context
+ * every Newton-Schulz product of all frequencies is one grouped persistent
+ * launch (one schedule, from the largest spectral bound over the
+ * frequencies); the batched factorisation route is the fallback.  On an
+ * FP64 context the frequencies are queued one after the other.  One
+ * synchronisation for the bounds (MIXED) and one at the end.
  *   K_out    device, n_omega x n_mu x n_mu float64 out, or NULL.
  * ISDF_ERR_NOT_SPD names the first frequency whose factor failed. */
 ISDF_API int smw_inverse_all(isdf_ctx* ctx, double* K_out);
