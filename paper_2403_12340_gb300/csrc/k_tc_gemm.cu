@@ -297,6 +297,7 @@ struct TcArgs {
   int tiles_m, tiles_n;        // tiles along M and N
   int count;                   // problems of the batch
   int splits;                  // K splits per problem (units: problem, split, tile)
+  int tma3;                    // the maps are 3-D (chunk, row, slab): one load brings every slice
   int a_brows, b_brows;        // rows between the slice stacks of consecutive problems (0: shared)
   long long c_bstride;         // elements between the C of consecutive problems
   double alpha, beta;
@@ -415,9 +416,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* sa = smem + st * stage_bytes;
         uint8_t* sb = sa + a.s * TC_BM * TC_BK * 2;
         const int kx = kc * TC_BK;
-        for (int l = 0; l < a.s; ++l) {
-          tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, a_row0 + l * a.a_rows_pad);
-          tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, b_row0 + l * a.b_rows_pad);
+        if (a.tma3) {  // the s slices of each operand in one copy each (slabs of rows_pad rows)
+          tc::tma_load_3d(sa, &tma, &full[st], kx, w.m0, w.bidx * (a.a_brows / a.a_rows_pad));
+          tc::tma_load_3d(sb, &tmb, &full[st], kx, w.n0, w.bidx * (a.b_brows / a.b_rows_pad));
+        } else {
+          for (int l = 0; l < a.s; ++l) {
+            tc::tma_load_2d(sa + l * TC_BM * TC_BK * 2, &tma, &full[st], kx, a_row0 + l * a.a_rows_pad);
+            tc::tma_load_2d(sb + l * BN * TC_BK * 2, &tmb, &full[st], kx, b_row0 + l * a.b_rows_pad);
+          }
         }
       }
     }
@@ -699,16 +705,44 @@ static cudaError_t make_map(CUtensorMap* m, const __nv_bfloat16* base, int kp, l
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 3-D map over the same array seen as slabs of rows_pad rows (a slice of a
+// stack, or a member of a batch): box 64 x box_rows x s, 128B swizzle.
+static cudaError_t make_map3(CUtensorMap* m, const __nv_bfloat16* base, int kp, int rows_pad, long long slabs,
+                             int box_rows, int s) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || (kp % 8)) return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows_pad, (cuuint64_t)slabs};
+  cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * (cuuint64_t)rows_pad};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, (cuuint32_t)s};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int BN, int NACC, int EPI>
 static cudaError_t tc_launch(const TcOperand& A, const TcOperand& B, TcArgs a, int splits, int batch,
                              double mma_flops, cudaStream_t st) {
   CUtensorMap ma, mb;
   const long long arows = (long long)A.rows_pad * a.s + (long long)a.a_brows * (batch - 1);
   const long long brows = (long long)B.rows_pad * a.s + (long long)a.b_brows * (batch - 1);
-  cudaError_t e = make_map(&ma, A.p, A.kp, arows, TC_BM);
-  if (e != cudaSuccess) return e;
-  e = make_map(&mb, B.p, B.kp, brows, BN);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  // one 3-D copy per operand and stage when the stacks are whole slabs of
+  // rows_pad rows and every tile lies inside one slab
+  a.tma3 = A.rows_pad % TC_BM == 0 && B.rows_pad % BN == 0 && a.a_brows % A.rows_pad == 0 &&
+           a.b_brows % B.rows_pad == 0;
+  if (a.tma3) {
+    e = make_map3(&ma, A.p, A.kp, A.rows_pad, arows / A.rows_pad, TC_BM, a.s);
+    if (e == cudaSuccess) e = make_map3(&mb, B.p, B.kp, B.rows_pad, brows / B.rows_pad, BN, a.s);
+    if (e != cudaSuccess) return e;
+  } else {
+    e = make_map(&ma, A.p, A.kp, arows, TC_BM);
+    if (e != cudaSuccess) return e;
+    e = make_map(&mb, B.p, B.kp, brows, BN);
+    if (e != cudaSuccess) return e;
+  }
   const int smem = tc_stages(a.s, BN) * tc_stage_bytes(a.s, BN) + 1024 + 256;
   // once per kernel (host threads of a batch may arrive together: setting it twice is harmless,
   // and a thread that reads true finds it set)
