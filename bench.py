@@ -88,7 +88,7 @@ def dominant_cell(cells):
 SLICE_PRODUCTS = 6
 
 
-def kernel_roofline(fam, phase, ms, cnt, work, steps, peaks):
+def kernel_roofline(fam, phase, ms, cnt, work, steps, peaks, workload="isdf48"):
     """Roofline of one (kernel family, phase) cell of the library's kernel
     timing: work per launch / average launch time against the peak of the
     unit that bounds the family."""
@@ -127,7 +127,9 @@ def kernel_roofline(fam, phase, ms, cnt, work, steps, peaks):
                      "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
                      "peak_source": f"HBM copy {peaks['source']}",
                      "work": "algorithmic bytes (input read + output write)"})
-    cell["traffic"] = NCU_DRAM_BYTES.get(cell["kernel"])
+    # the captures are of the isdf48 solve: another workload's cell of the same
+    # name moves other bytes, so it has no traffic figure
+    cell["traffic"] = NCU_DRAM_BYTES.get(cell["kernel"]) if workload == "isdf48" else None
     return cell
 
 
@@ -617,7 +619,8 @@ def run_batch(args):
         flops_run += (fl["points_chol"] + fl["fit_gram"] + fl["fit_trsm"] + fl["coulomb_fft"] + fl["coulomb_syrk"]
                       + BATCH_OMEGAS * (fl["polar_d"] + fl["whiten_d"] + fl["smw"]))
     peaks = measured_peaks()
-    cells = [kernel_roofline(f, ph, ms, cnt, w, 1, peaks) for (f, ph), (ms, cnt, w) in kprof.items() if cnt and ms > 0]
+    cells = [kernel_roofline(f, ph, ms, cnt, w, 1, peaks, workload="batch16")
+             for (f, ph), (ms, cnt, w) in kprof.items() if cnt and ms > 0]
     cells.sort(key=lambda c: -c["ms_per_step"])
     for c in cells:
         c["timed_in"] = f"a one-worker run after the timed runs ({prof_ms:.0f} ms for the whole batch)"

@@ -57,5 +57,8 @@ def test_dominant_cell_prefers_tensor_gemm():
     roof = bench.dominant_cell(cells)
     assert roof["kernel"] == "tc_gemm:fit_trsm"
     assert roof["traffic"] == bench.NCU_DRAM_BYTES["tc_gemm:fit_trsm"]
+    # the captured bytes are the isdf48 solve's: no figure for another workload's cell
+    other = bench.kernel_roofline("tc_gemm", "fit_trsm", 28.0, 10, 1e13, 10, peaks, workload="batch16")
+    assert other["traffic"] is None
     assert bench.dominant_cell(cells[:1])["kernel"] == "df_gemm:points_chol"
     assert bench.dominant_cell([]) is None
