@@ -828,16 +828,22 @@ static int smw_enqueue(isdf_ctx* c, int k, int* failT) {
     double* nb = c->ns_bound.p;
     CK(launch_row_abs_sum_max(c->G.p, r, r, nb, nb + 4, c->stream));
     CK(launch_row_abs_sum_max(Dk, r, r, nb + 1, nb + 4, c->stream));
+    // the host reads the bounds through the helper stream while M = I + G D,
+    // which needs none, is built on this one (if the bounds then rule the
+    // iteration out, the factorisation below overwrites M)
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(isdf::mixed_ns_prepare(c, Dk));
+    CK(cudaStreamWaitEvent(c->s3, c->ev_fork, 0));
     double h[2] = {0.0, 0.0};
-    CK(cudaMemcpyAsync(h, nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(h, nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s3));
+    CK(cudaStreamSynchronize(c->s3));
     double wmin = 0.0, wmax = 0.0;
     isdf::pair_weight_bounds(c->energies.data(), c->n_v, c->n_c, c->omega[k], &wmin, &wmax);
     const double kappa = isdf::ns_kappa(h[0], std::min(wmax, h[1]));
     isdf::NsPlan plan;
     if (std::isfinite(kappa) && isdf::ns_plan((kappa - 1.0) / (kappa + 1.0), plan)) {
       CK(cudaMemsetAsync(failT, 0xff, sizeof(int), c->stream));  // no factorisation to fail
-      CK(isdf::mixed_ns_capacitance(c, Dk, Kk, 2.0 / (1.0 + kappa), plan));
+      CK(isdf::mixed_ns_iterate(c, Dk, Kk, 2.0 / (1.0 + kappa), plan));
       c->xgd_ready = c->n_omega == 1;
       return ISDF_OK;
     }

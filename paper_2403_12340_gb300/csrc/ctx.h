@@ -244,10 +244,12 @@ struct NsPlan {
 // the iteration needs more than 12 steps.
 bool ns_plan(double e0, NsPlan& p);
 // K = -D (I + G D)^-1 for the D at Dk (r x r, ld r) and c->G, into Kk, on
-// the main stream, by the Newton-Schulz steps of `plan` for (I + G D)^-1
-// from X = alpha I (scratch: c->T, c->R, c->Xgd, which keeps X, and the
-// slices c->m_sd, m_sa, m_sb)
-cudaError_t mixed_ns_capacitance(isdf_ctx* c, const double* Dk, double* Kk, double alpha, const NsPlan& plan);
+// the main stream, in two parts: mixed_ns_prepare builds M = I + G D (in
+// c->T, its slices in c->m_sd), then mixed_ns_iterate runs the Newton-Schulz
+// steps of `plan` for M^-1 from X = alpha I and K = -D X (scratch: c->R,
+// c->Xgd, which keeps X, and the slices c->m_sa, m_sb)
+cudaError_t mixed_ns_prepare(isdf_ctx* c, const double* Dk);
+cudaError_t mixed_ns_iterate(isdf_ctx* c, const double* Dk, double* Kk, double alpha, const NsPlan& plan);
 // Upper end of the spectrum of I + G D, 1 + |G| |D| from bounds of the two
 // spectra (its lower end is 1: G D has the eigenvalues of D^1/2 G D^1/2 >= 0)
 double ns_kappa(double g_bound, double d_bound);

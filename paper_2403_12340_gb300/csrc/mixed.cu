@@ -30,22 +30,45 @@ constexpr int NSL = 3;  // BF16 slices per operand
 
 inline int pad(long long x, int m) { return (int)((x + m - 1) / m * m); }
 
+// Zero the padding of an NSL-slice stack (rows_pad x kp per slice) whose
+// writer fills rows 0..R-1 at columns [0, kv) and [kvp, kend) (kv = kvp = 0:
+// [0, kend)): the rows R..rows_pad-1 of every slice and, in every row, the
+// columns outside those ranges.  Together with the writer this leaves the
+// stack as zeroing all of it first would, but moves only the padding's bytes
+// (none where the shapes are multiples of the tiles, as at 48^3 / N_mu 1536,
+// where the whole-stack zeroing of the FFT's slices alone was 1 GB).
+inline cudaError_t zero_padding(__nv_bfloat16* p, int R, int kend, int rows_pad, int kp, cudaStream_t st, int kv = 0,
+                                int kvp = 0) {
+  const size_t pitch = (size_t)kp * 2, rows = (size_t)NSL * rows_pad;
+  cudaError_t e = cudaSuccess;
+  if (kv < kvp) e = cudaMemset2DAsync(p + kv, pitch, 0, (size_t)(kvp - kv) * 2, rows, st);
+  if (e == cudaSuccess && kend < kp) e = cudaMemset2DAsync(p + kend, pitch, 0, (size_t)(kp - kend) * 2, rows, st);
+  for (int l = 0; l < NSL && e == cudaSuccess && R < rows_pad; ++l)
+    e = cudaMemsetAsync(p + ((size_t)l * rows_pad + R) * kp, 0, (size_t)(rows_pad - R) * kp * 2, st);
+  return e;
+}
+
+// k_slice_cm writes rows 0..R-1 at the mapped columns of 0..C-1:
+// [0, kv) and [kvp, C - kv + kvp) (identity when kv = kvp = 0)
 inline cudaError_t slices_cm(DevBuf& buf, const double* src, long long lds, int R, int C, int rows_pad, int kp,
                              cudaStream_t st, int kv = 0, int kvp = 0) {
   const size_t n = (size_t)NSL * rows_pad * kp;
   cudaError_t e = ensure_bf16(buf, n);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(buf.p, 0, n * 2, st);
+  const int kvc = std::min(kv, C);
+  e = zero_padding(buf.bf(), R, kv > 0 ? C - kvc + kvp : C, rows_pad, kp, st, kvc, kv > 0 ? kvp : 0);
   if (e != cudaSuccess) return e;
   return launch_slice_colmajor(src, lds, R, C, kv, kvp, buf.bf(), rows_pad, kp, NSL, st);
 }
 
+// k_slice_rm writes rows 0..R-1 at columns 0..K-1 (and zeros up to the next
+// multiple of 8)
 inline cudaError_t slices_rm(DevBuf& buf, const double* src, long long lds, int R, int K, int rows_pad, int kp,
                              cudaStream_t st) {
   const size_t n = (size_t)NSL * rows_pad * kp;
   cudaError_t e = ensure_bf16(buf, n);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(buf.p, 0, n * 2, st);
+  e = zero_padding(buf.bf(), R, K, rows_pad, kp, st);
   if (e != cudaSuccess) return e;
   return launch_slice_rowmajor(src, lds, R, K, buf.bf(), rows_pad, kp, NSL, st);
 }
@@ -98,7 +121,7 @@ cudaError_t mixed_fit_gram(isdf_ctx* c, const double* phi, const double* phimu_p
   MK(slices_cm(c->m_phimus, phimu_p, r, r, n_e, rp, kp, st, n_v, kvp));
   const size_t nz = (size_t)NSL * nrp * rk;
   MK(ensure_bf16(c->m_zs, nz));
-  MK(cudaMemsetAsync(c->m_zs.p, 0, nz * 2, st));
+  MK(zero_padding(c->m_zs.bf(), (int)nr, r, nrp, rk, st));  // the epilogue writes rows < N_r, columns < r
   return tc_facesplit(op(c->m_phis, nrp, kp), op(c->m_phimus, rp, kp), (int)nr, r, kvp / 64, nullptr, 0,
                       c->m_zs.bf(), nrp, rk, c->d_status, st);
 }
@@ -122,8 +145,9 @@ cudaError_t mixed_fit_solve(isdf_ctx* c, double* theta, int r, bool linv_ready) 
   const size_t nth = (size_t)NSL * nrp * rk, ntt = (size_t)NSL * rp * kpg;
   MK(ensure_bf16(c->m_ths, nth));
   MK(ensure_bf16(c->m_thetas_t, ntt));
-  if (nrp != nr || rk != r) MK(cudaMemsetAsync(c->m_ths.p, 0, nth * 2, st));  // zero padding
-  if (rp != r || kpg != nr) MK(cudaMemsetAsync(c->m_thetas_t.p, 0, ntt * 2, st));
+  // the epilogue writes (m, n) of both for m < N_r, n < r
+  MK(zero_padding(c->m_ths.bf(), (int)nr, r, nrp, rk, st));
+  MK(zero_padding(c->m_thetas_t.bf(), r, (int)nr, rp, kpg, st));
   TcGroup whole_runs(0);
   MK(tc_gemm_f64_slices(op(c->m_zs, nrp, rk), op(c->m_linvs, rp, rk), (int)nr, r, theta, nr, true, c->m_ths.bf(), nrp,
                         rk, c->m_thetas_t.bf(), rp, kpg, c->d_status, st));
@@ -145,7 +169,8 @@ cudaError_t mixed_polar_G(isdf_ctx* c) {
     MK(ensure(c->m_s32, ((size_t)lds32 * r + 1) / 2));
     const size_t ns = (size_t)NSL * rp * kps;
     MK(ensure_bf16(c->m_ss, ns));
-    MK(cudaMemsetAsync(c->m_ss.p, 0, ns * 2, st));
+    // the z pass writes all 2 n_half reals of each of the r rows
+    MK(zero_padding(c->m_ss.bf(), r, (int)lds32, rp, kps, st));
     MK(launch_fft_forward_slices(c->fft, c->theta, c->n_r, r, (float*)c->m_s32.p, lds32, c->d_wsyrk, c->m_ss.bf(),
                                  rp, kps, NSL, c->smem_xy, c->smem_z, st));
   }
@@ -450,21 +475,28 @@ constexpr int kNsSlots = 2 + 2 * 12;
 // P - M^-1 P M grow once the iteration has converged.  Every product is a
 // full tensor-core GEMM; K, symmetric in exact arithmetic, is the lower
 // triangle of -D X, mirrored.  X stays in c->Xgd for the refinement of the
-// apply.
-cudaError_t mixed_ns_capacitance(isdf_ctx* c, const double* Dk, double* Kk, double alpha, const NsPlan& plan) {
+// apply.  M needs no bound, so mixed_ns_prepare builds it first, while the
+// host reads the bounds; mixed_ns_iterate follows on the same stream.
+cudaError_t mixed_ns_prepare(isdf_ctx* c, const double* Dk) {
   cudaStream_t st = c->stream;
   const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
   const size_t rr = (size_t)r * r;
   double* M = c->T.p;
-  double* X = c->Xgd.p;
-  double* Z = c->R.p;
   MK(cudaMemsetAsync(M, 0, rr * sizeof(double), st));
   MK(launch_add_identity(M, r, r, 1.0, st));
   MK(slices_cm(c->m_sd, c->G.p, r, r, r, rp, rk, st));  // rows of G
   MK(slices_cm(c->m_sa, Dk, r, r, r, rp, rk, st));      // rows of D (= its columns)
   MK(tc_gemm_f64(op(c->m_sd, rp, rk), op(c->m_sa, rp, rk), r, r, 1.0, 1.0, M, r, false, false, nullptr, 1,
                  c->num_sms, c->d_status, st));  // M = I + G D
-  MK(slices_cm(c->m_sd, M, r, r, r, rp, rk, st));  // rows of M, once
+  return slices_cm(c->m_sd, M, r, r, r, rp, rk, st);  // rows of M, once
+}
+
+cudaError_t mixed_ns_iterate(isdf_ctx* c, const double* Dk, double* Kk, double alpha, const NsPlan& plan) {
+  cudaStream_t st = c->stream;
+  const int r = c->rank, rp = pad(r, 128), rk = pad(r, 64);
+  const size_t rr = (size_t)r * r;
+  double* X = c->Xgd.p;
+  double* Z = c->R.p;
   MK(cudaMemsetAsync(X, 0, rr * sizeof(double), st));
   MK(launch_add_identity(X, r, r, alpha, st));
   for (int it = 0; it < plan.steps(); ++it) {
