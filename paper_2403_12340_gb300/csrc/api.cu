@@ -105,17 +105,22 @@ static bool factorize(int n, FftAxis& ax) {
 
 static int signed_freq(int k, int n) { return (2 * k < n) ? k : (2 * k == n ? k : k - n); }
 
-// Reads back the device status word (the stream must be synchronised).
-static int check_status(isdf_ctx* c, const char* where) {
-  unsigned st = 0;
-  cudaError_t e = cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(c, e, where);
+// The error a device status word reports, if any.
+static int status_error(isdf_ctx* c, unsigned st, const char* where) {
   if (st & ST_TIMEOUT) return fail(c, ISDF_ERR_TIMEOUT, std::string(where) + ": device wait timed out");
   if (st & ST_NONFINITE) return fail(c, ISDF_ERR_NONFINITE, std::string(where) + ": NaN or Inf in input");
   if (st & ST_NOT_SPD)
     return fail(c, ISDF_ERR_NOT_SPD, std::string(where) + ": matrix not positive definite");
   if (st & ST_BADINDEX) return fail(c, ISDF_ERR_INDEX, std::string(where) + ": index out of range");
   return ISDF_OK;
+}
+
+// Reads back the device status word (the stream must be synchronised).
+static int check_status(isdf_ctx* c, const char* where) {
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  return status_error(c, st, where);
 }
 
 extern "C" const char* isdf_version(void) { return "isdf-smw-gb300 0.1 (fp64, sm_103a)"; }
@@ -361,6 +366,47 @@ static int chol_inverse_workspace(isdf_ctx* c, int n, bool ahead = false) {
   return ISDF_OK;
 }
 
+// The fit after the factorisation of C C^T: theta for the leading r pivots
+// (d_perm on the device, the factor in c->Lc with ld n_mu); gram_done: the
+// Gram beside the factorisation used these points in this order.
+static int fit_tail(isdf_ctx* c, const double* phi, double* theta, int n_v, int n_c, int n_mu, int r, bool gram_done,
+                    bool fuse_inv, int prec) {
+  const int n_e = n_v + n_c;
+  // Lc was written with ld = n_mu; repack the leading rank x rank block with ld = rank
+  if (r > 0) {
+    CK(ensure(c->Bf, (size_t)r * r));
+    CK(cudaMemcpy2DAsync(c->Bf.p, r * sizeof(double), c->Lc.p, n_mu * sizeof(double), r * sizeof(double),
+                         r, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->Lc.p, c->Bf.p, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    // orbitals at the pivot points, in pivot order
+    CK(ensure(c->phimu_p, (size_t)r * n_e));
+    CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
+    if (prec == ISDF_PREC_MIXED) {
+      if (!gram_done) CK(isdf::mixed_fit_gram(c, phi, c->phimu_p.p, n_v, n_c, r));
+      // the inverse built beside the factorisation holds for the unpivoted full-rank factor
+      CK(isdf::mixed_fit_solve(c, theta, r, fuse_inv && gram_done));
+      // ||L||_F^2 = tr(C C^T) and ||L^-1||_F^2 = tr((C C^T)^-1), read by build_polarizability
+      CK(ensure(c->kappa_work, 2 + 256));
+      CK(launch_sumsq(c->Lc.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p, c->stream));
+      CK(launch_sumsq(c->m_linv.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p + 1, c->stream));
+    } else {
+      // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
+      if (!gram_done) {
+        PhaseScope ph(c, ISDF_PH_FIT_GRAM);
+        CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
+                                 c->stream));
+      }
+      PhaseScope ph(c, ISDF_PH_FIT_TRSM);
+      CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
+      CK(launch_trsm_right_lt(theta, c->n_r, (int)c->n_r, c->Bf.p, r, r, c->stream));
+    }
+  }
+  if (r < n_mu)
+    CK(cudaMemsetAsync(theta + c->n_r * r, 0, (size_t)c->n_r * (n_mu - r) * sizeof(double), c->stream));
+  return ISDF_OK;
+}
+
 extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const int64_t* mu_idx,
                         int n_mu, int prec, double* theta, int* rank_out) {
   if (!c) return ISDF_ERR_ARG;
@@ -417,6 +463,14 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   c->d_perm2 = c->d_idx + 2 * n_mu;
   if (!isdf::tl_capture)
     CK(cudaMemcpyAsync(c->d_idx, idx32.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  // mixed path: the identity order, for the rest of the fit that is queued
+  // before the factorisation's flags are read (below)
+  const bool tail_ahead = prec == ISDF_PREC_MIXED && !isdf::tl_capture;
+  if (tail_ahead) {
+    std::vector<int> ident(n_mu);
+    for (int i = 0; i < n_mu; ++i) ident[i] = i;
+    CK(cudaMemcpyAsync(c->d_perm, ident.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  }
   CK(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
   CK(launch_check_finite(phi, c->n_r * n_e, c->d_status, c->stream));
   // orbitals at the points, C C^T (face-split Gram of the point block), its pivoted Cholesky
@@ -479,7 +533,25 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   }
   int rc;
   int fail = -1, rank = 0;
-  if (!isdf::tl_capture) {  // captured: the flags are read after the replay (graph_check)
+  bool tail_queued = false;
+  if (tail_ahead) {
+    // mixed path: the rest of the fit is queued for the outcome the Gram
+    // beside the factorisation already assumed (no failed pivot: full rank,
+    // the given order), and the host reads the flags through the helper
+    // stream while it runs; after a failed pivot the pivoted route below
+    // redoes that work on the same stream
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    rc = fit_tail(c, phi, theta, n_v, n_c, n_mu, n_mu, true, fuse_inv, prec);
+    if (rc != ISDF_OK) return rc;
+    CK(cudaStreamWaitEvent(c->s3, c->ev_fork, 0));
+    unsigned hs[32];  // the status word [0] and the flags d_ints = d_status + 16
+    CK(cudaMemcpyAsync(hs, c->d_status, sizeof(hs), cudaMemcpyDeviceToHost, c->s3));
+    CK(cudaStreamSynchronize(c->s3));
+    rc = status_error(c, hs[0], "isdf_fit");
+    if (rc != ISDF_OK) return rc;
+    std::memcpy(&fail, hs + 17, sizeof(int));  // d_ints[1]
+    tail_queued = fail < 0;
+  } else if (!isdf::tl_capture) {  // captured: the flags are read after the replay (graph_check)
     CK(cudaStreamSynchronize(c->stream));
     rc = check_status(c, "isdf_fit");
     if (rc != ISDF_OK) return rc;
@@ -490,7 +562,7 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
   if (fail < 0) {
     rank = n_mu;
     for (int i = 0; i < n_mu; ++i) c->perm[i] = i;
-    if (!isdf::tl_capture)  // captured: the identity order of the eager fit is on the device
+    if (!isdf::tl_capture && !tail_queued)  // captured: the identity order of the eager fit is on the device
       CK(cudaMemcpyAsync(c->d_perm, c->perm.data(), n_mu * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   } else {
     {
@@ -511,39 +583,11 @@ extern "C" int isdf_fit(isdf_ctx* c, const double* phi, int n_v, int n_c, const 
     for (int i = 0; i < n_mu; ++i)
       if (!used[i]) c->perm[j++] = i;
   }
-  // Lc was written with ld = n_mu; repack the leading rank x rank block with ld = rank
   const int r = rank;
-  if (r > 0) {
-    CK(ensure(c->Bf, (size_t)r * r));
-    CK(cudaMemcpy2DAsync(c->Bf.p, r * sizeof(double), c->Lc.p, n_mu * sizeof(double), r * sizeof(double),
-                         r, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->Lc.p, c->Bf.p, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice,
-                       c->stream));
-    // orbitals at the pivot points, in pivot order
-    CK(ensure(c->phimu_p, (size_t)r * n_e));
-    CK(launch_gather_rows(c->phimu.p, n_mu, c->d_perm, r, n_e, c->phimu_p.p, r, c->stream));
-    if (prec == ISDF_PREC_MIXED) {
-      if (!gram_done) CK(isdf::mixed_fit_gram(c, phi, c->phimu_p.p, n_v, n_c, r));
-      // the inverse built beside the factorisation holds for the unpivoted full-rank factor
-      CK(isdf::mixed_fit_solve(c, theta, r, fuse_inv && gram_done));
-      // ||L||_F^2 = tr(C C^T) and ||L^-1||_F^2 = tr((C C^T)^-1), read by build_polarizability
-      CK(ensure(c->kappa_work, 2 + 256));
-      CK(launch_sumsq(c->Lc.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p, c->stream));
-      CK(launch_sumsq(c->m_linv.p, (long long)r * r, c->kappa_work.p + 2, c->kappa_work.p + 1, c->stream));
-    } else {
-      // M C_r^T by the Hadamard identity, then theta = (M C_r^T) L_r^-T in place
-      if (!gram_done) {
-        PhaseScope ph(c, ISDF_PH_FIT_GRAM);
-        CK(launch_facesplit_gram(phi, c->n_r, (int)c->n_r, c->phimu_p.p, r, r, n_v, n_e, theta, c->n_r,
-                                 c->stream));
-      }
-      PhaseScope ph(c, ISDF_PH_FIT_TRSM);
-      CK(launch_trsm_prep(c->Lc.p, r, r, c->Bf.p, r, c->stream));
-      CK(launch_trsm_right_lt(theta, c->n_r, (int)c->n_r, c->Bf.p, r, r, c->stream));
-    }
+  if (!tail_queued) {
+    int rc1 = fit_tail(c, phi, theta, n_v, n_c, n_mu, r, gram_done, fuse_inv, prec);
+    if (rc1 != ISDF_OK) return rc1;
   }
-  if (r < n_mu)
-    CK(cudaMemsetAsync(theta + c->n_r * r, 0, (size_t)c->n_r * (n_mu - r) * sizeof(double), c->stream));
   c->phi = phi;
   c->theta = theta;
   c->prec = prec;
