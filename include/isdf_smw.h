@@ -127,7 +127,11 @@ ISDF_API int isdf_destroy(isdf_ctx* ctx);
  *   rank_out host int out (may be NULL): numerical rank r of C C^T.  The
  *            Cholesky stops when the largest remaining pivot falls below
  *            n_mu * 2^-52 * max diag(C C^T); r < n_mu is not an error.
- * Synchronises the context stream once. */
+ * Waits once on the host, for the Cholesky factorisation of C C^T: the FP64
+ * path synchronises the context stream there; the MIXED path has queued the
+ * rest of the fit for the full-rank outcome first and reads the flags
+ * through a helper stream.  theta is complete once the context stream has
+ * run the call's work. */
 ISDF_API int isdf_fit(isdf_ctx* ctx, const double* phi, int n_v, int n_c, const int64_t* mu_idx, int n_mu,
              int prec, double* theta, int* rank_out);
 
@@ -164,6 +168,36 @@ ISDF_API int build_polarizability_contour(isdf_ctx* ctx, const double* energies,
  * negative ISDF_ERR_* on bad arguments or no gap.  The bound's constant is
  * not known, and in practice fewer nodes reach tol. */
 ISDF_API int isdf_contour_nodes(const double* energies, int n_v, int n_c, double tol);
+
+/* Host-only pieces of the MIXED capacitance route of smw_inverse, exported
+ * so that they can be checked without a GPU.
+ *
+ * isdf_pair_weight_bounds: bounds of the pair weights 2 d / (d^2 + w^2),
+ * d = e_c - e_v, over every occupied v and unoccupied c (the entries of
+ * Omega(i w)^-1 in D(w) = -2 C~ Omega(i w)^-1 C~^T, Eq. COmegaCstar), from
+ * the extreme energies: the weight is unimodal in d with its peak at d = w,
+ * so the extremes over [gap, width] lie at the ends or at w.  In the
+ * whitened basis the largest weight bounds the spectral norm of D.
+ *   energies host, n_v + n_c float64, occupied first, all occupied ones
+ *            below the unoccupied ones (else ISDF_ERR_ORDER).
+ *   w        frequency, >= 0.
+ *   wmin, wmax host out.
+ * Returns ISDF_OK or a negative ISDF_ERR_*. */
+ISDF_API int isdf_pair_weight_bounds(const double* energies, int n_v, int n_c, double w, double* wmin,
+                                     double* wmax);
+
+/* isdf_ns_schedule: the Newton-Schulz schedule for M = I + G D whose
+ * spectrum lies in [1, kappa] (kappa = 1 + |G| |D|, the bounds above and a
+ * Gershgorin bound of G): X_0 = alpha I, alpha = 2 / (1 + kappa), then
+ * X <- beta_k (2 X - X (M X)) with beta_k = 2 / (2 - e_k^2), from
+ * e_0 = (kappa - 1) / (kappa + 1) and e_{k+1} = e_k^2 / (2 - e_k^2), until
+ * e_k < 2^-26; step k runs its products on slices[k] BF16 slices (1, 2 or 3;
+ * 3 on the last two steps).
+ *   kappa      >= 1 (else ISDF_ERR_ARG).
+ *   max_steps  room in beta and slices (host out); 12 is always enough.
+ * Returns the number of steps, or 0 when the route is not taken (it would
+ * need more than 12 steps; smw_inverse then factors). */
+ISDF_API int isdf_ns_schedule(double kappa, int max_steps, double* beta, int* slices);
 
 /* SMW capacitance for frequency omega[omega_index] (K of Section "Cubic
  * scaling algorithm", Algorithm 3 step 3), in the singular-B-safe form

@@ -40,7 +40,8 @@ EXPORTED = ["isdf_create", "isdf_destroy", "isdf_fit", "build_polarizability", "
             "build_polarizability_contour", "isdf_contour_nodes", "isdf_cohsex", "isdf_batch_capture",
             "isdf_batch_replay", "isdf_set_autotune", "isdf_autotune_size", "isdf_autotune_entry",
             "isdf_autotune_clear", "isdf_device_allocations", "isdf_check_device_wait",
-            "isdf_adjoint_fit", "isdf_read_kernel_trace", "isdf_set_refinement"]
+            "isdf_adjoint_fit", "isdf_read_kernel_trace", "isdf_set_refinement",
+            "isdf_pair_weight_bounds", "isdf_ns_schedule"]
 NUM_PHASES = 9
 NUM_KERNEL_FAMILIES = 6
 
@@ -107,6 +108,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.build_polarizability_contour.restype = I
     lib.isdf_contour_nodes.argtypes = [P, I, I, D]
     lib.isdf_contour_nodes.restype = I
+    lib.isdf_pair_weight_bounds.argtypes = [P, I, I, D, ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.isdf_pair_weight_bounds.restype = I
+    lib.isdf_ns_schedule.argtypes = [D, I, P, P]
+    lib.isdf_ns_schedule.restype = I
     lib.isdf_cohsex.argtypes = [P, P, P, P]
     lib.isdf_cohsex.restype = I
     lib.smw_inverse_all.argtypes = [P, P]
@@ -283,6 +288,28 @@ def isdf_contour_nodes(energies, n_v: int, n_c: int, tol: float) -> int:
     if n < 0:
         raise IsdfError(n, "isdf_contour_nodes: bad arguments or no gap")
     return n
+
+
+def pair_weight_bounds(energies, n_v: int, n_c: int, w: float):
+    """(wmin, wmax) of the pair weights 2 d / (d^2 + w^2), d = e_c - e_v (host only)."""
+    e = np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().isdf_pair_weight_bounds(e.ctypes.data, int(n_v), int(n_c), float(w), ctypes.byref(lo),
+                                                ctypes.byref(hi))
+    if rc != 0:
+        raise IsdfError(rc, "isdf_pair_weight_bounds")
+    return lo.value, hi.value
+
+
+def ns_schedule(kappa: float):
+    """(beta, slices) of the Newton-Schulz steps for a spectrum in [1, kappa],
+    or None when the route would take more than 12 steps (host only)."""
+    beta = np.zeros(12, dtype=np.float64)
+    slices = np.zeros(12, dtype=np.int32)
+    n = load_library().isdf_ns_schedule(float(kappa), 12, beta.ctypes.data, slices.ctypes.data)
+    if n < 0:
+        raise IsdfError(n, "isdf_ns_schedule")
+    return None if n == 0 else (beta[:n].copy(), slices[:n].copy())
 
 
 def isdf_cohsex(ctx_vc, ctx_vn, ctx_nn, n_e: int, device="cuda"):

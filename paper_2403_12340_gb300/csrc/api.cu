@@ -841,6 +841,31 @@ extern "C" int build_polarizability_contour(isdf_ctx* c, const double* energies,
   return polar_impl(c, energies, &w0, 1, D_out, G_out, n_nodes);
 }
 
+extern "C" int isdf_pair_weight_bounds(const double* energies, int n_v, int n_c, double w, double* wmin,
+                                       double* wmax) {
+  if (!energies || !wmin || !wmax || n_v < 1 || n_c < 1 || !std::isfinite(w) || w < 0.0) return ISDF_ERR_ARG;
+  double emax_v = energies[0], emin_c = energies[n_v];
+  for (int i = 0; i < n_v + n_c; ++i)
+    if (!std::isfinite(energies[i])) return ISDF_ERR_NONFINITE;
+  for (int i = 0; i < n_v; ++i) emax_v = std::max(emax_v, energies[i]);
+  for (int j = n_v; j < n_v + n_c; ++j) emin_c = std::min(emin_c, energies[j]);
+  if (!(emax_v < emin_c)) return ISDF_ERR_ORDER;
+  isdf::pair_weight_bounds(energies, n_v, n_c, w, wmin, wmax);
+  return ISDF_OK;
+}
+
+extern "C" int isdf_ns_schedule(double kappa, int max_steps, double* beta, int* slices) {
+  if (!(kappa >= 1.0) || !std::isfinite(kappa) || max_steps < 1 || !beta || !slices) return ISDF_ERR_ARG;
+  isdf::NsPlan plan;
+  if (!isdf::ns_plan((kappa - 1.0) / (kappa + 1.0), plan)) return 0;
+  if (plan.steps() > max_steps) return ISDF_ERR_ARG;
+  for (int k = 0; k < plan.steps(); ++k) {
+    beta[k] = plan.beta[k];
+    slices[k] = plan.s[k];
+  }
+  return plan.steps();
+}
+
 extern "C" int isdf_contour_nodes(const double* energies, int n_v, int n_c, double tol) {
   if (!energies || n_v < 1 || n_c < 1 || !(tol > 0.0) || !(tol < 1.0)) return ISDF_ERR_ARG;
   double e_n = energies[0], e_lo = energies[n_v], e_hi = energies[n_v];
