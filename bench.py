@@ -499,6 +499,41 @@ def batch_systems():
         return list(ex.map(_gen_batch_system, range(n)))
 
 
+# The bounded CPU sample of the full-frequency set: (system index, number of
+# frequencies, None = all) -- the three smallest systems at every frequency
+# and one of middle size (45^3, N_v 89) at two; about 15-30 s of oracle work
+BATCH_CPU_SAMPLE = ((0, None), (1, None), (2, None), (8, 2))
+
+
+def batch_system_flops(s, n_omega):
+    """Algorithmic flops of one system of the set at n_omega frequencies: the
+    fit and G once, D(w), its whitening and K(w) per frequency."""
+    n_half2 = 2 * (s.n[0] // 2 + 1) * s.n[1] * s.n[2]
+    fl = algorithmic_flops(s.n_r, s.n_e, s.n_v * s.n_c, s.n_mu, 0, n_half2)
+    return (fl["points_chol"] + fl["fit_gram"] + fl["fit_trsm"] + fl["coulomb_fft"] + fl["coulomb_syrk"]
+            + n_omega * (fl["polar_d"] + fl["whiten_d"] + fl["smw"]))
+
+
+def oracle_batch_baseline(systems, omegas, sample=BATCH_CPU_SAMPLE, timer=None):
+    """The oracle's rate on the whole set from a bounded sample of it: the
+    sample's (system, frequency) units are timed, and the set's time is
+    taken as the set's algorithmic flops at the sample's flop rate (the
+    sample alone would overstate solves/s: its systems are the small ones).
+    Returns (solves/s of the set, seconds timed, units timed, flop rate)."""
+    timer = timer or oracle_batch_sample
+    t = f_sample = 0.0
+    units = 0
+    for i, nw in sample:
+        s = systems[min(i, len(systems) - 1)]
+        om = omegas if nw is None else omegas[:nw]
+        t += timer(s, om)
+        f_sample += batch_system_flops(s, len(om))
+        units += len(om)
+    rate = f_sample / t
+    f_all = sum(batch_system_flops(s, len(omegas)) for s in systems)
+    return len(systems) * len(omegas) * rate / f_all, t, units, rate
+
+
 def oracle_batch_sample(s, omegas):
     """The FP64 oracle on one system at every frequency: fit and G once, then
     B(w) and K(w) per frequency (the units the batch counts)."""
@@ -612,12 +647,7 @@ def run_batch(args):
     lat_all = np.concatenate(lats)
     svc_all = np.concatenate(svcs)
 
-    flops_run = 0.0
-    for s in systems:
-        n_half2 = 2 * (s.n[0] // 2 + 1) * s.n[1] * s.n[2]
-        fl = algorithmic_flops(s.n_r, s.n_e, s.n_v * s.n_c, s.n_mu, 0, n_half2)
-        flops_run += (fl["points_chol"] + fl["fit_gram"] + fl["fit_trsm"] + fl["coulomb_fft"] + fl["coulomb_syrk"]
-                      + BATCH_OMEGAS * (fl["polar_d"] + fl["whiten_d"] + fl["smw"]))
+    flops_run = sum(batch_system_flops(s, BATCH_OMEGAS) for s in systems)
     peaks = measured_peaks()
     cells = [kernel_roofline(f, ph, ms, cnt, w, 1, peaks, workload="batch16")
              for (f, ph), (ms, cnt, w) in kprof.items() if cnt and ms > 0]
@@ -627,11 +657,14 @@ def run_batch(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t = oracle_batch_sample(systems[0], omegas)
-        cpu = {"value": round(BATCH_OMEGAS / t, 3), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": (f"system 0 of the set ({systems[0].n[0]}^3, N_v={systems[0].n_v}, N_mu={systems[0].n_mu}) "
-                          f"at all {BATCH_OMEGAS} frequencies: fit and G once, B(w) and K(w) per frequency, "
-                          f"{t:.1f} s, numpy/scipy FP64")}
+        v, t, units, rate = oracle_batch_baseline(systems, omegas)
+        picked = ", ".join(f"{systems[min(i, n_sys - 1)].n[0]}^3/{systems[min(i, n_sys - 1)].n_v} at "
+                           f"{BATCH_OMEGAS if nw is None else nw}" for i, nw in BATCH_CPU_SAMPLE)
+        cpu = {"value": round(v, 4), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": (f"{units} (system, frequency) units of the set (grid^3/N_v at frequencies: {picked}), "
+                          f"fit and G once per system, B(w) and K(w) per frequency, {t:.1f} s of numpy/scipy "
+                          f"FP64 at {rate / 1e9:.1f} GFLOP/s algorithmic; the value is the whole set's "
+                          f"{n_sys * BATCH_OMEGAS} solves at that rate")}
     if rank == 0:
         sizes = ", ".join(f"{s.n[0]}^3/{s.n_v}" for s in systems)
         line = {

@@ -62,3 +62,33 @@ def test_dominant_cell_prefers_tensor_gemm():
     assert other["traffic"] is None
     assert bench.dominant_cell(cells[:1])["kernel"] == "df_gemm:points_chol"
     assert bench.dominant_cell([]) is None
+
+
+def test_batch_cpu_baseline_scales_the_sample_to_the_set():
+    """The full-frequency set's CPU baseline: the sampled units are timed,
+    and the set's time is its algorithmic flops at the sample's flop rate."""
+    from types import SimpleNamespace
+
+    import synth
+
+    systems = [SimpleNamespace(n=(n, n, n), n_r=n ** 3, n_v=nv, n_c=7 * nv, n_e=8 * nv, n_mu=12 * nv)
+               for n, nv in synth.BATCH_SYSTEMS]
+    omegas = list(range(32))
+    calls = []
+
+    def timer(s, om):  # an oracle that runs at exactly 10 GFLOP/s
+        calls.append((s.n[0], len(om)))
+        return bench.batch_system_flops(s, len(om)) / 1e10
+
+    v, t, units, rate = bench.oracle_batch_baseline(systems, omegas, timer=timer)
+    assert calls == [(24, 32), (27, 32), (30, 32), (45, 2)]
+    assert units == 3 * 32 + 2
+    assert rate == pytest.approx(1e10)
+    f_all = sum(bench.batch_system_flops(s, 32) for s in systems)
+    assert v == pytest.approx(16 * 32 / (f_all / 1e10))
+    # the sample alone would claim far more: its systems are the small ones
+    assert units / t > 5 * v
+    # a set smaller than the sample's indices takes its last system
+    v2, _, _, _ = bench.oracle_batch_baseline(systems[:4], omegas, timer=timer)
+    assert calls[-1] == (32, 2)
+    assert v2 > v
