@@ -1223,7 +1223,7 @@ isdf::KernelTimer::~KernelTimer() {
   c->kprof.push_back({fam, tl_prof_phase, e0, e1, work, st});
 }
 
-static_assert(KF_COUNT == ISDF_NUM_KERNEL_FAMILIES, "kernel families of the header and the launchers differ");
+static_assert((int)KF_COUNT == (int)ISDF_NUM_KERNEL_FAMILIES, "kernel families of the header and the launchers differ");
 static const char* kFamilyNames[KF_COUNT] = {"tc_gemm", "fp64_gemm", "chol_diag", "fft", "slice", "df_gemm"};
 
 extern "C" const char* isdf_kernel_family_name(int fam) {

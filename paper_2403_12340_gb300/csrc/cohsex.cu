@@ -35,10 +35,10 @@ int cx_fail(isdf_ctx* c, int code, const std::string& m) { return ctx_fail(c, co
     if (_e != cudaSuccess) return cx_fail(c, ISDF_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
   } while (0)
 
-__global__ void k_hadamard(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c,
-                           long long n) {
+// b = a .* b, in place (a and b distinct)
+__global__ void k_hadamard_in_place(const double* __restrict__ a, double* __restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    c[i] = a[i] * b[i];
+    b[i] *= a[i];
 }
 
 // out[n] = scale * sum_a X(a, n) Y(a, n), one block per column
@@ -105,7 +105,8 @@ int band_sum(isdf_ctx* c, const isdf_ctx* x, const double* M, int o0, int no, in
   XK(launch_gemm(P + (size_t)r * o0, r, false, P + (size_t)r * o0, r, false, r, r, no, 1.0, 0.0, g.p, r, true, 1,
                  nullptr, false, c->stream));
   note_launch();
-  k_hadamard<<<(unsigned)std::min<size_t>((rr + 255) / 256, 4096), 256, 0, c->stream>>>(M, g.p, g.p, (long long)rr);
+  k_hadamard_in_place<<<(unsigned)std::min<size_t>((rr + 255) / 256, 4096), 256, 0, c->stream>>>(M, g.p,
+                                                                                                  (long long)rr);
   XK(cudaGetLastError());
   XK(launch_gemm(g.p, r, false, P + (size_t)r * a0, r, true, r, nb, r, 1.0, 0.0, y.p, r, false, 1, nullptr, false,
                  c->stream));
